@@ -1,0 +1,485 @@
+"""Pins of the FP64 oracle against facts fixed outside it.
+
+Each test checks the oracle against a closed form, an invariant, an
+independent textbook construction or exact values of a published function,
+chosen so that a plausible slip in the oracle (a dropped term, a wrong sign,
+a shifted stencil, a transposed cross product) fails one of them:
+
+* lattice isotropy of D3Q27 (moment identities up to 4th order);
+* Peskin's 4-point function: exact values, partition of unity, first moment,
+  sum of squares 3/8 (Peskin 2002, Sec. 6);
+* equilibrium moments; collision == BGK with Guo's source term in the moments
+  rho, j, Pi and lies in the 2nd-order Hermite space; the implicit Coriolis
+  solve satisfies Eq. 3 when substituted back;
+* Taylor-Green decay at nu = (tau - 1/2)/3 in the xy, yz and zx planes;
+* Galilean advection of a vortex pattern (fixes the streaming direction);
+* exact mass conservation and momentum gain under a uniform body force;
+* immersed boundary: interpolation reproduces constant and linear fields,
+  spreading is its transpose, and the fluid's momentum and angular momentum
+  change by minus the reported body force and torque;
+* non-equilibrium extrapolation: uniform inflow is a fixed point and is
+  reached from rest; inlet/outflow/free-slip values on faces and edges;
+* frame force of Eq. 3 for a pure rotation (centrifugal and Euler terms).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import FREESLIP, OUTFLOW, PERIODIC, VELOCITY
+from paper_2206_01683_b300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ lattice
+
+def test_lattice_isotropy():
+    c, w = oracle.lattice()
+    c = c.astype(np.float64)
+    assert len({tuple(v) for v in c.astype(int)}) == 27
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.allclose(np.einsum("i,ia->a", w, c), 0.0, atol=1e-16)
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, c, c), np.eye(3) / 3.0, atol=1e-16)
+    assert np.allclose(np.einsum("i,ia,ib,ic->abc", w, c, c, c), 0.0, atol=1e-16)
+    d = np.eye(3)
+    iso4 = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+            + np.einsum("ad,bc->abcd", d, d)) / 9.0
+    assert np.allclose(np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c), iso4, atol=1e-16)
+
+
+# ------------------------------------------------------------- delta kernel
+
+def test_peskin_phi_golden_values():
+    rows = np.loadtxt(os.path.join(GOLDEN, "peskin_phi.txt"))
+    for r, v in rows:
+        assert abs(oracle.phi(r) - v) < 1e-15, (r, oracle.phi(r), v)
+
+
+def test_peskin_phi_moment_conditions():
+    r = np.arange(10000) / 10000.0
+    s0 = np.zeros_like(r)
+    s1 = np.zeros_like(r)
+    s2 = np.zeros_like(r)
+    for j in range(-3, 4):
+        ph = np.array([oracle.phi(x - j) for x in r])
+        s0 += ph
+        s1 += (r - j) * ph
+        s2 += ph * ph
+    assert np.max(np.abs(s0 - 1.0)) < 1e-15
+    assert np.max(np.abs(s1)) < 1e-15
+    assert np.max(np.abs(s2 - 3.0 / 8.0)) < 1e-15
+
+
+# ---------------------------------------------------------------- collision
+
+def _random_state(rng):
+    c, w = oracle.lattice()
+    fs = w * (1.0 + 0.05 * rng.standard_normal(27))
+    return c.astype(np.float64), w, fs
+
+
+def _bgk_guo(fs, G, tau, c, w):
+    """BGK with Guo's source term (Guo, Zheng & Shi 2002) written in
+    population space: f* = f - (f - f_eq)/tau + (1 - 1/(2 tau)) S,
+    S_i = w_i [(c_i - u)/cs2 + (c_i.u) c_i / cs2^2].G, u = (j + G/2)/rho,
+    and the classic second-order Maxwellian expansion for f_eq."""
+    rho = fs.sum()
+    u = (c.T @ fs + 0.5 * G) / rho
+    cu = c @ u
+    feq = w * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * (u @ u))
+    S = w * (3.0 * ((c - u) @ G) + 9.0 * cu * (c @ G))
+    return fs - (fs - feq) / tau + (1.0 - 0.5 / tau) * S
+
+
+def _moments(f, c):
+    return f.sum(), c.T @ f, np.einsum("i,ia,ib->ab", f, c, c)
+
+
+@pytest.mark.parametrize("tau", [0.52, 0.56, 0.8, 1.0, 1.7])
+def test_collision_matches_bgk_guo_moments(tau):
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        c, w, fs = _random_state(rng)
+        a0 = 1e-3 * rng.standard_normal(3)
+        fib = 1e-3 * rng.standard_normal(3)
+        out = oracle.collide_cell(fs, a0, fib, np.zeros(3), tau)
+        ref = _bgk_guo(fs, fs.sum() * a0 + fib, tau, c, w)
+        for m_out, m_ref in zip(_moments(out, c), _moments(ref, c)):
+            assert np.max(np.abs(np.asarray(m_out) - np.asarray(m_ref))) < 1e-15
+
+
+def test_collision_is_hermite2_regularized():
+    """f*_i / w_i is a polynomial of degree <= 2 in c_i (10 coefficients)."""
+    rng = np.random.default_rng(3)
+    c, w, fs = _random_state(rng)
+    out = oracle.collide_cell(fs, 1e-3 * np.ones(3), np.zeros(3), np.zeros(3), 0.6)
+    B = np.stack([np.ones(27), c[:, 0], c[:, 1], c[:, 2], c[:, 0] ** 2, c[:, 1] ** 2,
+                  c[:, 2] ** 2, c[:, 0] * c[:, 1], c[:, 0] * c[:, 2], c[:, 1] * c[:, 2]], 1)
+    coef, *_ = np.linalg.lstsq(B, out / w, rcond=None)
+    assert np.max(np.abs(B @ coef - out / w)) < 1e-14
+    # a plain BGK output is NOT in that space (the test can tell them apart)
+    ref = _bgk_guo(fs, fs.sum() * 1e-3 * np.ones(3), 0.6, c, w)
+    coef, *_ = np.linalg.lstsq(B, ref / w, rcond=None)
+    assert np.max(np.abs(B @ coef - ref / w)) > 1e-6
+
+
+def test_coriolis_solve_satisfies_eq3():
+    """With omega != 0 the post-collision momentum gain G must equal
+    rho a0 + fib - 2 rho omega x u with u = (j + G/2)/rho (Eq. 3's Coriolis
+    term evaluated at the velocity it produces)."""
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        c, w, fs = _random_state(rng)
+        a0 = 1e-3 * rng.standard_normal(3)
+        fib = 1e-3 * rng.standard_normal(3)
+        om = 0.05 * rng.standard_normal(3)
+        out = oracle.collide_cell(fs, a0, fib, om, 0.7)
+        rho, j = fs.sum(), c.T @ fs
+        G = c.T @ out - j
+        u = (j + 0.5 * G) / rho
+        assert abs(out.sum() - rho) < 1e-15
+        assert np.max(np.abs(G - (rho * a0 + fib - 2.0 * rho * np.cross(om, u)))) < 1e-16
+
+
+def test_equilibrium_moments():
+    rng = np.random.default_rng(5)
+    shape = (4, 3, 2)
+    n = 24
+    rho = 1.0 + 0.05 * rng.standard_normal(n)
+    u = 0.05 * rng.standard_normal((n, 3))
+    o = oracle.Oracle(shape, 0.7)
+    o.init_fields(rho, u)
+    f = o.populations()
+    c, _ = oracle.lattice()
+    c = c.astype(np.float64)
+    assert np.max(np.abs(f.sum(1) - rho)) < 1e-15
+    assert np.max(np.abs(f @ c - rho[:, None] * u)) < 1e-16
+    Pi = np.einsum("ni,ia,ib->nab", f, c, c)
+    ref = np.einsum("n,na,nb->nab", rho, u, u) + rho[:, None, None] * np.eye(3) / 3.0
+    assert np.max(np.abs(Pi - ref)) < 1e-15
+
+
+# ------------------------------------------------------ streaming + viscosity
+
+def _tg_amplitude(o, shape, plane):
+    _, u = o.fields()
+    a, b = plane
+    k = 2 * math.pi / shape[a]
+    z, y, x = np.meshgrid(*[np.arange(s) for s in shape[::-1]], indexing="ij")
+    pos = [x.ravel(), y.ravel(), z.ravel()]
+    basis = np.sin(k * pos[a]) * np.cos(k * pos[b])
+    return (u[:, a] * basis).sum() / (basis * basis).sum()
+
+
+def _tg_rate_error(L, tau, plane):
+    shape = [1, 1, 1]
+    shape[plane[0]] = L
+    shape[plane[1]] = L
+    shape = tuple(shape)
+    rho, u = inputs.taylor_green(shape, plane, U0=1e-3)
+    o = oracle.Oracle(shape, tau)
+    o.init_fields(rho, u)
+    nu = (tau - 0.5) / 3.0
+    k = 2 * math.pi / L
+    t1 = 50
+    t2 = t1 + int(round(0.5 / (2 * nu * k * k)))
+    o.step(n=t1)
+    A1 = _tg_amplitude(o, shape, plane)
+    o.step(n=t2 - t1)
+    A2 = _tg_amplitude(o, shape, plane)
+    rate = math.log(A1 / A2) / (t2 - t1)
+    return rate / (2 * nu * k * k) - 1.0
+
+
+@pytest.mark.parametrize("tau", [0.52, 0.56, 0.8, 1.0])
+@pytest.mark.parametrize("plane", [(0, 1), (1, 2), (2, 0)])
+def test_taylor_green_decay_rate(tau, plane):
+    """u = U0 (sin kx cos ky, -cos kx sin ky) decays as exp(-2 nu k^2 t),
+    nu = (tau - 1/2)/3 (incompressible Navier-Stokes closed form): the
+    measured rate is within 1e-3 of it (L = 64 where tau >= 0.8, else 32)."""
+    L = 64 if tau >= 0.8 else 32
+    err = _tg_rate_error(L, tau, plane)
+    assert abs(err) < 1e-3, err
+
+
+def test_taylor_green_second_order_convergence():
+    """The decay-rate error is O(k^2): halving k divides it by about 4."""
+    e16 = _tg_rate_error(16, 1.0, (0, 1))
+    e32 = _tg_rate_error(32, 1.0, (0, 1))
+    assert 3.5 < e16 / e32 < 4.5, (e16, e32)
+
+
+def test_galilean_advection_direction():
+    """A weak Taylor-Green pattern on a uniform stream u0 is carried along
+    +u0 at speed |u0| (pins the pull direction of streaming)."""
+    L = 64
+    shape = (L, L, 1)
+    rho, u = inputs.taylor_green(shape, (0, 1), U0=1e-4)
+    u0 = 0.05
+    u[:, 0] += u0
+    o = oracle.Oracle(shape, 0.8)
+    o.init_fields(rho, u)
+    T = 200
+    o.step(n=T)
+    _, uu = o.fields()
+    k = 2 * math.pi / L
+    z, y, x = np.meshgrid(np.arange(1), np.arange(L), np.arange(L), indexing="ij")
+    x, y = x.ravel(), y.ravel()
+    g = uu[:, 1] * (-np.sin(k * y))
+    s = math.atan2((g * np.sin(k * x)).sum(), (g * np.cos(k * x)).sum()) / k
+    assert abs(s - u0 * T) < 0.02 * u0 * T, (s, u0 * T)
+
+
+# ---------------------------------------------------- conservation + forcing
+
+def test_mass_conserved_periodic_with_ib_and_frame():
+    shape = (16, 16, 16)
+    rho, u = inputs.random_fields(shape, seed=1)
+    o = oracle.Oracle(shape, 0.6)
+    o.init_fields(rho, u)
+    m0 = math.fsum(o.populations().sum(1) - 1.0)
+    X0, dV = inputs.fibonacci_sphere(120, 3.0, (8.0, 8.0, 8.0))
+    vel = np.array([0.01, 0.005, 0.0])
+    frame = oracle.make_frame(acc=(1e-5, -2e-5, 1e-5), omega=(0, 0, 1e-3),
+                              domega=(1e-6, 0, 0), origin=(7.5, 7.5, 7.5))
+    for n in range(1000):
+        o.set_markers(X0 + vel * n, np.tile(vel, (120, 1)), dV)
+        o.step(frame)
+    m1 = math.fsum(o.populations().sum(1) - 1.0)
+    assert abs(m1 - m0) / (o.ncell + m0) < 1e-13
+    assert abs(o.mass_deviation() - m1) < 1e-9
+
+
+def test_uniform_body_force_momentum_gain():
+    """A uniform frame acceleration p'' is the uniform body force -rho p'':
+    the total momentum grows by exactly -p'' M per step."""
+    shape = (8, 6, 5)
+    rho, u = inputs.random_fields(shape, seed=2)
+    o = oracle.Oracle(shape, 0.7)
+    o.init_fields(rho, u)
+    c, _ = oracle.lattice()
+    acc = np.array([1e-4, -2e-4, 3e-4])
+    frame = oracle.make_frame(acc=acc)
+    for _ in range(3):
+        f0 = o.populations()
+        P0 = (f0 @ c).sum(0)
+        M = f0.sum()
+        o.step(frame)
+        P1 = (o.populations() @ c).sum(0)
+        assert np.max(np.abs((P1 - P0) - (-acc * M))) < 1e-12 * M * np.abs(acc).max() * 10
+
+
+# --------------------------------------------------------- immersed boundary
+
+def _grid_positions(shape):
+    z, y, x = np.meshgrid(*[np.arange(s) for s in shape[::-1]], indexing="ij")
+    return np.stack([x.ravel(), y.ravel(), z.ravel()], 1).astype(np.float64)
+
+
+@pytest.mark.parametrize("faces", [(PERIODIC,) * 6,
+                                   (VELOCITY, OUTFLOW, FREESLIP, FREESLIP, PERIODIC, PERIODIC)])
+def test_ib_interp_reproduces_linear_fields(faces):
+    shape = (14, 12, 10)
+    o = oracle.Oracle(shape, 0.7, faces=faces)
+    rng = np.random.default_rng(4)
+    X = np.stack([rng.uniform(3, 10, 40), rng.uniform(3, 8, 40), rng.uniform(3, 6, 40)], 1)
+    pos = _grid_positions(shape)
+    assert np.max(np.abs(o.interp(np.ones_like(pos), X) - 1.0)) < 1e-14
+    assert np.max(np.abs(o.interp(pos, X) - X)) < 1e-13
+
+
+def test_ib_spread_is_transpose_of_interp():
+    shape = (12, 10, 9)
+    o = oracle.Oracle(shape, 0.7)
+    rng = np.random.default_rng(8)
+    X = rng.uniform(-3, 15, (50, 3))       # includes positions that wrap
+    F = rng.standard_normal((50, 3))
+    g = rng.standard_normal((o.ncell, 3))
+    lhs = (o.spread(X, F) * g).sum()
+    rhs = (F * o.interp(g, X)).sum()
+    assert abs(lhs - rhs) < 1e-12 * abs(rhs)
+    # partition of unity: total spread equals total marker force
+    assert np.max(np.abs(o.spread(X, F).sum(0) - F.sum(0))) < 1e-12
+
+
+def test_ib_momentum_and_angular_momentum_balance():
+    """Without frame forces the fluid gains exactly what the markers push:
+    sum_x (j* - j) = -F_body and sum_x (x - ref) x (j* - j) = -T_body."""
+    shape = (24, 24, 24)
+    rho, u = inputs.random_fields(shape, seed=9, u_amp=0.01)
+    o = oracle.Oracle(shape, 0.7)
+    o.init_fields(rho, u)
+    X, dV = inputs.fibonacci_sphere(300, 5.0, (12.0, 11.5, 12.5))
+    rng = np.random.default_rng(10)
+    U = 0.02 * rng.standard_normal((300, 3))
+    seg = (np.arange(300) % 3).astype(np.int32)
+    ref = np.array([11.0, 12.0, 13.0])
+    o.set_markers(X, U, dV, seg=seg, nseg=3, ref=ref)
+    o.step()
+    c, _ = oracle.lattice()
+    _, j, _ = o.post_stream_moments()
+    js = o.populations() @ c
+    dj = js - j
+    ft = o.force_torque()
+    assert ft.shape == (4, 6)
+    assert np.allclose(ft[:3].sum(0), ft[3], rtol=0, atol=1e-13)
+    assert np.max(np.abs(dj.sum(0) + ft[3, :3])) < 1e-12
+    r = _grid_positions(shape) - ref
+    L = np.cross(r, dj).sum(0)
+    assert np.max(np.abs(L + ft[3, 3:])) < 1e-10
+    assert np.abs(ft[3, :3]).max() > 1e-3            # the test is not vacuous
+
+
+def test_comoving_markers_feel_no_force():
+    """Uniform fluid (velocity u0) under a uniform frame acceleration a0 = -p''
+    moves during the step at u0 + a0/2 (Guo's half-force velocity).  Markers
+    carried at exactly that velocity must feel zero direct force."""
+    shape = (16, 14, 12)
+    u0 = np.array([0.01, -0.02, 0.005])
+    acc = np.array([3e-4, 1e-4, -2e-4])
+    o = oracle.Oracle(shape, 0.7)
+    o.init_fields(np.ones(o.ncell), np.tile(u0, (o.ncell, 1)))
+    X, dV = inputs.fibonacci_sphere(150, 3.5, (8.0, 7.0, 6.0))
+    o.set_markers(X, np.tile(u0 - 0.5 * acc, (150, 1)), dV)
+    o.step(oracle.make_frame(acc=acc))
+    ft = o.force_torque()
+    assert np.max(np.abs(ft[:, :3])) < 1e-13 and np.max(np.abs(ft[:, 3:])) < 1e-12
+    o.set_markers(X, np.tile(u0, (150, 1)), dV)      # the unshifted velocity does feel a force
+    o.step(oracle.make_frame(acc=acc))
+    assert np.max(np.abs(o.force_torque()[-1, :3])) > 1e-3
+
+
+def test_marker_validation_near_open_faces():
+    o = oracle.Oracle((16, 12, 12), 0.7, faces=(VELOCITY, OUTFLOW, FREESLIP, FREESLIP,
+                                                 FREESLIP, FREESLIP))
+    ok = np.array([[2.0, 2.0, 8.9]])
+    o.set_markers(ok, np.zeros((1, 3)), np.ones(1))
+    for bad in ([1.99, 5, 5], [5, 5, 9.0], [13.0, 5, 5], [5, 1.5, 5]):
+        with pytest.raises(ValueError):
+            o.set_markers(np.array([bad]), np.zeros((1, 3)), np.ones(1))
+
+
+# ---------------------------------------------------------------- boundaries
+
+OPEN = (VELOCITY, OUTFLOW, FREESLIP, FREESLIP, FREESLIP, FREESLIP)
+
+
+def test_nee_uniform_inflow_is_fixed_point():
+    shape = (20, 10, 10)
+    uin = (0.03, 0.0, 0.0)
+    o = oracle.Oracle(shape, 0.6, faces=OPEN, u_in=uin)
+    o.init_fields(np.ones(o.ncell), np.tile(uin, (o.ncell, 1)))
+    f0 = o.populations()
+    o.step(n=10)
+    assert np.max(np.abs(o.populations() - f0)) < 1e-15
+
+
+def test_nee_reaches_uniform_inflow_from_rest():
+    shape = (12, 6, 6)
+    uin = (0.01, 0.0, 0.0)
+    o = oracle.Oracle(shape, 0.9, faces=OPEN, u_in=uin)
+    o.step(n=6000)
+    rho, u = o.fields()
+    assert np.max(np.abs(u - np.array(uin))) < 1e-10
+    assert np.max(np.abs(rho - 1.0)) < 1e-10
+
+
+def test_freeslip_walls_are_exact_for_tangential_shear():
+    """A shear wave u_x = U sin(k z), uniform in y, is tangential to free-slip
+    walls at y = 0, ny-1: the walled run must reproduce the fully periodic run
+    (the extrapolated non-equilibrium part carries the wave's shear stress)."""
+    shape = (6, 9, 16)
+    n = 6 * 9 * 16
+    z = np.repeat(np.arange(16), 6 * 9).astype(np.float64)
+    u = np.zeros((n, 3))
+    u[:, 0] = 0.02 * np.sin(2 * math.pi * z / 16)
+    walls = oracle.Oracle(shape, 0.8, faces=(PERIODIC, PERIODIC, FREESLIP, FREESLIP,
+                                             PERIODIC, PERIODIC))
+    per = oracle.Oracle(shape, 0.8)
+    for o in (walls, per):
+        o.init_fields(np.ones(n), u)
+        o.step(n=40)
+    assert np.max(np.abs(walls.populations() - per.populations())) < 1e-15
+    assert np.abs(per.fields()[1][:, 0]).max() > 0.01        # the wave is still there
+
+
+def test_nee_face_values_and_edge_precedence():
+    """Velocity inlet: u = u_in exactly (including on edges shared with side
+    walls: x-faces take precedence); outflow: rho = rho_out; free slip:
+    normal velocity zero."""
+    shape = (10, 8, 6)
+    uin = np.array([0.02, 0.01, 0.0])
+    o = oracle.Oracle(shape, 0.7, faces=OPEN, u_in=uin, rho_out=1.01)
+    rho0, u0 = inputs.random_fields(shape, seed=12)
+    o.init_fields(rho0, u0)
+    o.step(n=2)
+    rho, u = o.fields()
+    nx, ny, nz = shape
+    R = rho.reshape(nz, ny, nx)
+    Ug = u.reshape(nz, ny, nx, 3)
+    assert np.max(np.abs(Ug[:, :, 0, :] - uin)) < 1e-15              # whole inlet face
+    assert np.max(np.abs(R[:, :, -1] - 1.01)) < 1e-15                # whole outlet face
+    assert np.max(np.abs(Ug[:, 0, 1:-1, 1])) < 1e-16                 # y walls, x interior
+    assert np.max(np.abs(Ug[:, -1, 1:-1, 1])) < 1e-16
+    assert np.max(np.abs(Ug[0, 1:-1, 1:-1, 2])) < 1e-16              # z walls
+    assert np.max(np.abs(Ug[0, 0, 1:-1, 1:3])) < 1e-16               # y-z wall edge: both zero
+    assert np.abs(Ug[1:-1, 1:-1, 1:-1]).max() > 1e-4                 # interior is not trivial
+
+
+# ----------------------------------------------------------- frame (Eq. 3)
+
+def test_frame_accel_pure_rotation():
+    """Pure rotation about z through the origin: the centrifugal term is
+    omega^2 r radially outward and the Euler term is -domega z x r."""
+    om, dom = 0.01, 2e-4
+    fr = oracle.make_frame(omega=(0, 0, om), domega=(0, 0, dom), origin=(1.0, 2.0, 3.0))
+    rng = np.random.default_rng(0)
+    for _ in range(10):
+        x = rng.uniform(-10, 10, 3)
+        r = x - np.array([1.0, 2.0, 3.0])
+        a = oracle.frame_accel(fr, x)
+        rad = np.array([r[0], r[1], 0.0])
+        tang = np.array([-r[1], r[0], 0.0])
+        assert abs(a @ rad - om * om * (rad @ rad)) < 1e-15
+        assert abs(a @ tang + dom * (tang @ tang)) < 1e-15
+        assert abs(a[2]) < 1e-18
+    fr = oracle.make_frame(acc=(1.0, -2.0, 0.5))
+    assert np.allclose(oracle.frame_accel(fr, (3, 4, 5)), [-1.0, 2.0, -0.5])
+
+
+# ------------------------------------------------------- IB coupling (Stokes)
+
+@pytest.mark.slow
+def test_stokes_drag_periodic_sphere_array():
+    """A sphere translating at U through a periodic box whose mean fluid
+    momentum is held at zero (each step a uniform frame acceleration removes
+    what the markers pushed in) is Hasimoto's periodic array (Hasimoto 1959,
+    J. Fluid Mech. 5):  F = 6 pi rho nu a U / K(c),
+    K = 1 - 1.7601 c^(1/3) + c - 1.5593 c^2,  c = 4 pi a^3 / (3 L^3).
+    The diffuse IB surface acts half a cell outside the marker shell, so the
+    drag must match a = R + 0.5 within 5% and lie between a = R and a = R + 1;
+    it must oppose the motion."""
+    L, R, tau, Us = 40, 5.0, 1.0, 1e-3
+    nu = (tau - 0.5) / 3.0
+    M = float(L ** 3)
+    n = int(round(4 * math.pi * R * R))
+    X0, dV = inputs.fibonacci_sphere(n, R, ((L - 1) / 2 - 2,) * 3)
+    o = oracle.Oracle((L, L, L), tau)
+
+    def hasimoto(a):
+        c = 4 * math.pi * a ** 3 / (3 * L ** 3)
+        K = 1 - 1.7601 * c ** (1 / 3) + c - 1.5593 * c ** 2
+        return 6 * math.pi * nu * a * Us / K
+
+    Fb = 0.0
+    for step in range(1200):
+        o.set_markers(X0 + np.array([Us * step, 0, 0]), np.tile([Us, 0, 0], (n, 1)), dV)
+        o.step(oracle.make_frame(acc=(-Fb / M, 0, 0)))
+        Fb = o.force_torque()[-1, 0]
+    assert Fb < 0
+    drag = -Fb
+    assert hasimoto(R) < drag < hasimoto(R + 1.0)
+    assert abs(drag / hasimoto(R + 0.5) - 1.0) < 0.05, (drag, hasimoto(R + 0.5))
