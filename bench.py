@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Throughput of one IB-LBM time step (arXiv 2206.01683, Sec. III-B) on B300.
+
+Workload: the skinned swimmer in its moving frame -- a 256x128x128 D3Q27
+channel (velocity inlet u = 0.02 at -x, outflow at +x, free-slip side walls),
+tau = 0.52, a 6000-marker fish of body length 64 on a 5-segment spine driven
+by a travelling joint wave, and a seeded frame trajectory (Eq. 3).  One step
+= IB interpolation + direct forcing + spreading, fused stream/collide/
+boundary, FP64 force/torque/mass reduction; the marker pose of each step is
+an input (precomputed, resident in HBM for ``value``).
+
+Prints one JSON line (rank 0).  ``value`` is MLUPS over all ranks with the
+inputs resident in HBM; ``e2e`` is the same metric through the C ABI with
+the step's marker data copied from pinned host memory and the body force
+read back every step.  ``--impl reference`` times the FP64 CPU oracle instead
+(the only reference there is; rank 0 only).
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % HBM roofline per step (FP32 vs FP16-storage vs batched), 1×B300"
+OPEN_X = (1, 2, 3, 3, 3, 3)   # inlet, outflow, free-slip walls
+
+# DRAM traffic of k_stream_collide per cell update from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum divided by the cells of the
+# launch), valid only for the kernel source it was taken on.
+NCU_TRAFFIC = {
+    # "<sha256 of step_kernels.cuh>": bytes_per_cell
+}
+
+
+def kernel_source_hash():
+    p = os.path.join(ROOT, "paper_2206_01683_b300", "csrc", "step_kernels.cuh")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[4:]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for name, flag in zip(names, r[3][1:]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        sm = sorted(r[0] for r in rows)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows),
+                "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- workload
+
+def fish_workload(total_steps, shape=(256, 128, 128), length=64.0, n_markers=6000):
+    from paper_2206_01683_b300 import inputs
+    fish = inputs.fish_for_grid(shape, length, n_markers)
+    traj = inputs.FrameTrajectory(inputs.seed_for(2), inputs.domain_centre(shape))
+    X = np.zeros((total_steps, n_markers, 3), np.float32)
+    U = np.zeros((total_steps, n_markers, 3), np.float32)
+    frames = []
+    for n in range(total_steps):
+        x, u = fish.pose(n)
+        X[n], U[n] = x, u
+        frames.append(traj.at(n))
+    return fish, X, U, np.array(frames)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2206_01683_b300 import fishlbm
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    shape, tau, u_in = (256, 128, 128), 0.52, 0.02
+    ncell = shape[0] * shape[1] * shape[2]
+    W, K = args.warmup, args.steps
+    T = W + 2 * K + K   # warm-up, timed, roofline pass, e2e pass
+    fish, X, U, frames = fish_workload(T, shape)
+    fr = [fishlbm.frame_from_array(f) for f in frames]
+    stream = torch.cuda.Stream()
+    dom = fishlbm.Domain([fishlbm.env_desc(shape, tau, OPEN_X, (u_in, 0, 0), 1.0, (u_in, 0, 0))],
+                         stream=stream.cuda_stream)
+    Xd = torch.from_numpy(X).cuda()
+    Ud = torch.from_numpy(U).cuda()
+    dVd = torch.from_numpy(fish.dV.astype(np.float32)).cuda()
+    segd = torch.from_numpy(fish.seg.astype(np.int32)).cuda()
+    ref = tuple(float(v) for v in fish.joints_rest[0])
+    torch.cuda.synchronize()
+    dom.set_markers(Xd[0], Ud[0], dVd, segd, n_seg=5, ref=ref)
+
+    def dev_step(n):
+        dom.set_markers(Xd[n], Ud[n], None, None, n_seg=5, ref=ref)
+        dom.step(1, [fr[n]])
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    for n in range(W):
+        dev_step(n)
+    barrier()
+    dom.get_body_force_torque()
+
+    # ---- timed region: inputs resident in HBM
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for n in range(W, W + K):
+        dev_step(n)
+    e1.record(stream)
+    barrier()
+    clock_info = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    dom.get_body_force_torque()   # raises on a numeric fault
+
+    # ---- per-kernel durations over a second timed region (events around each launch)
+    dom.profile(True)
+    for n in range(W + K, W + 2 * K):
+        dev_step(n)
+    kms, kcount = dom.profile_read()
+    dom.profile(False)
+    k1_ms = kms[fishlbm.FG_K_STREAM_COLLIDE] / max(kcount[fishlbm.FG_K_STREAM_COLLIDE], 1)
+    ib_ms = kms[fishlbm.FG_K_IB] / max(kcount[fishlbm.FG_K_IB], 1)
+    red_ms = kms[fishlbm.FG_K_REDUCE] / max(kcount[fishlbm.FG_K_REDUCE], 1)
+    algo_bytes = dom.stream_collide_bytes()
+
+    # ---- end to end: host (pinned) marker buffers in, body force out, every step
+    Xh = torch.from_numpy(X).pin_memory()
+    Uh = torch.from_numpy(U).pin_memory()
+    out = np.zeros((6, 6))
+    barrier()
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    for n in range(W + 2 * K, W + 3 * K):
+        dom.set_markers(Xh[n], Uh[n], None, None, n_seg=5, ref=ref)
+        dom.step(1, [fr[n]])
+        out = dom.get_body_force_torque()
+    h1.record(stream)
+    barrier()
+    e2e_ms = h0.elapsed_time(h1)
+
+    if world > 1:
+        t = torch.tensor([ms, e2e_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return None
+    peak, peak_kind = measured_peaks()
+    achieved = algo_bytes / (k1_ms * 1e-3) / 1e9
+    bpc = NCU_TRAFFIC.get(kernel_source_hash())
+    mlups = world * ncell * K / (ms * 1e-3) / 1e6
+    h2d = 2 * X[0].nbytes + 64   # X, U and the frame
+    d2h = out.nbytes
+    line = {
+        "metric": METRIC,
+        "value": round(mlups, 1),
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": round(ms / K, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "swimmer_channel_256x128x128", "grid": list(shape), "tau": tau,
+                   "faces": "inlet -x (u=0.02), outflow +x, free-slip y/z",
+                   "markers": int(X.shape[1]), "segments": 5, "storage": "f32",
+                   "frame": "seeded accelerating + rotating (Eq. 3)",
+                   "l2": "inputs exceed L2 (populations 453 MB per buffer, 2 buffers)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "kernel": "k_stream_collide", "achieved": round(achieved, 1),
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4),
+                     "traffic": (round(bpc * ncell) if bpc else None),
+                     "algorithmic_bytes": int(algo_bytes),
+                     "kernel_ms": round(k1_ms, 5), "ib_ms": round(ib_ms, 5),
+                     "reduce_ms": round(red_ms, 5)},
+        "e2e": {"value": round(world * ncell * K / (e2e_ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": 3 * K,
+        "clocks": clock_info,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(fish, X, U, frames, shape, tau, u_in, steps=args.cpu_steps)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return line
+
+
+# -------------------------------------------------------------- oracle
+
+def oracle_steps(shape, tau, u_in, fish, X, U, frames, steps):
+    import oracle
+    o = oracle.Oracle(shape, tau, faces=OPEN_X, u_in=(u_in, 0, 0))
+    o.init_fields(None, np.tile([u_in, 0.0, 0.0], (o.ncell, 1)))
+    ref = fish.joints_rest[0]
+    times = []
+    for n in range(steps):
+        o.set_markers(X[n].astype(np.float64), U[n].astype(np.float64), fish.dV, seg=fish.seg,
+                      nseg=5, ref=ref)
+        t = time.perf_counter()
+        o.step(frames[n])
+        times.append(time.perf_counter() - t)
+    return times
+
+
+def cpu_baseline(fish, X, U, frames, shape, tau, u_in, steps):
+    ncell = shape[0] * shape[1] * shape[2]
+    times = oracle_steps(shape, tau, u_in, fish, X, U, frames, steps)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(ncell * steps / sum(times) / 1e6, 3), "unit": "MLUPS", "cores": cores,
+            "kind": "oracle",
+            "sample": "%d steps of the full %dx%dx%d swimmer channel (FP64 C oracle, OpenMP)"
+                      % (steps, *shape)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return None
+    # each step: one oracle step of the same physics on a 128x64x64 sample of
+    # the channel (body length 32, 1500 markers), so that K steps fit in minutes
+    shape, tau, u_in = (128, 64, 64), 0.52, 0.02
+    W, K = args.warmup, args.steps
+    fish, X, U, frames = fish_workload(W + K, shape, length=32.0, n_markers=1500)
+    import oracle
+    o = oracle.Oracle(shape, tau, faces=OPEN_X, u_in=(u_in, 0, 0))
+    o.init_fields(None, np.tile([u_in, 0.0, 0.0], (o.ncell, 1)))
+    ref = fish.joints_rest[0]
+    for n in range(W):
+        o.set_markers(X[n].astype(np.float64), U[n].astype(np.float64), fish.dV, seg=fish.seg, nseg=5, ref=ref)
+        o.step(frames[n])
+    t0 = time.perf_counter()
+    for n in range(W, W + K):
+        o.set_markers(X[n].astype(np.float64), U[n].astype(np.float64), fish.dV, seg=fish.seg, nseg=5, ref=ref)
+        o.step(frames[n])
+    dt = time.perf_counter() - t0
+    ncell = shape[0] * shape[1] * shape[2]
+    v = ncell * K / dt / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = "each step: one FP64 oracle step on a 128x64x64 sample of the swimmer channel (L=32, 1500 markers)"
+    return {
+        "impl": "reference",
+        "metric": METRIC, "value": round(v, 3), "unit": "MLUPS", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": round(dt / K * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "swimmer_channel_256x128x128", "sample": sample},
+        "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-steps", type=int, default=6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

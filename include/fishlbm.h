@@ -1,0 +1,207 @@
+/*
+ * fishlbm.h -- C ABI of the B300 (sm_103a) library that advances FishGym's
+ * fluid solver (arXiv 2206.01683, Sec. III-B "GPU-accelerated localized
+ * fluid-structure interaction"): one lattice Boltzmann time step on a D3Q27
+ * lattice, carried in the robot's accelerating local frame (the fictitious
+ * force of Eq. 3), closed by non-equilibrium extrapolation on the open faces
+ * of the moving domain (Sec. III-B "Simulation"), and two-way coupled to the
+ * uniformly sampled robot surface (Sec. III-B "Simulation", the external
+ * force tau_ext of Eq. 1) by a direct-forcing immersed boundary.
+ *
+ * Units are lattice units (dx = dt = 1, c_s^2 = 1/3).  Cell centres sit at
+ * integer coordinates 0..n-1 per axis; cell index c = x + nx*(y + ny*z).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an fg_status; fg_last_error() gives a thread-local
+ *    message for the last failure.  No C++ exception crosses the ABI.
+ *  - The library owns all device memory of a domain.  Caller buffers (host or
+ *    device) are only read or written during the call, except where a call
+ *    says it is asynchronous.
+ *  - All GPU work of a domain runs on the CUDA stream given at creation
+ *    (NULL = the legacy default stream).  fg_step is asynchronous; calls that
+ *    return data to the host synchronise that stream first.
+ *  - On an error the domain is unchanged, except FG_ERR_NUMERIC, which marks
+ *    the domain poisoned until fg_init_fields resets its state.
+ */
+#ifndef FISHLBM_H
+#define FISHLBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fg_domain fg_domain; /* opaque, owned by the library */
+
+typedef enum {
+    FG_OK = 0,
+    FG_ERR_INVALID = -1,  /* bad argument; nothing was changed */
+    FG_ERR_CUDA = -2,     /* a CUDA runtime call failed (message in fg_last_error) */
+    FG_ERR_OOM = -3,      /* device allocation failed */
+    FG_ERR_TIMEOUT = -4,  /* a bounded device wait gave up */
+    FG_ERR_NUMERIC = -5,  /* NaN/Inf in the mass or force reduction; domain poisoned */
+    FG_ERR_STATE = -6     /* call not valid in the domain's current state */
+} fg_status;
+
+/* Storage type of the populations.  Arithmetic is FP32 in every case; FP16
+ * and BF16 store f_i - w_i (the deviation from the rest state) scaled by a
+ * fixed power of two per velocity class. */
+typedef enum { FG_F32 = 0, FG_F16 = 1, FG_BF16 = 2 } fg_storage;
+
+/* Face condition.  Periodic faces come in pairs.  The three open kinds are
+ * closed by non-equilibrium extrapolation from the inward neighbour (Sec.
+ * III-B "Simulation"): a velocity inlet imposes u_in, an outflow imposes the
+ * density rho0 and extrapolates u, a free-slip wall extrapolates u with its
+ * normal component removed.  Boundary nodes are the outermost cell layer of
+ * a non-periodic face; where faces meet, x-faces govern. */
+typedef enum { FG_PERIODIC = 0, FG_VELOCITY = 1, FG_OUTFLOW = 2, FG_FREESLIP = 3 } fg_bc;
+
+typedef struct {
+    int nx, ny, nz;   /* cells per axis; >= 3 along a non-periodic axis */
+    double tau;       /* BGK relaxation time, > 0.5; nu = (tau - 1/2)/3 */
+    int face[6];      /* fg_bc for faces -x, +x, -y, +y, -z, +z */
+    double u_in[3];   /* inlet velocity of FG_VELOCITY faces */
+    double rho0;      /* initial density, and the density FG_OUTFLOW imposes */
+    double u0[3];     /* initial velocity */
+} fg_env_desc;
+
+/* Stream-collide kernel: AUTO picks STAGED when every row has at most 512
+ * cells, else PLAIN.  STAGED stages the source rows of each row group in
+ * shared memory with bulk copies (persistent, double-buffered); PLAIN reads
+ * global memory directly, one thread per cell.  Both compute the same step. */
+typedef enum { FG_KERNEL_AUTO = 0, FG_KERNEL_PLAIN = 1, FG_KERNEL_STAGED = 2 } fg_kernel_variant;
+
+typedef struct {
+    int storage;        /* fg_storage */
+    int layout;         /* 0: two-buffer pull scheme (the only layout) */
+    int deterministic;  /* 0 (reserved) */
+    int ib_iters;       /* direct-forcing passes per step; must be 1 */
+    int record_history; /* steps of (force, torque, mass) history kept on the
+                           device per environment (0 = none), ring buffer */
+    int kernel_variant; /* fg_kernel_variant */
+} fg_options;
+
+/* Frame motion of Eq. 3 for one environment: acc = translational
+ * acceleration p'' of the frame, omega = its angular velocity (Eq. 3's r'),
+ * domega = the rate of omega (r''), origin = the point x' is measured from.
+ * The fictitious acceleration is -acc - domega x x' - omega x (omega x x')
+ * - 2 omega x u. */
+typedef struct {
+    double acc[3], omega[3], domega[3], origin[3];
+} fg_frame;
+
+/* Create n_envs independent environments (n_envs > 1 is the batched form:
+ * every environment advances in the same kernel launches).  opt may be NULL
+ * (FP32, one pass).  cuda_stream is a cudaStream_t or NULL.  Populations are
+ * initialised at equilibrium with (rho0, u0); the frame is at rest with its
+ * origin at the domain centre.  Errors: FG_ERR_INVALID (sizes, tau, faces,
+ * options), FG_ERR_OOM, FG_ERR_CUDA.  *out is set only on FG_OK. */
+fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options* opt,
+                           void* cuda_stream, fg_domain** out);
+
+/* Copy the marker set of environment env: the robot surface sampled
+ * uniformly before the simulation (Sec. III-B "Simulation").
+ *   X[n][3]  positions (float, row-major), U[n][3] velocities at the current
+ *   step, dV[n] surface weight of each marker (area x 1 lu), seg[n] segment
+ *   id in [0, n_seg) (NULL: all 0), 1 <= n_seg <= 16, ref[3] the point
+ *   torques are taken about (NULL: origin).
+ * device_ptrs = 0: host arrays; 1: device arrays (copied on the stream,
+ * asynchronously).  dV and seg may be NULL on later calls with the same n to
+ * keep the previous values.  Periodic axes wrap X; along a non-periodic
+ * axis every marker must satisfy 2 <= X < n-3 so its 4-point stencil stays
+ * off the boundary layer: host arrays are checked here (FG_ERR_INVALID),
+ * device arrays in the step kernel, which skips such a marker and reports
+ * FG_ERR_INVALID from the next fg_get_body_force_torque. */
+fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const float* U,
+                         const float* dV, const int* seg, int n_seg, const double ref[3],
+                         int device_ptrs);
+
+/* Advance every environment by n_steps time steps (asynchronous on the
+ * domain's stream).  frames: NULL keeps the previous frames, else n_envs
+ * fg_frame entries applied to all n_steps.  One step: interpolate the
+ * post-stream velocity at the markers and spread the direct-forcing force;
+ * stream, collide (regularized BGK + Guo forcing with the frame force) and
+ * apply the open-face rule; reduce force, torque and mass in FP64. */
+fg_status fg_step(fg_domain* d, int n_steps, const fg_frame* frames);
+
+/* Force and torque the fluid exerts on the body in environment env during the
+ * last step (the tau_ext of Eq. 1), FP64: out[(n_seg + 1) * 6], one row
+ * (Fx, Fy, Fz, Tx, Ty, Tz) per segment, then the total.  Synchronises the
+ * stream.  Returns FG_ERR_NUMERIC if the step produced NaN/Inf. */
+fg_status fg_get_body_force_torque(fg_domain* d, int env, double* out);
+
+/* Release all device memory of the domain; NULL is ignored. */
+void fg_destroy(fg_domain* d);
+
+/* Thread-local message describing the last failed call ("" if none). */
+const char* fg_last_error(void);
+
+/* ---- state access (tests, checkpointing, diagnostics) ------------------ */
+
+/* The library's velocity order: c[27][3] in {-1,0,1}, w[27]. */
+fg_status fg_lattice(int* c, double* w);
+
+/* Reset env's populations to equilibrium from host FP64 fields rho[ncell] and
+ * u[ncell][3] (either NULL: rho0 / u0), clear the poisoned state.  Syncs. */
+fg_status fg_init_fields(fg_domain* d, int env, const double* rho, const double* u);
+
+/* Moments of env's stored post-collision state into host FP64 arrays:
+ * rho[ncell] = sum_i f_i, u[ncell][3] = sum_i c_i f_i / rho (either NULL).
+ * Synchronises. */
+fg_status fg_get_fields(fg_domain* d, int env, double* rho, double* u);
+
+/* Populations of env as host FP64 f[ncell][27] (library velocity order),
+ * decoded from the storage type.  Synchronises. */
+fg_status fg_get_populations(fg_domain* d, int env, double* f);
+
+/* Overwrite env's populations from host FP64 f[ncell][27] (library velocity
+ * order), rounded to the storage type.  Synchronises. */
+fg_status fg_set_populations(fg_domain* d, int env, const double* f);
+
+/* Marker force density F_l of the last step, host float F[n][3] (the fluid
+ * receives F_l dV_l spread by the delta kernel).  Synchronises. */
+fg_status fg_get_marker_force(fg_domain* d, int env, float* F);
+
+/* Total mass sum_x rho after the last step (FP64 reduction).  Synchronises. */
+fg_status fg_get_mass(fg_domain* d, int env, double* mass);
+
+/* Copy up to max_steps rows of env's recorded history, oldest first; each row
+ * is (n_seg + 1) * 6 force/torque values followed by the mass.  *n_rows gets
+ * the number of rows written.  Synchronises. */
+fg_status fg_get_history(fg_domain* d, int env, double* out, int max_steps, int* n_rows);
+
+/* Raw device-format state of env for checkpoint/restore (the populations in
+ * storage format, rows padded to a multiple of 8 cells): fg_state_bytes gives
+ * the size; save copies it to a host buffer, load copies it back (both sync). */
+fg_status fg_state_bytes(fg_domain* d, int env, unsigned long long* bytes);
+fg_status fg_save_state(fg_domain* d, int env, void* host_buf);
+fg_status fg_load_state(fg_domain* d, int env, const void* host_buf);
+
+/* Device status word (bit 0 numeric, bit 1 invalid marker, bit 2 timeout)
+ * without clearing it.  Synchronises. */
+fg_status fg_get_status(fg_domain* d, int* status);
+
+/* Number of time steps taken since creation or the last fg_init_fields. */
+fg_status fg_step_count(fg_domain* d, long long* steps);
+
+/* ---- timing ------------------------------------------------------------- */
+
+/* Kernel ids for the timing calls. */
+enum { FG_K_IB = 0, FG_K_STREAM_COLLIDE = 1, FG_K_REDUCE = 2, FG_K_COUNT = 3 };
+
+/* enable != 0: record a CUDA event pair around every kernel launch of
+ * fg_step (on the domain's stream); 0: stop.  Clears the accumulated times. */
+fg_status fg_profile(fg_domain* d, int enable);
+
+/* Sum of the recorded kernel durations (ms) and launch counts per kernel id
+ * since fg_profile(d, 1) or the previous read; clears them.  Synchronises. */
+fg_status fg_profile_read(fg_domain* d, double* ms, long long* launches);
+
+/* Algorithmic bytes one launch of the stream-collide kernel moves: 27 reads
+ * and 27 writes of a population per cell of every environment. */
+fg_status fg_stream_collide_bytes(fg_domain* d, unsigned long long* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FISHLBM_H */

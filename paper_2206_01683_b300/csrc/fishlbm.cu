@@ -1,0 +1,807 @@
+// fishlbm.cu -- host runtime and C ABI of the library (declared in
+// include/fishlbm.h).  Owns the device state of a domain: two population
+// buffers (pull scheme), the sparse IB force density with its 32-cell tile
+// stamps, marker arrays, FP64 reduction outputs, and the per-step launch
+// sequence k_ib -> k_stream_collide -> k_reduce on one CUDA stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fishlbm.h"
+#include "step_kernels.cuh"
+
+using namespace fl;
+
+namespace {
+
+thread_local std::string g_err;
+
+fg_status fail(fg_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+fg_status cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? FG_ERR_OOM : FG_ERR_CUDA;
+}
+
+#define CK(call)                                             \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+    } while (0)
+
+constexpr int PROFILE_CAP = 1 << 14;
+constexpr int MAX_STAGED_P = 512;   // longest row pitch the staged kernel takes
+
+struct MarkerRegion {
+    int n = 0, cap = 0, off = 0, nseg = 1;
+    bool has_dv = false;
+    double ref[3] = {0, 0, 0};
+};
+
+}  // namespace
+
+struct fg_domain {
+    int n_envs = 0;
+    fg_options opt{};
+    cudaStream_t stream = nullptr;
+    int esize = 4;                       // bytes per stored population
+    std::vector<fg_env_desc> desc;
+    std::vector<EnvDev> env;             // host copy of the device table
+    std::vector<FrameDev> frame;
+    std::vector<MarkerRegion> mk;
+    EnvDev* d_env = nullptr;
+    FrameDev* d_frame = nullptr;
+    void* pop[2] = {nullptr, nullptr};
+    int cur = 0;
+    unsigned long long pop_elems = 0, total_cells = 0, total_slots = 0;
+    float* fib = nullptr;
+    uint32_t* stamps = nullptr;
+    unsigned long long n_stamps = 0;
+    float* mass_part = nullptr;
+    int total_blocks = 0;                // plain stream-collide grid
+    int total_groups = 0;                // staged kernel row groups
+    bool staged = false;                 // stream-collide variant in use
+    int staged_grid = 0;                 // persistent blocks of the staged kernel
+    uint32_t buf_elems = 0;              // staged: elements per shared-memory buffer
+    size_t staged_smem = 0;
+    float *X = nullptr, *U = nullptr, *dV = nullptr, *Fm = nullptr;
+    int* seg = nullptr;
+    int marker_slots = 0;                // allocated marker slots
+    int total_markers = 0;
+    double* ft = nullptr;
+    double* mass = nullptr;
+    double* hist = nullptr;
+    int* status = nullptr;
+    long long steps = 0;
+    uint32_t stamp = 0;
+    bool poisoned = false;
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev[FG_K_COUNT];
+    int ev_used[FG_K_COUNT] = {0, 0, 0};
+    double prof_ms[FG_K_COUNT] = {0, 0, 0};
+    long long prof_n[FG_K_COUNT] = {0, 0, 0};
+};
+
+namespace {
+
+fg_status upload_env(fg_domain* d) {
+    CK(cudaMemcpyAsync(d->d_env, d->env.data(), sizeof(EnvDev) * d->n_envs, cudaMemcpyHostToDevice,
+                       d->stream));
+    return FG_OK;
+}
+
+fg_status upload_frames(fg_domain* d) {
+    CK(cudaMemcpyAsync(d->d_frame, d->frame.data(), sizeof(FrameDev) * d->n_envs,
+                       cudaMemcpyHostToDevice, d->stream));
+    return FG_OK;
+}
+
+void set_frame(FrameDev& f, const fg_frame& src) {
+    double oo = 0;
+    for (int a = 0; a < 3; ++a) {
+        f.acc[a] = (float)src.acc[a];
+        f.om[a] = (float)src.omega[a];
+        f.dom[a] = (float)src.domega[a];
+        f.org[a] = (float)src.origin[a];
+        oo += src.omega[a] * src.omega[a];
+    }
+    f.inv_1pom2 = (float)(1.0 / (1.0 + oo));
+    f.pad[0] = f.pad[1] = f.pad[2] = 0.f;
+}
+
+void free_all(fg_domain* d) {
+    if (!d) return;
+    void* ptrs[] = {d->d_env, d->d_frame, d->pop[0], d->pop[1], d->fib, d->stamps, d->mass_part,
+                    d->X, d->U, d->dV, d->Fm, d->seg, d->ft, d->mass, d->hist, d->status};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (int k = 0; k < FG_K_COUNT; ++k)
+        for (cudaEvent_t e : d->ev[k]) cudaEventDestroy(e);
+}
+
+template <class T>
+fg_status dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, "cudaMalloc");
+    }
+    return FG_OK;
+}
+
+// Re-layout marker storage so environment env can hold n markers.
+fg_status grow_markers(fg_domain* d, int env, int n) {
+    std::vector<MarkerRegion> nr = d->mk;
+    nr[env].cap = std::max(n, std::max(2 * nr[env].cap, 64));
+    int off = 0;
+    for (auto& r : nr) {
+        r.off = off;
+        off += r.cap;
+    }
+    float *X, *U, *dV, *Fm;
+    int* sg;
+    fg_status s;
+    if ((s = dalloc(&X, 3ull * off)) != FG_OK) return s;
+    if ((s = dalloc(&U, 3ull * off)) != FG_OK) { cudaFree(X); return s; }
+    if ((s = dalloc(&dV, off)) != FG_OK) { cudaFree(X); cudaFree(U); return s; }
+    if ((s = dalloc(&Fm, 3ull * off)) != FG_OK) { cudaFree(X); cudaFree(U); cudaFree(dV); return s; }
+    if ((s = dalloc(&sg, off)) != FG_OK) {
+        cudaFree(X); cudaFree(U); cudaFree(dV); cudaFree(Fm);
+        return s;
+    }
+    for (int e = 0; e < d->n_envs; ++e) {
+        const MarkerRegion& o = d->mk[e];
+        if (o.n == 0) continue;
+        CK(cudaMemcpyAsync(X + 3ull * nr[e].off, d->X + 3ull * o.off, sizeof(float) * 3 * o.n,
+                           cudaMemcpyDeviceToDevice, d->stream));
+        CK(cudaMemcpyAsync(U + 3ull * nr[e].off, d->U + 3ull * o.off, sizeof(float) * 3 * o.n,
+                           cudaMemcpyDeviceToDevice, d->stream));
+        CK(cudaMemcpyAsync(dV + nr[e].off, d->dV + o.off, sizeof(float) * o.n,
+                           cudaMemcpyDeviceToDevice, d->stream));
+        CK(cudaMemcpyAsync(Fm + 3ull * nr[e].off, d->Fm + 3ull * o.off, sizeof(float) * 3 * o.n,
+                           cudaMemcpyDeviceToDevice, d->stream));
+        CK(cudaMemcpyAsync(sg + nr[e].off, d->seg + o.off, sizeof(int) * o.n,
+                           cudaMemcpyDeviceToDevice, d->stream));
+    }
+    CK(cudaStreamSynchronize(d->stream));
+    if (d->X) { cudaFree(d->X); cudaFree(d->U); cudaFree(d->dV); cudaFree(d->Fm); cudaFree(d->seg); }
+    d->X = X; d->U = U; d->dV = dV; d->Fm = Fm; d->seg = sg;
+    d->marker_slots = off;
+    d->mk = nr;
+    return FG_OK;
+}
+
+void refresh_marker_table(fg_domain* d) {
+    int begin = 0;
+    for (int e = 0; e < d->n_envs; ++e) {
+        EnvDev& E = d->env[e];
+        E.mk_begin = begin;
+        E.n_markers = d->mk[e].n;
+        E.marker_off = d->mk[e].off;
+        E.nseg = d->mk[e].nseg;
+        for (int a = 0; a < 3; ++a) E.ref[a] = d->mk[e].ref[a];
+        begin += d->mk[e].n;
+    }
+    d->total_markers = begin;
+}
+
+template <class S>
+fg_status launch_step(fg_domain* d) {
+    typedef typename S::raw raw;
+    const raw* gin = (const raw*)d->pop[d->cur];
+    raw* gout = (raw*)d->pop[d->cur ^ 1];
+    const uint32_t stamp = ++d->stamp;
+    cudaEvent_t* evp[FG_K_COUNT] = {nullptr, nullptr, nullptr};
+    if (d->profiling) {
+        for (int k = 0; k < FG_K_COUNT; ++k) {
+            if (d->ev_used[k] + 2 > (int)d->ev[k].size()) {
+                // drain: accumulate what is recorded so far
+                CK(cudaStreamSynchronize(d->stream));
+                for (int i = 0; i + 1 < d->ev_used[k]; i += 2) {
+                    float ms = 0;
+                    CK(cudaEventElapsedTime(&ms, d->ev[k][i], d->ev[k][i + 1]));
+                    d->prof_ms[k] += ms;
+                    d->prof_n[k] += 1;
+                }
+                d->ev_used[k] = 0;
+            }
+            evp[k] = &d->ev[k][d->ev_used[k]];
+            d->ev_used[k] += 2;
+        }
+    }
+    if (d->total_markers > 0) {
+        if (evp[FG_K_IB]) CK(cudaEventRecord(evp[FG_K_IB][0], d->stream));
+        const int warps_per_block = IB_THREADS / 32;
+        const int blocks = (d->total_markers + warps_per_block - 1) / warps_per_block;
+        k_ib<S><<<blocks, IB_THREADS, 0, d->stream>>>(gin, d->d_env, d->d_frame, d->n_envs,
+                                                      d->total_markers, d->X, d->U, d->dV, d->Fm,
+                                                      d->fib, d->stamps, stamp, d->status);
+        if (evp[FG_K_IB]) CK(cudaEventRecord(evp[FG_K_IB][1], d->stream));
+    } else if (evp[FG_K_IB]) {
+        d->ev_used[FG_K_IB] -= 2;
+    }
+    if (evp[FG_K_STREAM_COLLIDE]) CK(cudaEventRecord(evp[FG_K_STREAM_COLLIDE][0], d->stream));
+    if (d->staged) {
+        k_stream_collide_staged<S><<<d->staged_grid, K1_THREADS, d->staged_smem, d->stream>>>(
+            gin, gout, d->d_env, d->d_frame, d->n_envs, d->total_groups, d->buf_elems, d->fib, d->stamps,
+            stamp, d->mass_part, d->status);
+    } else {
+        k_stream_collide<S><<<d->total_blocks, K1_THREADS, 0, d->stream>>>(
+            gin, gout, d->d_env, d->d_frame, d->n_envs, d->fib, d->stamps, stamp, d->mass_part);
+    }
+    if (evp[FG_K_STREAM_COLLIDE]) CK(cudaEventRecord(evp[FG_K_STREAM_COLLIDE][1], d->stream));
+    if (evp[FG_K_REDUCE]) CK(cudaEventRecord(evp[FG_K_REDUCE][0], d->stream));
+    k_reduce<<<dim3(d->n_envs, MAX_SEG + 2), RED_THREADS, 0, d->stream>>>(d->d_env, d->X, d->Fm, d->dV, d->seg,
+                                                       d->mass_part, d->ft, d->mass, d->hist,
+                                                       d->opt.record_history, d->steps, d->status);
+    if (evp[FG_K_REDUCE]) CK(cudaEventRecord(evp[FG_K_REDUCE][1], d->stream));
+    CK(cudaGetLastError());
+    d->cur ^= 1;
+    d->steps += 1;
+    return FG_OK;
+}
+
+template <class F>
+fg_status dispatch(int storage, F&& f) {
+    switch (storage) {
+        case FG_F32: return f(StoreF32());
+        case FG_F16: return f(StoreF16());
+        case FG_BF16: return f(StoreBF16());
+    }
+    return fail(FG_ERR_INVALID, "unknown storage");
+}
+
+
+// Shared memory, occupancy and persistent grid of the staged kernel.
+fg_status setup_staged(fg_domain* d) {
+    d->staged_smem = 2ull * d->buf_elems * d->esize;
+    int dev = 0, sms = 0, per_sm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    return dispatch(d->opt.storage, [&](auto tag) -> fg_status {
+        typedef decltype(tag) S;
+        CK(cudaFuncSetAttribute(k_stream_collide_staged<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)d->staged_smem));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_staged<S>, K1_THREADS,
+                                                         d->staged_smem));
+        if (per_sm < 1) return fail(FG_ERR_INVALID, "staged kernel does not fit on an SM");
+        d->staged_grid = std::min(d->total_groups, sms * per_sm);
+        return FG_OK;
+    });
+}
+
+size_t env_cells(const fg_domain* d, int env) {
+    return (size_t)d->env[env].n[0] * d->env[env].n[1] * d->env[env].n[2];
+}
+
+fg_status check_env(fg_domain* d, int env) {
+    if (!d) return fail(FG_ERR_INVALID, "null domain");
+    if (env < 0 || env >= d->n_envs) return fail(FG_ERR_INVALID, "environment index out of range");
+    return FG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fg_last_error(void) { return g_err.c_str(); }
+
+fg_status fg_lattice(int* c, double* w) {
+    if (!c || !w) return fail(FG_ERR_INVALID, "null output");
+    for (int i = 0; i < Q; ++i) {
+        c[3 * i] = cx(i); c[3 * i + 1] = cy(i); c[3 * i + 2] = cz(i);
+        w[i] = wd(i);
+    }
+    return FG_OK;
+}
+
+fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options* opt, void* cuda_stream,
+                           fg_domain** out) {
+    g_err.clear();
+    if (!envs || !out || n_envs < 1 || n_envs > 4096) return fail(FG_ERR_INVALID, "bad environment list");
+    fg_options o{};
+    o.storage = FG_F32; o.layout = 0; o.deterministic = 0; o.ib_iters = 1; o.record_history = 0;
+    o.kernel_variant = FG_KERNEL_AUTO;
+    if (opt) o = *opt;
+    if (o.kernel_variant < FG_KERNEL_AUTO || o.kernel_variant > FG_KERNEL_STAGED)
+        return fail(FG_ERR_INVALID, "unknown kernel variant");
+    if (o.storage < 0 || o.storage > 2) return fail(FG_ERR_INVALID, "unknown storage");
+    if (o.layout != 0) return fail(FG_ERR_INVALID, "only the two-buffer pull layout (0) exists");
+    if (o.ib_iters != 1) return fail(FG_ERR_INVALID, "ib_iters must be 1");
+    if (o.record_history < 0 || o.record_history > (1 << 20)) return fail(FG_ERR_INVALID, "record_history");
+    unsigned long long cells = 0;
+    for (int e = 0; e < n_envs; ++e) {
+        const fg_env_desc& E = envs[e];
+        int n[3] = {E.nx, E.ny, E.nz};
+        for (int a = 0; a < 3; ++a) {
+            if (n[a] < 1 || n[a] > 65536) return fail(FG_ERR_INVALID, "grid size out of range");
+            int lo = E.face[2 * a], hi = E.face[2 * a + 1];
+            if (lo < 0 || lo > 3 || hi < 0 || hi > 3) return fail(FG_ERR_INVALID, "unknown face kind");
+            if ((lo == FG_PERIODIC) != (hi == FG_PERIODIC))
+                return fail(FG_ERR_INVALID, "periodic faces must come in pairs");
+            if (lo != FG_PERIODIC && n[a] < 3) return fail(FG_ERR_INVALID, "open axis needs >= 3 cells");
+        }
+        if (!(E.tau > 0.5) || !std::isfinite(E.tau)) return fail(FG_ERR_INVALID, "tau must exceed 1/2");
+        if (!(E.rho0 > 0.0)) return fail(FG_ERR_INVALID, "rho0 must be positive");
+        unsigned long long ns = (unsigned long long)((E.nx + 7) / 8 * 8) * E.ny * E.nz;
+        if (ns >= (1ull << 31)) return fail(FG_ERR_INVALID, "too many cells in one environment");
+        cells += ns;
+    }
+    fg_domain* d = new (std::nothrow) fg_domain();
+    if (!d) return fail(FG_ERR_OOM, "host allocation");
+    d->n_envs = n_envs;
+    d->opt = o;
+    d->stream = (cudaStream_t)cuda_stream;
+    d->esize = o.storage == FG_F32 ? 4 : 2;
+    d->desc.assign(envs, envs + n_envs);
+    d->env.resize(n_envs);
+    d->frame.resize(n_envs);
+    d->mk.resize(n_envs);
+    unsigned long long slot_off = 0, stamp_off = 0, ncell_all = 0;
+    int block0 = 0, group0 = 0;
+    bool can_stage = true;
+    for (int e = 0; e < n_envs; ++e) {
+        const fg_env_desc& s = envs[e];
+        EnvDev& E = d->env[e];
+        std::memset(&E, 0, sizeof(E));
+        E.n[0] = s.nx; E.n[1] = s.ny; E.n[2] = s.nz;
+        E.P = (s.nx + 7) / 8 * 8;
+        E.nslot = (uint32_t)((unsigned long long)E.P * s.ny * s.nz);
+        E.rows = (uint32_t)s.ny * (uint32_t)s.nz;
+        E.div_P = make_fastdiv((uint32_t)E.P);
+        E.div_ny = make_fastdiv((uint32_t)s.ny);
+        for (int k = 0; k < 6; ++k) E.bc[k] = s.face[k];
+        for (int a = 0; a < 3; ++a) E.per[a] = s.face[2 * a] == FG_PERIODIC;
+        E.keep = (float)(1.0 - 1.0 / s.tau);
+        E.guo = (float)(1.0 - 0.5 / s.tau);
+        for (int a = 0; a < 3; ++a) E.u_in[a] = (float)s.u_in[a];
+        E.drho_out = (float)(s.rho0 - 1.0);
+        E.pop_off = 27ull * slot_off;
+        E.slot_off = slot_off;
+        E.block0 = block0;
+        E.nblocks = (int)((E.nslot + K1_THREADS - 1) / K1_THREADS);
+        E.rpg = std::max(1, std::min(GROUP_CELLS / E.P, (int)E.rows));
+        E.group0 = group0;
+        E.ngroups = (int)((E.rows + E.rpg - 1) / E.rpg);
+        E.stamp_off = (int)stamp_off;
+        E.nseg = 1;
+        if (E.P > MAX_STAGED_P) can_stage = false;
+        slot_off += E.nslot;
+        ncell_all += (unsigned long long)s.nx * s.ny * s.nz;
+        stamp_off += (E.nslot + 31) / 32;
+        block0 += E.nblocks;
+        group0 += E.ngroups;
+        fg_frame fr{};
+        fr.origin[0] = (s.nx - 1) * 0.5; fr.origin[1] = (s.ny - 1) * 0.5; fr.origin[2] = (s.nz - 1) * 0.5;
+        set_frame(d->frame[e], fr);
+    }
+    if (o.kernel_variant == FG_KERNEL_STAGED && !can_stage) {
+        delete d;
+        return fail(FG_ERR_INVALID, "staged kernel needs rows of at most 512 cells");
+    }
+    d->staged = o.kernel_variant == FG_KERNEL_STAGED || (o.kernel_variant == FG_KERNEL_AUTO && can_stage);
+    for (int e = 0; e < n_envs; ++e) {
+        EnvDev& E = d->env[e];
+        E.part0 = d->staged ? E.group0 : E.block0;
+        E.nparts = d->staged ? E.ngroups : E.nblocks;
+        d->buf_elems = std::max<uint32_t>(d->buf_elems, (uint32_t)(27 * E.rpg * E.P));
+    }
+    d->total_cells = ncell_all;
+    d->total_slots = slot_off;
+    d->pop_elems = 27ull * slot_off;
+    d->n_stamps = stamp_off;
+    d->total_blocks = block0;
+    d->total_groups = group0;
+    fg_status st = FG_OK;
+#define DA(ptr, n)                                   \
+    if ((st = dalloc(&(ptr), (n))) != FG_OK) {       \
+        free_all(d);                                 \
+        delete d;                                    \
+        return st;                                   \
+    }
+    DA(d->d_env, n_envs);
+    DA(d->d_frame, n_envs);
+    {
+        char *p0 = nullptr, *p1 = nullptr;
+        DA(p0, d->pop_elems * d->esize);
+        d->pop[0] = p0;
+        DA(p1, d->pop_elems * d->esize);
+        d->pop[1] = p1;
+    }
+    DA(d->fib, 3ull * slot_off);
+    DA(d->stamps, stamp_off);
+    DA(d->mass_part, std::max(block0, group0));
+    DA(d->ft, (size_t)n_envs * FT_ROW);
+    DA(d->mass, n_envs);
+    if (o.record_history > 0) DA(d->hist, (size_t)n_envs * o.record_history * HIST_ROW);
+    DA(d->status, 1);
+#undef DA
+    cudaError_t ce;
+    if ((ce = cudaMemsetAsync(d->pop[0], 0, d->pop_elems * d->esize, d->stream)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(d->pop[1], 0, d->pop_elems * d->esize, d->stream)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(d->fib, 0, sizeof(float) * 3ull * slot_off, d->stream)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(d->stamps, 0, sizeof(uint32_t) * stamp_off, d->stream)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(d->ft, 0, sizeof(double) * n_envs * FT_ROW, d->stream)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(d->status, 0, sizeof(int), d->stream)) != cudaSuccess) {
+        st = cuda_fail(ce, "cudaMemsetAsync");
+        free_all(d);
+        delete d;
+        return st;
+    }
+    if (d->staged && (st = setup_staged(d)) != FG_OK) {
+        free_all(d);
+        delete d;
+        return st;
+    }
+    refresh_marker_table(d);
+    if ((st = upload_env(d)) != FG_OK || (st = upload_frames(d)) != FG_OK) {
+        free_all(d);
+        delete d;
+        return st;
+    }
+    for (int e = 0; e < n_envs && st == FG_OK; ++e) st = fg_init_fields(d, e, nullptr, nullptr);
+    if (st != FG_OK) {
+        free_all(d);
+        delete d;
+        return st;
+    }
+    *out = d;
+    return FG_OK;
+}
+
+void fg_destroy(fg_domain* d) {
+    if (!d) return;
+    cudaStreamSynchronize(d->stream);
+    free_all(d);
+    delete d;
+}
+
+fg_status fg_init_fields(fg_domain* d, int env, const double* rho, const double* u) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    const size_t ncell = env_cells(d, env);
+    double *drho = nullptr, *du = nullptr;
+    if (rho) {
+        if ((st = dalloc(&drho, ncell)) != FG_OK) return st;
+        CK(cudaMemcpyAsync(drho, rho, sizeof(double) * ncell, cudaMemcpyHostToDevice, d->stream));
+    }
+    if (u) {
+        if ((st = dalloc(&du, 3ull * ncell)) != FG_OK) { if (drho) cudaFree(drho); return st; }
+        CK(cudaMemcpyAsync(du, u, sizeof(double) * 3 * ncell, cudaMemcpyHostToDevice, d->stream));
+    }
+    const fg_env_desc& s = d->desc[env];
+    const int blocks = (int)((ncell + 255) / 256);
+    st = dispatch(d->opt.storage, [&](auto tag) -> fg_status {
+        typedef decltype(tag) S;
+        k_init_eq<S><<<blocks, 256, 0, d->stream>>>((typename S::raw*)d->pop[d->cur], d->d_env, env, drho, du,
+                                                    s.rho0, s.u0[0], s.u0[1], s.u0[2]);
+        return FG_OK;
+    });
+    cudaError_t e1 = cudaGetLastError();
+    cudaError_t e2 = cudaStreamSynchronize(d->stream);
+    if (drho) cudaFree(drho);
+    if (du) cudaFree(du);
+    if (e1 != cudaSuccess) return cuda_fail(e1, "k_init_eq");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamSynchronize");
+    if (st != FG_OK) return st;
+    d->poisoned = false;
+    d->steps = 0;
+    CK(cudaMemsetAsync(d->status, 0, sizeof(int), d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    return FG_OK;
+}
+
+fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const float* U, const float* dV,
+                         const int* seg, int n_seg, const double ref[3], int device_ptrs) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    if (n < 0) return fail(FG_ERR_INVALID, "negative marker count");
+    if (n > 0 && (!X || !U)) return fail(FG_ERR_INVALID, "X and U are required");
+    if (n_seg < 1 || n_seg > MAX_SEG) return fail(FG_ERR_INVALID, "n_seg must be in [1, 16]");
+    MarkerRegion& r = d->mk[env];
+    if (n > 0 && !dV && !(r.has_dv && r.n == n))
+        return fail(FG_ERR_INVALID, "dV is required when the marker count changes");
+    if (!device_ptrs && n > 0) {
+        const EnvDev& E = d->env[env];
+        for (int l = 0; l < n; ++l) {
+            for (int a = 0; a < 3; ++a) {
+                const float x = X[3 * l + a];
+                if (!std::isfinite(x) || std::fabs(x) > 1.0e6f) return fail(FG_ERR_INVALID, "marker position not finite");
+                if (!E.per[a] && !(x >= 2.0f && x < (float)E.n[a] - 3.0f))
+                    return fail(FG_ERR_INVALID, "marker within 2 cells of a non-periodic face");
+                if (!std::isfinite(U[3 * l + a])) return fail(FG_ERR_INVALID, "marker velocity not finite");
+            }
+            if (dV && !std::isfinite(dV[l])) return fail(FG_ERR_INVALID, "marker weight not finite");
+            if (seg && (seg[l] < 0 || seg[l] >= n_seg)) return fail(FG_ERR_INVALID, "segment id out of range");
+        }
+    }
+    if (n > r.cap) {
+        if ((st = grow_markers(d, env, n)) != FG_OK) return st;
+    }
+    MarkerRegion& m = d->mk[env];
+    const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(d->X + 3ull * m.off, X, sizeof(float) * 3 * n, kind, d->stream));
+        CK(cudaMemcpyAsync(d->U + 3ull * m.off, U, sizeof(float) * 3 * n, kind, d->stream));
+        if (dV) CK(cudaMemcpyAsync(d->dV + m.off, dV, sizeof(float) * n, kind, d->stream));
+        if (seg) {
+            CK(cudaMemcpyAsync(d->seg + m.off, seg, sizeof(int) * n, kind, d->stream));
+        } else if (m.n != n || n_seg != m.nseg) {
+            CK(cudaMemsetAsync(d->seg + m.off, 0, sizeof(int) * n, d->stream));
+        }
+    }
+    const bool table_changed = m.n != n || m.nseg != n_seg ||
+                               (ref && (ref[0] != m.ref[0] || ref[1] != m.ref[1] || ref[2] != m.ref[2])) ||
+                               (!ref && (m.ref[0] != 0 || m.ref[1] != 0 || m.ref[2] != 0));
+    m.n = n;
+    m.nseg = n_seg;
+    if (dV) m.has_dv = true;
+    for (int a = 0; a < 3; ++a) m.ref[a] = ref ? ref[a] : 0.0;
+    if (table_changed) {
+        refresh_marker_table(d);
+        if ((st = upload_env(d)) != FG_OK) return st;
+    }
+    return FG_OK;
+}
+
+fg_status fg_step(fg_domain* d, int n_steps, const fg_frame* frames) {
+    if (!d) return fail(FG_ERR_INVALID, "null domain");
+    if (n_steps < 0) return fail(FG_ERR_INVALID, "negative step count");
+    if (d->poisoned) return fail(FG_ERR_STATE, "domain poisoned by a numeric fault; call fg_init_fields");
+    if (frames) {
+        for (int e = 0; e < d->n_envs; ++e) {
+            for (int a = 0; a < 3; ++a)
+                if (!std::isfinite(frames[e].acc[a]) || !std::isfinite(frames[e].omega[a]) ||
+                    !std::isfinite(frames[e].domega[a]) || !std::isfinite(frames[e].origin[a]))
+                    return fail(FG_ERR_INVALID, "frame not finite");
+        }
+        for (int e = 0; e < d->n_envs; ++e) set_frame(d->frame[e], frames[e]);
+        fg_status st = upload_frames(d);
+        if (st != FG_OK) return st;
+    }
+    for (int s = 0; s < n_steps; ++s) {
+        fg_status st = dispatch(d->opt.storage, [&](auto tag) { return launch_step<decltype(tag)>(d); });
+        if (st != FG_OK) return st;
+    }
+    return FG_OK;
+}
+
+fg_status fg_get_status(fg_domain* d, int* status) {
+    if (!d || !status) return fail(FG_ERR_INVALID, "null argument");
+    CK(cudaMemcpyAsync(status, d->status, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    return FG_OK;
+}
+
+static fg_status status_to_error(fg_domain* d) {
+    int s = 0;
+    fg_status st = fg_get_status(d, &s);
+    if (st != FG_OK) return st;
+    if (s & ST_NUMERIC) {
+        d->poisoned = true;
+        return fail(FG_ERR_NUMERIC, "NaN or Inf in the force or mass reduction");
+    }
+    if (s & ST_BAD_MARKER) {
+        CK(cudaMemsetAsync(d->status, 0, sizeof(int), d->stream));
+        CK(cudaStreamSynchronize(d->stream));
+        return fail(FG_ERR_INVALID, "a marker was outside the domain or within 2 cells of a non-periodic face");
+    }
+    if (s & ST_TIMEOUT) return fail(FG_ERR_TIMEOUT, "a bounded device wait gave up");
+    return FG_OK;
+}
+
+fg_status fg_get_body_force_torque(fg_domain* d, int env, double* out) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    if (!out) return fail(FG_ERR_INVALID, "null output");
+    const int rows = d->mk[env].nseg + 1;
+    CK(cudaMemcpyAsync(out, d->ft + (size_t)env * FT_ROW, sizeof(double) * 6 * rows, cudaMemcpyDeviceToHost,
+                       d->stream));
+    return status_to_error(d);
+}
+
+fg_status fg_get_mass(fg_domain* d, int env, double* mass) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    if (!mass) return fail(FG_ERR_INVALID, "null output");
+    CK(cudaMemcpyAsync(mass, d->mass + env, sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+    return status_to_error(d);
+}
+
+fg_status fg_get_marker_force(fg_domain* d, int env, float* F) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    const MarkerRegion& m = d->mk[env];
+    if (m.n == 0) return FG_OK;
+    if (!F) return fail(FG_ERR_INVALID, "null output");
+    CK(cudaMemcpyAsync(F, d->Fm + 3ull * m.off, sizeof(float) * 3 * m.n, cudaMemcpyDeviceToHost, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    return FG_OK;
+}
+
+fg_status fg_get_history(fg_domain* d, int env, double* out, int max_steps, int* n_rows) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    if (!out || !n_rows || max_steps < 0) return fail(FG_ERR_INVALID, "bad output");
+    const int cap = d->opt.record_history;
+    *n_rows = 0;
+    if (cap == 0) return fail(FG_ERR_STATE, "history was not enabled at creation");
+    const long long avail = std::min<long long>(d->steps, cap);
+    const long long nr = std::min<long long>(avail, max_steps);
+    std::vector<double> all((size_t)cap * HIST_ROW);
+    CK(cudaMemcpyAsync(all.data(), d->hist + (size_t)env * cap * HIST_ROW, sizeof(double) * all.size(),
+                       cudaMemcpyDeviceToHost, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    const int w = 6 * (d->mk[env].nseg + 1);
+    for (long long k = 0; k < nr; ++k) {
+        const long long step = d->steps - nr + k;  // oldest first
+        const double* row = all.data() + (size_t)(step % cap) * HIST_ROW;
+        std::memcpy(out + k * (w + 1), row, sizeof(double) * w);
+        out[k * (w + 1) + w] = row[FT_ROW];
+    }
+    *n_rows = (int)nr;
+    return FG_OK;
+}
+
+fg_status fg_get_fields(fg_domain* d, int env, double* rho, double* u) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    const size_t ncell = env_cells(d, env);
+    double *dr = nullptr, *du = nullptr;
+    if ((st = dalloc(&dr, ncell)) != FG_OK) return st;
+    if ((st = dalloc(&du, 3ull * ncell)) != FG_OK) { cudaFree(dr); return st; }
+    const int blocks = (int)((ncell + 255) / 256);
+    dispatch(d->opt.storage, [&](auto tag) -> fg_status {
+        typedef decltype(tag) S;
+        k_get_fields<S><<<blocks, 256, 0, d->stream>>>((const typename S::raw*)d->pop[d->cur], d->d_env, env,
+                                                       dr, du);
+        return FG_OK;
+    });
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && rho)
+        e = cudaMemcpyAsync(rho, dr, sizeof(double) * ncell, cudaMemcpyDeviceToHost, d->stream);
+    if (e == cudaSuccess && u)
+        e = cudaMemcpyAsync(u, du, sizeof(double) * 3 * ncell, cudaMemcpyDeviceToHost, d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    cudaFree(dr);
+    cudaFree(du);
+    if (e != cudaSuccess) return cuda_fail(e, "fg_get_fields");
+    return FG_OK;
+}
+
+fg_status fg_get_populations(fg_domain* d, int env, double* f) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    if (!f) return fail(FG_ERR_INVALID, "null output");
+    const size_t ncell = env_cells(d, env);
+    double* df = nullptr;
+    if ((st = dalloc(&df, 27ull * ncell)) != FG_OK) return st;
+    const int blocks = (int)((ncell + 255) / 256);
+    dispatch(d->opt.storage, [&](auto tag) -> fg_status {
+        typedef decltype(tag) S;
+        k_get_pop<S><<<blocks, 256, 0, d->stream>>>((const typename S::raw*)d->pop[d->cur], d->d_env, env, df);
+        return FG_OK;
+    });
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(f, df, sizeof(double) * 27 * ncell, cudaMemcpyDeviceToHost, d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    cudaFree(df);
+    if (e != cudaSuccess) return cuda_fail(e, "fg_get_populations");
+    return FG_OK;
+}
+
+fg_status fg_set_populations(fg_domain* d, int env, const double* f) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    if (!f) return fail(FG_ERR_INVALID, "null input");
+    const size_t ncell = env_cells(d, env);
+    double* df = nullptr;
+    if ((st = dalloc(&df, 27ull * ncell)) != FG_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(df, f, sizeof(double) * 27 * ncell, cudaMemcpyHostToDevice, d->stream);
+    const int blocks = (int)((ncell + 255) / 256);
+    if (e == cudaSuccess) {
+        dispatch(d->opt.storage, [&](auto tag) -> fg_status {
+            typedef decltype(tag) S;
+            k_set_pop<S><<<blocks, 256, 0, d->stream>>>((typename S::raw*)d->pop[d->cur], d->d_env, env, df);
+            return FG_OK;
+        });
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    cudaFree(df);
+    if (e != cudaSuccess) return cuda_fail(e, "fg_set_populations");
+    return FG_OK;
+}
+
+fg_status fg_state_bytes(fg_domain* d, int env, unsigned long long* bytes) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    if (!bytes) return fail(FG_ERR_INVALID, "null output");
+    *bytes = 27ull * d->env[env].nslot * d->esize;
+    return FG_OK;
+}
+
+fg_status fg_save_state(fg_domain* d, int env, void* host_buf) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    if (!host_buf) return fail(FG_ERR_INVALID, "null buffer");
+    const EnvDev& E = d->env[env];
+    const char* src = (const char*)d->pop[d->cur] + E.pop_off * d->esize;
+    CK(cudaMemcpyAsync(host_buf, src, 27ull * E.nslot * d->esize, cudaMemcpyDeviceToHost, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    return FG_OK;
+}
+
+fg_status fg_load_state(fg_domain* d, int env, const void* host_buf) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    if (!host_buf) return fail(FG_ERR_INVALID, "null buffer");
+    const EnvDev& E = d->env[env];
+    char* dst = (char*)d->pop[d->cur] + E.pop_off * d->esize;
+    CK(cudaMemcpyAsync(dst, host_buf, 27ull * E.nslot * d->esize, cudaMemcpyHostToDevice, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    return FG_OK;
+}
+
+fg_status fg_step_count(fg_domain* d, long long* steps) {
+    if (!d || !steps) return fail(FG_ERR_INVALID, "null argument");
+    *steps = d->steps;
+    return FG_OK;
+}
+
+fg_status fg_profile(fg_domain* d, int enable) {
+    if (!d) return fail(FG_ERR_INVALID, "null domain");
+    CK(cudaStreamSynchronize(d->stream));
+    if (enable && d->ev[0].empty()) {
+        for (int k = 0; k < FG_K_COUNT; ++k) {
+            d->ev[k].resize(PROFILE_CAP);
+            for (int i = 0; i < PROFILE_CAP; ++i) CK(cudaEventCreate(&d->ev[k][i]));
+        }
+    }
+    d->profiling = enable != 0;
+    for (int k = 0; k < FG_K_COUNT; ++k) {
+        d->ev_used[k] = 0;
+        d->prof_ms[k] = 0;
+        d->prof_n[k] = 0;
+    }
+    return FG_OK;
+}
+
+fg_status fg_profile_read(fg_domain* d, double* ms, long long* launches) {
+    if (!d || !ms || !launches) return fail(FG_ERR_INVALID, "null argument");
+    CK(cudaStreamSynchronize(d->stream));
+    for (int k = 0; k < FG_K_COUNT; ++k) {
+        for (int i = 0; i + 1 < d->ev_used[k]; i += 2) {
+            float t = 0;
+            CK(cudaEventElapsedTime(&t, d->ev[k][i], d->ev[k][i + 1]));
+            d->prof_ms[k] += t;
+            d->prof_n[k] += 1;
+        }
+        d->ev_used[k] = 0;
+        ms[k] = d->prof_ms[k];
+        launches[k] = d->prof_n[k];
+        d->prof_ms[k] = 0;
+        d->prof_n[k] = 0;
+    }
+    return FG_OK;
+}
+
+fg_status fg_stream_collide_bytes(fg_domain* d, unsigned long long* bytes) {
+    if (!d || !bytes) return fail(FG_ERR_INVALID, "null argument");
+    *bytes = 2ull * 27ull * d->total_cells * d->esize;
+    return FG_OK;
+}
+
+}  // extern "C"

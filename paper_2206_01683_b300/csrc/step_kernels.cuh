@@ -1,0 +1,725 @@
+// step_kernels.cuh -- the kernels of one time step (arXiv 2206.01683,
+// Sec. III-B) and the state-access kernels around them.
+//
+//   k_ib                     interpolate the post-stream velocity at every
+//                            marker (Peskin 4-point delta), form the
+//                            direct-forcing marker force and spread it back
+//                            onto the grid (one warp per marker)
+//   k_stream_collide_staged  pull-stream + moments + frame force (Eq. 3) +
+//                            regularized BGK/Guo collision + non-equilibrium
+//                            extrapolation, fused; persistent blocks stage the
+//                            27 source rows of each row group in shared memory
+//                            with bulk copies (TMA), double buffered
+//   k_stream_collide         the same update, one thread per cell with direct
+//                            global loads (any row length)
+//   k_reduce                 force/torque per body segment, mass, NaN watchdog
+//
+// Layout per environment: populations g[27][nslot] with g_i = f_i - w_i (the
+// deviation from the fluid at rest) in storage type S; slot = x + P (y + ny z)
+// with the row pitch P = nx rounded up to a multiple of 8, so every row starts
+// on a 32-byte (FP32) / 16-byte (FP16) boundary.  Slots x >= nx are padding
+// and never read.  Arithmetic is FP32; reductions end in FP64.
+#pragma once
+
+#include "async_copy.cuh"
+#include "lattice.cuh"
+
+namespace fl {
+
+constexpr int K1_THREADS = 256;  // threads of either stream-collide kernel
+constexpr int GROUP_CELLS = 256; // target cells (slots) per staged row group
+constexpr int IB_THREADS = 256;  // 8 markers per block
+constexpr int RED_THREADS = 1024;
+constexpr int MAX_SEG = 16;
+constexpr int FT_ROW = (MAX_SEG + 1) * 6;  // force/torque doubles per environment
+constexpr int HIST_ROW = FT_ROW + 1;       // + mass
+constexpr uint32_t WAIT_LIMIT = 1u << 22;  // mbarrier polls before giving up
+
+enum { BC_PERIODIC = 0, BC_VELOCITY = 1, BC_OUTFLOW = 2, BC_FREESLIP = 3 };
+enum { ST_NUMERIC = 1, ST_BAD_MARKER = 2, ST_TIMEOUT = 4 };
+
+// Static description of one environment on the device.
+struct EnvDev {
+    int n[3];                 // nx, ny, nz
+    int P;                    // row pitch (slots), multiple of 8
+    uint32_t nslot;           // P ny nz: stride between population planes
+    uint32_t rows;            // ny nz
+    FastDiv div_P, div_ny;
+    int bc[6];                // face kinds -x,+x,-y,+y,-z,+z
+    int per[3];               // axis periodic
+    float keep;               // 1 - 1/tau
+    float guo;                // 1 - 1/(2 tau)
+    float u_in[3];
+    float drho_out;           // outflow density - 1
+    unsigned long long pop_off;   // first element of this environment's g[27][nslot]
+    unsigned long long slot_off;  // first slot in per-slot arrays (IB force density)
+    int block0, nblocks;      // blocks of the plain stream-collide kernel
+    int group0, ngroups;      // row groups of the staged kernel
+    int rpg;                  // rows per group
+    int part0, nparts;        // mass partials written by the kernel in use
+    int stamp_off;            // first 32-slot tile stamp
+    int mk_begin;             // first marker in the compact marker numbering
+    int n_markers;
+    int marker_off;           // first marker slot in the marker arrays
+    int nseg;
+    double ref[3];            // torque reference point
+};
+
+// Frame motion of one environment (Eq. 3), refreshed by fg_step.
+struct FrameDev {
+    float acc[3], om[3], dom[3], org[3];
+    float inv_1pom2;          // 1 / (1 + |omega|^2)
+    float pad[3];
+};
+
+// Environment owning index v: the last e with key(e) <= v.
+template <int (EnvDev::*KEY)>
+__device__ __forceinline__ int env_of(const EnvDev* __restrict__ envs, int n_envs, int v) {
+    int lo = 0, hi = n_envs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (envs[mid].*KEY <= v) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Fictitious acceleration of Eq. 3 without the Coriolis term:
+// a0 = -acc - domega x r - omega x (omega x r), r = x - origin.
+__device__ __forceinline__ void frame_accel(const FrameDev& F, float x, float y, float z, float a[3]) {
+    const float rx = x - F.org[0], ry = y - F.org[1], rz = z - F.org[2];
+    const float t1x = F.dom[1] * rz - F.dom[2] * ry;
+    const float t1y = F.dom[2] * rx - F.dom[0] * rz;
+    const float t1z = F.dom[0] * ry - F.dom[1] * rx;
+    const float wx = F.om[1] * rz - F.om[2] * ry;
+    const float wy = F.om[2] * rx - F.om[0] * rz;
+    const float wz = F.om[0] * ry - F.om[1] * rx;
+    const float t3x = F.om[1] * wz - F.om[2] * wy;
+    const float t3y = F.om[2] * wx - F.om[0] * wz;
+    const float t3z = F.om[0] * wy - F.om[1] * wx;
+    a[0] = -F.acc[0] - t1x - t3x;
+    a[1] = -F.acc[1] - t1y - t3y;
+    a[2] = -F.acc[2] - t1z - t3z;
+}
+
+// Slot offsets that move a pull source p by -c along each axis, with
+// periodic wrap: *m for c = +1 (source p - 1), *p for c = -1 (source p + 1).
+// Along a non-periodic axis p is never on the outer layer, so no wrap occurs.
+struct PullOffsets {
+    int xm, xp, ym, yp, zm, zp;
+};
+
+__device__ __forceinline__ PullOffsets pull_offsets(const EnvDev& E, int px, int py, int pz) {
+    PullOffsets o;
+    const int nx = E.n[0], ny = E.n[1], nz = E.n[2], P = E.P, plane = E.P * E.n[1];
+    o.xm = (px == 0) ? nx - 1 : -1;
+    o.xp = (px == nx - 1) ? -(nx - 1) : 1;
+    o.ym = (py == 0) ? (ny - 1) * P : -P;
+    o.yp = (py == ny - 1) ? -(ny - 1) * P : P;
+    o.zm = (pz == 0) ? (nz - 1) * plane : -plane;
+    o.zp = (pz == nz - 1) ? -(nz - 1) * plane : plane;
+    return o;
+}
+
+__device__ __forceinline__ int pull_off(const PullOffsets& o, int i) {
+    const int a = cx(i) == 1 ? o.xm : (cx(i) == -1 ? o.xp : 0);
+    const int b = cy(i) == 1 ? o.ym : (cy(i) == -1 ? o.yp : 0);
+    const int c = cz(i) == 1 ? o.zm : (cz(i) == -1 ? o.zp : 0);
+    return a + b + c;
+}
+
+// Post-stream moments of the deviation g: dr = sum g, j = sum c g,
+// s_ab = sum c_a c_b g.  (rho = 1 + dr, Pi = s + cs2 I.)
+struct Moments {
+    float dr, jx, jy, jz, sxx, syy, szz, sxy, sxz, syz;
+};
+
+template <bool SECOND>
+__device__ __forceinline__ void accumulate(Moments& m, const float (&g)[Q]) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float v = g[i];
+        m.dr += v;
+        if (cx(i) == 1) m.jx += v; else if (cx(i) == -1) m.jx -= v;
+        if (cy(i) == 1) m.jy += v; else if (cy(i) == -1) m.jy -= v;
+        if (cz(i) == 1) m.jz += v; else if (cz(i) == -1) m.jz -= v;
+        if (SECOND) {
+            if (cx(i) != 0) m.sxx += v;
+            if (cy(i) != 0) m.syy += v;
+            if (cz(i) != 0) m.szz += v;
+            if (cx(i) * cy(i) == 1) m.sxy += v; else if (cx(i) * cy(i) == -1) m.sxy -= v;
+            if (cx(i) * cz(i) == 1) m.sxz += v; else if (cx(i) * cz(i) == -1) m.sxz -= v;
+            if (cy(i) * cz(i) == 1) m.syz += v; else if (cy(i) * cz(i) == -1) m.syz -= v;
+        }
+    }
+}
+
+// Moments at source slot p by direct (L2-cached) global loads.
+template <class S, bool SECOND>
+__device__ __forceinline__ Moments pull_moments(const typename S::raw* __restrict__ G, uint32_t nslot,
+                                                uint32_t p, const PullOffsets& o) {
+    Moments m = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        g[i] = S::load(G + (size_t)i * nslot + (uint32_t)((int)p + pull_off(o, i)), i);
+    accumulate<SECOND>(m, g);
+    return m;
+}
+
+// ------------------------------------------------ the per-cell update
+
+// Collision (interior) or open-face rule (boundary) from the pulled moments
+// m, then the Hermite-2 rebuild of all 27 outputs.  (sx, sy, sz) is the
+// inward normal of the non-periodic faces the cell lies on (0 for interior
+// cells).  Returns rho_out - 1 for the mass sum.
+template <class S>
+__device__ __forceinline__ float update_cell(const EnvDev& E, const FrameDev& F, const Moments& m, int x, int y,
+                                             int z, int sx, int sy, int sz, float fx, float fy, float fz,
+                                             typename S::raw* __restrict__ Go, uint32_t slot) {
+    const float cs2 = 1.0f / 3.0f;
+    const float rho = 1.0f + m.dr;
+    const float inv = 1.0f / rho;
+    float drout, Jx, Jy, Jz, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz;
+    if ((sx | sy | sz) == 0) {
+        float a0[3];
+        frame_accel(F, (float)x, (float)y, (float)z, a0);
+        // v = j/rho + a0/2 + fib/(2 rho);  u = (v - w x v + (w.v) w)/(1 + |w|^2)
+        const float vx = (m.jx + 0.5f * fx) * inv + 0.5f * a0[0];
+        const float vy = (m.jy + 0.5f * fy) * inv + 0.5f * a0[1];
+        const float vz = (m.jz + 0.5f * fz) * inv + 0.5f * a0[2];
+        const float wv = F.om[0] * vx + F.om[1] * vy + F.om[2] * vz;
+        const float ux = (vx - (F.om[1] * vz - F.om[2] * vy) + wv * F.om[0]) * F.inv_1pom2;
+        const float uy = (vy - (F.om[2] * vx - F.om[0] * vz) + wv * F.om[1]) * F.inv_1pom2;
+        const float uz = (vz - (F.om[0] * vy - F.om[1] * vx) + wv * F.om[2]) * F.inv_1pom2;
+        // G = rho a0 + fib - 2 rho w x u  (Eq. 3 with the IB force)
+        const float Gx = rho * a0[0] + fx - 2.0f * rho * (F.om[1] * uz - F.om[2] * uy);
+        const float Gy = rho * a0[1] + fy - 2.0f * rho * (F.om[2] * ux - F.om[0] * uz);
+        const float Gz = rho * a0[2] + fz - 2.0f * rho * (F.om[0] * uy - F.om[1] * ux);
+        Jx = m.jx + Gx; Jy = m.jy + Gy; Jz = m.jz + Gz;
+        // Q = Pi* - rho cs2 I = rho u u + (1 - 1/tau)(Pi - Pi_eq) + (1 - 1/(2tau))(u G + G u),
+        // with Pi - Pi_eq = s - dr cs2 I - rho u u
+        const float k = E.keep, gq = E.guo;
+        const float ruxx = rho * ux * ux, ruyy = rho * uy * uy, ruzz = rho * uz * uz;
+        const float ruxy = rho * ux * uy, ruxz = rho * ux * uz, ruyz = rho * uy * uz;
+        Qxx = ruxx + k * (m.sxx - m.dr * cs2 - ruxx) + gq * 2.0f * ux * Gx;
+        Qyy = ruyy + k * (m.syy - m.dr * cs2 - ruyy) + gq * 2.0f * uy * Gy;
+        Qzz = ruzz + k * (m.szz - m.dr * cs2 - ruzz) + gq * 2.0f * uz * Gz;
+        Qxy = ruxy + k * (m.sxy - ruxy) + gq * (ux * Gy + Gx * uy);
+        Qxz = ruxz + k * (m.sxz - ruxz) + gq * (ux * Gz + Gx * uz);
+        Qyz = ruyz + k * (m.syz - ruyz) + gq * (uy * Gz + Gy * uz);
+        drout = m.dr;
+    } else {
+        // non-equilibrium extrapolation (m are the moments of x_f = x + n):
+        // f* = f_eq(rho_b, u_b) + (1 - 1/tau) f_neq(x_f); x-faces govern on edges
+        const float ufx = m.jx * inv, ufy = m.jy * inv, ufz = m.jz * inv;
+        const int gov = sx != 0 ? 0 : (sy != 0 ? 1 : 2);
+        const int gs = gov == 0 ? sx : (gov == 1 ? sy : sz);
+        const int kind = E.bc[2 * gov + (gs < 0 ? 1 : 0)];
+        float ubx = ufx, uby = ufy, ubz = ufz;
+        drout = m.dr;
+        if (kind == BC_VELOCITY) {
+            ubx = E.u_in[0]; uby = E.u_in[1]; ubz = E.u_in[2];
+        } else if (kind == BC_OUTFLOW) {
+            drout = E.drho_out;
+        } else {
+            if (sx != 0 && E.bc[sx < 0 ? 1 : 0] == BC_FREESLIP) ubx = 0.f;
+            if (sy != 0 && E.bc[sy < 0 ? 3 : 2] == BC_FREESLIP) uby = 0.f;
+            if (sz != 0 && E.bc[sz < 0 ? 5 : 4] == BC_FREESLIP) ubz = 0.f;
+        }
+        const float rb = 1.0f + drout;
+        const float k = E.keep;
+        Jx = rb * ubx; Jy = rb * uby; Jz = rb * ubz;
+        Qxx = rb * ubx * ubx + k * (m.sxx - m.dr * cs2 - rho * ufx * ufx);
+        Qyy = rb * uby * uby + k * (m.syy - m.dr * cs2 - rho * ufy * ufy);
+        Qzz = rb * ubz * ubz + k * (m.szz - m.dr * cs2 - rho * ufz * ufz);
+        Qxy = rb * ubx * uby + k * (m.sxy - rho * ufx * ufy);
+        Qxz = rb * ubx * ubz + k * (m.sxz - rho * ufx * ufz);
+        Qyz = rb * uby * ubz + k * (m.syz - rho * ufy * ufz);
+    }
+    // Hermite-2 rebuild of the deviation: g*_i = w_i [dr + 3 c.J + 4.5 c c : Q - 1.5 tr Q]
+    const float A = drout - 1.5f * (Qxx + Qyy + Qzz);
+    const float dxx = 4.5f * Qxx, dyy = 4.5f * Qyy, dzz = 4.5f * Qzz;
+    const float oxy = 9.0f * Qxy, oxz = 9.0f * Qxz, oyz = 9.0f * Qyz;
+    const float tx = 3.0f * Jx, ty = 3.0f * Jy, tz = 3.0f * Jz;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        float even = A;
+        if (cx(i) != 0) even += dxx;
+        if (cy(i) != 0) even += dyy;
+        if (cz(i) != 0) even += dzz;
+        if (cx(i) * cy(i) == 1) even += oxy; else if (cx(i) * cy(i) == -1) even -= oxy;
+        if (cx(i) * cz(i) == 1) even += oxz; else if (cx(i) * cz(i) == -1) even -= oxz;
+        if (cy(i) * cz(i) == 1) even += oyz; else if (cy(i) * cz(i) == -1) even -= oyz;
+        float odd = 0.0f;
+        if (cx(i) == 1) odd += tx; else if (cx(i) == -1) odd -= tx;
+        if (cy(i) == 1) odd += ty; else if (cy(i) == -1) odd -= ty;
+        if (cz(i) == 1) odd += tz; else if (cz(i) == -1) odd -= tz;
+        S::store(Go + (size_t)i * E.nslot + slot, wf(i) * (even + odd), i);
+    }
+    return drout;
+}
+
+// Inward normal along one axis for coordinate v (0 on periodic axes).
+__device__ __forceinline__ int inward(const EnvDev& E, int axis, int v) {
+    if (E.per[axis]) return 0;
+    return v == 0 ? 1 : (v == E.n[axis] - 1 ? -1 : 0);
+}
+
+// IB force density at a slot if its 32-slot tile was stamped this step; the
+// stored value is cleared so the field is zero again for the next step.
+__device__ __forceinline__ void take_ib_force(const EnvDev& E, float* __restrict__ fib,
+                                              const uint32_t* __restrict__ stamps, uint32_t stamp,
+                                              uint32_t slot, float& fx, float& fy, float& fz) {
+    fx = fy = fz = 0.f;
+    if (__ldg(stamps + E.stamp_off + (slot >> 5)) == stamp) {
+        float* fb = fib + 3ull * E.slot_off;
+        fx = fb[slot]; fy = fb[E.nslot + slot]; fz = fb[2ull * E.nslot + slot];
+        fb[slot] = 0.f; fb[E.nslot + slot] = 0.f; fb[2ull * E.nslot + slot] = 0.f;
+    }
+}
+
+// ---------------------------------------------------------------- K2: IB
+
+// One warp per marker: lane (kx, ky, kz) with kx = lane & 3, ky = (lane>>2)&3,
+// kz = lane >> 4 owns stencil nodes (kx, ky, kz) and (kx, ky, kz + 2).
+template <class S>
+__global__ void __launch_bounds__(IB_THREADS, 4)
+k_ib(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs,
+     const FrameDev* __restrict__ frames, int n_envs, int total_markers,
+     const float* __restrict__ X, const float* __restrict__ U, const float* __restrict__ dV,
+     float* __restrict__ Fm, float* __restrict__ fib, uint32_t* __restrict__ stamps,
+     uint32_t stamp, int* __restrict__ status) {
+    const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= total_markers) return;  // whole warp
+    const int e = n_envs > 1 ? env_of<&EnvDev::mk_begin>(envs, n_envs, warp) : 0;
+    const EnvDev& E = envs[e];
+    const FrameDev F = frames[e];
+    const int slot = E.marker_off + (warp - E.mk_begin);
+
+    float xw[3];
+    int base[3];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float x = X[3 * slot + a];
+        const float N = (float)E.n[a];
+        float w = x;
+        if (!(fabsf(x) <= 1.0e6f)) ok = false;  // also rejects NaN
+        if (E.per[a]) {
+            w = x - floorf(x / N) * N;
+            if (w >= N) w -= N;
+            if (w < 0.0f) w += N;
+        } else if (!(x >= 2.0f && x < N - 3.0f)) {
+            ok = false;
+        }
+        xw[a] = w;
+        base[a] = ok ? (int)floorf(w) - 1 : 0;
+    }
+    if (!ok) {
+        if (lane == 0) {
+            Fm[3 * slot] = 0.f; Fm[3 * slot + 1] = 0.f; Fm[3 * slot + 2] = 0.f;
+            atomicOr(status, ST_BAD_MARKER);
+        }
+        return;
+    }
+    const int kx = lane & 3, ky = (lane >> 2) & 3, kz = lane >> 4;
+    const int mx = base[0] + kx, my = base[1] + ky;
+    const float wxy = peskin4(xw[0] - (float)mx) * peskin4(xw[1] - (float)my);
+    const int nx = E.n[0], ny = E.n[1], nz = E.n[2];
+    // node indices lie in [-1, n+2]; a true modulo also covers periodic axes
+    // shorter than the stencil (n < 4)
+    const int mxw = ((mx % nx) + nx) % nx;
+    const int myw = ((my % ny) + ny) % ny;
+    const typename S::raw* G = gin + E.pop_off;
+
+    float R = 0.f, Ux = 0.f, Uy = 0.f, Uz = 0.f;
+    float dlt[2];
+    uint32_t cell[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int mz = base[2] + kz + 2 * h;
+        const int mzw = ((mz % nz) + nz) % nz;
+        const float d = wxy * peskin4(xw[2] - (float)mz);
+        const uint32_t c = (uint32_t)mxw + (uint32_t)E.P * ((uint32_t)myw + (uint32_t)ny * (uint32_t)mzw);
+        const PullOffsets o = pull_offsets(E, mxw, myw, mzw);
+        const Moments m = pull_moments<S, false>(G, E.nslot, c, o);
+        const float rho = 1.0f + m.dr;
+        const float inv = 1.0f / rho;
+        float a0[3];
+        frame_accel(F, (float)mxw, (float)myw, (float)mzw, a0);
+        R += d * rho;
+        Ux += d * (m.jx * inv + 0.5f * a0[0]);
+        Uy += d * (m.jy * inv + 0.5f * a0[1]);
+        Uz += d * (m.jz * inv + 0.5f * a0[2]);
+        dlt[h] = d;
+        cell[h] = c;
+    }
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        R += __shfl_xor_sync(0xffffffffu, R, s);
+        Ux += __shfl_xor_sync(0xffffffffu, Ux, s);
+        Uy += __shfl_xor_sync(0xffffffffu, Uy, s);
+        Uz += __shfl_xor_sync(0xffffffffu, Uz, s);
+    }
+    // direct forcing: F_l = 2 R_l (U_l - U~_l); the grid receives F_l dV_l delta
+    const float Fx = 2.0f * R * (U[3 * slot] - Ux);
+    const float Fy = 2.0f * R * (U[3 * slot + 1] - Uy);
+    const float Fz = 2.0f * R * (U[3 * slot + 2] - Uz);
+    const float v = dV[slot];
+    float* fb = fib + 3ull * E.slot_off;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float s = v * dlt[h];
+        atomicAdd(fb + cell[h], Fx * s);
+        atomicAdd(fb + E.nslot + cell[h], Fy * s);
+        atomicAdd(fb + 2ull * E.nslot + cell[h], Fz * s);
+        stamps[E.stamp_off + (cell[h] >> 5)] = stamp;
+    }
+    if (lane == 0) {
+        Fm[3 * slot] = Fx; Fm[3 * slot + 1] = Fy; Fm[3 * slot + 2] = Fz;
+    }
+}
+
+// ------------------------------------------------- K1: stream + collide
+
+__device__ __forceinline__ float block_sum_f32(float v, float* wsum) {
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) v += __shfl_xor_sync(0xffffffffu, v, k);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = 0.f;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < K1_THREADS / 32; ++w) t += wsum[w];
+    return t;  // valid in thread 0
+}
+
+// Plain variant: one thread per slot, direct loads.
+template <class S>
+__global__ void __launch_bounds__(K1_THREADS)
+k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __restrict__ gout,
+                 const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, int n_envs,
+                 float* __restrict__ fib, const uint32_t* __restrict__ stamps, uint32_t stamp,
+                 float* __restrict__ mass_part) {
+    __shared__ float wsum[K1_THREADS / 32];
+    const int b = blockIdx.x;
+    const int e = n_envs > 1 ? env_of<&EnvDev::block0>(envs, n_envs, b) : 0;
+    const EnvDev& E = envs[e];
+    const uint32_t c = (uint32_t)(b - E.block0) * K1_THREADS + threadIdx.x;
+    float drout = 0.0f;
+    if (c < E.nslot) {
+        const uint32_t row = fdiv(c, E.div_P);
+        const int x = (int)(c - row * (uint32_t)E.P);
+        if (x < E.n[0]) {
+            const uint32_t zz = fdiv(row, E.div_ny);
+            const int y = (int)(row - zz * (uint32_t)E.n[1]);
+            const int z = (int)zz;
+            float fx, fy, fz;
+            take_ib_force(E, fib, stamps, stamp, c, fx, fy, fz);
+            const int sx = inward(E, 0, x), sy = inward(E, 1, y), sz = inward(E, 2, z);
+            // a boundary cell takes its moments from the inward neighbour x_f
+            const int px = x + sx, py = y + sy, pz = z + sz;
+            const uint32_t p = (uint32_t)((int)c + sx + (sy + sz * E.n[1]) * E.P);
+            const PullOffsets o = pull_offsets(E, px, py, pz);
+            const Moments m = pull_moments<S, true>(gin + E.pop_off, E.nslot, p, o);
+            drout = update_cell<S>(E, frames[e], m, x, y, z, sx, sy, sz, fx, fy, fz, gout + E.pop_off, c);
+        }
+    }
+    const float t = block_sum_f32(drout, wsum);
+    if (threadIdx.x == 0) mass_part[b] = t;
+}
+
+// Staged variant: persistent blocks walk row groups g = blockIdx.x,
+// blockIdx.x + gridDim.x, ...  For each group, warp 0 issues one bulk copy per
+// (population, row) of the source row it pulls from -- row (y + sy - cy,
+// z + sz - cz), whole rows of P slots -- into shared memory, completing on an
+// mbarrier.  The next group's copies are in flight while the current group
+// is computed from shared memory (two buffers).  Outputs go straight to
+// global memory with coalesced stores.
+template <class S>
+__device__ __forceinline__ void issue_group(const EnvDev& E, int g_local, const typename S::raw* __restrict__ gin,
+                                            typename S::raw* buf, uint64_t* bar) {
+    typedef typename S::raw raw;
+    const int lane = threadIdx.x & 31;
+    const int r0 = g_local * E.rpg;
+    const int R = min(E.rpg, (int)E.rows - r0);
+    const uint32_t row_bytes = (uint32_t)E.P * (uint32_t)sizeof(raw);
+    if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(Q * R) * row_bytes);
+    __syncwarp();
+    const int ny = E.n[1], nz = E.n[2];
+    const raw* G = gin + E.pop_off;
+    for (int k = lane; k < Q * R; k += 32) {
+        const int i = k % Q, r = k / Q;
+        const int row = r0 + r;
+        const int z = row / ny, y = row - z * ny;
+        int ys = y + inward(E, 1, y) - cy(i);
+        int zs = z + inward(E, 2, z) - cz(i);
+        ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);   // only periodic axes wrap
+        zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
+        const raw* src = G + (size_t)i * E.nslot + (size_t)(ys + ny * zs) * E.P;
+        raw* dst = buf + ((size_t)i * E.rpg + r) * E.P;
+        bulk_g2s(dst, src, row_bytes, bar);
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(K1_THREADS, 4)
+k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw* __restrict__ gout,
+                        const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, int n_envs,
+                        int total_groups, uint32_t buf_elems, float* __restrict__ fib,
+                        const uint32_t* __restrict__ stamps, uint32_t stamp, float* __restrict__ mass_part,
+                        int* __restrict__ status) {
+    typedef typename S::raw raw;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    raw* bufs = reinterpret_cast<raw*>(smem_raw);
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float wsum[2][K1_THREADS / 32];
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    int g = blockIdx.x;
+    if (g < total_groups && warp == 0) {
+        const int e = n_envs > 1 ? env_of<&EnvDev::group0>(envs, n_envs, g) : 0;
+        issue_group<S>(envs[e], g - envs[e].group0, gin, bufs, &bar[0]);
+    }
+    for (int k = 0; g < total_groups; g += gridDim.x, ++k) {
+        const int b = k & 1;
+        const int gn = g + gridDim.x;
+        if (gn < total_groups && warp == 0) {
+            const int en = n_envs > 1 ? env_of<&EnvDev::group0>(envs, n_envs, gn) : 0;
+            issue_group<S>(envs[en], gn - envs[en].group0, gin, bufs + (size_t)(b ^ 1) * buf_elems, &bar[b ^ 1]);
+        }
+        const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)(k >> 1) & 1u, WAIT_LIMIT);
+        if (__syncthreads_or(!ok)) {
+            // a copy never completed: report, let the copies in flight land, stop
+            if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+            mbar_wait_bounded(&bar[b], (uint32_t)(k >> 1) & 1u, WAIT_LIMIT);
+            if (gn < total_groups) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)((k + 1) >> 1) & 1u, WAIT_LIMIT);
+            return;
+        }
+        const int e = n_envs > 1 ? env_of<&EnvDev::group0>(envs, n_envs, g) : 0;
+        const EnvDev& E = envs[e];
+        const FrameDev F = frames[e];
+        const raw* sb = bufs + (size_t)b * buf_elems;
+        const int r0 = (g - E.group0) * E.rpg;
+        const int R = min(E.rpg, (int)E.rows - r0);
+        const int nx = E.n[0], ny = E.n[1];
+        const int span = R * E.P;
+        float drsum = 0.f;
+        for (int t = threadIdx.x; t < span; t += K1_THREADS) {
+            const int r = (int)fdiv((uint32_t)t, E.div_P);
+            const int x = t - r * E.P;
+            if (x >= nx) continue;
+            const int row = r0 + r;
+            const int z = (int)fdiv((uint32_t)row, E.div_ny);
+            const int y = row - z * ny;
+            const uint32_t slot = (uint32_t)row * (uint32_t)E.P + (uint32_t)x;
+            float fx, fy, fz;
+            take_ib_force(E, fib, stamps, stamp, slot, fx, fy, fz);
+            const int sx = inward(E, 0, x), sy = inward(E, 1, y), sz = inward(E, 2, z);
+            const int xs = x + sx;
+            const int xm = xs == 0 ? nx - 1 : xs - 1;      // source of c_x = +1
+            const int xp = xs == nx - 1 ? 0 : xs + 1;      // source of c_x = -1
+            float gv[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int xi = cx(i) == 1 ? xm : (cx(i) == -1 ? xp : xs);
+                gv[i] = S::decode(sb[((size_t)i * E.rpg + r) * E.P + xi], i);
+            }
+            Moments m = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            accumulate<true>(m, gv);
+            drsum += update_cell<S>(E, F, m, x, y, z, sx, sy, sz, fx, fy, fz, gout + E.pop_off, slot);
+        }
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) drsum += __shfl_xor_sync(0xffffffffu, drsum, s);
+        if ((threadIdx.x & 31) == 0) wsum[b][warp] = drsum;
+        __syncthreads();   // buffer b is free again; wsum[b] is complete
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+#pragma unroll
+            for (int w = 0; w < K1_THREADS / 32; ++w) t += wsum[b][w];
+            mass_part[g] = t;
+        }
+    }
+}
+
+// ------------------------------------------------------- K4: reduction
+
+// Sum over the block in FP64: a shuffle tree inside each warp, then warp 0
+// combines the warp totals with a second tree (no serial loop: FP64 latency
+// on B300 is long).  Fixed order, so the result is deterministic; valid in
+// thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) v += __shfl_xor_sync(0xffffffffu, v, k);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+        for (int k = 16; k >= 1; k >>= 1) t += __shfl_xor_sync(0xffffffffu, t, k);
+    }
+    return t;
+}
+
+// Compensated FP32 accumulation (Kahan): per-thread partial sums keep close
+// to FP64 accuracy while running on the FP32 pipes; B300's FP64 rate per SM
+// is too low to spend on every term.
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Grid (n_envs, MAX_SEG + 2).  Block (e, y): y < nseg sums segment y, y ==
+// nseg all markers (the total row), y == MAX_SEG + 1 the mass.  Force on the
+// body F = -sum F_l dV_l, torque T = -sum (X_l - ref) x F_l dV_l; mass =
+// ncell + sum (rho - 1).  Fixed summation order: the result is deterministic.
+__global__ void __launch_bounds__(RED_THREADS)
+k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const float* __restrict__ Fm,
+         const float* __restrict__ dV, const int* __restrict__ seg,
+         const float* __restrict__ mass_part, double* __restrict__ ft, double* __restrict__ mass,
+         double* __restrict__ hist, int hist_cap, long long hist_row, int* __restrict__ status) {
+    __shared__ double sh[RED_THREADS / 32];
+    const int e = blockIdx.x, y = blockIdx.y;
+    const EnvDev& E = envs[e];
+    const int ns = E.nseg;
+    double* hrow = hist_cap > 0 ? hist + ((size_t)e * hist_cap + (size_t)(hist_row % hist_cap)) * HIST_ROW
+                                : nullptr;
+    if (y == MAX_SEG + 1) {
+        Kahan km;
+        for (int i = threadIdx.x; i < E.nparts; i += blockDim.x) km.add(mass_part[E.part0 + i]);
+        const double m = block_sum(km.value(), sh);
+        if (threadIdx.x == 0) {
+            const double M = (double)E.n[0] * E.n[1] * E.n[2] + m;
+            mass[e] = M;
+            if (!isfinite(M)) atomicOr(status, ST_NUMERIC);
+            if (hrow) hrow[FT_ROW] = M;
+        }
+        return;
+    }
+    if (y > ns) return;
+    const float rfx = (float)E.ref[0], rfy = (float)E.ref[1], rfz = (float)E.ref[2];
+    Kahan acc[6];
+#pragma unroll 2
+    for (int l = threadIdx.x; l < E.n_markers; l += blockDim.x) {
+        const int q = E.marker_off + l;
+        const int sg = seg[q];
+        const float dv = dV[q];
+        const float f0 = Fm[3 * q], f1 = Fm[3 * q + 1], f2 = Fm[3 * q + 2];
+        const float rx = X[3 * q] - rfx, ry = X[3 * q + 1] - rfy, rz = X[3 * q + 2] - rfz;
+        const float v = (y == ns || sg == y) ? -dv : 0.0f;
+        const float Fx = f0 * v, Fy = f1 * v, Fz = f2 * v;
+        acc[0].add(Fx); acc[1].add(Fy); acc[2].add(Fz);
+        acc[3].add(ry * Fz - rz * Fy);
+        acc[4].add(rz * Fx - rx * Fz);
+        acc[5].add(rx * Fy - ry * Fx);
+    }
+    double* out = ft + (size_t)e * FT_ROW + 6 * y;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double t = block_sum(acc[k].value(), sh);
+        if (threadIdx.x == 0) {
+            out[k] = t;
+            if (hrow) hrow[6 * y + k] = t;
+            if (!isfinite(t)) bad = true;
+        }
+    }
+    if (bad) atomicOr(status, ST_NUMERIC);
+}
+
+// ----------------------------------------------------- state access
+// These run over cells c = x + nx (y + ny z) (the ABI's cell order).
+
+__device__ __forceinline__ uint32_t cell_to_slot(const EnvDev& E, uint32_t c) {
+    const uint32_t nx = (uint32_t)E.n[0];
+    const uint32_t row = c / nx;
+    return row * (uint32_t)E.P + (c - row * nx);
+}
+
+// f_eq(rho, u) - w on the Hermite-2 basis, computed in FP64.
+template <class S>
+__global__ void k_init_eq(typename S::raw* __restrict__ g, const EnvDev* __restrict__ envs, int e,
+                          const double* __restrict__ rho, const double* __restrict__ u,
+                          double rho0, double u0x, double u0y, double u0z) {
+    const EnvDev& E = envs[e];
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t ncell = (uint32_t)E.n[0] * E.n[1] * E.n[2];
+    if (c >= ncell) return;
+    const double r = rho ? rho[c] : rho0;
+    const double ux = u ? u[3 * (size_t)c] : u0x, uy = u ? u[3 * (size_t)c + 1] : u0y,
+                 uz = u ? u[3 * (size_t)c + 2] : u0z;
+    const double uu = ux * ux + uy * uy + uz * uz;
+    typename S::raw* G = g + E.pop_off;
+    const uint32_t s = cell_to_slot(E, c);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+        const double f = wd(i) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+        G[(size_t)i * E.nslot + s] = S::encode((float)(f - wd(i)), i);
+    }
+}
+
+// out[c][27] = w_i + g_i (FP64), library velocity order.
+template <class S>
+__global__ void k_get_pop(const typename S::raw* __restrict__ g, const EnvDev* __restrict__ envs, int e,
+                          double* __restrict__ out) {
+    const EnvDev& E = envs[e];
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= (uint32_t)E.n[0] * E.n[1] * E.n[2]) return;
+    const typename S::raw* G = g + E.pop_off;
+    const uint32_t s = cell_to_slot(E, c);
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        out[(size_t)c * Q + i] = wd(i) + (double)S::decode(G[(size_t)i * E.nslot + s], i);
+}
+
+template <class S>
+__global__ void k_set_pop(typename S::raw* __restrict__ g, const EnvDev* __restrict__ envs, int e,
+                          const double* __restrict__ in) {
+    const EnvDev& E = envs[e];
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= (uint32_t)E.n[0] * E.n[1] * E.n[2]) return;
+    typename S::raw* G = g + E.pop_off;
+    const uint32_t s = cell_to_slot(E, c);
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        G[(size_t)i * E.nslot + s] = S::encode((float)(in[(size_t)c * Q + i] - wd(i)), i);
+}
+
+// rho = 1 + sum g, u = sum c g / rho, in FP64 from the stored values.
+template <class S>
+__global__ void k_get_fields(const typename S::raw* __restrict__ g, const EnvDev* __restrict__ envs, int e,
+                             double* __restrict__ rho, double* __restrict__ u) {
+    const EnvDev& E = envs[e];
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= (uint32_t)E.n[0] * E.n[1] * E.n[2]) return;
+    const typename S::raw* G = g + E.pop_off;
+    const uint32_t s = cell_to_slot(E, c);
+    double dr = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const double v = (double)S::decode(G[(size_t)i * E.nslot + s], i);
+        dr += v;
+        jx += cx(i) * v; jy += cy(i) * v; jz += cz(i) * v;
+    }
+    const double r = 1.0 + dr;
+    rho[c] = r;
+    u[3 * (size_t)c] = jx / r; u[3 * (size_t)c + 1] = jy / r; u[3 * (size_t)c + 2] = jz / r;
+}
+
+}  // namespace fl

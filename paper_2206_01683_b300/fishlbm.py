@@ -1,0 +1,320 @@
+"""Thin Python binding of the C ABI in include/fishlbm.h (ctypes).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``libfishlbm.so`` next to this file.  If that library is missing or cannot be
+loaded the import of the binding fails loudly; there is no fallback path.
+
+The ``fg_*`` functions mirror the C names one to one.  ``Domain`` is a small
+convenience wrapper over them that accepts numpy arrays (host) or torch CUDA
+tensors (device pointers) for marker data.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfishlbm.so")
+
+FG_OK, FG_ERR_INVALID, FG_ERR_CUDA, FG_ERR_OOM = 0, -1, -2, -3
+FG_ERR_TIMEOUT, FG_ERR_NUMERIC, FG_ERR_STATE = -4, -5, -6
+FG_F32, FG_F16, FG_BF16 = 0, 1, 2
+FG_PERIODIC, FG_VELOCITY, FG_OUTFLOW, FG_FREESLIP = 0, 1, 2, 3
+FG_K_IB, FG_K_STREAM_COLLIDE, FG_K_REDUCE, FG_K_COUNT = 0, 1, 2, 3
+FG_KERNEL_AUTO, FG_KERNEL_PLAIN, FG_KERNEL_STAGED = 0, 1, 2
+VARIANT = {"auto": FG_KERNEL_AUTO, "plain": FG_KERNEL_PLAIN, "staged": FG_KERNEL_STAGED}
+STORAGE = {"f32": FG_F32, "f16": FG_F16, "bf16": FG_BF16}
+
+
+class FgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("fishlbm status %d: %s" % (status, msg))
+        self.status = status
+
+
+class fg_env_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("tau", ctypes.c_double), ("face", ctypes.c_int * 6),
+                ("u_in", ctypes.c_double * 3), ("rho0", ctypes.c_double),
+                ("u0", ctypes.c_double * 3)]
+
+
+class fg_options(ctypes.Structure):
+    _fields_ = [("storage", ctypes.c_int), ("layout", ctypes.c_int),
+                ("deterministic", ctypes.c_int), ("ib_iters", ctypes.c_int),
+                ("record_history", ctypes.c_int), ("kernel_variant", ctypes.c_int)]
+
+
+class fg_frame(ctypes.Structure):
+    _fields_ = [("acc", ctypes.c_double * 3), ("omega", ctypes.c_double * 3),
+                ("domega", ctypes.c_double * 3), ("origin", ctypes.c_double * 3)]
+
+
+# name -> (restype, argtypes); the exported symbols of include/fishlbm.h
+_V, _I, _D, _LL, _ULL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_ulonglong
+_P = ctypes.POINTER
+SIGNATURES = {
+    "fg_create_domain": (_I, [_P(fg_env_desc), _I, _P(fg_options), _V, _P(_V)]),
+    "fg_set_markers": (_I, [_V, _I, _I, _V, _V, _V, _V, _I, _P(_D), _I]),
+    "fg_step": (_I, [_V, _I, _P(fg_frame)]),
+    "fg_get_body_force_torque": (_I, [_V, _I, _P(_D)]),
+    "fg_destroy": (None, [_V]),
+    "fg_last_error": (ctypes.c_char_p, []),
+    "fg_lattice": (_I, [_P(_I), _P(_D)]),
+    "fg_init_fields": (_I, [_V, _I, _P(_D), _P(_D)]),
+    "fg_get_fields": (_I, [_V, _I, _P(_D), _P(_D)]),
+    "fg_get_populations": (_I, [_V, _I, _P(_D)]),
+    "fg_set_populations": (_I, [_V, _I, _P(_D)]),
+    "fg_get_marker_force": (_I, [_V, _I, _P(ctypes.c_float)]),
+    "fg_get_mass": (_I, [_V, _I, _P(_D)]),
+    "fg_get_history": (_I, [_V, _I, _P(_D), _I, _P(_I)]),
+    "fg_state_bytes": (_I, [_V, _I, _P(_ULL)]),
+    "fg_save_state": (_I, [_V, _I, _V]),
+    "fg_load_state": (_I, [_V, _I, _V]),
+    "fg_get_status": (_I, [_V, _P(_I)]),
+    "fg_step_count": (_I, [_V, _P(_LL)]),
+    "fg_profile": (_I, [_V, _I]),
+    "fg_profile_read": (_I, [_V, _P(_D), _P(_LL)]),
+    "fg_stream_collide_bytes": (_I, [_V, _P(_ULL)]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libfishlbm.so (raises if it is absent: build it with build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libfishlbm.so is not built (run paper_2206_01683_b300/build.py); "
+                              "there is no fallback implementation")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != FG_OK:
+        raise FgError(status, lib().fg_last_error().decode())
+
+
+def _dp(a):
+    return a.ctypes.data_as(_P(_D))
+
+
+# ----------------------------------------------------- C-named functions
+
+def fg_create_domain(envs, opt=None, stream=None):
+    arr = (fg_env_desc * len(envs))(*envs)
+    out = _V()
+    _check(lib().fg_create_domain(arr, len(envs), ctypes.byref(opt) if opt is not None else None,
+                                  _V(stream or 0), ctypes.byref(out)))
+    return out
+
+
+def fg_set_markers(d, env, n, X, U, dV, seg, n_seg, ref, device_ptrs):
+    refa = (_D * 3)(*ref) if ref is not None else None
+    _check(lib().fg_set_markers(d, env, n, X, U, dV, seg, n_seg, refa, device_ptrs))
+
+
+def fg_step(d, n_steps=1, frames=None):
+    fr = None
+    if frames is not None:
+        fr = (fg_frame * len(frames))(*frames)
+    _check(lib().fg_step(d, n_steps, fr))
+
+
+def fg_get_body_force_torque(d, env, n_seg):
+    out = np.zeros((n_seg + 1, 6))
+    _check(lib().fg_get_body_force_torque(d, env, _dp(out)))
+    return out
+
+
+def fg_destroy(d):
+    if d:
+        lib().fg_destroy(d)
+
+
+def fg_lattice():
+    c = np.zeros((27, 3), dtype=np.int32)
+    w = np.zeros(27)
+    _check(lib().fg_lattice(c.ctypes.data_as(_P(_I)), _dp(w)))
+    return c, w
+
+
+def make_frame(acc=(0.0, 0.0, 0.0), omega=(0.0, 0.0, 0.0), domega=(0.0, 0.0, 0.0),
+               origin=(0.0, 0.0, 0.0)):
+    f = fg_frame()
+    for a in range(3):
+        f.acc[a], f.omega[a], f.domega[a], f.origin[a] = acc[a], omega[a], domega[a], origin[a]
+    return f
+
+
+def frame_from_array(v):
+    """fg_frame from the 12 numbers (p'', omega, domega, origin)."""
+    v = [float(x) for x in v]
+    return make_frame(v[0:3], v[3:6], v[6:9], v[9:12])
+
+
+def env_desc(shape, tau, faces=(FG_PERIODIC,) * 6, u_in=(0.0, 0.0, 0.0), rho0=1.0,
+             u0=(0.0, 0.0, 0.0)):
+    e = fg_env_desc()
+    e.nx, e.ny, e.nz = shape
+    e.tau = tau
+    for k in range(6):
+        e.face[k] = faces[k]
+    for a in range(3):
+        e.u_in[a] = u_in[a]
+        e.u0[a] = u0[a]
+    e.rho0 = rho0
+    return e
+
+
+def _ptr_and_keep(a, dtype):
+    """(pointer, is_device, keepalive) for a numpy array or a torch tensor
+    (a CUDA tensor is passed as a device pointer, a CPU tensor, e.g. pinned,
+    as a host pointer; tensors must be contiguous and of the right dtype)."""
+    if a is None:
+        return None, None, None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous() or a.element_size() != np.dtype(dtype).itemsize:
+            raise ValueError("marker tensors must be contiguous float32 / int32")
+        return _V(a.data_ptr()), bool(a.is_cuda), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(_V), False, arr
+
+
+class Domain:
+    """Owns one fg_domain (one or many environments)."""
+
+    def __init__(self, envs, storage="f32", record_history=0, stream=None, variant="auto"):
+        self.envs = list(envs)
+        opt = fg_options()
+        opt.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        opt.layout = 0
+        opt.deterministic = 0
+        opt.ib_iters = 1
+        opt.record_history = int(record_history)
+        opt.kernel_variant = VARIANT[variant] if isinstance(variant, str) else int(variant)
+        self.storage = opt.storage
+        self.h = fg_create_domain(self.envs, opt, stream)
+        self.nseg = [1] * len(self.envs)
+        self.nmark = [0] * len(self.envs)
+
+    def close(self):
+        if getattr(self, "h", None):
+            fg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def ncell(self, env=0):
+        e = self.envs[env]
+        return e.nx * e.ny * e.nz
+
+    def set_markers(self, X, U, dV=None, seg=None, n_seg=1, ref=None, env=0):
+        n = int(X.shape[0])
+        pX, devX, kX = _ptr_and_keep(X, np.float32)
+        pU, devU, kU = _ptr_and_keep(U, np.float32)
+        pd, devd, kd = _ptr_and_keep(dV, np.float32)
+        ps, devs, ks = _ptr_and_keep(seg, np.int32)
+        dev = bool(devX)
+        for flag in (devU, devd, devs):
+            if flag is not None and flag != dev:
+                raise ValueError("marker arrays must all be host or all be device")
+        fg_set_markers(self.h, env, n, pX, pU, pd, ps, int(n_seg), ref, 1 if dev else 0)
+        self._keep = (kX, kU, kd, ks)
+        self.nseg[env] = int(n_seg)
+        self.nmark[env] = n
+
+    def step(self, n=1, frames=None):
+        if frames is not None and not isinstance(frames, (list, tuple)):
+            frames = [frames]
+        if frames is not None:
+            frames = [f if isinstance(f, fg_frame) else frame_from_array(f) for f in frames]
+        fg_step(self.h, n, frames)
+
+    def get_body_force_torque(self, env=0):
+        return fg_get_body_force_torque(self.h, env, self.nseg[env])
+
+    def init_fields(self, rho=None, u=None, env=0):
+        r = np.ascontiguousarray(rho, dtype=np.float64) if rho is not None else None
+        v = np.ascontiguousarray(u, dtype=np.float64) if u is not None else None
+        _check(lib().fg_init_fields(self.h, env, _dp(r) if r is not None else None,
+                                    _dp(v) if v is not None else None))
+
+    def fields(self, env=0):
+        n = self.ncell(env)
+        rho = np.zeros(n)
+        u = np.zeros((n, 3))
+        _check(lib().fg_get_fields(self.h, env, _dp(rho), _dp(u)))
+        return rho, u
+
+    def populations(self, env=0):
+        f = np.zeros((self.ncell(env), 27))
+        _check(lib().fg_get_populations(self.h, env, _dp(f)))
+        return f
+
+    def set_populations(self, f, env=0):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(self.ncell(env), 27)
+        _check(lib().fg_set_populations(self.h, env, _dp(f)))
+
+    def marker_force(self, env=0):
+        F = np.zeros((max(self.nmark[env], 1), 3), dtype=np.float32)
+        _check(lib().fg_get_marker_force(self.h, env, F.ctypes.data_as(_P(ctypes.c_float))))
+        return F[: self.nmark[env]]
+
+    def mass(self, env=0):
+        m = _D()
+        _check(lib().fg_get_mass(self.h, env, ctypes.byref(m)))
+        return m.value
+
+    def history(self, max_steps, env=0):
+        w = 6 * (self.nseg[env] + 1) + 1
+        out = np.zeros((max_steps, w))
+        n = _I()
+        _check(lib().fg_get_history(self.h, env, _dp(out), max_steps, ctypes.byref(n)))
+        return out[: n.value]
+
+    def state_bytes(self, env=0):
+        b = _ULL()
+        _check(lib().fg_state_bytes(self.h, env, ctypes.byref(b)))
+        return b.value
+
+    def save_state(self, env=0):
+        buf = np.zeros(self.state_bytes(env), dtype=np.uint8)
+        _check(lib().fg_save_state(self.h, env, buf.ctypes.data_as(_V)))
+        return buf
+
+    def load_state(self, buf, env=0):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(lib().fg_load_state(self.h, env, buf.ctypes.data_as(_V)))
+
+    def status(self):
+        s = _I()
+        _check(lib().fg_get_status(self.h, ctypes.byref(s)))
+        return s.value
+
+    def step_count(self):
+        s = _LL()
+        _check(lib().fg_step_count(self.h, ctypes.byref(s)))
+        return s.value
+
+    def profile(self, enable=True):
+        _check(lib().fg_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        ms = np.zeros(FG_K_COUNT)
+        n = np.zeros(FG_K_COUNT, dtype=np.int64)
+        _check(lib().fg_profile_read(self.h, _dp(ms), n.ctypes.data_as(_P(_LL))))
+        return ms, n
+
+    def stream_collide_bytes(self):
+        b = _ULL()
+        _check(lib().fg_stream_collide_bytes(self.h, ctypes.byref(b)))
+        return b.value

@@ -1,0 +1,65 @@
+"""The C-ABI library loads without a GPU and exports exactly what
+include/fishlbm.h declares; the Python binding covers every symbol.  No
+compute call is made here."""
+import ctypes
+import os
+import re
+
+from paper_2206_01683_b300 import build, fishlbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "fishlbm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return set(re.findall(r"\b(fg_[a-z_0-9]+)\s*\(", text))
+
+
+def test_header_declares_the_five_calls():
+    syms = declared_symbols()
+    for name in ("fg_create_domain", "fg_set_markers", "fg_step", "fg_get_body_force_torque",
+                 "fg_destroy"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol():
+    build.build()
+    L = ctypes.CDLL(fishlbm.LIB_PATH)
+    missing = [s for s in sorted(declared_symbols()) if not hasattr(L, s)]
+    assert not missing, missing
+
+
+def test_binding_signatures_match_header():
+    assert set(fishlbm.SIGNATURES) == declared_symbols()
+    fishlbm.lib()  # sets restype/argtypes for every symbol
+
+
+def test_struct_layouts():
+    assert ctypes.sizeof(fishlbm.fg_env_desc) == 4 * 3 + 4 + 8 + 4 * 6 + 8 * 3 + 8 + 8 * 3
+    assert ctypes.sizeof(fishlbm.fg_frame) == 12 * 8
+    assert ctypes.sizeof(fishlbm.fg_options) == 6 * 4
+
+
+def test_lattice_is_d3q27():
+    c, w = fishlbm.fg_lattice()       # host-only call
+    assert len({tuple(v) for v in c}) == 27
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert (c[26 - __import__("numpy").arange(27)] == -c).all()   # opposite of i is 26 - i
+
+
+def test_invalid_arguments_fail_without_gpu_work():
+    bad = fishlbm.env_desc((8, 8, 8), 0.5)      # tau must exceed 1/2
+    try:
+        fishlbm.fg_create_domain([bad])
+    except fishlbm.FgError as e:
+        assert e.status == fishlbm.FG_ERR_INVALID
+    else:
+        raise AssertionError("tau = 0.5 accepted")
+    bad = fishlbm.env_desc((8, 8, 2), 0.6, faces=(0, 0, 0, 0, 1, 2))   # open axis of 2 cells
+    try:
+        fishlbm.fg_create_domain([bad])
+    except fishlbm.FgError as e:
+        assert e.status == fishlbm.FG_ERR_INVALID
+    else:
+        raise AssertionError("2-cell open axis accepted")

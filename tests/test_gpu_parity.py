@@ -1,0 +1,267 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 oracle.
+
+Element-by-element comparisons on identical seeded inputs: populations,
+density, velocity, per-step body force/torque and mass, at sizes the oracle
+runs in seconds (several 256-cell blocks, ragged tails), the full-size
+swimmer channel for a few steps from a seeded state, the batched form, and
+the edge cases (no markers, a single cell, invalid markers, NaN input).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import FREESLIP, OUTFLOW, PERIODIC, VELOCITY
+from paper_2206_01683_b300 import fishlbm, inputs
+
+from parity_util import TOL_F32, Pair, f32, rel_l2
+
+pytestmark = pytest.mark.gpu
+VARIANTS = ["plain", "staged"]
+
+OPEN_X = (VELOCITY, OUTFLOW, FREESLIP, FREESLIP, FREESLIP, FREESLIP)
+
+
+def assert_parity(err, tol=TOL_F32, keys=("rho", "u", "force")):
+    for k in keys:
+        if k in err:
+            assert err[k] <= tol, (k, err)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_taylor_green_periodic(variant):
+    shape = (32, 24, 8)
+    rho, u = inputs.taylor_green(shape, (0, 1), U0=0.02)
+    r2, u2 = inputs.random_fields(shape, seed=3, u_amp=0.01, rho_amp=0.005)
+    p = Pair(shape, 0.56, variant=variant)
+    p.init(rho + r2 - 1.0, u + u2)
+    for _ in range(100):
+        p.step(record=False)
+    err = p.errors()
+    assert_parity(err, keys=("rho", "u", "pop"))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_sphere_in_periodic_box_full_run(variant):
+    """Rigid sphere (452 Fibonacci markers, R = 6) translating at 0.05 lu/step
+    through a 48x32x32 periodic box at tau = 0.56, 200 steps."""
+    cfg = inputs.SPHERE_BOX
+    p = Pair(cfg["shape"], cfg["tau"], variant=variant)
+    for n in range(cfg["steps"]):
+        X, U, dV = inputs.translating_sphere(cfg["n_markers"], cfg["radius"], cfg["center"],
+                                             cfg["velocity"], n)
+        p.markers(X, U, dV)
+        p.step()
+    err = p.errors()
+    assert_parity(err, keys=("rho", "u", "pop", "force", "torque"))
+    assert err["mass"] < 1e-9
+    drag = np.array([h[-1, 0] for h in p.force_hist_g])
+    assert drag[-1] < 0          # the fluid resists the motion
+
+
+def _fish_case(shape, tau, length, n_markers, steps, seed, amps=None, variant="auto"):
+    fish = inputs.fish_for_grid(shape, length, n_markers, amplitudes=amps)
+    traj = inputs.FrameTrajectory(seed, inputs.domain_centre(shape))
+    p = Pair(shape, tau, faces=OPEN_X, u_in=(0.02, 0.0, 0.0), variant=variant)
+    p.init(None, np.tile([0.02, 0.0, 0.0], (p.o.ncell, 1)))
+    ref = fish.joints_rest[0]
+    for n in range(steps):
+        X, U = fish.pose(n)
+        p.markers(X, U, fish.dV, seg=fish.seg, nseg=5, ref=ref)
+        p.step(traj.at(n))
+    return p
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_swimmer_open_channel_reduced(variant):
+    """Skinned swimmer in the moving frame with inlet/outflow/free-slip faces
+    (the full workload's physics at 96x48x48, body length 24, 900 markers)."""
+    p = _fish_case((96, 48, 48), 0.52, 24.0, 900, 150, seed=inputs.seed_for(2), variant=variant)
+    err = p.errors()
+    assert_parity(err, keys=("rho", "u", "pop", "force", "torque", "seg_force"))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_ragged_grid_mixed_faces_rotating_frame(variant):
+    """37x23x11 (rows padded to a pitch of 40, not a multiple of 32 or 256):
+    periodic x, free-slip y walls, inlet at -z and outflow at +z, rotating +
+    accelerating frame, markers straddling the periodic x wrap."""
+    shape = (37, 23, 11)
+    faces = (PERIODIC, PERIODIC, FREESLIP, FREESLIP, VELOCITY, OUTFLOW)
+    p = Pair(shape, 0.7, faces=faces, u_in=(0.005, 0.0, 0.01), rho0=1.002, variant=variant)
+    rho, u = inputs.random_fields(shape, seed=21, u_amp=0.01)
+    p.init(rho, u)
+    X, dV = inputs.fibonacci_sphere(60, 2.2, (35.5, 11.0, 5.0))   # straddles the x wrap
+    frame = oracle.make_frame(acc=(1e-5, -2e-5, 5e-6), omega=(2e-4, -1e-4, 3e-4),
+                              domega=(1e-6, 2e-6, -1e-6), origin=(18.0, 11.0, 5.0))
+    for n in range(60):
+        Xn = X + np.array([0.01 * n, 0.0, 0.0])
+        p.markers(Xn, np.tile([0.01, 0.0, 0.0], (60, 1)), dV, ref=(18.0, 11.0, 5.0))
+        p.step(frame)
+    err = p.errors()
+    assert_parity(err, keys=("rho", "u", "pop", "force", "torque"))
+
+
+def test_full_size_swimmer_channel_few_steps():
+    """The 256x128x128 swimmer channel (6000 markers, body length 64) in the
+    launch configuration of the benchmark (automatic kernel choice: staged),
+    3 steps from a seeded state."""
+    cfg = inputs.FISH_CHANNEL
+    shape = cfg["shape"]
+    p = Pair(shape, cfg["tau"], faces=OPEN_X, u_in=(cfg["u_in"], 0.0, 0.0))
+    rho, u = inputs.random_fields(shape, seed=inputs.seed_for(2), u_amp=0.02, rho_amp=0.004)
+    u[:, 0] += cfg["u_in"]
+    p.init(rho, u)
+    fish = inputs.fish_for_grid(shape, cfg["length"], cfg["n_markers"])
+    traj = inputs.FrameTrajectory(inputs.seed_for(2), inputs.domain_centre(shape))
+    for n in range(100, 103):
+        X, U = fish.pose(n)
+        p.markers(X, U, fish.dV, seg=fish.seg, nseg=5, ref=fish.joints_rest[0])
+        p.step(traj.at(n))
+    err = p.errors()
+    assert_parity(err, keys=("rho", "u", "pop", "force", "torque", "seg_force"))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_batched_environments_match_separate_oracles(variant):
+    shapes = [(40, 24, 24), (32, 32, 16), (21, 20, 28)]
+    taus = [0.52, 0.6, 0.8]
+    faces = [OPEN_X, (PERIODIC,) * 6, (PERIODIC, PERIODIC, FREESLIP, FREESLIP, PERIODIC, PERIODIC)]
+    envs = [fishlbm.env_desc(s, t, f, f32((0.02, 0, 0))) for s, t, f in zip(shapes, taus, faces)]
+    dom = fishlbm.Domain(envs, variant=variant)
+    ors = [oracle.Oracle(s, t, faces=f, u_in=f32((0.02, 0, 0))) for s, t, f in zip(shapes, taus, faces)]
+    from parity_util import gpu_to_oracle_perm
+    perm = gpu_to_oracle_perm()
+    marks = []
+    for e, s in enumerate(shapes):
+        X, dV = inputs.fibonacci_sphere(80 + 20 * e, 3.0, (s[0] / 2, s[1] / 2, s[2] / 2))
+        U = np.tile([0.01 * (e + 1), 0.0, -0.005], (X.shape[0], 1))
+        X32, U32, dV32 = (np.asarray(a, np.float32) for a in (X, U, dV))
+        dom.set_markers(X32, U32, dV32, env=e)
+        ors[e].set_markers(X32.astype(float), U32.astype(float), dV32.astype(float))
+        marks.append(X.shape[0])
+    trajs = [inputs.FrameTrajectory(100 + e, inputs.domain_centre(s)) for e, s in enumerate(shapes)]
+    for n in range(40):
+        frs = [f32(t.at(n)) for t in trajs]
+        dom.step(1, [fishlbm.frame_from_array(f) for f in frs])
+        for e in range(3):
+            ors[e].step(frs[e])
+    _, w = oracle.lattice()
+    for e in range(3):
+        ro, uo = ors[e].fields()
+        rg, ug = dom.fields(env=e)
+        assert rel_l2(rg, ro) <= TOL_F32 and rel_l2(ug, uo) <= TOL_F32, e
+        fo = ors[e].populations() - w
+        fg = dom.populations(env=e)[:, perm] - w
+        assert rel_l2(fg, fo) <= TOL_F32, e
+        assert rel_l2(dom.get_body_force_torque(env=e), ors[e].force_torque()) <= TOL_F32, e
+
+
+# ------------------------------------------------------------ edge cases
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_no_markers_and_single_cell(variant):
+    for shape in ((1, 1, 1), (2, 1, 1), (1, 3, 2), (9, 1, 1)):
+        p = Pair(shape, 0.8, variant=variant)
+        rho, u = inputs.random_fields(shape, seed=5)
+        p.init(rho, u)
+        for _ in range(5):
+            p.step(oracle.make_frame(acc=(1e-4, 0, 0)), record=False)
+        err = p.errors()
+        assert_parity(err, keys=("rho", "u", "pop"))
+        assert np.all(p.g.get_body_force_torque() == 0.0)
+
+
+def test_host_marker_validation():
+    d = fishlbm.Domain([fishlbm.env_desc((16, 12, 12), 0.7, OPEN_X)])
+    bad = np.array([[1.5, 6.0, 6.0]], np.float32)
+    with pytest.raises(fishlbm.FgError) as ei:
+        d.set_markers(bad, np.zeros_like(bad), np.ones(1, np.float32))
+    assert ei.value.status == fishlbm.FG_ERR_INVALID
+    with pytest.raises(fishlbm.FgError):
+        d.set_markers(np.array([[5, 6, 6]], np.float32), np.zeros((1, 3), np.float32),
+                      np.ones(1, np.float32), seg=np.array([3], np.int32), n_seg=2)
+
+
+def test_device_marker_outside_domain_is_skipped_and_reported():
+    torch = pytest.importorskip("torch")
+    d = fishlbm.Domain([fishlbm.env_desc((16, 12, 12), 0.7, OPEN_X)])
+    X = torch.tensor([[6.0, 6.0, 6.0], [14.0, 6.0, 6.0]], device="cuda")   # second is too close to +x
+    U = torch.zeros_like(X)
+    dV = torch.ones(2, device="cuda")
+    d.set_markers(X, U, dV)
+    d.step(1)
+    with pytest.raises(fishlbm.FgError) as ei:
+        d.get_body_force_torque()
+    assert ei.value.status == fishlbm.FG_ERR_INVALID
+    assert np.all(d.marker_force()[1] == 0.0)
+    d.set_markers(X[:1].contiguous(), U[:1].contiguous(), dV[:1].contiguous())
+    d.step(1)
+    d.get_body_force_torque()        # usable again
+
+
+def test_numeric_watchdog_poison_and_reset():
+    d = fishlbm.Domain([fishlbm.env_desc((8, 8, 8), 0.7)])
+    rho = np.ones(512)
+    rho[77] = np.nan
+    d.init_fields(rho, None)
+    d.step(1)
+    with pytest.raises(fishlbm.FgError) as ei:
+        d.get_body_force_torque()
+    assert ei.value.status == fishlbm.FG_ERR_NUMERIC
+    with pytest.raises(fishlbm.FgError) as ei:
+        d.step(1)
+    assert ei.value.status == fishlbm.FG_ERR_STATE
+    d.init_fields(None, None)
+    d.step(2)
+    d.get_body_force_torque()
+    assert abs(d.mass() - 512.0) < 1e-9
+
+
+def test_history_checkpoint_and_profile():
+    shape = (24, 16, 16)
+    d = fishlbm.Domain([fishlbm.env_desc(shape, 0.6)], record_history=8)
+    X, dV = inputs.fibonacci_sphere(100, 3.0, (12, 8, 8))
+    d.set_markers(np.float32(X), np.float32(np.tile([0.02, 0, 0], (100, 1))), np.float32(dV))
+    d.profile(True)
+    forces = []
+    for _ in range(12):
+        d.step(1)
+        forces.append(d.get_body_force_torque()[-1].copy())
+    ms, n = d.profile_read()
+    assert n[fishlbm.FG_K_IB] == 12 and n[fishlbm.FG_K_STREAM_COLLIDE] == 12 and n[fishlbm.FG_K_REDUCE] == 12
+    assert np.all(ms > 0)
+    h = d.history(100)
+    assert h.shape == (8, 13)
+    assert np.allclose(h[:, :6 * 2][:, 6:], np.array(forces[-8:]), rtol=0, atol=0)
+    assert np.all(np.abs(h[:, -1] - d.mass()) < 1e-6)
+    snap = d.save_state()
+    d.step(5)
+    a = d.populations()
+    d.load_state(snap)
+    d.step(5)
+    b = d.populations()
+    assert np.max(np.abs(a - b)) < 1e-6
+    assert d.step_count() == 22
+
+
+def test_long_rows_fall_back_to_plain_and_staged_rejects_them():
+    """Rows longer than 512 cells go to the plain kernel under AUTO; asking
+    for the staged kernel explicitly is an argument error."""
+    e = fishlbm.env_desc((600, 4, 3), 0.7)
+    d = fishlbm.Domain([e])          # AUTO -> plain
+    d.step(2)
+    d.get_body_force_torque()
+    with pytest.raises(fishlbm.FgError) as ei:
+        fishlbm.Domain([e], variant="staged")
+    assert ei.value.status == fishlbm.FG_ERR_INVALID
+
+
+def test_long_rows_parity():
+    p = Pair((520, 5, 4), 0.6)
+    rho, u = inputs.random_fields((520, 5, 4), seed=31)
+    p.init(rho, u)
+    for _ in range(10):
+        p.step(oracle.make_frame(acc=(1e-5, 0, 0), omega=(0, 0, 1e-4), origin=(260, 2, 1.5)), record=False)
+    assert_parity(p.errors(), keys=("rho", "u", "pop"))
