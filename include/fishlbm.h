@@ -200,6 +200,44 @@ fg_status fg_profile_read(fg_domain* d, double* ms, long long* launches);
  * and 27 writes of a population per cell of every environment. */
 fg_status fg_stream_collide_bytes(fg_domain* d, unsigned long long* bytes);
 
+/* ---- allocation-free body force -----------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory when they need the body force: a program
+ * whose device memory is wholly owned by another framework's pool, or a
+ * control loop that cannot afford the device-wide synchronisation that
+ * cudaMalloc and cudaFree imply.
+ *
+ * fg_body_force_noalloc computes what fg_step reports through
+ * fg_get_body_force_torque for a step that starts from the state g: the
+ * post-stream velocity interpolated at the markers (Peskin 4-point delta,
+ * frame half-force shift), the direct-forcing marker force F_l =
+ * 2 R_l (U_l - U~_l), and the force and torque on the body, FP64.  It does
+ * not spread the force or advance the fluid.  It allocates nothing: its
+ * scratch (one float triple per marker and a flag word) is a static device
+ * array of FG_NOALLOC_MAX_MARKERS markers, about 0.8 MB, that every GPU
+ * loading this library holds until the process exits.
+ *   env     grid size and faces (tau, u_in, rho0, u0 are not used)
+ *   g       device, FP32, the populations in the library's storage layout:
+ *           f_i - w_i as g[27][nz][ny][P], P = nx rounded up to a multiple of
+ *           8, velocity order of fg_lattice (what fg_save_state returns for
+ *           an FP32 domain)
+ *   X, U    device, float [n][3]; dV device float [n]; seg device int [n] in
+ *           [0, n_seg) or NULL; 1 <= n_seg <= 16; ref[3] host (NULL: origin)
+ *   frame   host, or NULL for a frame at rest with origin at the centre
+ *   out     device, double [(n_seg + 1) * 6]: one row per segment, then the
+ *           total; NaN rows if a marker lay outside its allowed range
+ *           (2 <= X < n-3 along non-periodic axes)
+ * Runs asynchronously on cuda_stream (a cudaStream_t, NULL = legacy default).
+ * The first call on a device looks up the scratch's device address with that
+ * device current; make that first call before any stream capture.  Every
+ * call uses the same scratch: calls that overlap on the GPU (on different
+ * streams, or from different threads) race and must be serialised by the
+ * caller.  n > FG_NOALLOC_MAX_MARKERS is rejected with FG_ERR_INVALID. */
+#define FG_NOALLOC_MAX_MARKERS 65536
+fg_status fg_body_force_noalloc(const fg_env_desc* env, const float* g, const float* X, const float* U,
+                                const float* dV, const int* seg, int n, int n_seg, const double ref[3],
+                                const fg_frame* frame, double* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -293,6 +293,9 @@ fg_status check_env(fg_domain* d, int env) {
 
 }  // namespace
 
+// Lets other translation units of the library report through fg_last_error.
+void fl_set_last_error(const char* msg) { g_err = msg; }
+
 extern "C" {
 
 const char* fg_last_error(void) { return g_err.c_str(); }

@@ -588,7 +588,7 @@ struct Kahan {
 // nseg all markers (the total row), y == MAX_SEG + 1 the mass.  Force on the
 // body F = -sum F_l dV_l, torque T = -sum (X_l - ref) x F_l dV_l; mass =
 // ncell + sum (rho - 1).  Fixed summation order: the result is deterministic.
-__global__ void __launch_bounds__(RED_THREADS)
+static __global__ void __launch_bounds__(RED_THREADS)
 k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const float* __restrict__ Fm,
          const float* __restrict__ dV, const int* __restrict__ seg,
          const float* __restrict__ mass_part, double* __restrict__ ft, double* __restrict__ mass,

@@ -76,7 +76,10 @@ SIGNATURES = {
     "fg_profile": (_I, [_V, _I]),
     "fg_profile_read": (_I, [_V, _P(_D), _P(_LL)]),
     "fg_stream_collide_bytes": (_I, [_V, _P(_ULL)]),
+    "fg_body_force_noalloc": (_I, [_P(fg_env_desc), _V, _V, _V, _V, _V, _I, _I, _P(_D),
+                                   _P(fg_frame), _V, _V]),
 }
+FG_NOALLOC_MAX_MARKERS = 65536
 
 _lib = None
 
@@ -132,6 +135,16 @@ def fg_get_body_force_torque(d, env, n_seg):
     out = np.zeros((n_seg + 1, 6))
     _check(lib().fg_get_body_force_torque(d, env, _dp(out)))
     return out
+
+
+def fg_body_force_noalloc(env, g, X, U, dV, seg, n, n_seg, ref, frame, out, stream=None):
+    """Allocation-free body force from a caller-owned FP32 state (device
+    pointers as ints or None); see include/fishlbm.h."""
+    refa = (_D * 3)(*ref) if ref is not None else None
+    _check(lib().fg_body_force_noalloc(ctypes.byref(env), _V(g), _V(X), _V(U), _V(dV),
+                                       _V(seg) if seg else None, n, n_seg, refa,
+                                       ctypes.byref(frame) if frame is not None else None,
+                                       _V(out), _V(stream or 0)))
 
 
 def fg_destroy(d):
