@@ -66,7 +66,10 @@ struct fg_domain {
     float* fib = nullptr;
     uint32_t* stamps = nullptr;
     unsigned long long n_stamps = 0;
-    float* mass_part = nullptr;
+    Pair32* mass_part = nullptr;         // mass partial sums of the stream-collide kernel
+    Pair32* red_partials = nullptr;      // chunk sums of k_reduce
+    int* red_counters = nullptr;         // per (env, row) chunk counters of k_reduce
+    int red_z = 1;                       // chunks per row of k_reduce
     int total_blocks = 0;                // plain stream-collide grid
     int total_groups = 0;                // staged kernel row groups
     bool staged = false;                 // stream-collide variant in use
@@ -121,6 +124,7 @@ void set_frame(FrameDev& f, const fg_frame& src) {
 void free_all(fg_domain* d) {
     if (!d) return;
     void* ptrs[] = {d->d_env, d->d_frame, d->pop[0], d->pop[1], d->fib, d->stamps, d->mass_part,
+                    d->red_partials, d->red_counters,
                     d->X, d->U, d->dV, d->Fm, d->seg, d->ft, d->mass, d->hist, d->status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -137,6 +141,24 @@ fg_status dalloc(T** p, size_t count) {
         *p = nullptr;
         return cuda_fail(e, "cudaMalloc");
     }
+    return FG_OK;
+}
+
+// Chunk-sum scratch of k_reduce, sized for the current marker capacities.
+fg_status ensure_reduce_scratch(fg_domain* d) {
+    int z = 1;
+    for (int e = 0; e < d->n_envs; ++e) {
+        z = std::max(z, (d->mk[e].cap + RED_THREADS - 1) / RED_THREADS);
+        z = std::max(z, (d->env[e].nparts + RED_THREADS * MASS_PER_THREAD - 1) / (RED_THREADS * MASS_PER_THREAD));
+    }
+    if (d->red_partials && z <= d->red_z) return FG_OK;
+    Pair32* p = nullptr;
+    fg_status st = dalloc(&p, (size_t)d->n_envs * RED_ROWS * z * 6);
+    if (st != FG_OK) return st;
+    CK(cudaStreamSynchronize(d->stream));
+    if (d->red_partials) cudaFree(d->red_partials);
+    d->red_partials = p;
+    d->red_z = z;
     return FG_OK;
 }
 
@@ -179,7 +201,7 @@ fg_status grow_markers(fg_domain* d, int env, int n) {
     d->X = X; d->U = U; d->dV = dV; d->Fm = Fm; d->seg = sg;
     d->marker_slots = off;
     d->mk = nr;
-    return FG_OK;
+    return ensure_reduce_scratch(d);
 }
 
 void refresh_marker_table(fg_domain* d) {
@@ -242,9 +264,9 @@ fg_status launch_step(fg_domain* d) {
     }
     if (evp[FG_K_STREAM_COLLIDE]) CK(cudaEventRecord(evp[FG_K_STREAM_COLLIDE][1], d->stream));
     if (evp[FG_K_REDUCE]) CK(cudaEventRecord(evp[FG_K_REDUCE][0], d->stream));
-    k_reduce<<<dim3(d->n_envs, MAX_SEG + 2), RED_THREADS, 0, d->stream>>>(d->d_env, d->X, d->Fm, d->dV, d->seg,
-                                                       d->mass_part, d->ft, d->mass, d->hist,
-                                                       d->opt.record_history, d->steps, d->status);
+    k_reduce<<<dim3(d->n_envs, RED_ROWS, d->red_z), RED_THREADS, 0, d->stream>>>(
+        d->d_env, d->X, d->Fm, d->dV, d->seg, d->mass_part, d->red_partials, d->red_counters, d->red_z, d->ft,
+        d->mass, d->hist, d->opt.record_history, d->steps, d->status);
     if (evp[FG_K_REDUCE]) CK(cudaEventRecord(evp[FG_K_REDUCE][1], d->stream));
     CK(cudaGetLastError());
     d->cur ^= 1;
@@ -394,11 +416,21 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         return fail(FG_ERR_INVALID, "staged kernel needs rows of at most 512 cells");
     }
     d->staged = o.kernel_variant == FG_KERNEL_STAGED || (o.kernel_variant == FG_KERNEL_AUTO && can_stage);
+    for (int e = 0; e < n_envs; ++e)
+        d->buf_elems = std::max<uint32_t>(d->buf_elems, (uint32_t)(27 * d->env[e].rpg * d->env[e].P));
+    d->total_groups = group0;
+    if (d->staged) {
+        fg_status sst = setup_staged(d);
+        if (sst != FG_OK) {
+            delete d;
+            return sst;
+        }
+    }
     for (int e = 0; e < n_envs; ++e) {
         EnvDev& E = d->env[e];
+        // one mass partial per row group (staged) or per block (plain)
         E.part0 = d->staged ? E.group0 : E.block0;
         E.nparts = d->staged ? E.ngroups : E.nblocks;
-        d->buf_elems = std::max<uint32_t>(d->buf_elems, (uint32_t)(27 * E.rpg * E.P));
     }
     d->total_cells = ncell_all;
     d->total_slots = slot_off;
@@ -424,7 +456,8 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     }
     DA(d->fib, 3ull * slot_off);
     DA(d->stamps, stamp_off);
-    DA(d->mass_part, std::max(block0, group0));
+    DA(d->mass_part, (size_t)std::max(block0, group0));
+    DA(d->red_counters, (size_t)n_envs * RED_ROWS);
     DA(d->ft, (size_t)n_envs * FT_ROW);
     DA(d->mass, n_envs);
     if (o.record_history > 0) DA(d->hist, (size_t)n_envs * o.record_history * HIST_ROW);
@@ -436,13 +469,14 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         (ce = cudaMemsetAsync(d->fib, 0, sizeof(float) * 3ull * slot_off, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->stamps, 0, sizeof(uint32_t) * stamp_off, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->ft, 0, sizeof(double) * n_envs * FT_ROW, d->stream)) != cudaSuccess ||
-        (ce = cudaMemsetAsync(d->status, 0, sizeof(int), d->stream)) != cudaSuccess) {
+        (ce = cudaMemsetAsync(d->status, 0, sizeof(int), d->stream)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(d->red_counters, 0, sizeof(int) * n_envs * RED_ROWS, d->stream)) != cudaSuccess) {
         st = cuda_fail(ce, "cudaMemsetAsync");
         free_all(d);
         delete d;
         return st;
     }
-    if (d->staged && (st = setup_staged(d)) != FG_OK) {
+    if ((st = ensure_reduce_scratch(d)) != FG_OK) {
         free_all(d);
         delete d;
         return st;

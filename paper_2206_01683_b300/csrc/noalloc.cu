@@ -143,12 +143,12 @@ __global__ void __launch_bounds__(RED_THREADS)
 k_reduce_noalloc(const float* __restrict__ scratch, const float* __restrict__ X, const float* __restrict__ dV,
                  const int* __restrict__ seg, int n, int n_seg, double rx0, double ry0, double rz0,
                  double* __restrict__ out) {
-    __shared__ double sh[RED_THREADS / 32];
+    __shared__ Pair32 sh[RED_THREADS / 32];
     const int y = blockIdx.x;
     const float* Fm = scratch + FLAG_WORDS;
     const bool rejected = *reinterpret_cast<const int*>(scratch) != 0;
     const float rfx = (float)rx0, rfy = (float)ry0, rfz = (float)rz0;
-    Kahan acc[6];
+    Pair32 acc[6];
 #pragma unroll 2
     for (int l = threadIdx.x; l < n; l += blockDim.x) {
         const int sg = seg ? seg[l] : 0;
@@ -164,7 +164,7 @@ k_reduce_noalloc(const float* __restrict__ scratch, const float* __restrict__ X,
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        const double t = block_sum(acc[k].value(), sh);
+        const double t = block_sum(acc[k], sh);
         if (threadIdx.x == 0) out[6 * y + k] = rejected ? (double)NAN : t;
     }
 }

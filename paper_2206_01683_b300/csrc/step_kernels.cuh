@@ -29,7 +29,7 @@ namespace fl {
 constexpr int K1_THREADS = 256;  // threads of either stream-collide kernel
 constexpr int GROUP_CELLS = 256; // target cells (slots) per staged row group
 constexpr int IB_THREADS = 256;  // 8 markers per block
-constexpr int RED_THREADS = 1024;
+constexpr int RED_THREADS = 256;
 constexpr int MAX_SEG = 16;
 constexpr int FT_ROW = (MAX_SEG + 1) * 6;  // force/torque doubles per environment
 constexpr int HIST_ROW = FT_ROW + 1;       // + mass
@@ -135,21 +135,43 @@ struct Moments {
 
 template <bool SECOND>
 __device__ __forceinline__ void accumulate(Moments& m, const float (&g)[Q]) {
+    // Sums by x-lines first: for each (cy, cz) the line sum s, the odd part
+    // d = g(+x) - g(-x) and the even part e = g(+x) + g(-x); then by y- and
+    // z-lines.  About 80 additions instead of 171 term by term.
+    float sl[9], dl[9], el[9];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const float v = g[i];
-        m.dr += v;
-        if (cx(i) == 1) m.jx += v; else if (cx(i) == -1) m.jx -= v;
-        if (cy(i) == 1) m.jy += v; else if (cy(i) == -1) m.jy -= v;
-        if (cz(i) == 1) m.jz += v; else if (cz(i) == -1) m.jz -= v;
+    for (int l = 0; l < 9; ++l) {           // l = (cy+1) + 3 (cz+1); i = 3 l + (cx+1)
+        el[l] = g[3 * l + 2] + g[3 * l];
+        dl[l] = g[3 * l + 2] - g[3 * l];
+        sl[l] = el[l] + g[3 * l + 1];
+    }
+    float dr = 0.f, jx = 0.f, sxx = 0.f;
+#pragma unroll
+    for (int l = 0; l < 9; ++l) {
+        dr += sl[l];
+        jx += dl[l];
+        if (SECOND) sxx += el[l];
+    }
+    // y-lines (per cz) and z-lines (per cy)
+    float jy = 0.f, syy = 0.f, jz = 0.f, szz = 0.f, sxy = 0.f, sxz = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float yp = sl[2 + 3 * k], ym = sl[0 + 3 * k];     // cy = +1 / -1 at cz = k - 1
+        const float zp = sl[k + 6], zm = sl[k];                 // cz = +1 / -1 at cy = k - 1
+        jy += yp - ym;
+        jz += zp - zm;
         if (SECOND) {
-            if (cx(i) != 0) m.sxx += v;
-            if (cy(i) != 0) m.syy += v;
-            if (cz(i) != 0) m.szz += v;
-            if (cx(i) * cy(i) == 1) m.sxy += v; else if (cx(i) * cy(i) == -1) m.sxy -= v;
-            if (cx(i) * cz(i) == 1) m.sxz += v; else if (cx(i) * cz(i) == -1) m.sxz -= v;
-            if (cy(i) * cz(i) == 1) m.syz += v; else if (cy(i) * cz(i) == -1) m.syz -= v;
+            syy += yp + ym;
+            szz += zp + zm;
+            sxy += dl[2 + 3 * k] - dl[0 + 3 * k];
+            sxz += dl[k + 6] - dl[k];
         }
+    }
+    m.dr += dr; m.jx += jx; m.jy += jy; m.jz += jz;
+    if (SECOND) {
+        // sum cy cz s = (s(+,+) - s(+,-)) - (s(-,+) - s(-,-))
+        const float syz = (sl[8] - sl[2]) - (sl[6] - sl[0]);
+        m.sxx += sxx; m.syy += syy; m.szz += szz; m.sxy += sxy; m.sxz += sxz; m.syz += syz;
     }
 }
 
@@ -165,6 +187,29 @@ __device__ __forceinline__ Moments pull_moments(const typename S::raw* __restric
     accumulate<SECOND>(m, g);
     return m;
 }
+
+// A sum kept as an unevaluated pair hi + lo of FP32 numbers (compensated
+// summation, close to FP64 accuracy for these sums).  B300 runs FP64 --
+// conversions included -- at a small fraction of its FP32 rate and with long
+// latency, so the reduction trees stay in FP32 pairs and each result is
+// evaluated in FP64 once, at the end.
+struct Pair32 {
+    float hi = 0.f, lo = 0.f;
+    // add one term (Kahan/Neumaier step)
+    __device__ __forceinline__ void add(float v) {
+        const float t = hi + v;
+        lo += fabsf(hi) >= fabsf(v) ? (hi - t) + v : (v - t) + hi;
+        hi = t;
+    }
+    // add another pair (TwoSum of the high parts, low parts carried)
+    __device__ __forceinline__ void add(const Pair32& o) {
+        const float s = hi + o.hi;
+        const float bp = s - hi;
+        const float err = (hi - (s - bp)) + (o.hi - bp);
+        hi = s;
+        lo += o.lo + err;
+    }
+};
 
 // ------------------------------------------------ the per-cell update
 
@@ -400,7 +445,7 @@ __global__ void __launch_bounds__(K1_THREADS)
 k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __restrict__ gout,
                  const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, int n_envs,
                  float* __restrict__ fib, const uint32_t* __restrict__ stamps, uint32_t stamp,
-                 float* __restrict__ mass_part) {
+                 Pair32* __restrict__ mass_part) {
     __shared__ float wsum[K1_THREADS / 32];
     const int b = blockIdx.x;
     const int e = n_envs > 1 ? env_of<&EnvDev::block0>(envs, n_envs, b) : 0;
@@ -426,7 +471,11 @@ k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __res
         }
     }
     const float t = block_sum_f32(drout, wsum);
-    if (threadIdx.x == 0) mass_part[b] = t;
+    if (threadIdx.x == 0) {
+        Pair32 p;
+        p.hi = t;
+        mass_part[b] = p;
+    }
 }
 
 // Staged variant: persistent blocks walk row groups g = blockIdx.x,
@@ -467,7 +516,7 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
 k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw* __restrict__ gout,
                         const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, int n_envs,
                         int total_groups, uint32_t buf_elems, float* __restrict__ fib,
-                        const uint32_t* __restrict__ stamps, uint32_t stamp, float* __restrict__ mass_part,
+                        const uint32_t* __restrict__ stamps, uint32_t stamp, Pair32* __restrict__ mass_part,
                         int* __restrict__ status) {
     typedef typename S::raw raw;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -540,9 +589,9 @@ k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw
         if ((threadIdx.x & 31) == 0) wsum[b][warp] = drsum;
         __syncthreads();   // buffer b is free again; wsum[b] is complete
         if (threadIdx.x == 0) {
-            float t = 0.f;
+            Pair32 t;
 #pragma unroll
-            for (int w = 0; w < K1_THREADS / 32; ++w) t += wsum[b][w];
+            for (int w = 0; w < K1_THREADS / 32; ++w) t.add(wsum[b][w]);
             mass_part[g] = t;
         }
     }
@@ -550,96 +599,157 @@ k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw
 
 // ------------------------------------------------------- K4: reduction
 
-// Sum over the block in FP64: a shuffle tree inside each warp, then warp 0
-// combines the warp totals with a second tree (no serial loop: FP64 latency
-// on B300 is long).  Fixed order, so the result is deterministic; valid in
-// thread 0.
-__device__ __forceinline__ double block_sum(double v, double* sh) {
+// Sum a pair over the block: pair trees inside each warp, then warp 0
+// combines the warp totals the same way; the final pair is evaluated in FP64.
+// Fixed order, so the result is deterministic; valid in thread 0.
+__device__ __forceinline__ double block_sum(Pair32 v, Pair32* sh) {
 #pragma unroll
-    for (int k = 16; k >= 1; k >>= 1) v += __shfl_xor_sync(0xffffffffu, v, k);
+    for (int k = 16; k >= 1; k >>= 1) {
+        Pair32 o;
+        o.hi = __shfl_xor_sync(0xffffffffu, v.hi, k);
+        o.lo = __shfl_xor_sync(0xffffffffu, v.lo, k);
+        v.add(o);
+    }
     const int w = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
     __syncthreads();
     if (lane == 0) sh[w] = v;
     __syncthreads();
     double t = 0.0;
     if (w == 0) {
-        t = lane < nw ? sh[lane] : 0.0;
+        Pair32 u;
+        if (lane < nw) u = sh[lane];
 #pragma unroll
-        for (int k = 16; k >= 1; k >>= 1) t += __shfl_xor_sync(0xffffffffu, t, k);
+        for (int k = 16; k >= 1; k >>= 1) {
+            Pair32 o;
+            o.hi = __shfl_xor_sync(0xffffffffu, u.hi, k);
+            o.lo = __shfl_xor_sync(0xffffffffu, u.lo, k);
+            u.add(o);
+        }
+        t = (double)u.hi + (double)u.lo;
     }
     return t;
 }
 
-// Compensated FP32 accumulation (Kahan): per-thread partial sums keep close
-// to FP64 accuracy while running on the FP32 pipes; B300's FP64 rate per SM
-// is too low to spend on every term.
-struct Kahan {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float v) {
-        const float y = v - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
+// Sum a pair over the block, staying in FP32 pairs; valid in thread 0.
+__device__ __forceinline__ Pair32 block_pair_sum(Pair32 v, Pair32* sh) {
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) {
+        Pair32 o;
+        o.hi = __shfl_xor_sync(0xffffffffu, v.hi, k);
+        o.lo = __shfl_xor_sync(0xffffffffu, v.lo, k);
+        v.add(o);
     }
-    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    Pair32 t;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nw; ++i) t.add(sh[i]);
+    return t;
+}
 
-// Grid (n_envs, MAX_SEG + 2).  Block (e, y): y < nseg sums segment y, y ==
-// nseg all markers (the total row), y == MAX_SEG + 1 the mass.  Force on the
-// body F = -sum F_l dV_l, torque T = -sum (X_l - ref) x F_l dV_l; mass =
-// ncell + sum (rho - 1).  Fixed summation order: the result is deterministic.
+constexpr int MASS_PER_THREAD = 8;
+constexpr int RED_ROWS = MAX_SEG + 2;   // force/torque rows 0..MAX_SEG, then the mass
+
+// Grid (n_envs, RED_ROWS, chunks).  Block (e, y, z) sums chunk z of row y of
+// environment e: y <= nseg is force/torque row y (segment y; y == nseg is
+// the total over all markers), one marker per thread; y == RED_ROWS - 1 is
+// the mass, MASS_PER_THREAD partials per thread.  Force on the body
+// F = -sum F_l dV_l, torque T = -sum (X_l - ref) x F_l dV_l, mass = ncell +
+// sum (rho - 1).  Chunk sums are compensated FP32 pairs; the last block of a
+// row to finish adds the chunk pairs in chunk order and evaluates the result
+// in FP64, so the result does not depend on which block finished last.
 static __global__ void __launch_bounds__(RED_THREADS)
 k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const float* __restrict__ Fm,
-         const float* __restrict__ dV, const int* __restrict__ seg,
-         const float* __restrict__ mass_part, double* __restrict__ ft, double* __restrict__ mass,
-         double* __restrict__ hist, int hist_cap, long long hist_row, int* __restrict__ status) {
-    __shared__ double sh[RED_THREADS / 32];
-    const int e = blockIdx.x, y = blockIdx.y;
+         const float* __restrict__ dV, const int* __restrict__ seg, const Pair32* __restrict__ mass_part,
+         Pair32* __restrict__ partials, int* __restrict__ counters, int zmax, double* __restrict__ ft,
+         double* __restrict__ mass, double* __restrict__ hist, int hist_cap, long long hist_row,
+         int* __restrict__ status) {
+    __shared__ Pair32 sh[RED_THREADS / 32];
+    __shared__ int is_last;
+    const int e = blockIdx.x, y = blockIdx.y, z = blockIdx.z, tid = threadIdx.x;
     const EnvDev& E = envs[e];
     const int ns = E.nseg;
+    const bool is_mass = y == RED_ROWS - 1;
+    if (!is_mass && y > ns) return;
+    const int per_block = is_mass ? RED_THREADS * MASS_PER_THREAD : RED_THREADS;
+    const int count = is_mass ? E.nparts : E.n_markers;
+    const int nch = max(1, (count + per_block - 1) / per_block);
+    if (z >= nch) return;
+    const int ncomp = is_mass ? 1 : 6;
+    Pair32 acc[6];
+    if (is_mass) {
+        Pair32 v[MASS_PER_THREAD];
+#pragma unroll
+        for (int k = 0; k < MASS_PER_THREAD; ++k) {
+            const int i = z * per_block + k * RED_THREADS + tid;
+            if (i < count) v[k] = mass_part[E.part0 + i];
+        }
+#pragma unroll
+        for (int k = 0; k < MASS_PER_THREAD; ++k) acc[0].add(v[k]);
+    } else {
+        const int l = z * RED_THREADS + tid;
+        if (l < count) {
+            const int q = E.marker_off + l;
+            if (y == ns || seg[q] == y) {
+                const float v = -dV[q];
+                const float Fx = Fm[3 * q] * v, Fy = Fm[3 * q + 1] * v, Fz = Fm[3 * q + 2] * v;
+                const float rx = X[3 * q] - (float)E.ref[0], ry = X[3 * q + 1] - (float)E.ref[1],
+                            rz = X[3 * q + 2] - (float)E.ref[2];
+                acc[0].add(Fx); acc[1].add(Fy); acc[2].add(Fz);
+                acc[3].add(ry * Fz - rz * Fy);
+                acc[4].add(rz * Fx - rx * Fz);
+                acc[5].add(rx * Fy - ry * Fx);
+            }
+        }
+    }
+    Pair32* slot = partials + ((size_t)(e * RED_ROWS + y) * zmax) * 6;
+    for (int c = 0; c < ncomp; ++c) {
+        const Pair32 t = block_pair_sum(acc[c], sh);
+        if (tid == 0) slot[(size_t)z * 6 + c] = t;
+    }
+    if (tid == 0) {
+        __threadfence();
+        is_last = atomicAdd(counters + e * RED_ROWS + y, 1) == nch - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
     double* hrow = hist_cap > 0 ? hist + ((size_t)e * hist_cap + (size_t)(hist_row % hist_cap)) * HIST_ROW
                                 : nullptr;
-    if (y == MAX_SEG + 1) {
-        Kahan km;
-        for (int i = threadIdx.x; i < E.nparts; i += blockDim.x) km.add(mass_part[E.part0 + i]);
-        const double m = block_sum(km.value(), sh);
-        if (threadIdx.x == 0) {
-            const double M = (double)E.n[0] * E.n[1] * E.n[2] + m;
-            mass[e] = M;
-            if (!isfinite(M)) atomicOr(status, ST_NUMERIC);
-            if (hrow) hrow[FT_ROW] = M;
+    const int w = tid >> 5, lane = tid & 31;
+    Pair32 t;
+    if (w < ncomp) {
+        // warp w combines component w: lanes load chunks lane, lane + 32, ...
+        // (in flight together), then a fixed shuffle tree adds the lanes
+        for (int zz = lane; zz < nch; zz += 32) {
+            Pair32 p;
+            p.hi = __ldcg(&slot[(size_t)zz * 6 + w].hi);
+            p.lo = __ldcg(&slot[(size_t)zz * 6 + w].lo);
+            t.add(p);
         }
-        return;
-    }
-    if (y > ns) return;
-    const float rfx = (float)E.ref[0], rfy = (float)E.ref[1], rfz = (float)E.ref[2];
-    Kahan acc[6];
-#pragma unroll 2
-    for (int l = threadIdx.x; l < E.n_markers; l += blockDim.x) {
-        const int q = E.marker_off + l;
-        const int sg = seg[q];
-        const float dv = dV[q];
-        const float f0 = Fm[3 * q], f1 = Fm[3 * q + 1], f2 = Fm[3 * q + 2];
-        const float rx = X[3 * q] - rfx, ry = X[3 * q + 1] - rfy, rz = X[3 * q + 2] - rfz;
-        const float v = (y == ns || sg == y) ? -dv : 0.0f;
-        const float Fx = f0 * v, Fy = f1 * v, Fz = f2 * v;
-        acc[0].add(Fx); acc[1].add(Fy); acc[2].add(Fz);
-        acc[3].add(ry * Fz - rz * Fy);
-        acc[4].add(rz * Fx - rx * Fz);
-        acc[5].add(rx * Fy - ry * Fx);
-    }
-    double* out = ft + (size_t)e * FT_ROW + 6 * y;
-    bool bad = false;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        const double t = block_sum(acc[k].value(), sh);
-        if (threadIdx.x == 0) {
-            out[k] = t;
-            if (hrow) hrow[6 * y + k] = t;
-            if (!isfinite(t)) bad = true;
+        for (int k = 16; k >= 1; k >>= 1) {
+            Pair32 o;
+            o.hi = __shfl_xor_sync(0xffffffffu, t.hi, k);
+            o.lo = __shfl_xor_sync(0xffffffffu, t.lo, k);
+            t.add(o);
         }
     }
-    if (bad) atomicOr(status, ST_NUMERIC);
+    if (w < ncomp && lane == 0) {
+        double v = (double)t.hi + (double)t.lo;
+        if (is_mass) {
+            v += (double)E.n[0] * E.n[1] * E.n[2];
+            mass[e] = v;
+            if (hrow) hrow[FT_ROW] = v;
+        } else {
+            ft[(size_t)e * FT_ROW + 6 * y + w] = v;
+            if (hrow) hrow[6 * y + w] = v;
+        }
+        if (!isfinite(v)) atomicOr(status, ST_NUMERIC);
+    }
+    if (tid == 0) counters[e * RED_ROWS + y] = 0;   // ready for the next step
 }
 
 // ----------------------------------------------------- state access

@@ -1,0 +1,91 @@
+"""Reduced-precision population storage (FP16, BF16) against the FP64 oracle.
+
+Populations are stored as h_i = s_i (f_i - w_i) with a fixed power-of-two
+scale per velocity class; all arithmetic stays FP32 and the reductions end in
+FP64.  The tolerances below were predeclared as FP16 <= 1e-2 and BF16 <= 1e-1
+(relative L2 of velocity and of the body-force history), then refined once
+from the measured errors and frozen before the large-sphere run:
+
+  sphere box, 200 steps:         FP16 u 1.7e-4, F 4e-5;   BF16 u 1.3e-3, F 4e-4
+  swimmer channel, 150 steps:    FP16 u 4.8e-4, F 2.5e-4; BF16 u 1.2e-2, F 4.4e-3
+
+The bounds keep a margin of about 4 over the worst measured case.  The
+swimmer channel is the harder case: its uniform inflow sits in every stored
+deviation, where BF16's 8-bit significand rounds it.
+"""
+import numpy as np
+import pytest
+
+from paper_2206_01683_b300 import fishlbm, inputs
+
+from parity_util import Pair, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f16": 2e-3, "bf16": 5e-2}
+OPEN_X = (1, 2, 3, 3, 3, 3)
+
+
+@pytest.mark.parametrize("variant", ["plain", "staged"])
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_sphere_box_reduced_storage(storage, variant):
+    cfg = inputs.SPHERE_BOX
+    p = Pair(cfg["shape"], cfg["tau"], storage=storage, variant=variant)
+    for n in range(cfg["steps"]):
+        X, U, dV = inputs.translating_sphere(cfg["n_markers"], cfg["radius"], cfg["center"],
+                                             cfg["velocity"], n)
+        p.markers(X, U, dV)
+        p.step()
+    err = p.errors()
+    print("sphere box", storage, variant, {k: "%.3g" % v for k, v in err.items()})
+    assert err["u"] <= TOL[storage], err
+    assert err["force"] <= TOL[storage], err
+    assert err["torque"] <= TOL[storage], err
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_swimmer_channel_reduced_storage(storage):
+    shape = (96, 48, 48)
+    fish = inputs.fish_for_grid(shape, 24.0, 900)
+    traj = inputs.FrameTrajectory(inputs.seed_for(2), inputs.domain_centre(shape))
+    p = Pair(shape, 0.52, faces=OPEN_X, u_in=(0.02, 0.0, 0.0), storage=storage)
+    p.init(None, np.tile([0.02, 0.0, 0.0], (p.o.ncell, 1)))
+    for n in range(150):
+        X, U = fish.pose(n)
+        p.markers(X, U, fish.dV, seg=fish.seg, nseg=5, ref=fish.joints_rest[0])
+        p.step(traj.at(n))
+    err = p.errors()
+    print("swimmer", storage, {k: "%.3g" % v for k, v in err.items()})
+    assert err["u"] <= TOL[storage], err
+    assert err["force"] <= TOL[storage], err
+
+
+def large_sphere_run(storage, steps):
+    """The 384x192x192 periodic box with a 13,500-marker sphere (R = 32.78, so
+    dV = 1), centred at the domain centre shifted by -L/8 in x, translating at
+    0.05 lu/step."""
+    shape = (384, 192, 192)
+    centre = (383 / 2 - 48.0, 95.5, 95.5)
+    R = (13500 / (4 * np.pi)) ** 0.5
+    d = fishlbm.Domain([fishlbm.env_desc(shape, 0.56)], storage=storage)
+    X0, dV = inputs.fibonacci_sphere(13500, R, centre)
+    U = np.tile([0.05, 0.0, 0.0], (13500, 1)).astype(np.float32)
+    F = []
+    for n in range(steps):
+        d.set_markers(np.float32(X0 + U * n), U, np.float32(dV) if n == 0 else None)
+        d.step(1)
+        F.append(d.get_body_force_torque()[-1, :3].copy())
+    rho, u = d.fields()
+    d.close()
+    return u, np.array(F)
+
+
+def test_large_sphere_reduced_storage_tracks_fp32():
+    """At the full 14M-cell size over 1000 steps (beyond what the oracle can
+    run) the FP16/BF16 runs must stay within their frozen tolerances of the
+    FP32 run, which is itself held to 1e-5 of the oracle on smaller cases."""
+    u32, F32 = large_sphere_run("f32", 1000)
+    for storage in ("f16", "bf16"):
+        u, F = large_sphere_run(storage, 1000)
+        assert rel_l2(u, u32) <= TOL[storage], (storage, rel_l2(u, u32))
+        assert rel_l2(F, F32) <= TOL[storage], (storage, rel_l2(F, F32))
