@@ -78,6 +78,11 @@ typedef struct {
     int record_history; /* steps of (force, torque, mass) history kept on the
                            device per environment (0 = none), ring buffer */
     int kernel_variant; /* fg_kernel_variant */
+    int use_graphs;     /* 1: each step is replayed from a captured CUDA graph
+                           (captured on first use and whenever the marker count or
+                           marker storage changes); 0: direct launches.  Steps taken
+                           while fg_profile is on always launch directly.  Default
+                           (opt == NULL): 1 */
 } fg_options;
 
 /* Frame motion of Eq. 3 for one environment: acc = translational
@@ -91,7 +96,7 @@ typedef struct {
 
 /* Create n_envs independent environments (n_envs > 1 is the batched form:
  * every environment advances in the same kernel launches).  opt may be NULL
- * (FP32, one pass).  cuda_stream is a cudaStream_t or NULL.  Populations are
+ * (FP32, one pass, automatic kernel choice, graphs on).  cuda_stream is a cudaStream_t or NULL.  Populations are
  * initialised at equilibrium with (rho0, u0); the frame is at rest with its
  * origin at the domain centre.  Errors: FG_ERR_INVALID (sizes, tau, faces,
  * options), FG_ERR_OOM, FG_ERR_CUDA.  *out is set only on FG_OK. */

@@ -85,8 +85,20 @@ struct fg_domain {
     double* hist = nullptr;
     int* status = nullptr;
     long long steps = 0;
-    uint32_t stamp = 0;
+    StepState* d_state = nullptr;        // stamp / step / completion count on the device
+    int* env_done = nullptr;             // per environment: rows of k_reduce finished
     bool poisoned = false;
+    // CUDA graphs of one step, one per population-buffer parity; rebuilt when
+    // a launch parameter baked into them changes
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    struct GraphKey {
+        const void* X = nullptr;
+        const void* red = nullptr;
+        int total_markers = -1, red_z = -1;
+        bool operator==(const GraphKey& o) const {
+            return X == o.X && red == o.red && total_markers == o.total_markers && red_z == o.red_z;
+        }
+    } graph_key;
     bool profiling = false;
     std::vector<cudaEvent_t> ev[FG_K_COUNT];
     int ev_used[FG_K_COUNT] = {0, 0, 0};
@@ -123,8 +135,10 @@ void set_frame(FrameDev& f, const fg_frame& src) {
 
 void free_all(fg_domain* d) {
     if (!d) return;
+    for (int p = 0; p < 2; ++p)
+        if (d->graph[p]) cudaGraphExecDestroy(d->graph[p]);
     void* ptrs[] = {d->d_env, d->d_frame, d->pop[0], d->pop[1], d->fib, d->stamps, d->mass_part,
-                    d->red_partials, d->red_counters,
+                    d->red_partials, d->red_counters, d->d_state, d->env_done,
                     d->X, d->U, d->dV, d->Fm, d->seg, d->ft, d->mass, d->hist, d->status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -218,13 +232,45 @@ void refresh_marker_table(fg_domain* d) {
     d->total_markers = begin;
 }
 
+// Launch the kernels of one step reading buffer `parity` on stream s; with
+// ev != nullptr an event pair is recorded around each kernel.
+template <class S>
+fg_status enqueue_step(fg_domain* d, int parity, cudaStream_t s, cudaEvent_t* const* ev) {
+    typedef typename S::raw raw;
+    const raw* gin = (const raw*)d->pop[parity];
+    raw* gout = (raw*)d->pop[parity ^ 1];
+    if (d->total_markers > 0) {
+        if (ev) CK(cudaEventRecord(ev[FG_K_IB][0], s));
+        const int warps_per_block = IB_THREADS / 32;
+        const int blocks = (d->total_markers + warps_per_block - 1) / warps_per_block;
+        k_ib<S><<<blocks, IB_THREADS, 0, s>>>(gin, d->d_env, d->d_frame, d->n_envs, d->total_markers, d->X, d->U,
+                                               d->dV, d->Fm, d->fib, d->stamps, d->d_state, d->status);
+        if (ev) CK(cudaEventRecord(ev[FG_K_IB][1], s));
+    }
+    if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][0], s));
+    if (d->staged) {
+        k_stream_collide_staged<S><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
+            gin, gout, d->d_env, d->d_frame, d->n_envs, d->total_groups, d->buf_elems, d->fib, d->stamps,
+            d->d_state, d->mass_part, d->status);
+    } else {
+        k_stream_collide<S><<<d->total_blocks, K1_THREADS, 0, s>>>(gin, gout, d->d_env, d->d_frame, d->n_envs,
+                                                                   d->fib, d->stamps, d->d_state, d->mass_part);
+    }
+    if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][1], s));
+    if (ev) CK(cudaEventRecord(ev[FG_K_REDUCE][0], s));
+    k_reduce<<<dim3(d->n_envs, RED_ROWS, d->red_z), RED_THREADS, 0, s>>>(
+        d->d_env, d->X, d->Fm, d->dV, d->seg, d->mass_part, d->red_partials, d->red_counters, d->env_done,
+        d->n_envs, d->red_z, d->ft, d->mass, d->hist, d->opt.record_history, d->d_state, d->status);
+    if (ev) CK(cudaEventRecord(ev[FG_K_REDUCE][1], s));
+    CK(cudaGetLastError());
+    return FG_OK;
+}
+
+// One step with direct launches (and per-kernel events when profiling).
 template <class S>
 fg_status launch_step(fg_domain* d) {
-    typedef typename S::raw raw;
-    const raw* gin = (const raw*)d->pop[d->cur];
-    raw* gout = (raw*)d->pop[d->cur ^ 1];
-    const uint32_t stamp = ++d->stamp;
     cudaEvent_t* evp[FG_K_COUNT] = {nullptr, nullptr, nullptr};
+    bool use_ev = false;
     if (d->profiling) {
         for (int k = 0; k < FG_K_COUNT; ++k) {
             if (d->ev_used[k] + 2 > (int)d->ev[k].size()) {
@@ -239,36 +285,55 @@ fg_status launch_step(fg_domain* d) {
                 d->ev_used[k] = 0;
             }
             evp[k] = &d->ev[k][d->ev_used[k]];
-            d->ev_used[k] += 2;
+            if (k != FG_K_IB || d->total_markers > 0) d->ev_used[k] += 2;
         }
+        use_ev = true;
     }
-    if (d->total_markers > 0) {
-        if (evp[FG_K_IB]) CK(cudaEventRecord(evp[FG_K_IB][0], d->stream));
-        const int warps_per_block = IB_THREADS / 32;
-        const int blocks = (d->total_markers + warps_per_block - 1) / warps_per_block;
-        k_ib<S><<<blocks, IB_THREADS, 0, d->stream>>>(gin, d->d_env, d->d_frame, d->n_envs,
-                                                      d->total_markers, d->X, d->U, d->dV, d->Fm,
-                                                      d->fib, d->stamps, stamp, d->status);
-        if (evp[FG_K_IB]) CK(cudaEventRecord(evp[FG_K_IB][1], d->stream));
-    } else if (evp[FG_K_IB]) {
-        d->ev_used[FG_K_IB] -= 2;
+    fg_status st = enqueue_step<S>(d, d->cur, d->stream, use_ev ? evp : nullptr);
+    if (st != FG_OK) return st;
+    d->cur ^= 1;
+    d->steps += 1;
+    return FG_OK;
+}
+
+// One step replayed from a captured graph (captured on first use, and again
+// whenever a launch parameter baked into it changes).
+template <class S>
+fg_status graph_step(fg_domain* d) {
+    fg_domain::GraphKey key;
+    key.X = d->X;
+    key.red = d->red_partials;
+    key.total_markers = d->total_markers;
+    key.red_z = d->red_z;
+    if (!(key == d->graph_key)) {
+        for (int p = 0; p < 2; ++p)
+            if (d->graph[p]) {
+                cudaGraphExecDestroy(d->graph[p]);
+                d->graph[p] = nullptr;
+            }
+        d->graph_key = key;
     }
-    if (evp[FG_K_STREAM_COLLIDE]) CK(cudaEventRecord(evp[FG_K_STREAM_COLLIDE][0], d->stream));
-    if (d->staged) {
-        k_stream_collide_staged<S><<<d->staged_grid, K1_THREADS, d->staged_smem, d->stream>>>(
-            gin, gout, d->d_env, d->d_frame, d->n_envs, d->total_groups, d->buf_elems, d->fib, d->stamps,
-            stamp, d->mass_part, d->status);
-    } else {
-        k_stream_collide<S><<<d->total_blocks, K1_THREADS, 0, d->stream>>>(
-            gin, gout, d->d_env, d->d_frame, d->n_envs, d->fib, d->stamps, stamp, d->mass_part);
+    const int p = d->cur;
+    if (!d->graph[p]) {
+        cudaStream_t cs;
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            fg_status st = enqueue_step<S>(d, p, cs, nullptr);
+            e = cudaStreamEndCapture(cs, &g);
+            if (st != FG_OK) {
+                if (g) cudaGraphDestroy(g);
+                cudaStreamDestroy(cs);
+                return st;
+            }
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&d->graph[p], g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return cuda_fail(e, "capturing the step graph");
     }
-    if (evp[FG_K_STREAM_COLLIDE]) CK(cudaEventRecord(evp[FG_K_STREAM_COLLIDE][1], d->stream));
-    if (evp[FG_K_REDUCE]) CK(cudaEventRecord(evp[FG_K_REDUCE][0], d->stream));
-    k_reduce<<<dim3(d->n_envs, RED_ROWS, d->red_z), RED_THREADS, 0, d->stream>>>(
-        d->d_env, d->X, d->Fm, d->dV, d->seg, d->mass_part, d->red_partials, d->red_counters, d->red_z, d->ft,
-        d->mass, d->hist, d->opt.record_history, d->steps, d->status);
-    if (evp[FG_K_REDUCE]) CK(cudaEventRecord(evp[FG_K_REDUCE][1], d->stream));
-    CK(cudaGetLastError());
+    CK(cudaGraphLaunch(d->graph[p], d->stream));
     d->cur ^= 1;
     d->steps += 1;
     return FG_OK;
@@ -338,6 +403,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     fg_options o{};
     o.storage = FG_F32; o.layout = 0; o.deterministic = 0; o.ib_iters = 1; o.record_history = 0;
     o.kernel_variant = FG_KERNEL_AUTO;
+    o.use_graphs = 1;
     if (opt) o = *opt;
     if (o.kernel_variant < FG_KERNEL_AUTO || o.kernel_variant > FG_KERNEL_STAGED)
         return fail(FG_ERR_INVALID, "unknown kernel variant");
@@ -458,19 +524,28 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     DA(d->stamps, stamp_off);
     DA(d->mass_part, (size_t)std::max(block0, group0));
     DA(d->red_counters, (size_t)n_envs * RED_ROWS);
+    DA(d->env_done, (size_t)n_envs);
+    DA(d->d_state, 1);
     DA(d->ft, (size_t)n_envs * FT_ROW);
     DA(d->mass, n_envs);
     if (o.record_history > 0) DA(d->hist, (size_t)n_envs * o.record_history * HIST_ROW);
     DA(d->status, 1);
 #undef DA
     cudaError_t ce;
+    StepState initial_state;
+    initial_state.stamp = 1;
+    initial_state.envs_done = 0;
+    initial_state.step = 0;
     if ((ce = cudaMemsetAsync(d->pop[0], 0, d->pop_elems * d->esize, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->pop[1], 0, d->pop_elems * d->esize, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->fib, 0, sizeof(float) * 3ull * slot_off, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->stamps, 0, sizeof(uint32_t) * stamp_off, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->ft, 0, sizeof(double) * n_envs * FT_ROW, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->status, 0, sizeof(int), d->stream)) != cudaSuccess ||
-        (ce = cudaMemsetAsync(d->red_counters, 0, sizeof(int) * n_envs * RED_ROWS, d->stream)) != cudaSuccess) {
+        (ce = cudaMemsetAsync(d->red_counters, 0, sizeof(int) * n_envs * RED_ROWS, d->stream)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(d->env_done, 0, sizeof(int) * n_envs, d->stream)) != cudaSuccess ||
+        (ce = cudaMemcpyAsync(d->d_state, &initial_state, sizeof(StepState), cudaMemcpyHostToDevice,
+                              d->stream)) != cudaSuccess) {
         st = cuda_fail(ce, "cudaMemsetAsync");
         free_all(d);
         delete d;
@@ -534,6 +609,8 @@ fg_status fg_init_fields(fg_domain* d, int env, const double* rho, const double*
     if (st != FG_OK) return st;
     d->poisoned = false;
     d->steps = 0;
+    const long long zero_step = 0;
+    CK(cudaMemcpyAsync(&d->d_state->step, &zero_step, sizeof(long long), cudaMemcpyHostToDevice, d->stream));
     CK(cudaMemsetAsync(d->status, 0, sizeof(int), d->stream));
     CK(cudaStreamSynchronize(d->stream));
     return FG_OK;
@@ -607,8 +684,11 @@ fg_status fg_step(fg_domain* d, int n_steps, const fg_frame* frames) {
         fg_status st = upload_frames(d);
         if (st != FG_OK) return st;
     }
+    const bool graphs = d->opt.use_graphs && !d->profiling;
     for (int s = 0; s < n_steps; ++s) {
-        fg_status st = dispatch(d->opt.storage, [&](auto tag) { return launch_step<decltype(tag)>(d); });
+        fg_status st = dispatch(d->opt.storage, [&](auto tag) {
+            return graphs ? graph_step<decltype(tag)>(d) : launch_step<decltype(tag)>(d);
+        });
         if (st != FG_OK) return st;
     }
     return FG_OK;

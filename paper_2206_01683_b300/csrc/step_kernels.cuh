@@ -72,6 +72,16 @@ struct FrameDev {
     float pad[3];
 };
 
+// Per-step values kept on the device, so that a captured step can be
+// replayed unchanged: the tile stamp of the current step (never 0), the step
+// number (history row), and a count of environments whose reduction is done.
+// The last block of k_reduce to finish advances stamp and step.
+struct StepState {
+    uint32_t stamp;
+    int envs_done;
+    long long step;
+};
+
 // Environment owning index v: the last e with key(e) <= v.
 template <int (EnvDev::*KEY)>
 __device__ __forceinline__ int env_of(const EnvDev* __restrict__ envs, int n_envs, int v) {
@@ -333,10 +343,11 @@ k_ib(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs,
      const FrameDev* __restrict__ frames, int n_envs, int total_markers,
      const float* __restrict__ X, const float* __restrict__ U, const float* __restrict__ dV,
      float* __restrict__ Fm, float* __restrict__ fib, uint32_t* __restrict__ stamps,
-     uint32_t stamp, int* __restrict__ status) {
+     const StepState* __restrict__ st, int* __restrict__ status) {
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (warp >= total_markers) return;  // whole warp
+    const uint32_t stamp = st->stamp;
     const int e = n_envs > 1 ? env_of<&EnvDev::mk_begin>(envs, n_envs, warp) : 0;
     const EnvDev& E = envs[e];
     const FrameDev F = frames[e];
@@ -444,9 +455,10 @@ template <class S>
 __global__ void __launch_bounds__(K1_THREADS)
 k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __restrict__ gout,
                  const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, int n_envs,
-                 float* __restrict__ fib, const uint32_t* __restrict__ stamps, uint32_t stamp,
+                 float* __restrict__ fib, const uint32_t* __restrict__ stamps, const StepState* __restrict__ st,
                  Pair32* __restrict__ mass_part) {
     __shared__ float wsum[K1_THREADS / 32];
+    const uint32_t stamp = st->stamp;
     const int b = blockIdx.x;
     const int e = n_envs > 1 ? env_of<&EnvDev::block0>(envs, n_envs, b) : 0;
     const EnvDev& E = envs[e];
@@ -516,9 +528,10 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
 k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw* __restrict__ gout,
                         const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, int n_envs,
                         int total_groups, uint32_t buf_elems, float* __restrict__ fib,
-                        const uint32_t* __restrict__ stamps, uint32_t stamp, Pair32* __restrict__ mass_part,
-                        int* __restrict__ status) {
+                        const uint32_t* __restrict__ stamps, const StepState* __restrict__ st,
+                        Pair32* __restrict__ mass_part, int* __restrict__ status) {
     typedef typename S::raw raw;
+    const uint32_t stamp = st->stamp;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     raw* bufs = reinterpret_cast<raw*>(smem_raw);
     __shared__ __align__(8) uint64_t bar[2];
@@ -663,9 +676,9 @@ constexpr int RED_ROWS = MAX_SEG + 2;   // force/torque rows 0..MAX_SEG, then th
 static __global__ void __launch_bounds__(RED_THREADS)
 k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const float* __restrict__ Fm,
          const float* __restrict__ dV, const int* __restrict__ seg, const Pair32* __restrict__ mass_part,
-         Pair32* __restrict__ partials, int* __restrict__ counters, int zmax, double* __restrict__ ft,
-         double* __restrict__ mass, double* __restrict__ hist, int hist_cap, long long hist_row,
-         int* __restrict__ status) {
+         Pair32* __restrict__ partials, int* __restrict__ counters, int* __restrict__ env_done, int n_envs,
+         int zmax, double* __restrict__ ft, double* __restrict__ mass, double* __restrict__ hist, int hist_cap,
+         StepState* __restrict__ st, int* __restrict__ status) {
     __shared__ Pair32 sh[RED_THREADS / 32];
     __shared__ int is_last;
     const int e = blockIdx.x, y = blockIdx.y, z = blockIdx.z, tid = threadIdx.x;
@@ -716,8 +729,6 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    double* hrow = hist_cap > 0 ? hist + ((size_t)e * hist_cap + (size_t)(hist_row % hist_cap)) * HIST_ROW
-                                : nullptr;
     const int w = tid >> 5, lane = tid & 31;
     Pair32 t;
     if (w < ncomp) {
@@ -742,14 +753,30 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
         if (is_mass) {
             v += (double)E.n[0] * E.n[1] * E.n[2];
             mass[e] = v;
-            if (hrow) hrow[FT_ROW] = v;
         } else {
             ft[(size_t)e * FT_ROW + 6 * y + w] = v;
-            if (hrow) hrow[6 * y + w] = v;
         }
         if (!isfinite(v)) atomicOr(status, ST_NUMERIC);
+        __threadfence();
     }
-    if (tid == 0) counters[e * RED_ROWS + y] = 0;   // ready for the next step
+    __syncthreads();
+    if (tid != 0) return;
+    counters[e * RED_ROWS + y] = 0;   // ready for the next step
+    // The last row of environment e to finish records the history row; the
+    // last environment to finish advances the step state.
+    __threadfence();
+    if (atomicAdd(env_done + e, 1) != ns + 1) return;   // rows 0..ns and the mass row
+    env_done[e] = 0;
+    if (hist_cap > 0) {
+        double* h = hist + ((size_t)e * hist_cap + (size_t)(st->step % hist_cap)) * HIST_ROW;
+        for (int k = 0; k < 6 * (ns + 1); ++k) h[k] = __ldcg(ft + (size_t)e * FT_ROW + k);
+        h[FT_ROW] = __ldcg(mass + e);
+    }
+    __threadfence();
+    if (atomicAdd(&st->envs_done, 1) != n_envs - 1) return;
+    st->envs_done = 0;
+    st->step += 1;
+    st->stamp = st->stamp == 0xffffffffu ? 1u : st->stamp + 1u;
 }
 
 // ----------------------------------------------------- state access

@@ -42,7 +42,8 @@ class fg_env_desc(ctypes.Structure):
 class fg_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("layout", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("ib_iters", ctypes.c_int),
-                ("record_history", ctypes.c_int), ("kernel_variant", ctypes.c_int)]
+                ("record_history", ctypes.c_int), ("kernel_variant", ctypes.c_int),
+                ("use_graphs", ctypes.c_int)]
 
 
 class fg_frame(ctypes.Structure):
@@ -204,7 +205,8 @@ def _ptr_and_keep(a, dtype):
 class Domain:
     """Owns one fg_domain (one or many environments)."""
 
-    def __init__(self, envs, storage="f32", record_history=0, stream=None, variant="auto"):
+    def __init__(self, envs, storage="f32", record_history=0, stream=None, variant="auto",
+                 graphs=True):
         self.envs = list(envs)
         opt = fg_options()
         opt.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
@@ -213,6 +215,7 @@ class Domain:
         opt.ib_iters = 1
         opt.record_history = int(record_history)
         opt.kernel_variant = VARIANT[variant] if isinstance(variant, str) else int(variant)
+        opt.use_graphs = 1 if graphs else 0
         self.storage = opt.storage
         self.h = fg_create_domain(self.envs, opt, stream)
         self.nseg = [1] * len(self.envs)
