@@ -133,6 +133,128 @@ def fish_workload(total_steps, shape=(256, 128, 128), length=64.0, n_markers=600
     return fish, X, U, np.array(frames)
 
 
+def _barrier(world):
+    import torch
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+
+def _timed(stream, world, fn, steps):
+    """Milliseconds for fn(n) over the given step indices, CUDA events on the
+    library's stream, barrier + synchronize on both sides."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _barrier(world)
+    e0.record(stream)
+    for n in steps:
+        fn(n)
+    e1.record(stream)
+    _barrier(world)
+    return e0.elapsed_time(e1)
+
+
+def _max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([x], device="cuda", dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t[0])
+
+
+def _kernel_ms(dom, fn, steps):
+    """Mean event-timed duration (ms) of each kernel over the given steps."""
+    from paper_2206_01683_b300 import fishlbm
+    dom.profile(True)
+    for n in steps:
+        fn(n)
+    kms, cnt = dom.profile_read()
+    dom.profile(False)
+    return [kms[k] / max(cnt[k], 1) for k in range(fishlbm.FG_K_COUNT)]
+
+
+def storage_form(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, K, world, peak):
+    """The swimmer-channel step with populations stored as FP16 / BF16."""
+    import torch
+    from paper_2206_01683_b300 import fishlbm
+    stream = torch.cuda.Stream()
+    dom = fishlbm.Domain([fishlbm.env_desc(shape, tau, OPEN_X, (u_in, 0, 0), 1.0, (u_in, 0, 0))],
+                         storage=storage, stream=stream.cuda_stream)
+    dom.set_markers(Xd[0], Ud[0], dVd, segd, n_seg=5, ref=ref)
+
+    def step(n):
+        dom.set_markers(Xd[n], Ud[n], None, None, n_seg=5, ref=ref)
+        dom.step(1, [fr[n]])
+
+    for n in range(W):
+        step(n)
+    ms = _max_over_ranks(_timed(stream, world, step, range(W, W + K)), world)
+    dom.get_body_force_torque()
+    k = _kernel_ms(dom, step, range(W + K, W + 2 * K))
+    ncell = shape[0] * shape[1] * shape[2]
+    gbs = dom.stream_collide_bytes() / (k[1] * 1e-3) / 1e9
+    dom.close()
+    return {"value": round(world * ncell * K / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+            "ms_per_step": round(ms / K, 5), "storage": storage,
+            "roofline": {"bound": "hbm", "kernel": "k_stream_collide", "achieved": round(gbs, 1),
+                         "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+                         "algorithmic_bytes_per_cell": 108, "kernel_ms": round(k[1], 5)}}
+
+
+def batched_form(W, K, world, peak, n_envs=64):
+    """64 independent single-fish environments, grid sizes drawn by seed from
+    {96x64x64, 128x64x64, 160x80x80, 192x96x96}, fish of 0.4 x grid length
+    with 1500-4000 markers and its own wave amplitude and frame trajectory,
+    all advanced by the same launches (one graph replay per step)."""
+    import torch
+    from paper_2206_01683_b300 import fishlbm, inputs
+    draws = inputs.batch_envs(n_envs, inputs.seed_for(4))
+    descs, fishes, trajs = [], [], []
+    for d in draws:
+        shape = d["shape"]
+        descs.append(fishlbm.env_desc(shape, 0.52, OPEN_X, (0.02, 0, 0), 1.0, (0.02, 0, 0)))
+        j = np.arange(1, 5)
+        fishes.append(inputs.fish_for_grid(shape, 0.4 * shape[0], d["n_markers"],
+                                           amplitudes=d["amplitude"] * j / 4.0))
+        trajs.append(inputs.FrameTrajectory(d["frame_seed"], inputs.domain_centre(shape)))
+    T = W + 2 * K
+    ts = np.arange(T)
+    stream = torch.cuda.Stream()
+    dom = fishlbm.Domain(descs, stream=stream.cuda_stream)
+    XU = []
+    for e, f in enumerate(fishes):
+        X, U = f.poses(ts)
+        XU.append((torch.from_numpy(X.astype(np.float32)).cuda(), torch.from_numpy(U.astype(np.float32)).cuda()))
+        ref = tuple(float(v) for v in f.joints_rest[0])
+        dom.set_markers(XU[e][0][0], XU[e][1][0], torch.from_numpy(f.dV.astype(np.float32)).cuda(),
+                        torch.from_numpy(f.seg).cuda(), n_seg=5, ref=ref, env=e)
+    refs = [tuple(float(v) for v in f.joints_rest[0]) for f in fishes]
+    frames = [[fishlbm.frame_from_array(t.at(n)) for t in trajs] for n in range(T)]
+
+    def step(n):
+        for e in range(n_envs):
+            dom.set_markers(XU[e][0][n], XU[e][1][n], None, None, n_seg=5, ref=refs[e], env=e)
+        dom.step(1, frames[n])
+
+    for n in range(W):
+        step(n)
+    ms = _max_over_ranks(_timed(stream, world, step, range(W, W + K)), world)
+    for e in range(n_envs):
+        dom.get_body_force_torque(env=e)
+    k = _kernel_ms(dom, step, range(W + K, W + 2 * K))
+    cells = sum(d["shape"][0] * d["shape"][1] * d["shape"][2] for d in draws)
+    gbs = dom.stream_collide_bytes() / (k[1] * 1e-3) / 1e9
+    dom.close()
+    return {"value": round(world * cells * K / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+            "ms_per_step": round(ms / K, 5), "envs": n_envs, "cells": int(cells),
+            "markers": int(sum(d["n_markers"] for d in draws)),
+            "roofline": {"bound": "hbm", "kernel": "k_stream_collide", "achieved": round(gbs, 1),
+                         "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+                         "kernel_ms": round(k[1], 5), "ib_ms": round(k[0], 5), "reduce_ms": round(k[2], 5)}}
+
+
 def run_ours(args):
     import torch
 
@@ -215,15 +337,22 @@ def run_ours(args):
     barrier()
     e2e_ms = h0.elapsed_time(h1)
 
-    if world > 1:
-        t = torch.tensor([ms, e2e_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
+    ms = _max_over_ranks(ms, world)
+    e2e_ms = _max_over_ranks(e2e_ms, world)
+    peak, peak_kind = measured_peaks()
+    forms = None
+    if not args.no_forms:
+        # every rank runs every form (their barriers and reductions pair up)
+        Kf = min(K, args.form_steps)
+        forms = {
+            "f16": storage_form("f16", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world, peak),
+            "bf16": storage_form("bf16", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world, peak),
+            "batched": batched_form(W, Kf, world, peak),
+        }
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return None
-    peak, peak_kind = measured_peaks()
     achieved = algo_bytes / (k1_ms * 1e-3) / 1e9
     bpc = NCU_TRAFFIC.get(kernel_source_hash())
     mlups = world * ncell * K / (ms * 1e-3) / 1e6
@@ -260,6 +389,11 @@ def run_ours(args):
         "gpu_launches": 3 * K,
         "clocks": clock_info,
     }
+    if forms is not None:
+        line["forms"] = dict(
+            f32={"value": line["value"], "unit": "MLUPS", "ms_per_step": line["ms_per_step"],
+                 "roofline": {"achieved": line["roofline"]["achieved"], "frac": line["roofline"]["frac"],
+                              "algorithmic_bytes_per_cell": 216}}, **forms)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(fish, X, U, frames, shape, tau, u_in, steps=args.cpu_steps)
     if world > 1:
@@ -340,6 +474,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16/batched forms")
+    ap.add_argument("--form-steps", type=int, default=50)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

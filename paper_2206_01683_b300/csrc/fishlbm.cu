@@ -74,7 +74,7 @@ struct fg_domain {
     int total_groups = 0;                // staged kernel row groups
     bool staged = false;                 // stream-collide variant in use
     int staged_grid = 0;                 // persistent blocks of the staged kernel
-    uint32_t buf_elems = 0;              // staged: elements per shared-memory buffer
+    int staged_gc = 256;                 // staged: slots per population in shared memory
     size_t staged_smem = 0;
     float *X = nullptr, *U = nullptr, *dV = nullptr, *Fm = nullptr;
     int* seg = nullptr;
@@ -130,7 +130,19 @@ void set_frame(FrameDev& f, const fg_frame& src) {
         oo += src.omega[a] * src.omega[a];
     }
     f.inv_1pom2 = (float)(1.0 / (1.0 + oo));
-    f.pad[0] = f.pad[1] = f.pad[2] = 0.f;
+    // a0(p) = -acc - domega x r - omega x (omega x r), r = p - origin
+    //       = c0 - M p,  M = [domega]x + omega omega^T - |omega|^2 I,  c0 = -acc + M origin
+    const double* w = src.omega;
+    const double* dw = src.domega;
+    double M[9] = {0.0, -dw[2], dw[1], dw[2], 0.0, -dw[0], -dw[1], dw[0], 0.0};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) M[3 * a + b] += w[a] * w[b] - (a == b ? oo : 0.0);
+    for (int k = 0; k < 9; ++k) f.M[k] = (float)M[k];
+    for (int a = 0; a < 3; ++a) {
+        double c = -src.acc[a];
+        for (int b = 0; b < 3; ++b) c += M[3 * a + b] * src.origin[b];
+        f.c0[a] = (float)c;
+    }
 }
 
 void free_all(fg_domain* d) {
@@ -249,9 +261,14 @@ fg_status enqueue_step(fg_domain* d, int parity, cudaStream_t s, cudaEvent_t* co
     }
     if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][0], s));
     if (d->staged) {
-        k_stream_collide_staged<S><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
-            gin, gout, d->d_env, d->d_frame, d->n_envs, d->total_groups, d->buf_elems, d->fib, d->stamps,
-            d->d_state, d->mass_part, d->status);
+        if (d->staged_gc == 256)
+            k_stream_collide_staged<S, 256><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
+                gin, gout, d->d_env, d->d_frame, d->n_envs, d->total_groups, d->fib, d->stamps, d->d_state,
+                d->mass_part, d->status);
+        else
+            k_stream_collide_staged<S, 512><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
+                gin, gout, d->d_env, d->d_frame, d->n_envs, d->total_groups, d->fib, d->stamps, d->d_state,
+                d->mass_part, d->status);
     } else {
         k_stream_collide<S><<<d->total_blocks, K1_THREADS, 0, s>>>(gin, gout, d->d_env, d->d_frame, d->n_envs,
                                                                    d->fib, d->stamps, d->d_state, d->mass_part);
@@ -351,21 +368,28 @@ fg_status dispatch(int storage, F&& f) {
 
 
 // Shared memory, occupancy and persistent grid of the staged kernel.
+template <class S, int GC>
+fg_status staged_occupancy(fg_domain* d, int* per_sm) {
+    CK(cudaFuncSetAttribute(k_stream_collide_staged<S, GC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)d->staged_smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_stream_collide_staged<S, GC>, K1_THREADS,
+                                                     d->staged_smem));
+    return FG_OK;
+}
+
 fg_status setup_staged(fg_domain* d) {
-    d->staged_smem = 2ull * d->buf_elems * d->esize;
+    d->staged_smem = 2ull * 27 * d->staged_gc * d->esize;
     int dev = 0, sms = 0, per_sm = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    return dispatch(d->opt.storage, [&](auto tag) -> fg_status {
+    fg_status st = dispatch(d->opt.storage, [&](auto tag) -> fg_status {
         typedef decltype(tag) S;
-        CK(cudaFuncSetAttribute(k_stream_collide_staged<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)d->staged_smem));
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_staged<S>, K1_THREADS,
-                                                         d->staged_smem));
-        if (per_sm < 1) return fail(FG_ERR_INVALID, "staged kernel does not fit on an SM");
-        d->staged_grid = std::min(d->total_groups, sms * per_sm);
-        return FG_OK;
+        return d->staged_gc == 256 ? staged_occupancy<S, 256>(d, &per_sm) : staged_occupancy<S, 512>(d, &per_sm);
     });
+    if (st != FG_OK) return st;
+    if (per_sm < 1) return fail(FG_ERR_INVALID, "staged kernel does not fit on an SM");
+    d->staged_grid = std::min(d->total_groups, sms * per_sm);
+    return FG_OK;
 }
 
 size_t env_cells(const fg_domain* d, int env) {
@@ -442,6 +466,9 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     unsigned long long slot_off = 0, stamp_off = 0, ncell_all = 0;
     int block0 = 0, group0 = 0;
     bool can_stage = true;
+    int maxP = 8;
+    for (int e = 0; e < n_envs; ++e) maxP = std::max(maxP, (envs[e].nx + 7) / 8 * 8);
+    d->staged_gc = maxP <= 256 ? 256 : 512;
     for (int e = 0; e < n_envs; ++e) {
         const fg_env_desc& s = envs[e];
         EnvDev& E = d->env[e];
@@ -462,7 +489,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         E.slot_off = slot_off;
         E.block0 = block0;
         E.nblocks = (int)((E.nslot + K1_THREADS - 1) / K1_THREADS);
-        E.rpg = std::max(1, std::min(GROUP_CELLS / E.P, (int)E.rows));
+        E.rpg = std::max(1, std::min(d->staged_gc / E.P, (int)E.rows));
         E.group0 = group0;
         E.ngroups = (int)((E.rows + E.rpg - 1) / E.rpg);
         E.stamp_off = (int)stamp_off;
@@ -482,8 +509,6 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         return fail(FG_ERR_INVALID, "staged kernel needs rows of at most 512 cells");
     }
     d->staged = o.kernel_variant == FG_KERNEL_STAGED || (o.kernel_variant == FG_KERNEL_AUTO && can_stage);
-    for (int e = 0; e < n_envs; ++e)
-        d->buf_elems = std::max<uint32_t>(d->buf_elems, (uint32_t)(27 * d->env[e].rpg * d->env[e].P));
     d->total_groups = group0;
     if (d->staged) {
         fg_status sst = setup_staged(d);

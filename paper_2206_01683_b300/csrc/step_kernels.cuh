@@ -27,7 +27,6 @@
 namespace fl {
 
 constexpr int K1_THREADS = 256;  // threads of either stream-collide kernel
-constexpr int GROUP_CELLS = 256; // target cells (slots) per staged row group
 constexpr int IB_THREADS = 256;  // 8 markers per block
 constexpr int RED_THREADS = 256;
 constexpr int MAX_SEG = 16;
@@ -65,11 +64,16 @@ struct EnvDev {
     double ref[3];            // torque reference point
 };
 
-// Frame motion of one environment (Eq. 3), refreshed by fg_step.
+// Frame motion of one environment (Eq. 3), refreshed by fg_step.  Besides
+// the raw quantities it carries the affine form of the velocity-independent
+// fictitious acceleration, a0(p) = c0 - M p with M = [domega]x +
+// [omega]x [omega]x and c0 = -acc + M origin ([v]x r = v x r), computed on the
+// host, so a cell evaluates it with 9 multiply-adds.
 struct FrameDev {
     float acc[3], om[3], dom[3], org[3];
     float inv_1pom2;          // 1 / (1 + |omega|^2)
-    float pad[3];
+    float M[9];               // row-major
+    float c0[3];
 };
 
 // Per-step values kept on the device, so that a captured step can be
@@ -236,8 +240,12 @@ __device__ __forceinline__ float update_cell(const EnvDev& E, const FrameDev& F,
     const float inv = 1.0f / rho;
     float drout, Jx, Jy, Jz, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz;
     if ((sx | sy | sz) == 0) {
+        // a0 = c0 - M p (the affine form of Eq. 3 without Coriolis)
+        const float px = (float)x, py = (float)y, pz = (float)z;
         float a0[3];
-        frame_accel(F, (float)x, (float)y, (float)z, a0);
+        a0[0] = F.c0[0] - (F.M[0] * px + F.M[1] * py + F.M[2] * pz);
+        a0[1] = F.c0[1] - (F.M[3] * px + F.M[4] * py + F.M[5] * pz);
+        a0[2] = F.c0[2] - (F.M[6] * px + F.M[7] * py + F.M[8] * pz);
         // v = j/rho + a0/2 + fib/(2 rho);  u = (v - w x v + (w.v) w)/(1 + |w|^2)
         const float vx = (m.jx + 0.5f * fx) * inv + 0.5f * a0[0];
         const float vy = (m.jy + 0.5f * fy) * inv + 0.5f * a0[1];
@@ -495,9 +503,10 @@ k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __res
 // (population, row) of the source row it pulls from -- row (y + sy - cy,
 // z + sz - cz), whole rows of P slots -- into shared memory, completing on an
 // mbarrier.  The next group's copies are in flight while the current group
-// is computed from shared memory (two buffers).  Outputs go straight to
-// global memory with coalesced stores.
-template <class S>
+// is computed from shared memory (two buffers).  Shared memory holds each
+// population at a fixed stride of GC slots, so the 27 loads of a cell differ
+// only by immediate offsets.  Outputs go straight to global memory.
+template <class S, int GC>
 __device__ __forceinline__ void issue_group(const EnvDev& E, int g_local, const typename S::raw* __restrict__ gin,
                                             typename S::raw* buf, uint64_t* bar) {
     typedef typename S::raw raw;
@@ -518,24 +527,37 @@ __device__ __forceinline__ void issue_group(const EnvDev& E, int g_local, const 
         ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);   // only periodic axes wrap
         zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
         const raw* src = G + (size_t)i * E.nslot + (size_t)(ys + ny * zs) * E.P;
-        raw* dst = buf + ((size_t)i * E.rpg + r) * E.P;
+        raw* dst = buf + (size_t)i * GC + (size_t)r * E.P;
         bulk_g2s(dst, src, row_bytes, bar);
     }
 }
 
-template <class S>
+// Environment scalars a cell update needs, held in registers while a block
+// works through groups of one environment.
+struct EnvRegs {
+    int nx, ny, P, per_x, per_y, per_z, nz;
+    uint32_t nslot;
+    unsigned long long pop_off;
+    int stamp_off;
+    unsigned long long slot_off;
+    FastDiv div_P, div_ny;
+    int group0, rpg, rows;
+};
+
+template <class S, int GC>
 __global__ void __launch_bounds__(K1_THREADS, 4)
 k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw* __restrict__ gout,
                         const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, int n_envs,
-                        int total_groups, uint32_t buf_elems, float* __restrict__ fib,
-                        const uint32_t* __restrict__ stamps, const StepState* __restrict__ st,
-                        Pair32* __restrict__ mass_part, int* __restrict__ status) {
+                        int total_groups, float* __restrict__ fib, const uint32_t* __restrict__ stamps,
+                        const StepState* __restrict__ st, Pair32* __restrict__ mass_part,
+                        int* __restrict__ status) {
     typedef typename S::raw raw;
-    const uint32_t stamp = st->stamp;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     raw* bufs = reinterpret_cast<raw*>(smem_raw);
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float wsum[2][K1_THREADS / 32];
+    constexpr uint32_t BUF = (uint32_t)Q * GC;
+    const uint32_t stamp = st->stamp;
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -547,14 +569,25 @@ k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw
     int g = blockIdx.x;
     if (g < total_groups && warp == 0) {
         const int e = n_envs > 1 ? env_of<&EnvDev::group0>(envs, n_envs, g) : 0;
-        issue_group<S>(envs[e], g - envs[e].group0, gin, bufs, &bar[0]);
+        issue_group<S, GC>(envs[e], g - envs[e].group0, gin, bufs, &bar[0]);
     }
+    int cur_e = -1;
+    EnvRegs R;
     for (int k = 0; g < total_groups; g += gridDim.x, ++k) {
         const int b = k & 1;
         const int gn = g + gridDim.x;
         if (gn < total_groups && warp == 0) {
             const int en = n_envs > 1 ? env_of<&EnvDev::group0>(envs, n_envs, gn) : 0;
-            issue_group<S>(envs[en], gn - envs[en].group0, gin, bufs + (size_t)(b ^ 1) * buf_elems, &bar[b ^ 1]);
+            issue_group<S, GC>(envs[en], gn - envs[en].group0, gin, bufs + (size_t)(b ^ 1) * BUF, &bar[b ^ 1]);
+        }
+        const int e = n_envs > 1 ? env_of<&EnvDev::group0>(envs, n_envs, g) : 0;
+        if (e != cur_e) {   // block-uniform
+            const EnvDev& E = envs[e];
+            R.nx = E.n[0]; R.ny = E.n[1]; R.nz = E.n[2]; R.P = E.P;
+            R.per_x = E.per[0]; R.per_y = E.per[1]; R.per_z = E.per[2];
+            R.nslot = E.nslot; R.pop_off = E.pop_off; R.stamp_off = E.stamp_off; R.slot_off = E.slot_off;
+            R.div_P = E.div_P; R.div_ny = E.div_ny; R.group0 = E.group0; R.rpg = E.rpg; R.rows = (int)E.rows;
+            cur_e = e;
         }
         const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)(k >> 1) & 1u, WAIT_LIMIT);
         if (__syncthreads_or(!ok)) {
@@ -564,38 +597,41 @@ k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw
             if (gn < total_groups) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)((k + 1) >> 1) & 1u, WAIT_LIMIT);
             return;
         }
-        const int e = n_envs > 1 ? env_of<&EnvDev::group0>(envs, n_envs, g) : 0;
-        const EnvDev& E = envs[e];
-        const FrameDev F = frames[e];
-        const raw* sb = bufs + (size_t)b * buf_elems;
-        const int r0 = (g - E.group0) * E.rpg;
-        const int R = min(E.rpg, (int)E.rows - r0);
-        const int nx = E.n[0], ny = E.n[1];
-        const int span = R * E.P;
+        const raw* sb = bufs + (size_t)b * BUF;
+        const int r0 = (g - R.group0) * R.rpg;
+        const int span = min(R.rpg, R.rows - r0) * R.P;
         float drsum = 0.f;
         for (int t = threadIdx.x; t < span; t += K1_THREADS) {
-            const int r = (int)fdiv((uint32_t)t, E.div_P);
-            const int x = t - r * E.P;
-            if (x >= nx) continue;
+            const int r = (int)fdiv((uint32_t)t, R.div_P);
+            const int x = t - r * R.P;
+            if (x >= R.nx) continue;
             const int row = r0 + r;
-            const int z = (int)fdiv((uint32_t)row, E.div_ny);
-            const int y = row - z * ny;
-            const uint32_t slot = (uint32_t)row * (uint32_t)E.P + (uint32_t)x;
-            float fx, fy, fz;
-            take_ib_force(E, fib, stamps, stamp, slot, fx, fy, fz);
-            const int sx = inward(E, 0, x), sy = inward(E, 1, y), sz = inward(E, 2, z);
+            const int z = (int)fdiv((uint32_t)row, R.div_ny);
+            const int y = row - z * R.ny;
+            const uint32_t slot = (uint32_t)row * (uint32_t)R.P + (uint32_t)x;
+            // IB force density of a stamped tile (cleared after use)
+            float fx = 0.f, fy = 0.f, fz = 0.f;
+            if (__ldg(stamps + R.stamp_off + (slot >> 5)) == stamp) {
+                float* fb = fib + 3ull * R.slot_off + slot;
+                fx = fb[0]; fy = fb[R.nslot]; fz = fb[2ull * R.nslot];
+                fb[0] = 0.f; fb[R.nslot] = 0.f; fb[2ull * R.nslot] = 0.f;
+            }
+            const int sx = R.per_x ? 0 : (x == 0 ? 1 : (x == R.nx - 1 ? -1 : 0));
+            const int sy = R.per_y ? 0 : (y == 0 ? 1 : (y == R.ny - 1 ? -1 : 0));
+            const int sz = R.per_z ? 0 : (z == 0 ? 1 : (z == R.nz - 1 ? -1 : 0));
             const int xs = x + sx;
-            const int xm = xs == 0 ? nx - 1 : xs - 1;      // source of c_x = +1
-            const int xp = xs == nx - 1 ? 0 : xs + 1;      // source of c_x = -1
+            const int xm = xs == 0 ? R.nx - 1 : xs - 1;      // source of c_x = +1
+            const int xp = xs == R.nx - 1 ? 0 : xs + 1;      // source of c_x = -1
+            const raw* rb = sb + r * R.P;
             float gv[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const int xi = cx(i) == 1 ? xm : (cx(i) == -1 ? xp : xs);
-                gv[i] = S::decode(sb[((size_t)i * E.rpg + r) * E.P + xi], i);
+                gv[i] = S::decode(rb[i * GC + xi], i);
             }
             Moments m = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             accumulate<true>(m, gv);
-            drsum += update_cell<S>(E, F, m, x, y, z, sx, sy, sz, fx, fy, fz, gout + E.pop_off, slot);
+            drsum += update_cell<S>(envs[e], frames[e], m, x, y, z, sx, sy, sz, fx, fy, fz, gout + R.pop_off, slot);
         }
 #pragma unroll
         for (int s = 16; s >= 1; s >>= 1) drsum += __shfl_xor_sync(0xffffffffu, drsum, s);

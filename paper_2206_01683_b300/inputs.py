@@ -162,6 +162,47 @@ class Fish:
         return X, U
 
 
+    def poses(self, ts):
+        """Marker positions and velocities for many times at once:
+        X, U of shape (len(ts), n, 3), float64."""
+        ts = np.asarray(ts, dtype=np.float64)
+        T = ts.size
+        w = 2.0 * math.pi / self.period
+        th = self.A[None, :] * np.sin(w * ts[:, None] - self.phi[None, :])          # (T, 4)
+        dth = self.A[None, :] * w * np.cos(w * ts[:, None] - self.phi[None, :])
+        ang = np.concatenate([np.zeros((T, 1)), np.cumsum(th, axis=1)], axis=1)    # (T, 5)
+        c, s = np.cos(ang), np.sin(ang)
+        trans = np.zeros((T, N_SEGMENTS, 2))
+        joint_world = np.zeros((T, N_SEGMENTS - 1, 2))
+        for k in range(1, N_SEGMENTS):
+            Pk = self.joints_rest[k - 1, :2]
+            cp, sp = c[:, k - 1], s[:, k - 1]
+            jw = np.stack([cp * Pk[0] - sp * Pk[1], sp * Pk[0] + cp * Pk[1]], axis=1) + trans[:, k - 1]
+            joint_world[:, k - 1] = jw
+            ck, sk = c[:, k], s[:, k]
+            trans[:, k] = jw - np.stack([ck * Pk[0] - sk * Pk[1], sk * Pk[0] + ck * Pk[1]], axis=1)
+        p = self.rest[:, :2]
+        X = np.zeros((T, self.n, 3))
+        U = np.zeros((T, self.n, 3))
+        X[:, :, 2] = self.rest[None, :, 2]
+        for k in range(N_SEGMENTS):
+            qx = c[:, k, None] * p[None, :, 0] - s[:, k, None] * p[None, :, 1] + trans[:, k, None, 0]
+            qy = s[:, k, None] * p[None, :, 0] + c[:, k, None] * p[None, :, 1] + trans[:, k, None, 1]
+            vx = np.zeros_like(qx)
+            vy = np.zeros_like(qy)
+            for jj in range(1, k + 1):
+                dx = qx - joint_world[:, jj - 1, None, 0]
+                dy = qy - joint_world[:, jj - 1, None, 1]
+                vx += -dth[:, jj - 1, None] * dy
+                vy += dth[:, jj - 1, None] * dx
+            wk = self.W[None, :, k]
+            X[:, :, 0] += wk * qx
+            X[:, :, 1] += wk * qy
+            U[:, :, 0] += wk * vx
+            U[:, :, 1] += wk * vy
+        return X, U
+
+
 def fish_for_grid(shape, length, n_markers, amplitudes=None, phases=None):
     """Fish with its head tip at x = nx/4, centred in y and z."""
     nx, ny, nz = shape
