@@ -40,6 +40,9 @@ fg_status cuda_fail(cudaError_t e, const char* what) {
 
 constexpr int PROFILE_CAP = 1 << 14;
 constexpr int MAX_STAGED_P = 512;   // longest row pitch the staged kernel takes
+#ifndef STAGED_MINB
+#define STAGED_MINB 4                // resident blocks per SM the staged kernel is compiled for
+#endif
 
 struct MarkerRegion {
     int n = 0, cap = 0, off = 0, nseg = 1;
@@ -262,11 +265,11 @@ fg_status enqueue_step(fg_domain* d, int parity, cudaStream_t s, cudaEvent_t* co
     if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][0], s));
     if (d->staged) {
         if (d->staged_gc == 256)
-            k_stream_collide_staged<S, 256><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
+            k_stream_collide_staged<S, 256, STAGED_MINB><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
                 gin, gout, d->d_env, d->d_frame, d->n_envs, d->total_groups, d->fib, d->stamps, d->d_state,
                 d->mass_part, d->status);
         else
-            k_stream_collide_staged<S, 512><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
+            k_stream_collide_staged<S, 512, STAGED_MINB><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
                 gin, gout, d->d_env, d->d_frame, d->n_envs, d->total_groups, d->fib, d->stamps, d->d_state,
                 d->mass_part, d->status);
     } else {
@@ -370,10 +373,10 @@ fg_status dispatch(int storage, F&& f) {
 // Shared memory, occupancy and persistent grid of the staged kernel.
 template <class S, int GC>
 fg_status staged_occupancy(fg_domain* d, int* per_sm) {
-    CK(cudaFuncSetAttribute(k_stream_collide_staged<S, GC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)d->staged_smem));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_stream_collide_staged<S, GC>, K1_THREADS,
-                                                     d->staged_smem));
+    CK(cudaFuncSetAttribute(k_stream_collide_staged<S, GC, STAGED_MINB>,
+                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->staged_smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_stream_collide_staged<S, GC, STAGED_MINB>,
+                                                     K1_THREADS, d->staged_smem));
     return FG_OK;
 }
 

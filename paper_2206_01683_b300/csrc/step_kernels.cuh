@@ -225,6 +225,39 @@ struct Pair32 {
     }
 };
 
+// Constants of the cell update for one environment and step, gathered so a
+// kernel can hold them in registers instead of re-reading them per cell.
+struct CellConsts {
+    float keep, guo, drho_out;
+    float u_in[3];
+    int bc;                   // 2 bits per face, faces -x,+x,-y,+y,-z,+z
+    float om[3], inv_1pom2;
+    float c0[3], M[9];
+    uint32_t nslot;
+};
+
+__device__ __forceinline__ CellConsts load_consts(const EnvDev& E, const FrameDev& F) {
+    CellConsts C;
+    C.keep = E.keep; C.guo = E.guo; C.drho_out = E.drho_out;
+    int bc = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) bc |= (E.bc[k] & 3) << (2 * k);
+    C.bc = bc;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        C.u_in[a] = E.u_in[a];
+        C.om[a] = F.om[a];
+        C.c0[a] = F.c0[a];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) C.M[k] = F.M[k];
+    C.inv_1pom2 = F.inv_1pom2;
+    C.nslot = E.nslot;
+    return C;
+}
+
+__device__ __forceinline__ int face_kind(int bc, int face) { return (bc >> (2 * face)) & 3; }
+
 // ------------------------------------------------ the per-cell update
 
 // Collision (interior) or open-face rule (boundary) from the pulled moments
@@ -232,8 +265,8 @@ struct Pair32 {
 // inward normal of the non-periodic faces the cell lies on (0 for interior
 // cells).  Returns rho_out - 1 for the mass sum.
 template <class S>
-__device__ __forceinline__ float update_cell(const EnvDev& E, const FrameDev& F, const Moments& m, int x, int y,
-                                             int z, int sx, int sy, int sz, float fx, float fy, float fz,
+__device__ __forceinline__ float update_cell(const CellConsts& F, const Moments& m, int x, int y, int z, int sx,
+                                             int sy, int sz, float fx, float fy, float fz,
                                              typename S::raw* __restrict__ Go, uint32_t slot) {
     const float cs2 = 1.0f / 3.0f;
     const float rho = 1.0f + m.dr;
@@ -261,7 +294,7 @@ __device__ __forceinline__ float update_cell(const EnvDev& E, const FrameDev& F,
         Jx = m.jx + Gx; Jy = m.jy + Gy; Jz = m.jz + Gz;
         // Q = Pi* - rho cs2 I = rho u u + (1 - 1/tau)(Pi - Pi_eq) + (1 - 1/(2tau))(u G + G u),
         // with Pi - Pi_eq = s - dr cs2 I - rho u u
-        const float k = E.keep, gq = E.guo;
+        const float k = F.keep, gq = F.guo;
         const float ruxx = rho * ux * ux, ruyy = rho * uy * uy, ruzz = rho * uz * uz;
         const float ruxy = rho * ux * uy, ruxz = rho * ux * uz, ruyz = rho * uy * uz;
         Qxx = ruxx + k * (m.sxx - m.dr * cs2 - ruxx) + gq * 2.0f * ux * Gx;
@@ -277,20 +310,20 @@ __device__ __forceinline__ float update_cell(const EnvDev& E, const FrameDev& F,
         const float ufx = m.jx * inv, ufy = m.jy * inv, ufz = m.jz * inv;
         const int gov = sx != 0 ? 0 : (sy != 0 ? 1 : 2);
         const int gs = gov == 0 ? sx : (gov == 1 ? sy : sz);
-        const int kind = E.bc[2 * gov + (gs < 0 ? 1 : 0)];
+        const int kind = face_kind(F.bc, 2 * gov + (gs < 0 ? 1 : 0));
         float ubx = ufx, uby = ufy, ubz = ufz;
         drout = m.dr;
         if (kind == BC_VELOCITY) {
-            ubx = E.u_in[0]; uby = E.u_in[1]; ubz = E.u_in[2];
+            ubx = F.u_in[0]; uby = F.u_in[1]; ubz = F.u_in[2];
         } else if (kind == BC_OUTFLOW) {
-            drout = E.drho_out;
+            drout = F.drho_out;
         } else {
-            if (sx != 0 && E.bc[sx < 0 ? 1 : 0] == BC_FREESLIP) ubx = 0.f;
-            if (sy != 0 && E.bc[sy < 0 ? 3 : 2] == BC_FREESLIP) uby = 0.f;
-            if (sz != 0 && E.bc[sz < 0 ? 5 : 4] == BC_FREESLIP) ubz = 0.f;
+            if (sx != 0 && face_kind(F.bc, sx < 0 ? 1 : 0) == BC_FREESLIP) ubx = 0.f;
+            if (sy != 0 && face_kind(F.bc, sy < 0 ? 3 : 2) == BC_FREESLIP) uby = 0.f;
+            if (sz != 0 && face_kind(F.bc, sz < 0 ? 5 : 4) == BC_FREESLIP) ubz = 0.f;
         }
         const float rb = 1.0f + drout;
-        const float k = E.keep;
+        const float k = F.keep;
         Jx = rb * ubx; Jy = rb * uby; Jz = rb * ubz;
         Qxx = rb * ubx * ubx + k * (m.sxx - m.dr * cs2 - rho * ufx * ufx);
         Qyy = rb * uby * uby + k * (m.syy - m.dr * cs2 - rho * ufy * ufy);
@@ -299,25 +332,30 @@ __device__ __forceinline__ float update_cell(const EnvDev& E, const FrameDev& F,
         Qxz = rb * ubx * ubz + k * (m.sxz - rho * ufx * ufz);
         Qyz = rb * uby * ubz + k * (m.syz - rho * ufy * ufz);
     }
-    // Hermite-2 rebuild of the deviation: g*_i = w_i [dr + 3 c.J + 4.5 c c : Q - 1.5 tr Q]
-    const float A = drout - 1.5f * (Qxx + Qyy + Qzz);
-    const float dxx = 4.5f * Qxx, dyy = 4.5f * Qyy, dzz = 4.5f * Qzz;
-    const float oxy = 9.0f * Qxy, oxz = 9.0f * Qxz, oyz = 9.0f * Qyz;
-    const float tx = 3.0f * Jx, ty = 3.0f * Jy, tz = 3.0f * Jz;
+    // Hermite-2 rebuild of the deviation: g*_i = w_i [dr + 3 c.J + 4.5 c c : Q - 1.5 tr Q],
+    // organised by x-lines (cy, cz):  v(cx) = E + cx^2 dxx + O + cx B  with
+    //   E = A + cy^2 dyy + cz^2 dzz + cy cz oyz,  O = cy ty + cz tz,  B = tx + cy oxy + cz oxz.
+    const float sc = S::POLY;
+    const float A = sc * (drout - 1.5f * (Qxx + Qyy + Qzz));
+    const float dxx = sc * 4.5f * Qxx, dyy = sc * 4.5f * Qyy, dzz = sc * 4.5f * Qzz;
+    const float oxy = sc * 9.0f * Qxy, oxz = sc * 9.0f * Qxz, oyz = sc * 9.0f * Qyz;
+    const float tx = sc * 3.0f * Jx, ty = sc * 3.0f * Jy, tz = sc * 3.0f * Jz;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        float even = A;
-        if (cx(i) != 0) even += dxx;
-        if (cy(i) != 0) even += dyy;
-        if (cz(i) != 0) even += dzz;
-        if (cx(i) * cy(i) == 1) even += oxy; else if (cx(i) * cy(i) == -1) even -= oxy;
-        if (cx(i) * cz(i) == 1) even += oxz; else if (cx(i) * cz(i) == -1) even -= oxz;
-        if (cy(i) * cz(i) == 1) even += oyz; else if (cy(i) * cz(i) == -1) even -= oyz;
-        float odd = 0.0f;
-        if (cx(i) == 1) odd += tx; else if (cx(i) == -1) odd -= tx;
-        if (cy(i) == 1) odd += ty; else if (cy(i) == -1) odd -= ty;
-        if (cz(i) == 1) odd += tz; else if (cz(i) == -1) odd -= tz;
-        S::store(Go + (size_t)i * E.nslot + slot, wf(i) * (even + odd), i);
+    for (int l = 0; l < 9; ++l) {
+        const int ly = l % 3 - 1, lz = l / 3 - 1;      // this line's cy, cz
+        float E = A, O = 0.0f, B = tx;
+        if (ly != 0) E += dyy;
+        if (lz != 0) E += dzz;
+        if (ly * lz == 1) E += oyz; else if (ly * lz == -1) E -= oyz;
+        if (ly == 1) O += ty; else if (ly == -1) O -= ty;
+        if (lz == 1) O += tz; else if (lz == -1) O -= tz;
+        if (ly == 1) B += oxy; else if (ly == -1) B -= oxy;
+        if (lz == 1) B += oxz; else if (lz == -1) B -= oxz;
+        const float v0 = E + O;
+        const float v1 = v0 + dxx;
+        S::emit(Go + (size_t)(3 * l + 1) * F.nslot + slot, v0, 3 * l + 1);   // cx = 0
+        S::emit(Go + (size_t)(3 * l + 2) * F.nslot + slot, v1 + B, 3 * l + 2); // cx = +1
+        S::emit(Go + (size_t)(3 * l) * F.nslot + slot, v1 - B, 3 * l);        // cx = -1
     }
     return drout;
 }
@@ -487,7 +525,7 @@ k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __res
             const uint32_t p = (uint32_t)((int)c + sx + (sy + sz * E.n[1]) * E.P);
             const PullOffsets o = pull_offsets(E, px, py, pz);
             const Moments m = pull_moments<S, true>(gin + E.pop_off, E.nslot, p, o);
-            drout = update_cell<S>(E, frames[e], m, x, y, z, sx, sy, sz, fx, fy, fz, gout + E.pop_off, c);
+            drout = update_cell<S>(load_consts(E, frames[e]), m, x, y, z, sx, sy, sz, fx, fy, fz, gout + E.pop_off, c);
         }
     }
     const float t = block_sum_f32(drout, wsum);
@@ -544,8 +582,8 @@ struct EnvRegs {
     int group0, rpg, rows;
 };
 
-template <class S, int GC>
-__global__ void __launch_bounds__(K1_THREADS, 4)
+template <class S, int GC, int MINB>
+__global__ void __launch_bounds__(K1_THREADS, MINB)
 k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw* __restrict__ gout,
                         const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, int n_envs,
                         int total_groups, float* __restrict__ fib, const uint32_t* __restrict__ stamps,
@@ -573,6 +611,7 @@ k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw
     }
     int cur_e = -1;
     EnvRegs R;
+    __shared__ CellConsts C;   // constants of the environment in hand, read by every cell
     for (int k = 0; g < total_groups; g += gridDim.x, ++k) {
         const int b = k & 1;
         const int gn = g + gridDim.x;
@@ -587,6 +626,9 @@ k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw
             R.per_x = E.per[0]; R.per_y = E.per[1]; R.per_z = E.per[2];
             R.nslot = E.nslot; R.pop_off = E.pop_off; R.stamp_off = E.stamp_off; R.slot_off = E.slot_off;
             R.div_P = E.div_P; R.div_ny = E.div_ny; R.group0 = E.group0; R.rpg = E.rpg; R.rows = (int)E.rows;
+            __syncthreads();   // previous environment's constants no longer in use
+            if (threadIdx.x == 0) C = load_consts(E, frames[e]);
+            __syncthreads();
             cur_e = e;
         }
         const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)(k >> 1) & 1u, WAIT_LIMIT);
@@ -631,7 +673,7 @@ k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw
             }
             Moments m = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             accumulate<true>(m, gv);
-            drsum += update_cell<S>(envs[e], frames[e], m, x, y, z, sx, sy, sz, fx, fy, fz, gout + R.pop_off, slot);
+            drsum += update_cell<S>(C, m, x, y, z, sx, sy, sz, fx, fy, fz, gout + R.pop_off, slot);
         }
 #pragma unroll
         for (int s = 16; s >= 1; s >>= 1) drsum += __shfl_xor_sync(0xffffffffu, drsum, s);
