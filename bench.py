@@ -181,7 +181,7 @@ def storage_form(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W,
     from paper_2206_01683_b300 import fishlbm
     stream = torch.cuda.Stream()
     dom = fishlbm.Domain([fishlbm.env_desc(shape, tau, OPEN_X, (u_in, 0, 0), 1.0, (u_in, 0, 0))],
-                         storage=storage, stream=stream.cuda_stream)
+                         storage=storage, stream=stream.cuda_stream, autotune=True)
     dom.set_markers(Xd[0], Ud[0], dVd, segd, n_seg=5, ref=ref)
 
     def step(n):
@@ -195,9 +195,10 @@ def storage_form(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W,
     k = _kernel_ms(dom, step, range(W + K, W + 2 * K))
     ncell = shape[0] * shape[1] * shape[2]
     gbs = dom.stream_collide_bytes() / (k[1] * 1e-3) / 1e9
+    variant = dom.stream_collide_variant()
     dom.close()
     return {"value": round(world * ncell * K / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
-            "ms_per_step": round(ms / K, 5), "storage": storage,
+            "ms_per_step": round(ms / K, 5), "storage": storage, "kernel_variant": variant,
             "roofline": {"bound": "hbm", "kernel": "k_stream_collide", "achieved": round(gbs, 1),
                          "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
                          "algorithmic_bytes_per_cell": 108, "kernel_ms": round(k[1], 5)}}
@@ -222,7 +223,7 @@ def batched_form(W, K, world, peak, n_envs=64):
     T = W + 2 * K
     ts = np.arange(T)
     stream = torch.cuda.Stream()
-    dom = fishlbm.Domain(descs, stream=stream.cuda_stream)
+    dom = fishlbm.Domain(descs, stream=stream.cuda_stream, autotune=True)
     XU = []
     for e, f in enumerate(fishes):
         X, U = f.poses(ts)
@@ -246,9 +247,10 @@ def batched_form(W, K, world, peak, n_envs=64):
     k = _kernel_ms(dom, step, range(W + K, W + 2 * K))
     cells = sum(d["shape"][0] * d["shape"][1] * d["shape"][2] for d in draws)
     gbs = dom.stream_collide_bytes() / (k[1] * 1e-3) / 1e9
+    variant = dom.stream_collide_variant()
     dom.close()
     return {"value": round(world * cells * K / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
-            "ms_per_step": round(ms / K, 5), "envs": n_envs, "cells": int(cells),
+            "ms_per_step": round(ms / K, 5), "envs": n_envs, "cells": int(cells), "kernel_variant": variant,
             "markers": int(sum(d["n_markers"] for d in draws)),
             "roofline": {"bound": "hbm", "kernel": "k_stream_collide", "achieved": round(gbs, 1),
                          "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
@@ -273,7 +275,7 @@ def run_ours(args):
     fr = [fishlbm.frame_from_array(f) for f in frames]
     stream = torch.cuda.Stream()
     dom = fishlbm.Domain([fishlbm.env_desc(shape, tau, OPEN_X, (u_in, 0, 0), 1.0, (u_in, 0, 0))],
-                         stream=stream.cuda_stream)
+                         stream=stream.cuda_stream, autotune=True)
     Xd = torch.from_numpy(X).cuda()
     Ud = torch.from_numpy(U).cuda()
     dVd = torch.from_numpy(fish.dV.astype(np.float32)).cuda()
@@ -376,7 +378,8 @@ def run_ours(args):
                    "markers": int(X.shape[1]), "segments": 5, "storage": "f32",
                    "frame": "seeded accelerating + rotating (Eq. 3)",
                    "l2": "inputs exceed L2 (populations 453 MB per buffer, 2 buffers)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "kernel_variant": dom.stream_collide_variant()},
         "roofline": {"bound": "hbm", "kernel": "k_stream_collide", "achieved": round(achieved, 1),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),

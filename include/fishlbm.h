@@ -65,10 +65,12 @@ typedef struct {
 } fg_env_desc;
 
 /* Stream-collide kernel: AUTO picks STAGED when every row has at most 512
- * cells, else PLAIN.  STAGED stages the source rows of each row group in
- * shared memory with bulk copies (persistent, double-buffered); PLAIN reads
- * global memory directly, one thread per cell.  Both compute the same step. */
-typedef enum { FG_KERNEL_AUTO = 0, FG_KERNEL_PLAIN = 1, FG_KERNEL_STAGED = 2 } fg_kernel_variant;
+ * cells, else PLAIN (and with the autotune option, the fastest candidate).
+ * STAGED stages the source rows of each row group in shared memory with bulk
+ * copies (persistent, double-buffered), 256 slots per population when rows
+ * fit, else 512; STAGED512 forces 512.  PLAIN reads global memory directly,
+ * one thread per cell.  All compute the same step. */
+typedef enum { FG_KERNEL_AUTO = 0, FG_KERNEL_PLAIN = 1, FG_KERNEL_STAGED = 2, FG_KERNEL_STAGED512 = 3 } fg_kernel_variant;
 
 typedef struct {
     int storage;        /* fg_storage */
@@ -78,6 +80,7 @@ typedef struct {
     int record_history; /* steps of (force, torque, mass) history kept on the
                            device per environment (0 = none), ring buffer */
     int kernel_variant; /* fg_kernel_variant */
+    int autotune;       /* 1 (with kernel_variant AUTO): run fg_autotune at creation */
     int use_graphs;     /* 1: each step is replayed from a captured CUDA graph
                            (captured on first use and whenever the marker count or
                            marker storage changes); 0: direct launches.  Steps taken
@@ -200,6 +203,19 @@ fg_status fg_profile(fg_domain* d, int enable);
 /* Sum of the recorded kernel durations (ms) and launch counts per kernel id
  * since fg_profile(d, 1) or the previous read; clears them.  Synchronises. */
 fg_status fg_profile_read(fg_domain* d, double* ms, long long* launches);
+
+/* Stream-collide variants (the autotuner's candidates). */
+enum { FG_K1_PLAIN = 0, FG_K1_STAGED256 = 1, FG_K1_STAGED512 = 2, FG_K1_NVARIANTS = 3 };
+
+/* Time every stream-collide variant that can run this domain's rows (a few
+ * launches each, on the domain's own buffers: the state is not changed) and
+ * keep the fastest.  choice (nullable) gets the FG_K1_* kept; ms (nullable,
+ * FG_K1_NVARIANTS entries) the mean launch time of each, -1 where not
+ * runnable.  Synchronises; graphs are recaptured on the next step. */
+fg_status fg_autotune(fg_domain* d, int* choice, double* ms);
+
+/* The FG_K1_* variant in use. */
+fg_status fg_stream_collide_variant(fg_domain* d, int* variant);
 
 /* Algorithmic bytes one launch of the stream-collide kernel moves: 27 reads
  * and 27 writes of a population per cell of every environment. */

@@ -40,9 +40,11 @@ fg_status cuda_fail(cudaError_t e, const char* what) {
 
 constexpr int PROFILE_CAP = 1 << 14;
 constexpr int MAX_STAGED_P = 512;   // longest row pitch the staged kernel takes
-#ifndef STAGED_MINB
-#define STAGED_MINB 4                // resident blocks per SM the staged kernel is compiled for
-#endif
+
+// Stream-collide variants the domain can run (and the autotuner times):
+// the plain kernel, and the staged kernel with 256 or 512 slots per
+// population in shared memory (compiled for 4 and 2 resident blocks per SM).
+enum { K1_PLAIN = 0, K1_STAGED256 = 1, K1_STAGED512 = 2, K1_NVARIANTS = 3 };
 
 struct MarkerRegion {
     int n = 0, cap = 0, off = 0, nseg = 1;
@@ -75,10 +77,13 @@ struct fg_domain {
     int red_z = 1;                       // chunks per row of k_reduce
     int total_blocks = 0;                // plain stream-collide grid
     int total_groups = 0;                // staged kernel row groups
-    bool staged = false;                 // stream-collide variant in use
+    int k1 = K1_PLAIN;                   // stream-collide variant in use (K1_*)
+    bool staged = false;                 // k1 != K1_PLAIN
     int staged_grid = 0;                 // persistent blocks of the staged kernel
     int staged_gc = 256;                 // staged: slots per population in shared memory
     size_t staged_smem = 0;
+    size_t mass_part_cap = 0;
+    int max_P = 8;
     float *X = nullptr, *U = nullptr, *dV = nullptr, *Fm = nullptr;
     int* seg = nullptr;
     int marker_slots = 0;                // allocated marker slots
@@ -247,6 +252,23 @@ void refresh_marker_table(fg_domain* d) {
     d->total_markers = begin;
 }
 
+// The stream-collide launch of the variant in use (gin -> gout).
+template <class S>
+void enqueue_k1(fg_domain* d, const typename S::raw* gin, typename S::raw* gout, cudaStream_t s) {
+    if (d->k1 == K1_STAGED256) {
+        k_stream_collide_staged<S, 256, 4><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
+            gin, gout, d->d_env, d->d_frame, d->n_envs, d->total_groups, d->fib, d->stamps, d->d_state,
+            d->mass_part, d->status);
+    } else if (d->k1 == K1_STAGED512) {
+        k_stream_collide_staged<S, 512, 2><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
+            gin, gout, d->d_env, d->d_frame, d->n_envs, d->total_groups, d->fib, d->stamps, d->d_state,
+            d->mass_part, d->status);
+    } else {
+        k_stream_collide<S><<<d->total_blocks, K1_THREADS, 0, s>>>(gin, gout, d->d_env, d->d_frame, d->n_envs,
+                                                                   d->fib, d->stamps, d->d_state, d->mass_part);
+    }
+}
+
 // Launch the kernels of one step reading buffer `parity` on stream s; with
 // ev != nullptr an event pair is recorded around each kernel.
 template <class S>
@@ -263,19 +285,7 @@ fg_status enqueue_step(fg_domain* d, int parity, cudaStream_t s, cudaEvent_t* co
         if (ev) CK(cudaEventRecord(ev[FG_K_IB][1], s));
     }
     if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][0], s));
-    if (d->staged) {
-        if (d->staged_gc == 256)
-            k_stream_collide_staged<S, 256, STAGED_MINB><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
-                gin, gout, d->d_env, d->d_frame, d->n_envs, d->total_groups, d->fib, d->stamps, d->d_state,
-                d->mass_part, d->status);
-        else
-            k_stream_collide_staged<S, 512, STAGED_MINB><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
-                gin, gout, d->d_env, d->d_frame, d->n_envs, d->total_groups, d->fib, d->stamps, d->d_state,
-                d->mass_part, d->status);
-    } else {
-        k_stream_collide<S><<<d->total_blocks, K1_THREADS, 0, s>>>(gin, gout, d->d_env, d->d_frame, d->n_envs,
-                                                                   d->fib, d->stamps, d->d_state, d->mass_part);
-    }
+    enqueue_k1<S>(d, gin, gout, s);
     if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][1], s));
     if (ev) CK(cudaEventRecord(ev[FG_K_REDUCE][0], s));
     k_reduce<<<dim3(d->n_envs, RED_ROWS, d->red_z), RED_THREADS, 0, s>>>(
@@ -371,28 +381,75 @@ fg_status dispatch(int storage, F&& f) {
 
 
 // Shared memory, occupancy and persistent grid of the staged kernel.
-template <class S, int GC>
+template <class S, int GC, int MINB>
 fg_status staged_occupancy(fg_domain* d, int* per_sm) {
-    CK(cudaFuncSetAttribute(k_stream_collide_staged<S, GC, STAGED_MINB>,
-                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->staged_smem));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_stream_collide_staged<S, GC, STAGED_MINB>,
-                                                     K1_THREADS, d->staged_smem));
+    CK(cudaFuncSetAttribute(k_stream_collide_staged<S, GC, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)d->staged_smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_stream_collide_staged<S, GC, MINB>, K1_THREADS,
+                                                     d->staged_smem));
     return FG_OK;
 }
 
-fg_status setup_staged(fg_domain* d) {
-    d->staged_smem = 2ull * 27 * d->staged_gc * d->esize;
-    int dev = 0, sms = 0, per_sm = 0;
-    CK(cudaGetDevice(&dev));
-    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    fg_status st = dispatch(d->opt.storage, [&](auto tag) -> fg_status {
-        typedef decltype(tag) S;
-        return d->staged_gc == 256 ? staged_occupancy<S, 256>(d, &per_sm) : staged_occupancy<S, 512>(d, &per_sm);
-    });
+bool k1_runnable(const fg_domain* d, int v) {
+    if (v == K1_PLAIN) return true;
+    if (v == K1_STAGED256) return d->max_P <= 256;
+    return v == K1_STAGED512 && d->max_P <= 512;
+}
+
+// Select the stream-collide variant: row groups, mass partials, persistent
+// grid and shared memory follow from it.  With allocate, grows the buffers
+// that depend on it and uploads the environment table (graphs are rebuilt).
+fg_status configure_k1(fg_domain* d, int v, bool allocate) {
+    if (!k1_runnable(d, v)) return fail(FG_ERR_INVALID, "stream-collide variant cannot run these rows");
+    d->k1 = v;
+    d->staged = v != K1_PLAIN;
+    d->staged_gc = v == K1_STAGED512 ? 512 : 256;
+    int group0 = 0;
+    for (int e = 0; e < d->n_envs; ++e) {
+        EnvDev& E = d->env[e];
+        E.rpg = std::max(1, std::min(d->staged_gc / E.P, (int)E.rows));
+        E.group0 = group0;
+        E.ngroups = (int)((E.rows + E.rpg - 1) / E.rpg);
+        group0 += E.ngroups;
+        // one mass partial per row group (staged) or per block (plain)
+        E.part0 = d->staged ? E.group0 : E.block0;
+        E.nparts = d->staged ? E.ngroups : E.nblocks;
+    }
+    d->total_groups = group0;
+    if (d->staged) {
+        d->staged_smem = 2ull * 27 * d->staged_gc * d->esize;
+        int dev = 0, sms = 0, per_sm = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        fg_status st = dispatch(d->opt.storage, [&](auto tag) -> fg_status {
+            typedef decltype(tag) S;
+            return v == K1_STAGED256 ? staged_occupancy<S, 256, 4>(d, &per_sm)
+                                     : staged_occupancy<S, 512, 2>(d, &per_sm);
+        });
+        if (st != FG_OK) return st;
+        if (per_sm < 1) return fail(FG_ERR_INVALID, "staged kernel does not fit on an SM");
+        d->staged_grid = std::min(d->total_groups, sms * per_sm);
+    }
+    if (!allocate) return FG_OK;
+    const size_t need = (size_t)std::max(d->total_blocks, d->total_groups);
+    if (need > d->mass_part_cap) {
+        Pair32* p = nullptr;
+        fg_status st = dalloc(&p, need);
+        if (st != FG_OK) return st;
+        CK(cudaStreamSynchronize(d->stream));
+        if (d->mass_part) cudaFree(d->mass_part);
+        d->mass_part = p;
+        d->mass_part_cap = need;
+    }
+    fg_status st = ensure_reduce_scratch(d);
     if (st != FG_OK) return st;
-    if (per_sm < 1) return fail(FG_ERR_INVALID, "staged kernel does not fit on an SM");
-    d->staged_grid = std::min(d->total_groups, sms * per_sm);
-    return FG_OK;
+    for (int p = 0; p < 2; ++p)
+        if (d->graph[p]) {
+            cudaGraphExecDestroy(d->graph[p]);
+            d->graph[p] = nullptr;
+        }
+    d->graph_key = fg_domain::GraphKey();
+    return upload_env(d);
 }
 
 size_t env_cells(const fg_domain* d, int env) {
@@ -431,8 +488,9 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     o.storage = FG_F32; o.layout = 0; o.deterministic = 0; o.ib_iters = 1; o.record_history = 0;
     o.kernel_variant = FG_KERNEL_AUTO;
     o.use_graphs = 1;
+    o.autotune = 0;
     if (opt) o = *opt;
-    if (o.kernel_variant < FG_KERNEL_AUTO || o.kernel_variant > FG_KERNEL_STAGED)
+    if (o.kernel_variant < FG_KERNEL_AUTO || o.kernel_variant > FG_KERNEL_STAGED512)
         return fail(FG_ERR_INVALID, "unknown kernel variant");
     if (o.storage < 0 || o.storage > 2) return fail(FG_ERR_INVALID, "unknown storage");
     if (o.layout != 0) return fail(FG_ERR_INVALID, "only the two-buffer pull layout (0) exists");
@@ -467,11 +525,9 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     d->frame.resize(n_envs);
     d->mk.resize(n_envs);
     unsigned long long slot_off = 0, stamp_off = 0, ncell_all = 0;
-    int block0 = 0, group0 = 0;
+    int block0 = 0;
     bool can_stage = true;
-    int maxP = 8;
-    for (int e = 0; e < n_envs; ++e) maxP = std::max(maxP, (envs[e].nx + 7) / 8 * 8);
-    d->staged_gc = maxP <= 256 ? 256 : 512;
+    for (int e = 0; e < n_envs; ++e) d->max_P = std::max(d->max_P, (envs[e].nx + 7) / 8 * 8);
     for (int e = 0; e < n_envs; ++e) {
         const fg_env_desc& s = envs[e];
         EnvDev& E = d->env[e];
@@ -492,9 +548,6 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         E.slot_off = slot_off;
         E.block0 = block0;
         E.nblocks = (int)((E.nslot + K1_THREADS - 1) / K1_THREADS);
-        E.rpg = std::max(1, std::min(d->staged_gc / E.P, (int)E.rows));
-        E.group0 = group0;
-        E.ngroups = (int)((E.rows + E.rpg - 1) / E.rpg);
         E.stamp_off = (int)stamp_off;
         E.nseg = 1;
         if (E.P > MAX_STAGED_P) can_stage = false;
@@ -502,36 +555,19 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         ncell_all += (unsigned long long)s.nx * s.ny * s.nz;
         stamp_off += (E.nslot + 31) / 32;
         block0 += E.nblocks;
-        group0 += E.ngroups;
         fg_frame fr{};
         fr.origin[0] = (s.nx - 1) * 0.5; fr.origin[1] = (s.ny - 1) * 0.5; fr.origin[2] = (s.nz - 1) * 0.5;
         set_frame(d->frame[e], fr);
     }
-    if (o.kernel_variant == FG_KERNEL_STAGED && !can_stage) {
+    if ((o.kernel_variant == FG_KERNEL_STAGED || o.kernel_variant == FG_KERNEL_STAGED512) && !can_stage) {
         delete d;
         return fail(FG_ERR_INVALID, "staged kernel needs rows of at most 512 cells");
-    }
-    d->staged = o.kernel_variant == FG_KERNEL_STAGED || (o.kernel_variant == FG_KERNEL_AUTO && can_stage);
-    d->total_groups = group0;
-    if (d->staged) {
-        fg_status sst = setup_staged(d);
-        if (sst != FG_OK) {
-            delete d;
-            return sst;
-        }
-    }
-    for (int e = 0; e < n_envs; ++e) {
-        EnvDev& E = d->env[e];
-        // one mass partial per row group (staged) or per block (plain)
-        E.part0 = d->staged ? E.group0 : E.block0;
-        E.nparts = d->staged ? E.ngroups : E.nblocks;
     }
     d->total_cells = ncell_all;
     d->total_slots = slot_off;
     d->pop_elems = 27ull * slot_off;
     d->n_stamps = stamp_off;
     d->total_blocks = block0;
-    d->total_groups = group0;
     fg_status st = FG_OK;
 #define DA(ptr, n)                                   \
     if ((st = dalloc(&(ptr), (n))) != FG_OK) {       \
@@ -550,7 +586,6 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     }
     DA(d->fib, 3ull * slot_off);
     DA(d->stamps, stamp_off);
-    DA(d->mass_part, (size_t)std::max(block0, group0));
     DA(d->red_counters, (size_t)n_envs * RED_ROWS);
     DA(d->env_done, (size_t)n_envs);
     DA(d->d_state, 1);
@@ -579,18 +614,24 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         delete d;
         return st;
     }
-    if ((st = ensure_reduce_scratch(d)) != FG_OK) {
-        free_all(d);
-        delete d;
-        return st;
-    }
     refresh_marker_table(d);
+    {
+        const int first = o.kernel_variant == FG_KERNEL_PLAIN || !can_stage ? K1_PLAIN
+                          : o.kernel_variant == FG_KERNEL_STAGED512              ? K1_STAGED512
+                          : (d->max_P <= 256 ? K1_STAGED256 : K1_STAGED512);
+        if ((st = configure_k1(d, first, true)) != FG_OK) {
+            free_all(d);
+            delete d;
+            return st;
+        }
+    }
     if ((st = upload_env(d)) != FG_OK || (st = upload_frames(d)) != FG_OK) {
         free_all(d);
         delete d;
         return st;
     }
     for (int e = 0; e < n_envs && st == FG_OK; ++e) st = fg_init_fields(d, e, nullptr, nullptr);
+    if (st == FG_OK && o.autotune && o.kernel_variant == FG_KERNEL_AUTO) st = fg_autotune(d, nullptr, nullptr);
     if (st != FG_OK) {
         free_all(d);
         delete d;
@@ -940,6 +981,59 @@ fg_status fg_profile_read(fg_domain* d, double* ms, long long* launches) {
         d->prof_ms[k] = 0;
         d->prof_n[k] = 0;
     }
+    return FG_OK;
+}
+
+fg_status fg_autotune(fg_domain* d, int* choice, double* ms) {
+    if (!d) return fail(FG_ERR_INVALID, "null domain");
+    if (d->poisoned) return fail(FG_ERR_STATE, "domain poisoned by a numeric fault; call fg_init_fields");
+    CK(cudaStreamSynchronize(d->stream));
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    int best = -1;
+    double best_ms = 1e300;
+    fg_status st = FG_OK;
+    for (int v = 0; v < K1_NVARIANTS && st == FG_OK; ++v) {
+        if (ms) ms[v] = -1.0;
+        if (!k1_runnable(d, v)) continue;
+        if ((st = configure_k1(d, v, true)) != FG_OK) break;
+        // The stream-collide kernel alone, reading the current state and writing
+        // the other buffer (which the next step overwrites); no tile carries the
+        // next step's stamp yet, so the IB force field is left untouched.
+        st = dispatch(d->opt.storage, [&](auto tag) -> fg_status {
+            typedef decltype(tag) S;
+            typedef typename S::raw raw;
+            const raw* gin = (const raw*)d->pop[d->cur];
+            raw* gout = (raw*)d->pop[d->cur ^ 1];
+            for (int w = 0; w < 2; ++w) enqueue_k1<S>(d, gin, gout, d->stream);
+            CK(cudaEventRecord(a, d->stream));
+            for (int r = 0; r < 5; ++r) enqueue_k1<S>(d, gin, gout, d->stream);
+            CK(cudaEventRecord(b, d->stream));
+            CK(cudaGetLastError());
+            CK(cudaEventSynchronize(b));
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, a, b));
+            const double per = t / 5.0;
+            if (ms) ms[v] = per;
+            if (per < best_ms) {
+                best_ms = per;
+                best = v;
+            }
+            return FG_OK;
+        });
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != FG_OK) return st;
+    if ((st = configure_k1(d, best, true)) != FG_OK) return st;
+    if (choice) *choice = best;
+    return FG_OK;
+}
+
+fg_status fg_stream_collide_variant(fg_domain* d, int* variant) {
+    if (!d || !variant) return fail(FG_ERR_INVALID, "null argument");
+    *variant = d->k1;
     return FG_OK;
 }
 

@@ -21,8 +21,11 @@ FG_ERR_TIMEOUT, FG_ERR_NUMERIC, FG_ERR_STATE = -4, -5, -6
 FG_F32, FG_F16, FG_BF16 = 0, 1, 2
 FG_PERIODIC, FG_VELOCITY, FG_OUTFLOW, FG_FREESLIP = 0, 1, 2, 3
 FG_K_IB, FG_K_STREAM_COLLIDE, FG_K_REDUCE, FG_K_COUNT = 0, 1, 2, 3
-FG_KERNEL_AUTO, FG_KERNEL_PLAIN, FG_KERNEL_STAGED = 0, 1, 2
-VARIANT = {"auto": FG_KERNEL_AUTO, "plain": FG_KERNEL_PLAIN, "staged": FG_KERNEL_STAGED}
+FG_KERNEL_AUTO, FG_KERNEL_PLAIN, FG_KERNEL_STAGED, FG_KERNEL_STAGED512 = 0, 1, 2, 3
+FG_K1_PLAIN, FG_K1_STAGED256, FG_K1_STAGED512, FG_K1_NVARIANTS = 0, 1, 2, 3
+K1_NAMES = {0: "plain", 1: "staged256", 2: "staged512"}
+VARIANT = {"auto": FG_KERNEL_AUTO, "plain": FG_KERNEL_PLAIN, "staged": FG_KERNEL_STAGED,
+           "staged512": FG_KERNEL_STAGED512}
 STORAGE = {"f32": FG_F32, "f16": FG_F16, "bf16": FG_BF16}
 
 
@@ -43,7 +46,7 @@ class fg_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("layout", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("ib_iters", ctypes.c_int),
                 ("record_history", ctypes.c_int), ("kernel_variant", ctypes.c_int),
-                ("use_graphs", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("use_graphs", ctypes.c_int)]
 
 
 class fg_frame(ctypes.Structure):
@@ -77,6 +80,8 @@ SIGNATURES = {
     "fg_profile": (_I, [_V, _I]),
     "fg_profile_read": (_I, [_V, _P(_D), _P(_LL)]),
     "fg_stream_collide_bytes": (_I, [_V, _P(_ULL)]),
+    "fg_autotune": (_I, [_V, _P(_I), _P(_D)]),
+    "fg_stream_collide_variant": (_I, [_V, _P(_I)]),
     "fg_body_force_noalloc": (_I, [_P(fg_env_desc), _V, _V, _V, _V, _V, _I, _I, _P(_D),
                                    _P(fg_frame), _V, _V]),
 }
@@ -206,7 +211,7 @@ class Domain:
     """Owns one fg_domain (one or many environments)."""
 
     def __init__(self, envs, storage="f32", record_history=0, stream=None, variant="auto",
-                 graphs=True):
+                 graphs=True, autotune=False):
         self.envs = list(envs)
         opt = fg_options()
         opt.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
@@ -216,6 +221,7 @@ class Domain:
         opt.record_history = int(record_history)
         opt.kernel_variant = VARIANT[variant] if isinstance(variant, str) else int(variant)
         opt.use_graphs = 1 if graphs else 0
+        opt.autotune = 1 if autotune else 0
         self.storage = opt.storage
         self.h = fg_create_domain(self.envs, opt, stream)
         self.nseg = [1] * len(self.envs)
@@ -329,6 +335,19 @@ class Domain:
         n = np.zeros(FG_K_COUNT, dtype=np.int64)
         _check(lib().fg_profile_read(self.h, _dp(ms), n.ctypes.data_as(_P(_LL))))
         return ms, n
+
+    def autotune(self):
+        """Time the stream-collide variants, keep the fastest; returns
+        (name of the kept variant, {name: ms per launch})."""
+        choice = _I()
+        ms = np.zeros(FG_K1_NVARIANTS)
+        _check(lib().fg_autotune(self.h, ctypes.byref(choice), _dp(ms)))
+        return K1_NAMES[choice.value], {K1_NAMES[k]: float(ms[k]) for k in range(FG_K1_NVARIANTS) if ms[k] >= 0}
+
+    def stream_collide_variant(self):
+        v = _I()
+        _check(lib().fg_stream_collide_variant(self.h, ctypes.byref(v)))
+        return K1_NAMES[v.value]
 
     def stream_collide_bytes(self):
         b = _ULL()

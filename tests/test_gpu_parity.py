@@ -18,7 +18,7 @@ from paper_2206_01683_b300 import fishlbm, inputs
 from parity_util import TOL_F32, Pair, f32, rel_l2
 
 pytestmark = pytest.mark.gpu
-VARIANTS = ["plain", "staged"]
+VARIANTS = ["plain", "staged", "staged512"]
 
 OPEN_X = (VELOCITY, OUTFLOW, FREESLIP, FREESLIP, FREESLIP, FREESLIP)
 
@@ -291,3 +291,25 @@ def test_graph_replay_matches_direct_launches():
     h0, h1 = doms[0].history(16), doms[1].history(16)
     assert h0.shape == h1.shape == (16, 13)
     assert rel_l2(h0, h1) < 1e-6
+
+
+def test_autotune_keeps_a_runnable_variant_and_the_state():
+    """The autotuner times the candidates on the domain's own buffers without
+    changing the state, keeps the fastest, and steps continue identically."""
+    shape = (96, 40, 24)
+    rho, u = inputs.random_fields(shape, seed=51)
+    a = fishlbm.Domain([fishlbm.env_desc(shape, 0.6)], variant="plain")
+    b = fishlbm.Domain([fishlbm.env_desc(shape, 0.6)])
+    for d in (a, b):
+        d.init_fields(rho, u)
+        d.step(3)
+    before = b.populations()
+    kept, ms = b.autotune()
+    assert set(ms) == {"plain", "staged256", "staged512"} and all(v > 0 for v in ms.values())
+    assert kept == min(ms, key=ms.get) == b.stream_collide_variant()
+    assert np.array_equal(b.populations(), before)
+    for d in (a, b):
+        d.step(4)
+    assert rel_l2(b.populations(), a.populations()) < 1e-6
+    big = fishlbm.Domain([fishlbm.env_desc((300, 4, 4), 0.6)], autotune=True)
+    assert big.stream_collide_variant() in ("plain", "staged512")
