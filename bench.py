@@ -36,7 +36,9 @@ OPEN_X = (1, 2, 3, 3, 3, 3)   # inlet, outflow, free-slip walls
 # (dram__bytes_read.sum + dram__bytes_write.sum divided by the cells of the
 # launch), valid only for the kernel source it was taken on.
 NCU_TRAFFIC = {
-    # "<sha256 of step_kernels.cuh>": bytes_per_cell
+    # k_stream_collide_staged<StoreF32, 256, 4>, swimmer channel: 440.08 MB read +
+    # 399.73 MB written per launch over 4,194,304 cells
+    "843afb4ed741874e813782545710862e993c0d630d74579ba46f645ccdfcd463": 200.23,
 }
 
 
@@ -175,13 +177,20 @@ def _kernel_ms(dom, fn, steps):
     return [kms[k] / max(cnt[k], 1) for k in range(fishlbm.FG_K_COUNT)]
 
 
-def storage_form(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, K, world, peak):
+def _variant_kw(args):
+    """Domain options for --variant: autotune (default) or a fixed kernel."""
+    if args.variant == "autotune":
+        return {"autotune": True}
+    return {"variant": args.variant}
+
+
+def storage_form(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, K, world, peak, vkw):
     """The swimmer-channel step with populations stored as FP16 / BF16."""
     import torch
     from paper_2206_01683_b300 import fishlbm
     stream = torch.cuda.Stream()
     dom = fishlbm.Domain([fishlbm.env_desc(shape, tau, OPEN_X, (u_in, 0, 0), 1.0, (u_in, 0, 0))],
-                         storage=storage, stream=stream.cuda_stream, autotune=True)
+                         storage=storage, stream=stream.cuda_stream, **vkw)
     dom.set_markers(Xd[0], Ud[0], dVd, segd, n_seg=5, ref=ref)
 
     def step(n):
@@ -204,7 +213,7 @@ def storage_form(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W,
                          "algorithmic_bytes_per_cell": 108, "kernel_ms": round(k[1], 5)}}
 
 
-def batched_form(W, K, world, peak, n_envs=64):
+def batched_form(W, K, world, peak, vkw, n_envs=64):
     """64 independent single-fish environments, grid sizes drawn by seed from
     {96x64x64, 128x64x64, 160x80x80, 192x96x96}, fish of 0.4 x grid length
     with 1500-4000 markers and its own wave amplitude and frame trajectory,
@@ -223,7 +232,7 @@ def batched_form(W, K, world, peak, n_envs=64):
     T = W + 2 * K
     ts = np.arange(T)
     stream = torch.cuda.Stream()
-    dom = fishlbm.Domain(descs, stream=stream.cuda_stream, autotune=True)
+    dom = fishlbm.Domain(descs, stream=stream.cuda_stream, **vkw)
     XU = []
     for e, f in enumerate(fishes):
         X, U = f.poses(ts)
@@ -275,7 +284,7 @@ def run_ours(args):
     fr = [fishlbm.frame_from_array(f) for f in frames]
     stream = torch.cuda.Stream()
     dom = fishlbm.Domain([fishlbm.env_desc(shape, tau, OPEN_X, (u_in, 0, 0), 1.0, (u_in, 0, 0))],
-                         stream=stream.cuda_stream, autotune=True)
+                         stream=stream.cuda_stream, **_variant_kw(args))
     Xd = torch.from_numpy(X).cuda()
     Ud = torch.from_numpy(U).cuda()
     dVd = torch.from_numpy(fish.dV.astype(np.float32)).cuda()
@@ -347,9 +356,11 @@ def run_ours(args):
         # every rank runs every form (their barriers and reductions pair up)
         Kf = min(K, args.form_steps)
         forms = {
-            "f16": storage_form("f16", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world, peak),
-            "bf16": storage_form("bf16", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world, peak),
-            "batched": batched_form(W, Kf, world, peak),
+            "f16": storage_form("f16", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world, peak,
+                                _variant_kw(args)),
+            "bf16": storage_form("bf16", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world, peak,
+                                 _variant_kw(args)),
+            "batched": batched_form(W, Kf, world, peak, _variant_kw(args)),
         }
     if rank != 0:
         if world > 1:
@@ -479,6 +490,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16/batched forms")
     ap.add_argument("--form-steps", type=int, default=50)
+    ap.add_argument("--variant", default="autotune", choices=["autotune", "plain", "staged", "staged512"],
+                    help="stream-collide kernel: autotuned at creation (default) or fixed")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
