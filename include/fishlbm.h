@@ -184,12 +184,42 @@ fg_status fg_state_bytes(fg_domain* d, int env, unsigned long long* bytes);
 fg_status fg_save_state(fg_domain* d, int env, void* host_buf);
 fg_status fg_load_state(fg_domain* d, int env, const void* host_buf);
 
+/* Device-to-device copy of env's raw state (fg_state_bytes bytes, the
+ * populations in storage format) to (to_buf = 1) or from (to_buf = 0) a
+ * caller device buffer, asynchronous on the stream (checkpoints). */
+fg_status fg_copy_state(fg_domain* d, int env, void* buf, int to_buf);
+
 /* Device status word (bit 0 numeric, bit 1 invalid marker, bit 2 timeout)
  * without clearing it.  Synchronises. */
 fg_status fg_get_status(fg_domain* d, int* status);
 
 /* Number of time steps taken since creation or the last fg_init_fields. */
 fg_status fg_step_count(fg_domain* d, long long* steps);
+
+/* ---- discrete adjoint ---------------------------------------------------
+ * For gradients of losses built from the body force/torque rows with respect
+ * to the marker positions and velocities (hence, through the caller's
+ * skinning, the swimmer's joint-wave parameters).  Single environment, FP32
+ * storage, periodic faces; frame forces included.  The domain keeps the
+ * adjoint state lam = dL/df* (all zero after fg_adjoint_reset, the terminal
+ * condition of a loss that does not read the final state).  The caller
+ * replays the steps backwards: before the adjoint of step n it puts the
+ * state f*^n into the domain (fg_copy_state / checkpoint + recompute) and the
+ * step's markers (fg_set_markers); then fg_adjoint_step turns lam^{n+1} into
+ * lam^n and writes the step's marker gradients.  The forward state is not
+ * changed. */
+fg_status fg_adjoint_reset(fg_domain* d);
+
+/* frames: the step's frame (NULL keeps the last one); gF: host, (n_seg + 1) * 6
+ * loss gradient w.r.t. the step's force/torque rows as fg_get_body_force_torque
+ * reports them (NULL: none); gX, gU: device float [n][3] outputs, dL/dX_l and
+ * dL/dU_l of this step.  Asynchronous on the stream. */
+fg_status fg_adjoint_step(fg_domain* d, const fg_frame* frames, const double* gF, float* gX, float* gU);
+
+/* The adjoint state lam as host FP64 [ncell][27] (library velocity order):
+ * read it, or overwrite it (tests).  Both synchronise. */
+fg_status fg_get_adjoint(fg_domain* d, double* lam);
+fg_status fg_set_adjoint(fg_domain* d, const double* lam);
 
 /* ---- timing ------------------------------------------------------------- */
 

@@ -15,6 +15,7 @@
 
 #include "../../include/fishlbm.h"
 #include "step_kernels.cuh"
+#include "adjoint_kernels.cuh"
 
 using namespace fl;
 
@@ -84,6 +85,14 @@ struct fg_domain {
     size_t staged_smem = 0;
     size_t mass_part_cap = 0;
     int max_P = 8;
+    // adjoint state (allocated on first use): lam ping-pong, dL/dfib, dL/drho,
+    // dL/du~ fields, and the loss gradient rows of the current step
+    float* adj_lam[2] = {nullptr, nullptr};
+    int adj_cur = 0;
+    float* adj_lfib = nullptr;
+    float* adj_lrho = nullptr;
+    float* adj_lut = nullptr;
+    float* adj_gF = nullptr;
     float *X = nullptr, *U = nullptr, *dV = nullptr, *Fm = nullptr;
     int* seg = nullptr;
     int marker_slots = 0;                // allocated marker slots
@@ -157,6 +166,9 @@ void free_all(fg_domain* d) {
     if (!d) return;
     for (int p = 0; p < 2; ++p)
         if (d->graph[p]) cudaGraphExecDestroy(d->graph[p]);
+    void* adj[] = {d->adj_lam[0], d->adj_lam[1], d->adj_lfib, d->adj_lrho, d->adj_lut, d->adj_gF};
+    for (void* p : adj)
+        if (p) cudaFree(p);
     void* ptrs[] = {d->d_env, d->d_frame, d->pop[0], d->pop[1], d->fib, d->stamps, d->mass_part,
                     d->red_partials, d->red_counters, d->d_state, d->env_done,
                     d->X, d->U, d->dV, d->Fm, d->seg, d->ft, d->mass, d->hist, d->status};
@@ -981,6 +993,125 @@ fg_status fg_profile_read(fg_domain* d, double* ms, long long* launches) {
         d->prof_ms[k] = 0;
         d->prof_n[k] = 0;
     }
+    return FG_OK;
+}
+
+static fg_status adjoint_check(fg_domain* d) {
+    if (!d) return fail(FG_ERR_INVALID, "null domain");
+    if (d->n_envs != 1) return fail(FG_ERR_INVALID, "the adjoint takes a single environment");
+    if (d->opt.storage != FG_F32) return fail(FG_ERR_INVALID, "the adjoint takes FP32 storage");
+    for (int k = 0; k < 6; ++k)
+        if (d->desc[0].face[k] != FG_PERIODIC) return fail(FG_ERR_INVALID, "the adjoint takes periodic domains");
+    if (d->poisoned) return fail(FG_ERR_STATE, "domain poisoned by a numeric fault; call fg_init_fields");
+    if (!d->adj_lam[0]) {
+        const size_t ns = d->total_slots;
+        fg_status st;
+        if ((st = dalloc(&d->adj_lam[0], 27 * ns)) != FG_OK) return st;
+        if ((st = dalloc(&d->adj_lam[1], 27 * ns)) != FG_OK) return st;
+        if ((st = dalloc(&d->adj_lfib, 3 * ns)) != FG_OK) return st;
+        if ((st = dalloc(&d->adj_lrho, ns)) != FG_OK) return st;
+        if ((st = dalloc(&d->adj_lut, 3 * ns)) != FG_OK) return st;
+        if ((st = dalloc(&d->adj_gF, FT_ROW)) != FG_OK) return st;
+        CK(cudaMemsetAsync(d->adj_lam[0], 0, sizeof(float) * 27 * ns, d->stream));
+        CK(cudaMemsetAsync(d->adj_lam[1], 0, sizeof(float) * 27 * ns, d->stream));
+        CK(cudaMemsetAsync(d->adj_lfib, 0, sizeof(float) * 3 * ns, d->stream));
+        CK(cudaMemsetAsync(d->adj_lrho, 0, sizeof(float) * ns, d->stream));
+        CK(cudaMemsetAsync(d->adj_lut, 0, sizeof(float) * 3 * ns, d->stream));
+    }
+    return FG_OK;
+}
+
+fg_status fg_adjoint_reset(fg_domain* d) {
+    fg_status st = adjoint_check(d);
+    if (st != FG_OK) return st;
+    CK(cudaMemsetAsync(d->adj_lam[d->adj_cur], 0, sizeof(float) * 27 * d->total_slots, d->stream));
+    return FG_OK;
+}
+
+fg_status fg_adjoint_step(fg_domain* d, const fg_frame* frames, const double* gF, float* gX, float* gU) {
+    fg_status st = adjoint_check(d);
+    if (st != FG_OK) return st;
+    const int n = d->mk[0].n;
+    if (n > 0 && (!gX || !gU)) return fail(FG_ERR_INVALID, "gX and gU are required");
+    if (frames) {
+        set_frame(d->frame[0], frames[0]);
+        if ((st = upload_frames(d)) != FG_OK) return st;
+    }
+    const int rows = d->mk[0].nseg + 1;
+    std::vector<float> g(FT_ROW, 0.0f);
+    if (gF)
+        for (int k = 0; k < 6 * rows; ++k) g[k] = (float)gF[k];
+    CK(cudaMemcpyAsync(d->adj_gF, g.data(), sizeof(float) * FT_ROW, cudaMemcpyHostToDevice, d->stream));
+    const float* f = (const float*)d->pop[d->cur];
+    const float* lam_in = d->adj_lam[d->adj_cur];
+    float* lam_out = d->adj_lam[d->adj_cur ^ 1];
+    const EnvDev& E = d->env[0];
+    const int blocks = (int)((E.nslot + K1_THREADS - 1) / K1_THREADS);
+    // the step's IB force field (forward interpolation + spreading)
+    if (n > 0) {
+        const int wb = IB_THREADS / 32;
+        k_ib<StoreF32><<<(n + wb - 1) / wb, IB_THREADS, 0, d->stream>>>(
+            f, d->d_env, d->d_frame, 1, n, d->X, d->U, d->dV, d->Fm, d->fib, d->stamps, d->d_state, d->status);
+        k_adj_tiles<<<blocks, K1_THREADS, 0, d->stream>>>(f, lam_in, d->d_env, d->d_frame, d->fib, d->stamps,
+                                                          d->d_state, d->adj_lfib);
+        k_adj_ib<<<(n + wb - 1) / wb, IB_THREADS, 0, d->stream>>>(
+            f, d->d_env, d->d_frame, n, d->X, d->U, d->dV, d->seg, d->adj_lfib, d->adj_gF, d->mk[0].nseg,
+            d->adj_lrho, d->adj_lut, gX, gU);
+    }
+    k_adj_stream_collide<<<blocks, K1_THREADS, 0, d->stream>>>(f, lam_in, lam_out, d->d_env, d->d_frame, d->fib,
+                                                               d->stamps, d->d_state, d->adj_lfib, d->adj_lrho,
+                                                               d->adj_lut);
+    k_advance_stamp<<<1, 1, 0, d->stream>>>(d->d_state);
+    CK(cudaGetLastError());
+    d->adj_cur ^= 1;
+    return FG_OK;
+}
+
+fg_status fg_get_adjoint(fg_domain* d, double* lam) {
+    fg_status st = adjoint_check(d);
+    if (st != FG_OK) return st;
+    if (!lam) return fail(FG_ERR_INVALID, "null output");
+    const EnvDev& E = d->env[0];
+    std::vector<float> raw((size_t)27 * E.nslot);
+    CK(cudaMemcpyAsync(raw.data(), d->adj_lam[d->adj_cur], sizeof(float) * raw.size(), cudaMemcpyDeviceToHost,
+                       d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    const size_t ncell = env_cells(d, 0);
+    for (size_t c = 0; c < ncell; ++c) {
+        const size_t row = c / E.n[0], x = c - row * E.n[0], s = row * E.P + x;
+        for (int i = 0; i < 27; ++i) lam[c * 27 + i] = raw[(size_t)i * E.nslot + s];
+    }
+    return FG_OK;
+}
+
+fg_status fg_set_adjoint(fg_domain* d, const double* lam) {
+    fg_status st = adjoint_check(d);
+    if (st != FG_OK) return st;
+    if (!lam) return fail(FG_ERR_INVALID, "null input");
+    const EnvDev& E = d->env[0];
+    std::vector<float> raw((size_t)27 * E.nslot, 0.0f);
+    const size_t ncell = env_cells(d, 0);
+    for (size_t c = 0; c < ncell; ++c) {
+        const size_t row = c / E.n[0], x = c - row * E.n[0], s = row * E.P + x;
+        for (int i = 0; i < 27; ++i) raw[(size_t)i * E.nslot + s] = (float)lam[c * 27 + i];
+    }
+    CK(cudaMemcpyAsync(d->adj_lam[d->adj_cur], raw.data(), sizeof(float) * raw.size(), cudaMemcpyHostToDevice,
+                       d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    return FG_OK;
+}
+
+fg_status fg_copy_state(fg_domain* d, int env, void* buf, int to_buf) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    if (!buf) return fail(FG_ERR_INVALID, "null buffer");
+    const EnvDev& E = d->env[env];
+    char* state = (char*)d->pop[d->cur] + E.pop_off * d->esize;
+    const size_t bytes = 27ull * E.nslot * d->esize;
+    if (to_buf)
+        CK(cudaMemcpyAsync(buf, state, bytes, cudaMemcpyDeviceToDevice, d->stream));
+    else
+        CK(cudaMemcpyAsync(state, buf, bytes, cudaMemcpyDeviceToDevice, d->stream));
     return FG_OK;
 }
 

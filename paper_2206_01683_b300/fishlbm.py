@@ -81,6 +81,11 @@ SIGNATURES = {
     "fg_profile_read": (_I, [_V, _P(_D), _P(_LL)]),
     "fg_stream_collide_bytes": (_I, [_V, _P(_ULL)]),
     "fg_autotune": (_I, [_V, _P(_I), _P(_D)]),
+    "fg_copy_state": (_I, [_V, _I, _V, _I]),
+    "fg_adjoint_reset": (_I, [_V]),
+    "fg_adjoint_step": (_I, [_V, _P(fg_frame), _P(_D), _V, _V]),
+    "fg_get_adjoint": (_I, [_V, _P(_D)]),
+    "fg_set_adjoint": (_I, [_V, _P(_D)]),
     "fg_stream_collide_variant": (_I, [_V, _P(_I)]),
     "fg_body_force_noalloc": (_I, [_P(fg_env_desc), _V, _V, _V, _V, _V, _I, _I, _P(_D),
                                    _P(fg_frame), _V, _V]),
@@ -335,6 +340,36 @@ class Domain:
         n = np.zeros(FG_K_COUNT, dtype=np.int64)
         _check(lib().fg_profile_read(self.h, _dp(ms), n.ctypes.data_as(_P(_LL))))
         return ms, n
+
+    def copy_state(self, buf, to_buf, env=0):
+        """Copy the raw state to / from a device buffer (an int pointer or a
+        CUDA tensor of state_bytes() bytes)."""
+        p = buf.data_ptr() if hasattr(buf, "data_ptr") else int(buf)
+        _check(lib().fg_copy_state(self.h, env, _V(p), 1 if to_buf else 0))
+
+    def adjoint_reset(self):
+        _check(lib().fg_adjoint_reset(self.h))
+
+    def adjoint_step(self, frame=None, gF=None, gX=None, gU=None):
+        """One adjoint step; gX, gU are CUDA float tensors (n, 3) to fill."""
+        fr = None
+        if frame is not None:
+            fr = ctypes.byref(frame if isinstance(frame, fg_frame) else frame_from_array(frame))
+        g = None
+        if gF is not None:
+            g = np.ascontiguousarray(gF, dtype=np.float64).ravel()
+        _check(lib().fg_adjoint_step(self.h, fr, _dp(g) if g is not None else None,
+                                     _V(gX.data_ptr()) if gX is not None else None,
+                                     _V(gU.data_ptr()) if gU is not None else None))
+
+    def adjoint(self):
+        lam = np.zeros((self.ncell(0), 27))
+        _check(lib().fg_get_adjoint(self.h, _dp(lam)))
+        return lam
+
+    def set_adjoint(self, lam):
+        lam = np.ascontiguousarray(lam, dtype=np.float64).reshape(self.ncell(0), 27)
+        _check(lib().fg_set_adjoint(self.h, _dp(lam)))
 
     def autotune(self):
         """Time the stream-collide variants, keep the fastest; returns
