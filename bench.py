@@ -158,12 +158,37 @@ def _timed(stream, world, fn, steps):
 
 
 def _max_over_ranks(x, world):
+    """Max of x over ranks (the slowest rank sets the job's time)."""
     if world == 1:
         return x
     import torch
-    t = torch.tensor([x], device="cuda", dtype=torch.float64)
-    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t[0])
+
+
+def adjoint_form():
+    """Cost of the thrust gradient (forward with checkpoints + recompute and
+    adjoint backward) on the 128x64x64 channel, one fish of 1500 markers,
+    200 steps, checkpoint every 20, as a multiple of the forward."""
+    import torch
+    from paper_2206_01683_b300 import adjoint, inputs
+    cfg = inputs.ADJOINT_CHANNEL
+    prob = adjoint.ThrustProblem(cfg["shape"], cfg["tau"], cfg["length"], cfg["n_markers"], cfg["steps"],
+                                 checkpoint=cfg["checkpoint"])
+    best = None
+    for _ in range(3):   # the first repetition warms up
+        th = adjoint.default_theta().requires_grad_(True)
+        L = adjoint.SwimThrust.apply(th, prob)
+        (g,) = torch.autograd.grad(L, th)
+        best = (prob.forward_ms, prob.backward_ms, float(L.detach()), g.detach().numpy().tolist())
+    fwd, bwd, L, g = best
+    return {"workload": "adjoint_channel_128x64x64_periodic", "steps": cfg["steps"],
+            "checkpoint": cfg["checkpoint"], "markers": cfg["n_markers"],
+            "forward_ms": round(fwd, 3), "backward_ms": round(bwd, 3),
+            "cost_multiple": round(bwd / fwd, 3), "loss_thrust": L, "grad_norm": float(np.linalg.norm(g))}
 
 
 def _kernel_ms(dom, fn, steps):
@@ -361,6 +386,7 @@ def run_ours(args):
             "bf16": storage_form("bf16", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world, peak,
                                  _variant_kw(args)),
             "batched": batched_form(W, Kf, world, peak, _variant_kw(args)),
+            "adjoint": adjoint_form(),
         }
     if rank != 0:
         if world > 1:
