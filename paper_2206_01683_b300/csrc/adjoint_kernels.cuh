@@ -149,7 +149,7 @@ __device__ __forceinline__ void affine_a0(const CellConsts& C, int x, int y, int
 // dL/dfib at the cells of stamped tiles (one thread per slot).
 __global__ void __launch_bounds__(K1_THREADS)
 k_adj_tiles(const float* __restrict__ f, const float* __restrict__ lam, const EnvDev* __restrict__ envs,
-            const FrameDev* __restrict__ frames, const float* __restrict__ fib, const uint32_t* __restrict__ stamps,
+            const FrameDev* __restrict__ frames, const float4* __restrict__ fib, const uint32_t* __restrict__ stamps,
             const StepState* __restrict__ st, float* __restrict__ lfib) {
     const EnvDev& E = envs[0];
     const uint32_t c = blockIdx.x * K1_THREADS + threadIdx.x;
@@ -160,7 +160,8 @@ k_adj_tiles(const float* __restrict__ f, const float* __restrict__ lam, const En
     if (x >= E.n[0]) return;
     const CellConsts C = load_consts(E, frames[0]);
     const Moments m = adj_forward_moments(E, f, c, x, y, z);
-    const float fb[3] = {fib[c], fib[E.nslot + c], fib[2ull * E.nslot + c]};
+    const float4 f4 = fib[c];
+    const float fb[3] = {f4.x, f4.y, f4.z};
     float a0[3];
     affine_a0(C, x, y, z, a0);
     float lm[Q], lg[Q], lf[3];
@@ -315,7 +316,7 @@ k_adj_ib(const float* __restrict__ f, const EnvDev* __restrict__ envs, const Fra
 // lam_out_i(x - c_i) = dL/dfs_i(x).  Clears the IB fields of stamped tiles.
 __global__ void __launch_bounds__(K1_THREADS)
 k_adj_stream_collide(const float* __restrict__ f, const float* __restrict__ lam_in, float* __restrict__ lam_out,
-                     const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, float* __restrict__ fib,
+                     const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, float4* __restrict__ fib,
                      const uint32_t* __restrict__ stamps, const StepState* __restrict__ st,
                      float* __restrict__ lfib, float* __restrict__ lrho, float* __restrict__ lut) {
     const EnvDev& E = envs[0];
@@ -328,10 +329,11 @@ k_adj_stream_collide(const float* __restrict__ f, const float* __restrict__ lam_
     const bool stamped = __ldg(stamps + E.stamp_off + (c >> 5)) == st->stamp;
     float fb[3] = {0.f, 0.f, 0.f}, lr = 0.f, lu[3] = {0.f, 0.f, 0.f};
     if (stamped) {
-        fb[0] = fib[c]; fb[1] = fib[E.nslot + c]; fb[2] = fib[2ull * E.nslot + c];
+        const float4 f4 = fib[c];
+        fb[0] = f4.x; fb[1] = f4.y; fb[2] = f4.z;
         lr = lrho[c];
         lu[0] = lut[c]; lu[1] = lut[E.nslot + c]; lu[2] = lut[2ull * E.nslot + c];
-        fib[c] = 0.f; fib[E.nslot + c] = 0.f; fib[2ull * E.nslot + c] = 0.f;
+        fib[c] = make_float4(0.f, 0.f, 0.f, 0.f);
         lfib[c] = 0.f; lfib[E.nslot + c] = 0.f; lfib[2ull * E.nslot + c] = 0.f;
         lrho[c] = 0.f;
         lut[c] = 0.f; lut[E.nslot + c] = 0.f; lut[2ull * E.nslot + c] = 0.f;

@@ -2,7 +2,8 @@
 // include/fishlbm.h).  Owns the device state of a domain: two population
 // buffers (pull scheme), the sparse IB force density with its 32-cell tile
 // stamps, marker arrays, FP64 reduction outputs, and the per-step launch
-// sequence k_ib -> k_stream_collide -> k_reduce on one CUDA stream.
+// sequence k_ib_step (cooperative) -> k_stream_collide -> k_reduce on one
+// CUDA stream.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,6 +17,7 @@
 #include "../../include/fishlbm.h"
 #include "step_kernels.cuh"
 #include "adjoint_kernels.cuh"
+#include "ib_kernels.cuh"
 
 using namespace fl;
 
@@ -69,9 +71,14 @@ struct fg_domain {
     void* pop[2] = {nullptr, nullptr};
     int cur = 0;
     unsigned long long pop_elems = 0, total_cells = 0, total_slots = 0;
-    float* fib = nullptr;
+    float4* fib = nullptr;               // IB force density per slot (x, y, z, unused)
     uint32_t* stamps = nullptr;
     unsigned long long n_stamps = 0;
+    float4* ib_nodes = nullptr;          // per slot: rho, u~ of the stamped tiles' cells
+    unsigned* ib_bar = nullptr;          // grid barrier of k_ib_step: arrival counter, base
+    int ib_per_sm = 0;                   // resident blocks of k_ib_step per SM
+    uint32_t stamp_host = 1;             // host mirror of StepState::stamp
+    int n_sms = 0;
     Pair32* mass_part = nullptr;         // mass partial sums of the stream-collide kernel
     Pair32* red_partials = nullptr;      // chunk sums of k_reduce
     int* red_counters = nullptr;         // per (env, row) chunk counters of k_reduce
@@ -169,8 +176,8 @@ void free_all(fg_domain* d) {
     void* adj[] = {d->adj_lam[0], d->adj_lam[1], d->adj_lfib, d->adj_lrho, d->adj_lut, d->adj_gF};
     for (void* p : adj)
         if (p) cudaFree(p);
-    void* ptrs[] = {d->d_env, d->d_frame, d->pop[0], d->pop[1], d->fib, d->stamps, d->mass_part,
-                    d->red_partials, d->red_counters, d->d_state, d->env_done,
+    void* ptrs[] = {d->d_env, d->d_frame, d->pop[0], d->pop[1], d->fib, d->stamps, d->ib_nodes, d->ib_bar,
+                    d->mass_part, d->red_partials, d->red_counters, d->d_state, d->env_done,
                     d->X, d->U, d->dV, d->Fm, d->seg, d->ft, d->mass, d->hist, d->status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -290,10 +297,22 @@ fg_status enqueue_step(fg_domain* d, int parity, cudaStream_t s, cudaEvent_t* co
     raw* gout = (raw*)d->pop[parity ^ 1];
     if (d->total_markers > 0) {
         if (ev) CK(cudaEventRecord(ev[FG_K_IB][0], s));
-        const int warps_per_block = IB_THREADS / 32;
-        const int blocks = (d->total_markers + warps_per_block - 1) / warps_per_block;
-        k_ib<S><<<blocks, IB_THREADS, 0, s>>>(gin, d->d_env, d->d_frame, d->n_envs, d->total_markers, d->X, d->U,
-                                               d->dV, d->Fm, d->fib, d->stamps, d->d_state, d->status);
+        // all resident blocks: the scan phase covers every tile stamp
+        const int blocks = d->ib_per_sm * d->n_sms;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)blocks);
+        cfg.blockDim = dim3(IB_THREADS);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        CK(cudaLaunchKernelEx(&cfg, k_ib_step<S>, gin, (const EnvDev*)d->d_env, (const FrameDev*)d->d_frame,
+                              d->n_envs, d->total_markers, (int)d->n_stamps, (const float*)d->X, (const float*)d->U,
+                              (const float*)d->dV, d->Fm, d->fib, d->stamps, (const StepState*)d->d_state,
+                              d->ib_nodes, d->ib_bar, d->status));
         if (ev) CK(cudaEventRecord(ev[FG_K_IB][1], s));
     }
     if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][0], s));
@@ -532,6 +551,15 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     d->opt = o;
     d->stream = (cudaStream_t)cuda_stream;
     d->esize = o.storage == FG_F32 ? 4 : 2;
+    {
+        int dev = 0;
+        cudaError_t ce = cudaGetDevice(&dev);
+        if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&d->n_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (ce != cudaSuccess) {
+            delete d;
+            return cuda_fail(ce, "cudaDeviceGetAttribute");
+        }
+    }
     d->desc.assign(envs, envs + n_envs);
     d->env.resize(n_envs);
     d->frame.resize(n_envs);
@@ -596,8 +624,10 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         DA(p1, d->pop_elems * d->esize);
         d->pop[1] = p1;
     }
-    DA(d->fib, 3ull * slot_off);
+    DA(d->fib, slot_off);
     DA(d->stamps, stamp_off);
+    DA(d->ib_nodes, slot_off);
+    DA(d->ib_bar, 2);
     DA(d->red_counters, (size_t)n_envs * RED_ROWS);
     DA(d->env_done, (size_t)n_envs);
     DA(d->d_state, 1);
@@ -613,10 +643,11 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     initial_state.step = 0;
     if ((ce = cudaMemsetAsync(d->pop[0], 0, d->pop_elems * d->esize, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->pop[1], 0, d->pop_elems * d->esize, d->stream)) != cudaSuccess ||
-        (ce = cudaMemsetAsync(d->fib, 0, sizeof(float) * 3ull * slot_off, d->stream)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(d->fib, 0, sizeof(float4) * slot_off, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->stamps, 0, sizeof(uint32_t) * stamp_off, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->ft, 0, sizeof(double) * n_envs * FT_ROW, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->status, 0, sizeof(int), d->stream)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(d->ib_bar, 0, 2 * sizeof(unsigned), d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->red_counters, 0, sizeof(int) * n_envs * RED_ROWS, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->env_done, 0, sizeof(int) * n_envs, d->stream)) != cudaSuccess ||
         (ce = cudaMemcpyAsync(d->d_state, &initial_state, sizeof(StepState), cudaMemcpyHostToDevice,
@@ -632,6 +663,17 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
                           : o.kernel_variant == FG_KERNEL_STAGED512              ? K1_STAGED512
                           : (d->max_P <= 256 ? K1_STAGED256 : K1_STAGED512);
         if ((st = configure_k1(d, first, true)) != FG_OK) {
+            free_all(d);
+            delete d;
+            return st;
+        }
+        // resident blocks per SM of the cooperative IB kernel
+        st = dispatch(o.storage, [&](auto tag) -> fg_status {
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d->ib_per_sm, k_ib_step<decltype(tag)>, IB_THREADS,
+                                                             0));
+            return d->ib_per_sm > 0 ? FG_OK : fail(FG_ERR_CUDA, "k_ib_step cannot be resident");
+        });
+        if (st != FG_OK) {
             free_all(d);
             delete d;
             return st;
@@ -693,6 +735,8 @@ fg_status fg_init_fields(fg_domain* d, int env, const double* rho, const double*
     const long long zero_step = 0;
     CK(cudaMemcpyAsync(&d->d_state->step, &zero_step, sizeof(long long), cudaMemcpyHostToDevice, d->stream));
     CK(cudaMemsetAsync(d->status, 0, sizeof(int), d->stream));
+    // after a barrier timeout the barrier words are inconsistent
+    CK(cudaMemsetAsync(d->ib_bar, 0, 2 * sizeof(unsigned), d->stream));
     CK(cudaStreamSynchronize(d->stream));
     return FG_OK;
 }
@@ -750,6 +794,15 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
     return FG_OK;
 }
 
+// Called after every launch sequence that advances the device stamp.  When
+// the stamp wraps to 1, tiles may still carry 1 from long ago; k_ib_step lists
+// a tile only when it changes the stamp, so all stamps are cleared then.
+static fg_status note_stamp_advance(fg_domain* d) {
+    d->stamp_host = d->stamp_host == 0xffffffffu ? 1u : d->stamp_host + 1u;
+    if (d->stamp_host == 1u) CK(cudaMemsetAsync(d->stamps, 0, sizeof(uint32_t) * d->n_stamps, d->stream));
+    return FG_OK;
+}
+
 fg_status fg_step(fg_domain* d, int n_steps, const fg_frame* frames) {
     if (!d) return fail(FG_ERR_INVALID, "null domain");
     if (n_steps < 0) return fail(FG_ERR_INVALID, "negative step count");
@@ -771,6 +824,7 @@ fg_status fg_step(fg_domain* d, int n_steps, const fg_frame* frames) {
             return graphs ? graph_step<decltype(tag)>(d) : launch_step<decltype(tag)>(d);
         });
         if (st != FG_OK) return st;
+        if ((st = note_stamp_advance(d)) != FG_OK) return st;
     }
     return FG_OK;
 }
@@ -795,7 +849,10 @@ static fg_status status_to_error(fg_domain* d) {
         CK(cudaStreamSynchronize(d->stream));
         return fail(FG_ERR_INVALID, "a marker was outside the domain or within 2 cells of a non-periodic face");
     }
-    if (s & ST_TIMEOUT) return fail(FG_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (s & ST_TIMEOUT) {
+        d->poisoned = true;
+        return fail(FG_ERR_TIMEOUT, "a bounded device wait gave up; call fg_init_fields");
+    }
     return FG_OK;
 }
 
@@ -1064,7 +1121,7 @@ fg_status fg_adjoint_step(fg_domain* d, const fg_frame* frames, const double* gF
     k_advance_stamp<<<1, 1, 0, d->stream>>>(d->d_state);
     CK(cudaGetLastError());
     d->adj_cur ^= 1;
-    return FG_OK;
+    return note_stamp_advance(d);
 }
 
 fg_status fg_get_adjoint(fg_domain* d, double* lam) {

@@ -1,0 +1,282 @@
+// ib_kernels.cuh -- the immersed-boundary part of a step (arXiv 2206.01683,
+// Sec. III-B: direct-forcing IB with the 4-point Peskin delta) as one
+// persistent cooperative kernel in three phases separated by grid barriers.
+// Neighbouring markers share most of their stencil nodes, so the post-stream
+// moments are computed once per node instead of once per (marker, node):
+//   mark    one half-warp per marker stamps the 32-slot tiles of its 4x4x4
+//           stencil with the step's stamp (plain stores)
+//   nodes   warps read the tile stamps, strided over the grid so that the
+//           stamped tiles spread evenly; for each stamped tile the warp
+//           computes rho and u~ = j/rho + a0/2 of its 32 cells (coalesced
+//           pulls), one float4 per cell
+//   force   one half-warp per marker: R, U~ from the 64 node float4s,
+//           F = 2 R (U - U~), spread F dV delta onto the nodes (vector
+//           reductions into the float4 force field)
+//
+// The forces and the grid force density equal those of the single-pass k_ib
+// (same per-node arithmetic, same delta weights), which the adjoint keeps.
+// Data written in one phase and read in a later one (tile stamps, node
+// values) is read with ld.global.cg, never through the non-coherent path.
+#pragma once
+
+#include "step_kernels.cuh"
+
+namespace fl {
+
+// Stencil of one marker along each axis (periodic wrap, validity as in k_ib).
+struct Stencil {
+    float xw[3];
+    int base[3];
+    bool ok;
+};
+
+__device__ __forceinline__ Stencil marker_stencil(const EnvDev& E, const float* __restrict__ X, int slot) {
+    Stencil st;
+    st.ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float x = X[3 * slot + a];
+        const float N = (float)E.n[a];
+        float w = x;
+        if (!(fabsf(x) <= 1.0e6f)) st.ok = false;  // also rejects NaN
+        if (E.per[a]) {
+            w = x - floorf(x / N) * N;
+            if (w >= N) w -= N;
+            if (w < 0.0f) w += N;
+        } else if (!(x >= 2.0f && x < N - 3.0f)) {
+            st.ok = false;
+        }
+        st.xw[a] = w;
+        st.base[a] = st.ok ? (int)floorf(w) - 1 : 0;
+    }
+    return st;
+}
+
+constexpr uint32_t GRID_WAIT_LIMIT = 1u << 22;  // barrier polls before giving up
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_add_release_gpu(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid barrier of a cooperative launch (all blocks resident at once) on an
+// arrival counter bar[0] that only grows; bar[1] holds its value at the
+// start of the launch (the base).  Barrier k waits until the counter reaches
+// base + k * gridDim.x.  Each block adds 1 with release semantics (its writes
+// are ordered before thread 0's arrival by __syncthreads) and polls with
+// acquire loads.  Polls are bounded: a block that gives up records
+// ST_TIMEOUT and returns false; the host then poisons the domain and zeroes
+// both words.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned base, unsigned k, int* status) {
+    __shared__ int pass;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned target = base + k * gridDim.x;
+        int ok = 1;
+        red_add_release_gpu(bar, 1u);
+        uint32_t i = 0;
+        while ((int)(ld_acquire_gpu(bar) - target) < 0) {
+            if (++i == GRID_WAIT_LIMIT) {
+                ok = 0;
+                atomicOr(status, ST_TIMEOUT);
+                break;
+            }
+        }
+        pass = ok;
+    }
+    __syncthreads();
+    return pass != 0;
+}
+
+// Half-warp stencil walk: half-lane h (0..15) owns the stencil column
+// (kx, ky) = (h & 3, h >> 2) and its four nodes kz = 0..3.
+struct Column {
+    int mxw, myw;      // wrapped node x, y
+    float wxy;         // phi(X - mx) phi(Y - my)
+};
+
+__device__ __forceinline__ Column stencil_column(const EnvDev& E, const Stencil& S, int h) {
+    Column col;
+    const int mx = S.base[0] + (h & 3), my = S.base[1] + (h >> 2);
+    col.wxy = peskin4(S.xw[0] - (float)mx) * peskin4(S.xw[1] - (float)my);
+    col.mxw = ((mx % E.n[0]) + E.n[0]) % E.n[0];
+    col.myw = ((my % E.n[1]) + E.n[1]) % E.n[1];
+    return col;
+}
+
+__device__ __forceinline__ uint32_t column_slot(const EnvDev& E, const Column& col, int mz) {
+    const int mzw = ((mz % E.n[2]) + E.n[2]) % E.n[2];
+    return (uint32_t)col.mxw + (uint32_t)E.P * ((uint32_t)col.myw + (uint32_t)E.n[1] * (uint32_t)mzw);
+}
+
+// mark: stamp the tiles of one marker's stencil (plain idempotent stores;
+// the tiles of one column are distinct, they differ in z).
+__device__ __forceinline__ void ib_mark(const EnvDev& E, const Stencil& S, int h, uint32_t stamp,
+                                        uint32_t* stamps) {
+    const Column col = stencil_column(E, S, h);
+#pragma unroll
+    for (int kz = 0; kz < 4; ++kz) stamps[E.stamp_off + (column_slot(E, col, S.base[2] + kz) >> 5)] = stamp;
+}
+
+// nodes: post-stream rho and u~ of the 32 cells of tile t (one warp).
+template <class S>
+__device__ __forceinline__ void ib_nodes(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs,
+                                         const FrameDev* __restrict__ frames, int n_envs, int t, int lane,
+                                         float4* nodes) {
+    const int e = n_envs > 1 ? env_of<&EnvDev::stamp_off>(envs, n_envs, t) : 0;
+    const EnvDev& E = envs[e];
+    const uint32_t c = (uint32_t)(t - E.stamp_off) * 32u + (uint32_t)lane;
+    if (c >= E.nslot) return;
+    const uint32_t row = fdiv(c, E.div_P);
+    const int x = (int)(c - row * (uint32_t)E.P);
+    if (x >= E.n[0]) return;
+    const uint32_t zz = fdiv(row, E.div_ny);
+    const int y = (int)(row - zz * (uint32_t)E.n[1]);
+    const int z = (int)zz;
+    // the stencil nodes of valid markers lie off the outer layer of an open
+    // axis; other cells of the tile may not, and pull_offsets then wraps
+    // (in-bounds reads of values that no marker uses)
+    const PullOffsets o = pull_offsets(E, x, y, z);
+    const Moments m = pull_moments<S, false>(gin + E.pop_off, E.nslot, c, o);
+    const float rho = 1.0f + m.dr, inv = 1.0f / rho;
+    float a0[3];
+    frame_accel(frames[e], (float)x, (float)y, (float)z, a0);
+    nodes[E.slot_off + c] = make_float4(rho, m.jx * inv + 0.5f * a0[0], m.jy * inv + 0.5f * a0[1],
+                                        m.jz * inv + 0.5f * a0[2]);
+}
+
+// One marker of a half-warp: its environment, slot, stencil, U and dV.
+struct MarkerRef {
+    int e, slot;
+    Stencil S;
+    float U[3], dV;
+};
+
+__device__ __forceinline__ MarkerRef load_marker(const EnvDev* __restrict__ envs, int n_envs, int m,
+                                                 const float* __restrict__ X, const float* __restrict__ U,
+                                                 const float* __restrict__ dV) {
+    MarkerRef r;
+    r.e = n_envs > 1 ? env_of<&EnvDev::mk_begin>(envs, n_envs, m) : 0;
+    const EnvDev& E = envs[r.e];
+    r.slot = E.marker_off + (m - E.mk_begin);
+    r.S = marker_stencil(E, X, r.slot);
+    r.U[0] = U[3 * r.slot]; r.U[1] = U[3 * r.slot + 1]; r.U[2] = U[3 * r.slot + 2];
+    r.dV = dV[r.slot];
+    return r;
+}
+
+// force: interpolate R, U~ from the node values, form F, spread F dV delta.
+// `active` is false for a half-warp without a (valid) marker, which still
+// takes part in the shuffles.
+__device__ __forceinline__ void ib_force(const EnvDev& E, const MarkerRef& r, bool active, int h,
+                                         float* __restrict__ Fm, float4* __restrict__ fib, const float4* nodes) {
+    float R = 0.f, Ux = 0.f, Uy = 0.f, Uz = 0.f;
+    float dlt[4];
+    uint32_t cell[4];
+    if (active) {
+        const Column col = stencil_column(E, r.S, h);
+#pragma unroll
+        for (int kz = 0; kz < 4; ++kz) {
+            const int mz = r.S.base[2] + kz;
+            cell[kz] = column_slot(E, col, mz);
+            dlt[kz] = col.wxy * peskin4(r.S.xw[2] - (float)mz);
+        }
+#pragma unroll
+        for (int kz = 0; kz < 4; ++kz) {
+            const float4 nd = __ldcg(nodes + E.slot_off + cell[kz]);
+            R += dlt[kz] * nd.x;
+            Ux += dlt[kz] * nd.y;
+            Uy += dlt[kz] * nd.z;
+            Uz += dlt[kz] * nd.w;
+        }
+    }
+#pragma unroll
+    for (int s = 8; s >= 1; s >>= 1) {
+        R += __shfl_xor_sync(0xffffffffu, R, s);
+        Ux += __shfl_xor_sync(0xffffffffu, Ux, s);
+        Uy += __shfl_xor_sync(0xffffffffu, Uy, s);
+        Uz += __shfl_xor_sync(0xffffffffu, Uz, s);
+    }
+    if (!active) return;
+    // direct forcing: F_l = 2 R_l (U_l - U~_l); the grid receives F_l dV_l delta
+    const float Fx = 2.0f * R * (r.U[0] - Ux);
+    const float Fy = 2.0f * R * (r.U[1] - Uy);
+    const float Fz = 2.0f * R * (r.U[2] - Uz);
+    float4* fb = fib + E.slot_off;
+#pragma unroll
+    for (int kz = 0; kz < 4; ++kz) {
+        const float s = r.dV * dlt[kz];
+        atomicAdd(fb + cell[kz], make_float4(Fx * s, Fy * s, Fz * s, 0.f));   // one vector reduction
+    }
+    if (h == 0) {
+        Fm[3 * r.slot] = Fx; Fm[3 * r.slot + 1] = Fy; Fm[3 * r.slot + 2] = Fz;
+    }
+}
+
+// The IB part of one step.  Launched cooperatively with at most as many
+// blocks as fit on the device at once; half-warps stride over markers (the
+// first marker of each half-warp stays in registers from the mark phase to
+// the force phase), warps over tile stamps.
+template <class S>
+__global__ void __launch_bounds__(IB_THREADS, 4)
+k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs,
+          const FrameDev* __restrict__ frames, int n_envs, int total_markers, int n_stamps,
+          const float* __restrict__ X, const float* __restrict__ U, const float* __restrict__ dV,
+          float* __restrict__ Fm, float4* __restrict__ fib, uint32_t* stamps, const StepState* __restrict__ st,
+          float4* nodes, unsigned* bar, int* status) {
+    const int lane = threadIdx.x & 31, h = lane & 15;
+    const int gw = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    const uint32_t stamp = st->stamp;
+    const unsigned base = __ldcg(bar + 1);
+    const int m0 = 2 * gw + (lane >> 4);
+    // mark
+    MarkerRef first;
+    first.S.ok = false;
+    if (m0 < total_markers) {
+        first = load_marker(envs, n_envs, m0, X, U, dV);
+        if (first.S.ok) ib_mark(envs[first.e], first.S, h, stamp, stamps);
+    }
+    for (int m = m0 + 2 * nw; m < total_markers; m += 2 * nw) {
+        const int e = n_envs > 1 ? env_of<&EnvDev::mk_begin>(envs, n_envs, m) : 0;
+        const EnvDev& E = envs[e];
+        const Stencil Sm = marker_stencil(E, X, E.marker_off + (m - E.mk_begin));
+        if (Sm.ok) ib_mark(E, Sm, h, stamp, stamps);   // invalid markers are reported by the force phase
+    }
+    if (!grid_barrier(bar, base, 1, status)) return;
+    // nodes: lane k of warp gw reads the stamp of tile gw + nw (k + 32 j)
+    for (int t0 = gw; t0 < n_stamps; t0 += 32 * nw) {
+        const long long t = (long long)t0 + (long long)lane * nw;
+        const bool hit = t < n_stamps && __ldcg(stamps + t) == stamp;
+        unsigned hits = __ballot_sync(0xffffffffu, hit);
+        while (hits) {
+            const int k = __ffs(hits) - 1;
+            hits &= hits - 1u;
+            ib_nodes<S>(gin, envs, frames, n_envs, t0 + k * nw, lane, nodes);
+        }
+    }
+    if (!grid_barrier(bar, base, 2, status)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) bar[1] = base + 2u * gridDim.x;   // the next launch's base
+    // force (both halves of a warp run the same number of iterations)
+    for (int mb = 2 * gw; mb < total_markers; mb += 2 * nw) {
+        const int m = mb + (lane >> 4);
+        const bool here = m < total_markers;
+        MarkerRef r;
+        r.e = 0;
+        r.slot = 0;
+        r.S.ok = false;
+        if (here) r = mb == 2 * gw ? first : load_marker(envs, n_envs, m, X, U, dV);
+        if (here && !r.S.ok && h == 0) {
+            Fm[3 * r.slot] = 0.f; Fm[3 * r.slot + 1] = 0.f; Fm[3 * r.slot + 2] = 0.f;
+            atomicOr(status, ST_BAD_MARKER);
+        }
+        ib_force(envs[r.e], r, here && r.S.ok, h, Fm, fib, nodes);
+    }
+}
+
+}  // namespace fl

@@ -368,14 +368,15 @@ __device__ __forceinline__ int inward(const EnvDev& E, int axis, int v) {
 
 // IB force density at a slot if its 32-slot tile was stamped this step; the
 // stored value is cleared so the field is zero again for the next step.
-__device__ __forceinline__ void take_ib_force(const EnvDev& E, float* __restrict__ fib,
+__device__ __forceinline__ void take_ib_force(const EnvDev& E, float4* __restrict__ fib,
                                               const uint32_t* __restrict__ stamps, uint32_t stamp,
                                               uint32_t slot, float& fx, float& fy, float& fz) {
     fx = fy = fz = 0.f;
     if (__ldg(stamps + E.stamp_off + (slot >> 5)) == stamp) {
-        float* fb = fib + 3ull * E.slot_off;
-        fx = fb[slot]; fy = fb[E.nslot + slot]; fz = fb[2ull * E.nslot + slot];
-        fb[slot] = 0.f; fb[E.nslot + slot] = 0.f; fb[2ull * E.nslot + slot] = 0.f;
+        float4* fb = fib + E.slot_off + slot;
+        const float4 f = *fb;
+        fx = f.x; fy = f.y; fz = f.z;
+        *fb = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -388,7 +389,7 @@ __global__ void __launch_bounds__(IB_THREADS, 4)
 k_ib(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs,
      const FrameDev* __restrict__ frames, int n_envs, int total_markers,
      const float* __restrict__ X, const float* __restrict__ U, const float* __restrict__ dV,
-     float* __restrict__ Fm, float* __restrict__ fib, uint32_t* __restrict__ stamps,
+     float* __restrict__ Fm, float4* __restrict__ fib, uint32_t* __restrict__ stamps,
      const StepState* __restrict__ st, int* __restrict__ status) {
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -469,13 +470,11 @@ k_ib(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs,
     const float Fy = 2.0f * R * (U[3 * slot + 1] - Uy);
     const float Fz = 2.0f * R * (U[3 * slot + 2] - Uz);
     const float v = dV[slot];
-    float* fb = fib + 3ull * E.slot_off;
+    float4* fb = fib + E.slot_off;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const float s = v * dlt[h];
-        atomicAdd(fb + cell[h], Fx * s);
-        atomicAdd(fb + E.nslot + cell[h], Fy * s);
-        atomicAdd(fb + 2ull * E.nslot + cell[h], Fz * s);
+        atomicAdd(fb + cell[h], make_float4(Fx * s, Fy * s, Fz * s, 0.f));
         stamps[E.stamp_off + (cell[h] >> 5)] = stamp;
     }
     if (lane == 0) {
@@ -501,7 +500,7 @@ template <class S>
 __global__ void __launch_bounds__(K1_THREADS)
 k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __restrict__ gout,
                  const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, int n_envs,
-                 float* __restrict__ fib, const uint32_t* __restrict__ stamps, const StepState* __restrict__ st,
+                 float4* __restrict__ fib, const uint32_t* __restrict__ stamps, const StepState* __restrict__ st,
                  Pair32* __restrict__ mass_part) {
     __shared__ float wsum[K1_THREADS / 32];
     const uint32_t stamp = st->stamp;
@@ -586,7 +585,7 @@ template <class S, int GC, int MINB>
 __global__ void __launch_bounds__(K1_THREADS, MINB)
 k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw* __restrict__ gout,
                         const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, int n_envs,
-                        int total_groups, float* __restrict__ fib, const uint32_t* __restrict__ stamps,
+                        int total_groups, float4* __restrict__ fib, const uint32_t* __restrict__ stamps,
                         const StepState* __restrict__ st, Pair32* __restrict__ mass_part,
                         int* __restrict__ status) {
     typedef typename S::raw raw;
@@ -654,9 +653,10 @@ k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw
             // IB force density of a stamped tile (cleared after use)
             float fx = 0.f, fy = 0.f, fz = 0.f;
             if (__ldg(stamps + R.stamp_off + (slot >> 5)) == stamp) {
-                float* fb = fib + 3ull * R.slot_off + slot;
-                fx = fb[0]; fy = fb[R.nslot]; fz = fb[2ull * R.nslot];
-                fb[0] = 0.f; fb[R.nslot] = 0.f; fb[2ull * R.nslot] = 0.f;
+                float4* fb = fib + R.slot_off + slot;
+                const float4 f = *fb;
+                fx = f.x; fy = f.y; fz = f.z;
+                *fb = make_float4(0.f, 0.f, 0.f, 0.f);
             }
             const int sx = R.per_x ? 0 : (x == 0 ? 1 : (x == R.nx - 1 ? -1 : 0));
             const int sy = R.per_y ? 0 : (y == 0 ? 1 : (y == R.ny - 1 ? -1 : 0));
