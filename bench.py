@@ -36,9 +36,9 @@ OPEN_X = (1, 2, 3, 3, 3, 3)   # inlet, outflow, free-slip walls
 # (dram__bytes_read.sum + dram__bytes_write.sum divided by the cells of the
 # launch), valid only for the kernel source it was taken on.
 NCU_TRAFFIC = {
-    # k_stream_collide_staged<StoreF32, 256, 4>, swimmer channel: 440.08 MB read +
-    # 399.73 MB written per launch over 4,194,304 cells
-    "286cb3212b01501e2cf383e1ba1186ae9de75cfe14a8671ad1816ab908c728b4": 200.23,
+    # k_stream_collide_staged<StoreF32, 256, 4>, swimmer channel: 440.06 MB read +
+    # 399.37 MB written per launch over 4,194,304 cells
+    "87bd2a07582bd0380edc70fba6b02292454bb0df4b6821f1a70c2441a349a1e5": 200.14,
 }
 
 
@@ -429,7 +429,7 @@ def run_ours(args):
                      "reduce_ms": round(red_ms, 5)},
         "e2e": {"value": round(world * ncell * K / (e2e_ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": 5 * K,   # k_ib_mark, k_ib_nodes, k_ib_force, stream-collide, k_reduce
+        "gpu_launches": 4 * K,   # marker copy, k_ib_step, stream-collide, k_reduce
         "clocks": clock_info,
     }
     if forms is not None:

@@ -21,6 +21,16 @@
 
 using namespace fl;
 
+// Marker positions and velocities of one environment from caller-owned
+// device arrays (count values each), in one launch.
+__global__ void k_copy_markers(float* __restrict__ X, float* __restrict__ U, const float* __restrict__ Xs,
+                                      const float* __restrict__ Us, int count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * count; i += gridDim.x * blockDim.x) {
+        if (i < count) X[i] = Xs[i];
+        else U[i - count] = Us[i - count];
+    }
+}
+
 namespace {
 
 thread_local std::string g_err;
@@ -771,8 +781,15 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
     MarkerRegion& m = d->mk[env];
     const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (n > 0) {
-        CK(cudaMemcpyAsync(d->X + 3ull * m.off, X, sizeof(float) * 3 * n, kind, d->stream));
-        CK(cudaMemcpyAsync(d->U + 3ull * m.off, U, sizeof(float) * 3 * n, kind, d->stream));
+        if (device_ptrs) {
+            // one launch for both arrays (the per-step marker update)
+            const int blocks = (int)std::min<long long>((6ll * n + 255) / 256, 4096);
+            k_copy_markers<<<blocks, 256, 0, d->stream>>>(d->X + 3ull * m.off, d->U + 3ull * m.off, X, U, 3 * n);
+            CK(cudaGetLastError());
+        } else {
+            CK(cudaMemcpyAsync(d->X + 3ull * m.off, X, sizeof(float) * 3 * n, kind, d->stream));
+            CK(cudaMemcpyAsync(d->U + 3ull * m.off, U, sizeof(float) * 3 * n, kind, d->stream));
+        }
         if (dV) CK(cudaMemcpyAsync(d->dV + m.off, dV, sizeof(float) * n, kind, d->stream));
         if (seg) {
             CK(cudaMemcpyAsync(d->seg + m.off, seg, sizeof(int) * n, kind, d->stream));
@@ -795,8 +812,8 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
 }
 
 // Called after every launch sequence that advances the device stamp.  When
-// the stamp wraps to 1, tiles may still carry 1 from long ago; k_ib_step lists
-// a tile only when it changes the stamp, so all stamps are cleared then.
+// the stamp wraps to 1, tiles may still carry 1 from long ago, and k_ib_step
+// would take them as stamped this step, so all stamps are cleared then.
 static fg_status note_stamp_advance(fg_domain* d) {
     d->stamp_host = d->stamp_host == 0xffffffffu ? 1u : d->stamp_host + 1u;
     if (d->stamp_host == 1u) CK(cudaMemsetAsync(d->stamps, 0, sizeof(uint32_t) * d->n_stamps, d->stream));
