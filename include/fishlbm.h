@@ -128,7 +128,8 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
  * fg_frame entries applied to all n_steps.  One step: interpolate the
  * post-stream velocity at the markers and spread the direct-forcing force;
  * stream, collide (regularized BGK + Guo forcing with the frame force) and
- * apply the open-face rule; reduce force, torque and mass in FP64. */
+ * apply the open-face rule; reduce force, torque and mass (compensated FP32
+ * pair sums on the device, evaluated in FP64 when read). */
 fg_status fg_step(fg_domain* d, int n_steps, const fg_frame* frames);
 
 /* Force and torque the fluid exerts on the body in environment env during the
@@ -169,7 +170,8 @@ fg_status fg_set_populations(fg_domain* d, int env, const double* f);
  * receives F_l dV_l spread by the delta kernel).  Synchronises. */
 fg_status fg_get_marker_force(fg_domain* d, int env, float* F);
 
-/* Total mass sum_x rho after the last step (FP64 reduction).  Synchronises. */
+/* Total mass sum_x rho after the last step: ncell + sum (rho - 1), the sum a
+ * compensated FP32 pair on the device, evaluated in FP64.  Synchronises. */
 fg_status fg_get_mass(fg_domain* d, int env, double* mass);
 
 /* Copy up to max_steps rows of env's recorded history, oldest first; each row

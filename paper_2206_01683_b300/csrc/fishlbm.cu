@@ -18,6 +18,8 @@
 #include "step_kernels.cuh"
 #include "adjoint_kernels.cuh"
 #include "ib_kernels.cuh"
+#include "reduce_kernels.cuh"
+#include "state_kernels.cuh"
 
 using namespace fl;
 
@@ -91,7 +93,7 @@ struct fg_domain {
     int n_sms = 0;
     Pair32* mass_part = nullptr;         // mass partial sums of the stream-collide kernel
     Pair32* red_partials = nullptr;      // chunk sums of k_reduce
-    int* red_counters = nullptr;         // per (env, row) chunk counters of k_reduce
+    int* red_counters = nullptr;         // per environment: finished blocks of k_reduce
     int red_z = 1;                       // chunks per row of k_reduce
     int total_blocks = 0;                // plain stream-collide grid
     int total_groups = 0;                // staged kernel row groups
@@ -114,13 +116,12 @@ struct fg_domain {
     int* seg = nullptr;
     int marker_slots = 0;                // allocated marker slots
     int total_markers = 0;
-    double* ft = nullptr;
-    double* mass = nullptr;
-    double* hist = nullptr;
+    Pair32* ft = nullptr;                // force/torque rows (compensated pairs)
+    Pair32* mass = nullptr;              // sum of (rho - 1) per environment
+    Pair32* hist = nullptr;              // history ring: force/torque rows + mass
     int* status = nullptr;
     long long steps = 0;
     StepState* d_state = nullptr;        // stamp / step / completion count on the device
-    int* env_done = nullptr;             // per environment: rows of k_reduce finished
     bool poisoned = false;
     // CUDA graphs of one step, one per population-buffer parity; rebuilt when
     // a launch parameter baked into them changes
@@ -187,7 +188,7 @@ void free_all(fg_domain* d) {
     for (void* p : adj)
         if (p) cudaFree(p);
     void* ptrs[] = {d->d_env, d->d_frame, d->pop[0], d->pop[1], d->fib, d->stamps, d->ib_nodes, d->ib_bar,
-                    d->mass_part, d->red_partials, d->red_counters, d->d_state, d->env_done,
+                    d->mass_part, d->red_partials, d->red_counters, d->d_state,
                     d->X, d->U, d->dV, d->Fm, d->seg, d->ft, d->mass, d->hist, d->status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -330,8 +331,8 @@ fg_status enqueue_step(fg_domain* d, int parity, cudaStream_t s, cudaEvent_t* co
     if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][1], s));
     if (ev) CK(cudaEventRecord(ev[FG_K_REDUCE][0], s));
     k_reduce<<<dim3(d->n_envs, RED_ROWS, d->red_z), RED_THREADS, 0, s>>>(
-        d->d_env, d->X, d->Fm, d->dV, d->seg, d->mass_part, d->red_partials, d->red_counters, d->env_done,
-        d->n_envs, d->red_z, d->ft, d->mass, d->hist, d->opt.record_history, d->d_state, d->status);
+        d->d_env, d->X, d->Fm, d->dV, d->seg, d->mass_part, d->red_partials, d->red_counters, d->n_envs,
+        d->red_z, d->ft, d->mass, d->hist, d->opt.record_history, d->d_state, d->status);
     if (ev) CK(cudaEventRecord(ev[FG_K_REDUCE][1], s));
     CK(cudaGetLastError());
     return FG_OK;
@@ -493,6 +494,9 @@ fg_status configure_k1(fg_domain* d, int v, bool allocate) {
     return upload_env(d);
 }
 
+// FP64 value of a compensated pair produced on the device.
+double pair_value(const Pair32& p) { return (double)p.hi + (double)p.lo; }
+
 size_t env_cells(const fg_domain* d, int env) {
     return (size_t)d->env[env].n[0] * d->env[env].n[1] * d->env[env].n[2];
 }
@@ -639,9 +643,8 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     DA(d->ib_nodes, slot_off);
     DA(d->ib_bar, 2);
     DA(d->red_counters, (size_t)n_envs * RED_ROWS);
-    DA(d->env_done, (size_t)n_envs);
     DA(d->d_state, 1);
-    DA(d->ft, (size_t)n_envs * FT_ROW);
+    DA(d->ft, (size_t)n_envs * FT_ROW);   // compensated pairs, evaluated on the host
     DA(d->mass, n_envs);
     if (o.record_history > 0) DA(d->hist, (size_t)n_envs * o.record_history * HIST_ROW);
     DA(d->status, 1);
@@ -655,11 +658,11 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         (ce = cudaMemsetAsync(d->pop[1], 0, d->pop_elems * d->esize, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->fib, 0, sizeof(float4) * slot_off, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->stamps, 0, sizeof(uint32_t) * stamp_off, d->stream)) != cudaSuccess ||
-        (ce = cudaMemsetAsync(d->ft, 0, sizeof(double) * n_envs * FT_ROW, d->stream)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(d->ft, 0, sizeof(Pair32) * n_envs * FT_ROW, d->stream)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(d->mass, 0, sizeof(Pair32) * n_envs, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->status, 0, sizeof(int), d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->ib_bar, 0, 2 * sizeof(unsigned), d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->red_counters, 0, sizeof(int) * n_envs * RED_ROWS, d->stream)) != cudaSuccess ||
-        (ce = cudaMemsetAsync(d->env_done, 0, sizeof(int) * n_envs, d->stream)) != cudaSuccess ||
         (ce = cudaMemcpyAsync(d->d_state, &initial_state, sizeof(StepState), cudaMemcpyHostToDevice,
                               d->stream)) != cudaSuccess) {
         st = cuda_fail(ce, "cudaMemsetAsync");
@@ -878,17 +881,25 @@ fg_status fg_get_body_force_torque(fg_domain* d, int env, double* out) {
     if (st != FG_OK) return st;
     if (!out) return fail(FG_ERR_INVALID, "null output");
     const int rows = d->mk[env].nseg + 1;
-    CK(cudaMemcpyAsync(out, d->ft + (size_t)env * FT_ROW, sizeof(double) * 6 * rows, cudaMemcpyDeviceToHost,
+    Pair32 p[FT_ROW];
+    CK(cudaMemcpyAsync(p, d->ft + (size_t)env * FT_ROW, sizeof(Pair32) * 6 * rows, cudaMemcpyDeviceToHost,
                        d->stream));
-    return status_to_error(d);
+    st = status_to_error(d);   // synchronises
+    if (st != FG_OK) return st;
+    for (int k = 0; k < 6 * rows; ++k) out[k] = pair_value(p[k]);
+    return FG_OK;
 }
 
 fg_status fg_get_mass(fg_domain* d, int env, double* mass) {
     fg_status st = check_env(d, env);
     if (st != FG_OK) return st;
     if (!mass) return fail(FG_ERR_INVALID, "null output");
-    CK(cudaMemcpyAsync(mass, d->mass + env, sizeof(double), cudaMemcpyDeviceToHost, d->stream));
-    return status_to_error(d);
+    Pair32 p;
+    CK(cudaMemcpyAsync(&p, d->mass + env, sizeof(Pair32), cudaMemcpyDeviceToHost, d->stream));
+    st = status_to_error(d);   // synchronises
+    if (st != FG_OK) return st;
+    *mass = (double)env_cells(d, env) + pair_value(p);
+    return FG_OK;
 }
 
 fg_status fg_get_marker_force(fg_domain* d, int env, float* F) {
@@ -911,16 +922,17 @@ fg_status fg_get_history(fg_domain* d, int env, double* out, int max_steps, int*
     if (cap == 0) return fail(FG_ERR_STATE, "history was not enabled at creation");
     const long long avail = std::min<long long>(d->steps, cap);
     const long long nr = std::min<long long>(avail, max_steps);
-    std::vector<double> all((size_t)cap * HIST_ROW);
-    CK(cudaMemcpyAsync(all.data(), d->hist + (size_t)env * cap * HIST_ROW, sizeof(double) * all.size(),
+    std::vector<Pair32> all((size_t)cap * HIST_ROW);
+    CK(cudaMemcpyAsync(all.data(), d->hist + (size_t)env * cap * HIST_ROW, sizeof(Pair32) * all.size(),
                        cudaMemcpyDeviceToHost, d->stream));
     CK(cudaStreamSynchronize(d->stream));
     const int w = 6 * (d->mk[env].nseg + 1);
+    const double ncell = (double)env_cells(d, env);
     for (long long k = 0; k < nr; ++k) {
         const long long step = d->steps - nr + k;  // oldest first
-        const double* row = all.data() + (size_t)(step % cap) * HIST_ROW;
-        std::memcpy(out + k * (w + 1), row, sizeof(double) * w);
-        out[k * (w + 1) + w] = row[FT_ROW];
+        const Pair32* row = all.data() + (size_t)(step % cap) * HIST_ROW;
+        for (int c = 0; c < w; ++c) out[k * (w + 1) + c] = pair_value(row[c]);
+        out[k * (w + 1) + w] = ncell + pair_value(row[FT_ROW]);
     }
     *n_rows = (int)nr;
     return FG_OK;

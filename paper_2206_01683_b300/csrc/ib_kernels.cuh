@@ -14,7 +14,8 @@
 //           reductions into the float4 force field)
 //
 // The forces and the grid force density equal those of the single-pass k_ib
-// (same per-node arithmetic, same delta weights), which the adjoint keeps.
+// below (same per-node arithmetic, same delta weights), which the adjoint's
+// recomputation uses.
 // Data written in one phase and read in a later one (tile stamps, node
 // values) is read with ld.global.cg, never through the non-coherent path.
 #pragma once
@@ -22,6 +23,110 @@
 #include "step_kernels.cuh"
 
 namespace fl {
+
+// ------------------------------------------------- single pass (adjoint)
+
+// One warp per marker: lane (kx, ky, kz) with kx = lane & 3, ky = (lane>>2)&3,
+// kz = lane >> 4 owns stencil nodes (kx, ky, kz) and (kx, ky, kz + 2).
+template <class S>
+__global__ void __launch_bounds__(IB_THREADS, 4)
+k_ib(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs,
+     const FrameDev* __restrict__ frames, int n_envs, int total_markers,
+     const float* __restrict__ X, const float* __restrict__ U, const float* __restrict__ dV,
+     float* __restrict__ Fm, float4* __restrict__ fib, uint32_t* __restrict__ stamps,
+     const StepState* __restrict__ st, int* __restrict__ status) {
+    const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= total_markers) return;  // whole warp
+    const uint32_t stamp = st->stamp;
+    const int e = n_envs > 1 ? env_of<&EnvDev::mk_begin>(envs, n_envs, warp) : 0;
+    const EnvDev& E = envs[e];
+    const FrameDev F = frames[e];
+    const int slot = E.marker_off + (warp - E.mk_begin);
+
+    float xw[3];
+    int base[3];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float x = X[3 * slot + a];
+        const float N = (float)E.n[a];
+        float w = x;
+        if (!(fabsf(x) <= 1.0e6f)) ok = false;  // also rejects NaN
+        if (E.per[a]) {
+            w = x - floorf(x / N) * N;
+            if (w >= N) w -= N;
+            if (w < 0.0f) w += N;
+        } else if (!(x >= 2.0f && x < N - 3.0f)) {
+            ok = false;
+        }
+        xw[a] = w;
+        base[a] = ok ? (int)floorf(w) - 1 : 0;
+    }
+    if (!ok) {
+        if (lane == 0) {
+            Fm[3 * slot] = 0.f; Fm[3 * slot + 1] = 0.f; Fm[3 * slot + 2] = 0.f;
+            atomicOr(status, ST_BAD_MARKER);
+        }
+        return;
+    }
+    const int kx = lane & 3, ky = (lane >> 2) & 3, kz = lane >> 4;
+    const int mx = base[0] + kx, my = base[1] + ky;
+    const float wxy = peskin4(xw[0] - (float)mx) * peskin4(xw[1] - (float)my);
+    const int nx = E.n[0], ny = E.n[1], nz = E.n[2];
+    // node indices lie in [-1, n+2]; a true modulo also covers periodic axes
+    // shorter than the stencil (n < 4)
+    const int mxw = ((mx % nx) + nx) % nx;
+    const int myw = ((my % ny) + ny) % ny;
+    const typename S::raw* G = gin + E.pop_off;
+
+    float R = 0.f, Ux = 0.f, Uy = 0.f, Uz = 0.f;
+    float dlt[2];
+    uint32_t cell[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int mz = base[2] + kz + 2 * h;
+        const int mzw = ((mz % nz) + nz) % nz;
+        const float d = wxy * peskin4(xw[2] - (float)mz);
+        const uint32_t c = (uint32_t)mxw + (uint32_t)E.P * ((uint32_t)myw + (uint32_t)ny * (uint32_t)mzw);
+        const PullOffsets o = pull_offsets(E, mxw, myw, mzw);
+        const Moments m = pull_moments<S, false>(G, E.nslot, c, o);
+        const float rho = 1.0f + m.dr;
+        const float inv = 1.0f / rho;
+        float a0[3];
+        frame_accel(F, (float)mxw, (float)myw, (float)mzw, a0);
+        R += d * rho;
+        Ux += d * (m.jx * inv + 0.5f * a0[0]);
+        Uy += d * (m.jy * inv + 0.5f * a0[1]);
+        Uz += d * (m.jz * inv + 0.5f * a0[2]);
+        dlt[h] = d;
+        cell[h] = c;
+    }
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        R += __shfl_xor_sync(0xffffffffu, R, s);
+        Ux += __shfl_xor_sync(0xffffffffu, Ux, s);
+        Uy += __shfl_xor_sync(0xffffffffu, Uy, s);
+        Uz += __shfl_xor_sync(0xffffffffu, Uz, s);
+    }
+    // direct forcing: F_l = 2 R_l (U_l - U~_l); the grid receives F_l dV_l delta
+    const float Fx = 2.0f * R * (U[3 * slot] - Ux);
+    const float Fy = 2.0f * R * (U[3 * slot + 1] - Uy);
+    const float Fz = 2.0f * R * (U[3 * slot + 2] - Uz);
+    const float v = dV[slot];
+    float4* fb = fib + E.slot_off;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float s = v * dlt[h];
+        atomicAdd(fb + cell[h], make_float4(Fx * s, Fy * s, Fz * s, 0.f));
+        stamps[E.stamp_off + (cell[h] >> 5)] = stamp;
+    }
+    if (lane == 0) {
+        Fm[3 * slot] = Fx; Fm[3 * slot + 1] = Fy; Fm[3 * slot + 2] = Fz;
+    }
+}
+
+// ------------------------------------------------- k_ib_step (the step)
 
 // Stencil of one marker along each axis (periodic wrap, validity as in k_ib).
 struct Stencil {

@@ -23,7 +23,7 @@
 #include <string>
 
 #include "../../include/fishlbm.h"
-#include "step_kernels.cuh"
+#include "reduce_kernels.cuh"
 
 using namespace fl;
 

@@ -1,0 +1,198 @@
+// reduce_kernels.cuh -- the reductions that end a step (arXiv 2206.01683:
+// the body force and torque, tau_ext of Eq. 1, per segment and in total; the
+// mass; a NaN watchdog), in compensated FP32 pairs evaluated in FP64.
+#pragma once
+
+#include "step_kernels.cuh"
+
+namespace fl {
+
+// Sum a pair over the block: pair trees inside each warp, then warp 0
+// combines the warp totals the same way; the final pair is evaluated in FP64.
+// Fixed order, so the result is deterministic; valid in thread 0.
+__device__ __forceinline__ double block_sum(Pair32 v, Pair32* sh) {
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) {
+        Pair32 o;
+        o.hi = __shfl_xor_sync(0xffffffffu, v.hi, k);
+        o.lo = __shfl_xor_sync(0xffffffffu, v.lo, k);
+        v.add(o);
+    }
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        Pair32 u;
+        if (lane < nw) u = sh[lane];
+#pragma unroll
+        for (int k = 16; k >= 1; k >>= 1) {
+            Pair32 o;
+            o.hi = __shfl_xor_sync(0xffffffffu, u.hi, k);
+            o.lo = __shfl_xor_sync(0xffffffffu, u.lo, k);
+            u.add(o);
+        }
+        t = (double)u.hi + (double)u.lo;
+    }
+    return t;
+}
+
+constexpr int MASS_PER_THREAD = 8;
+constexpr int RED_ROWS = MAX_SEG + 2;   // force/torque rows 0..MAX_SEG, then the mass
+
+// Grid (n_envs, RED_ROWS, chunks).  Block (e, y, z) sums chunk z of row y of
+// environment e: y <= nseg is force/torque row y (segment y; y == nseg is
+// the total over all markers), one marker per thread; y == RED_ROWS - 1 is
+// the mass, MASS_PER_THREAD partials per thread.  Force on the body
+// F = -sum F_l dV_l, torque T = -sum (X_l - ref) x F_l dV_l, mass = ncell +
+// sum (rho - 1).  Chunk sums are compensated FP32 pairs (all components of a
+// block reduced together: one shuffle tree per component, then the warp
+// totals in warp order).  One counter per environment counts its blocks; the
+// last one adds, for every row and component, the chunk pairs in chunk order
+// (a warp per component) and evaluates the result in FP64, so the result does
+// not depend on which block finished last.  Results stay compensated FP32
+// pairs on the device (ft, the mass without the cell count, the history row);
+// the host evaluates hi + lo in FP64 when it reads them (FP64 arithmetic is
+// slow on this part).  The last environment to finish advances the step
+// state.
+static __global__ void __launch_bounds__(RED_THREADS)
+k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const float* __restrict__ Fm,
+         const float* __restrict__ dV, const int* __restrict__ seg, const Pair32* __restrict__ mass_part,
+         Pair32* __restrict__ partials, int* __restrict__ counters, int n_envs, int zmax,
+         Pair32* __restrict__ ft, Pair32* __restrict__ mass, Pair32* __restrict__ hist, int hist_cap,
+         StepState* __restrict__ st, int* __restrict__ status) {
+    constexpr int NW = RED_THREADS / 32;
+    __shared__ Pair32 sh[NW][6];
+    __shared__ int is_last;
+    const int e = blockIdx.x, y = blockIdx.y, z = blockIdx.z, tid = threadIdx.x;
+    const int w = tid >> 5, lane = tid & 31;
+    const EnvDev& E = envs[e];
+    const int ns = E.nseg;
+    const int nch_f = max(1, (E.n_markers + RED_THREADS - 1) / RED_THREADS);
+    const int nch_m = max(1, (E.nparts + RED_THREADS * MASS_PER_THREAD - 1) / (RED_THREADS * MASS_PER_THREAD));
+    const bool is_mass = y == RED_ROWS - 1;
+    if (is_mass ? z >= nch_m : (y > ns || z >= nch_f)) return;
+    Pair32 acc[6];
+    if (is_mass) {
+        const int per_block = RED_THREADS * MASS_PER_THREAD;
+        Pair32 v[MASS_PER_THREAD];
+#pragma unroll
+        for (int k = 0; k < MASS_PER_THREAD; ++k) {
+            const int i = z * per_block + k * RED_THREADS + tid;
+            if (i < E.nparts) v[k] = mass_part[E.part0 + i];
+        }
+#pragma unroll
+        for (int k = 0; k < MASS_PER_THREAD; ++k) acc[0].add(v[k]);
+    } else {
+        const int l = z * RED_THREADS + tid;
+        if (l < E.n_markers) {
+            const int q = E.marker_off + l;
+            if (y == ns || seg[q] == y) {
+                const float v = -dV[q];
+                const float Fx = Fm[3 * q] * v, Fy = Fm[3 * q + 1] * v, Fz = Fm[3 * q + 2] * v;
+                const float rx = X[3 * q] - (float)E.ref[0], ry = X[3 * q + 1] - (float)E.ref[1],
+                            rz = X[3 * q + 2] - (float)E.ref[2];
+                acc[0].add(Fx); acc[1].add(Fy); acc[2].add(Fz);
+                acc[3].add(ry * Fz - rz * Fy);
+                acc[4].add(rz * Fx - rx * Fz);
+                acc[5].add(rx * Fy - ry * Fx);
+            }
+        }
+    }
+    const int ncomp = is_mass ? 1 : 6;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        if (c < ncomp) {
+#pragma unroll
+            for (int k = 16; k >= 1; k >>= 1) {
+                Pair32 o;
+                o.hi = __shfl_xor_sync(0xffffffffu, acc[c].hi, k);
+                o.lo = __shfl_xor_sync(0xffffffffu, acc[c].lo, k);
+                acc[c].add(o);
+            }
+            if (lane == 0) sh[w][c] = acc[c];
+        }
+    }
+    __syncthreads();
+    Pair32* slot = partials + ((size_t)(e * RED_ROWS + y) * zmax) * 6;
+    if (tid < ncomp) {
+        Pair32 t;
+        for (int i = 0; i < NW; ++i) t.add(sh[i][tid]);
+        slot[(size_t)z * 6 + tid] = t;
+        __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        is_last = atomicAdd(counters + e, 1) == (ns + 1) * nch_f + nch_m - 1;
+        if (is_last) __threadfence();
+    }
+    __syncthreads();
+    if (!is_last) return;   // the partials are read through L2 (ld.global.cg) below
+    // last block of environment e: item k < 6 (ns + 1) is force/torque
+    // component k % 6 of row k / 6, item 6 (ns + 1) the mass.  A warp per
+    // item; each warp takes ILP items at a time so that their loads are in
+    // flight together.
+    constexpr int ILP = 8;
+    const int items = 6 * (ns + 1) + 1;
+    for (int k0 = w; k0 < items; k0 += ILP * NW) {
+        Pair32 t[ILP];
+        const Pair32* src[ILP];
+        int nch[ILP], cc[ILP];
+#pragma unroll
+        for (int j = 0; j < ILP; ++j) {
+            const int k = k0 + j * NW;
+            const bool m_item = k == items - 1;
+            const int yy = m_item ? RED_ROWS - 1 : k / 6;
+            cc[j] = m_item ? 0 : k % 6;
+            nch[j] = k >= items ? 0 : (m_item ? nch_m : nch_f);
+            src[j] = partials + ((size_t)(e * RED_ROWS + yy) * zmax) * 6;
+        }
+        const int nmax = max(nch_f, nch_m);
+        for (int zz = lane; zz < nmax; zz += 32) {
+            Pair32 p[ILP];
+#pragma unroll
+            for (int j = 0; j < ILP; ++j) {
+                if (zz < nch[j]) {
+                    p[j].hi = __ldcg(&src[j][(size_t)zz * 6 + cc[j]].hi);
+                    p[j].lo = __ldcg(&src[j][(size_t)zz * 6 + cc[j]].lo);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < ILP; ++j) t[j].add(p[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < ILP; ++j) {
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                Pair32 o;
+                o.hi = __shfl_xor_sync(0xffffffffu, t[j].hi, s);
+                o.lo = __shfl_xor_sync(0xffffffffu, t[j].lo, s);
+                t[j].add(o);
+            }
+            const int k = k0 + j * NW;
+            if (lane == 0 && k < items) {
+                if (k == items - 1) mass[e] = t[j];
+                else ft[(size_t)e * FT_ROW + k] = t[j];
+                if (!(isfinite(t[j].hi) && isfinite(t[j].lo))) atomicOr(status, ST_NUMERIC);
+            }
+        }
+    }
+    __syncthreads();
+    if (hist_cap > 0) {
+        Pair32* h = hist + ((size_t)e * hist_cap + (size_t)(st->step % hist_cap)) * HIST_ROW;
+        for (int k = tid; k < items; k += RED_THREADS)
+            h[k == items - 1 ? FT_ROW : k] = k == items - 1 ? mass[e] : ft[(size_t)e * FT_ROW + k];
+    }
+    if (tid != 0) return;
+    counters[e] = 0;   // ready for the next step
+    if (n_envs > 1) {
+        __threadfence();
+        if (atomicAdd(&st->envs_done, 1) != n_envs - 1) return;
+        st->envs_done = 0;
+    }
+    st->step += 1;
+    st->stamp = st->stamp == 0xffffffffu ? 1u : st->stamp + 1u;
+}
+
+}  // namespace fl

@@ -1,10 +1,7 @@
-// step_kernels.cuh -- the kernels of one time step (arXiv 2206.01683,
-// Sec. III-B) and the state-access kernels around them.
+// step_kernels.cuh -- the stream-collide kernels of one time step (arXiv
+// 2206.01683, Sec. III-B) and the device types and per-cell helpers that the
+// other kernels of the step share.
 //
-//   k_ib                     interpolate the post-stream velocity at every
-//                            marker (Peskin 4-point delta), form the
-//                            direct-forcing marker force and spread it back
-//                            onto the grid (one warp per marker)
 //   k_stream_collide_staged  pull-stream + moments + frame force (Eq. 3) +
 //                            regularized BGK/Guo collision + non-equilibrium
 //                            extrapolation, fused; persistent blocks stage the
@@ -12,7 +9,9 @@
 //                            with bulk copies (TMA), double buffered
 //   k_stream_collide         the same update, one thread per cell with direct
 //                            global loads (any row length)
-//   k_reduce                 force/torque per body segment, mass, NaN watchdog
+//
+// The IB kernels are in ib_kernels.cuh, the force/torque/mass reduction in
+// reduce_kernels.cuh and the state-access kernels in state_kernels.cuh.
 //
 // Layout per environment: populations g[27][nslot] with g_i = f_i - w_i (the
 // deviation from the fluid at rest) in storage type S; slot = x + P (y + ny z)
@@ -380,108 +379,6 @@ __device__ __forceinline__ void take_ib_force(const EnvDev& E, float4* __restric
     }
 }
 
-// ---------------------------------------------------------------- K2: IB
-
-// One warp per marker: lane (kx, ky, kz) with kx = lane & 3, ky = (lane>>2)&3,
-// kz = lane >> 4 owns stencil nodes (kx, ky, kz) and (kx, ky, kz + 2).
-template <class S>
-__global__ void __launch_bounds__(IB_THREADS, 4)
-k_ib(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs,
-     const FrameDev* __restrict__ frames, int n_envs, int total_markers,
-     const float* __restrict__ X, const float* __restrict__ U, const float* __restrict__ dV,
-     float* __restrict__ Fm, float4* __restrict__ fib, uint32_t* __restrict__ stamps,
-     const StepState* __restrict__ st, int* __restrict__ status) {
-    const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (warp >= total_markers) return;  // whole warp
-    const uint32_t stamp = st->stamp;
-    const int e = n_envs > 1 ? env_of<&EnvDev::mk_begin>(envs, n_envs, warp) : 0;
-    const EnvDev& E = envs[e];
-    const FrameDev F = frames[e];
-    const int slot = E.marker_off + (warp - E.mk_begin);
-
-    float xw[3];
-    int base[3];
-    bool ok = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float x = X[3 * slot + a];
-        const float N = (float)E.n[a];
-        float w = x;
-        if (!(fabsf(x) <= 1.0e6f)) ok = false;  // also rejects NaN
-        if (E.per[a]) {
-            w = x - floorf(x / N) * N;
-            if (w >= N) w -= N;
-            if (w < 0.0f) w += N;
-        } else if (!(x >= 2.0f && x < N - 3.0f)) {
-            ok = false;
-        }
-        xw[a] = w;
-        base[a] = ok ? (int)floorf(w) - 1 : 0;
-    }
-    if (!ok) {
-        if (lane == 0) {
-            Fm[3 * slot] = 0.f; Fm[3 * slot + 1] = 0.f; Fm[3 * slot + 2] = 0.f;
-            atomicOr(status, ST_BAD_MARKER);
-        }
-        return;
-    }
-    const int kx = lane & 3, ky = (lane >> 2) & 3, kz = lane >> 4;
-    const int mx = base[0] + kx, my = base[1] + ky;
-    const float wxy = peskin4(xw[0] - (float)mx) * peskin4(xw[1] - (float)my);
-    const int nx = E.n[0], ny = E.n[1], nz = E.n[2];
-    // node indices lie in [-1, n+2]; a true modulo also covers periodic axes
-    // shorter than the stencil (n < 4)
-    const int mxw = ((mx % nx) + nx) % nx;
-    const int myw = ((my % ny) + ny) % ny;
-    const typename S::raw* G = gin + E.pop_off;
-
-    float R = 0.f, Ux = 0.f, Uy = 0.f, Uz = 0.f;
-    float dlt[2];
-    uint32_t cell[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int mz = base[2] + kz + 2 * h;
-        const int mzw = ((mz % nz) + nz) % nz;
-        const float d = wxy * peskin4(xw[2] - (float)mz);
-        const uint32_t c = (uint32_t)mxw + (uint32_t)E.P * ((uint32_t)myw + (uint32_t)ny * (uint32_t)mzw);
-        const PullOffsets o = pull_offsets(E, mxw, myw, mzw);
-        const Moments m = pull_moments<S, false>(G, E.nslot, c, o);
-        const float rho = 1.0f + m.dr;
-        const float inv = 1.0f / rho;
-        float a0[3];
-        frame_accel(F, (float)mxw, (float)myw, (float)mzw, a0);
-        R += d * rho;
-        Ux += d * (m.jx * inv + 0.5f * a0[0]);
-        Uy += d * (m.jy * inv + 0.5f * a0[1]);
-        Uz += d * (m.jz * inv + 0.5f * a0[2]);
-        dlt[h] = d;
-        cell[h] = c;
-    }
-#pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) {
-        R += __shfl_xor_sync(0xffffffffu, R, s);
-        Ux += __shfl_xor_sync(0xffffffffu, Ux, s);
-        Uy += __shfl_xor_sync(0xffffffffu, Uy, s);
-        Uz += __shfl_xor_sync(0xffffffffu, Uz, s);
-    }
-    // direct forcing: F_l = 2 R_l (U_l - U~_l); the grid receives F_l dV_l delta
-    const float Fx = 2.0f * R * (U[3 * slot] - Ux);
-    const float Fy = 2.0f * R * (U[3 * slot + 1] - Uy);
-    const float Fz = 2.0f * R * (U[3 * slot + 2] - Uz);
-    const float v = dV[slot];
-    float4* fb = fib + E.slot_off;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const float s = v * dlt[h];
-        atomicAdd(fb + cell[h], make_float4(Fx * s, Fy * s, Fz * s, 0.f));
-        stamps[E.stamp_off + (cell[h] >> 5)] = stamp;
-    }
-    if (lane == 0) {
-        Fm[3 * slot] = Fx; Fm[3 * slot + 1] = Fy; Fm[3 * slot + 2] = Fz;
-    }
-}
-
 // ------------------------------------------------- K1: stream + collide
 
 __device__ __forceinline__ float block_sum_f32(float v, float* wsum) {
@@ -686,255 +583,6 @@ k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw
             mass_part[g] = t;
         }
     }
-}
-
-// ------------------------------------------------------- K4: reduction
-
-// Sum a pair over the block: pair trees inside each warp, then warp 0
-// combines the warp totals the same way; the final pair is evaluated in FP64.
-// Fixed order, so the result is deterministic; valid in thread 0.
-__device__ __forceinline__ double block_sum(Pair32 v, Pair32* sh) {
-#pragma unroll
-    for (int k = 16; k >= 1; k >>= 1) {
-        Pair32 o;
-        o.hi = __shfl_xor_sync(0xffffffffu, v.hi, k);
-        o.lo = __shfl_xor_sync(0xffffffffu, v.lo, k);
-        v.add(o);
-    }
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (w == 0) {
-        Pair32 u;
-        if (lane < nw) u = sh[lane];
-#pragma unroll
-        for (int k = 16; k >= 1; k >>= 1) {
-            Pair32 o;
-            o.hi = __shfl_xor_sync(0xffffffffu, u.hi, k);
-            o.lo = __shfl_xor_sync(0xffffffffu, u.lo, k);
-            u.add(o);
-        }
-        t = (double)u.hi + (double)u.lo;
-    }
-    return t;
-}
-
-// Sum a pair over the block, staying in FP32 pairs; valid in thread 0.
-__device__ __forceinline__ Pair32 block_pair_sum(Pair32 v, Pair32* sh) {
-#pragma unroll
-    for (int k = 16; k >= 1; k >>= 1) {
-        Pair32 o;
-        o.hi = __shfl_xor_sync(0xffffffffu, v.hi, k);
-        o.lo = __shfl_xor_sync(0xffffffffu, v.lo, k);
-        v.add(o);
-    }
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    Pair32 t;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < nw; ++i) t.add(sh[i]);
-    return t;
-}
-
-constexpr int MASS_PER_THREAD = 8;
-constexpr int RED_ROWS = MAX_SEG + 2;   // force/torque rows 0..MAX_SEG, then the mass
-
-// Grid (n_envs, RED_ROWS, chunks).  Block (e, y, z) sums chunk z of row y of
-// environment e: y <= nseg is force/torque row y (segment y; y == nseg is
-// the total over all markers), one marker per thread; y == RED_ROWS - 1 is
-// the mass, MASS_PER_THREAD partials per thread.  Force on the body
-// F = -sum F_l dV_l, torque T = -sum (X_l - ref) x F_l dV_l, mass = ncell +
-// sum (rho - 1).  Chunk sums are compensated FP32 pairs; the last block of a
-// row to finish adds the chunk pairs in chunk order and evaluates the result
-// in FP64, so the result does not depend on which block finished last.
-static __global__ void __launch_bounds__(RED_THREADS)
-k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const float* __restrict__ Fm,
-         const float* __restrict__ dV, const int* __restrict__ seg, const Pair32* __restrict__ mass_part,
-         Pair32* __restrict__ partials, int* __restrict__ counters, int* __restrict__ env_done, int n_envs,
-         int zmax, double* __restrict__ ft, double* __restrict__ mass, double* __restrict__ hist, int hist_cap,
-         StepState* __restrict__ st, int* __restrict__ status) {
-    __shared__ Pair32 sh[RED_THREADS / 32];
-    __shared__ int is_last;
-    const int e = blockIdx.x, y = blockIdx.y, z = blockIdx.z, tid = threadIdx.x;
-    const EnvDev& E = envs[e];
-    const int ns = E.nseg;
-    const bool is_mass = y == RED_ROWS - 1;
-    if (!is_mass && y > ns) return;
-    const int per_block = is_mass ? RED_THREADS * MASS_PER_THREAD : RED_THREADS;
-    const int count = is_mass ? E.nparts : E.n_markers;
-    const int nch = max(1, (count + per_block - 1) / per_block);
-    if (z >= nch) return;
-    const int ncomp = is_mass ? 1 : 6;
-    Pair32 acc[6];
-    if (is_mass) {
-        Pair32 v[MASS_PER_THREAD];
-#pragma unroll
-        for (int k = 0; k < MASS_PER_THREAD; ++k) {
-            const int i = z * per_block + k * RED_THREADS + tid;
-            if (i < count) v[k] = mass_part[E.part0 + i];
-        }
-#pragma unroll
-        for (int k = 0; k < MASS_PER_THREAD; ++k) acc[0].add(v[k]);
-    } else {
-        const int l = z * RED_THREADS + tid;
-        if (l < count) {
-            const int q = E.marker_off + l;
-            if (y == ns || seg[q] == y) {
-                const float v = -dV[q];
-                const float Fx = Fm[3 * q] * v, Fy = Fm[3 * q + 1] * v, Fz = Fm[3 * q + 2] * v;
-                const float rx = X[3 * q] - (float)E.ref[0], ry = X[3 * q + 1] - (float)E.ref[1],
-                            rz = X[3 * q + 2] - (float)E.ref[2];
-                acc[0].add(Fx); acc[1].add(Fy); acc[2].add(Fz);
-                acc[3].add(ry * Fz - rz * Fy);
-                acc[4].add(rz * Fx - rx * Fz);
-                acc[5].add(rx * Fy - ry * Fx);
-            }
-        }
-    }
-    Pair32* slot = partials + ((size_t)(e * RED_ROWS + y) * zmax) * 6;
-    for (int c = 0; c < ncomp; ++c) {
-        const Pair32 t = block_pair_sum(acc[c], sh);
-        if (tid == 0) slot[(size_t)z * 6 + c] = t;
-    }
-    if (tid == 0) {
-        __threadfence();
-        is_last = atomicAdd(counters + e * RED_ROWS + y, 1) == nch - 1;
-    }
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    const int w = tid >> 5, lane = tid & 31;
-    Pair32 t;
-    if (w < ncomp) {
-        // warp w combines component w: lanes load chunks lane, lane + 32, ...
-        // (in flight together), then a fixed shuffle tree adds the lanes
-        for (int zz = lane; zz < nch; zz += 32) {
-            Pair32 p;
-            p.hi = __ldcg(&slot[(size_t)zz * 6 + w].hi);
-            p.lo = __ldcg(&slot[(size_t)zz * 6 + w].lo);
-            t.add(p);
-        }
-#pragma unroll
-        for (int k = 16; k >= 1; k >>= 1) {
-            Pair32 o;
-            o.hi = __shfl_xor_sync(0xffffffffu, t.hi, k);
-            o.lo = __shfl_xor_sync(0xffffffffu, t.lo, k);
-            t.add(o);
-        }
-    }
-    if (w < ncomp && lane == 0) {
-        double v = (double)t.hi + (double)t.lo;
-        if (is_mass) {
-            v += (double)E.n[0] * E.n[1] * E.n[2];
-            mass[e] = v;
-        } else {
-            ft[(size_t)e * FT_ROW + 6 * y + w] = v;
-        }
-        if (!isfinite(v)) atomicOr(status, ST_NUMERIC);
-        __threadfence();
-    }
-    __syncthreads();
-    if (tid != 0) return;
-    counters[e * RED_ROWS + y] = 0;   // ready for the next step
-    // The last row of environment e to finish records the history row; the
-    // last environment to finish advances the step state.
-    __threadfence();
-    if (atomicAdd(env_done + e, 1) != ns + 1) return;   // rows 0..ns and the mass row
-    env_done[e] = 0;
-    if (hist_cap > 0) {
-        double* h = hist + ((size_t)e * hist_cap + (size_t)(st->step % hist_cap)) * HIST_ROW;
-        for (int k = 0; k < 6 * (ns + 1); ++k) h[k] = __ldcg(ft + (size_t)e * FT_ROW + k);
-        h[FT_ROW] = __ldcg(mass + e);
-    }
-    __threadfence();
-    if (atomicAdd(&st->envs_done, 1) != n_envs - 1) return;
-    st->envs_done = 0;
-    st->step += 1;
-    st->stamp = st->stamp == 0xffffffffu ? 1u : st->stamp + 1u;
-}
-
-// ----------------------------------------------------- state access
-// These run over cells c = x + nx (y + ny z) (the ABI's cell order).
-
-__device__ __forceinline__ uint32_t cell_to_slot(const EnvDev& E, uint32_t c) {
-    const uint32_t nx = (uint32_t)E.n[0];
-    const uint32_t row = c / nx;
-    return row * (uint32_t)E.P + (c - row * nx);
-}
-
-// f_eq(rho, u) - w on the Hermite-2 basis, computed in FP64.
-template <class S>
-__global__ void k_init_eq(typename S::raw* __restrict__ g, const EnvDev* __restrict__ envs, int e,
-                          const double* __restrict__ rho, const double* __restrict__ u,
-                          double rho0, double u0x, double u0y, double u0z) {
-    const EnvDev& E = envs[e];
-    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t ncell = (uint32_t)E.n[0] * E.n[1] * E.n[2];
-    if (c >= ncell) return;
-    const double r = rho ? rho[c] : rho0;
-    const double ux = u ? u[3 * (size_t)c] : u0x, uy = u ? u[3 * (size_t)c + 1] : u0y,
-                 uz = u ? u[3 * (size_t)c + 2] : u0z;
-    const double uu = ux * ux + uy * uy + uz * uz;
-    typename S::raw* G = g + E.pop_off;
-    const uint32_t s = cell_to_slot(E, c);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-        const double f = wd(i) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-        G[(size_t)i * E.nslot + s] = S::encode((float)(f - wd(i)), i);
-    }
-}
-
-// out[c][27] = w_i + g_i (FP64), library velocity order.
-template <class S>
-__global__ void k_get_pop(const typename S::raw* __restrict__ g, const EnvDev* __restrict__ envs, int e,
-                          double* __restrict__ out) {
-    const EnvDev& E = envs[e];
-    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= (uint32_t)E.n[0] * E.n[1] * E.n[2]) return;
-    const typename S::raw* G = g + E.pop_off;
-    const uint32_t s = cell_to_slot(E, c);
-#pragma unroll
-    for (int i = 0; i < Q; ++i)
-        out[(size_t)c * Q + i] = wd(i) + (double)S::decode(G[(size_t)i * E.nslot + s], i);
-}
-
-template <class S>
-__global__ void k_set_pop(typename S::raw* __restrict__ g, const EnvDev* __restrict__ envs, int e,
-                          const double* __restrict__ in) {
-    const EnvDev& E = envs[e];
-    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= (uint32_t)E.n[0] * E.n[1] * E.n[2]) return;
-    typename S::raw* G = g + E.pop_off;
-    const uint32_t s = cell_to_slot(E, c);
-#pragma unroll
-    for (int i = 0; i < Q; ++i)
-        G[(size_t)i * E.nslot + s] = S::encode((float)(in[(size_t)c * Q + i] - wd(i)), i);
-}
-
-// rho = 1 + sum g, u = sum c g / rho, in FP64 from the stored values.
-template <class S>
-__global__ void k_get_fields(const typename S::raw* __restrict__ g, const EnvDev* __restrict__ envs, int e,
-                             double* __restrict__ rho, double* __restrict__ u) {
-    const EnvDev& E = envs[e];
-    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= (uint32_t)E.n[0] * E.n[1] * E.n[2]) return;
-    const typename S::raw* G = g + E.pop_off;
-    const uint32_t s = cell_to_slot(E, c);
-    double dr = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const double v = (double)S::decode(G[(size_t)i * E.nslot + s], i);
-        dr += v;
-        jx += cx(i) * v; jy += cy(i) * v; jz += cz(i) * v;
-    }
-    const double r = 1.0 + dr;
-    rho[c] = r;
-    u[3 * (size_t)c] = jx / r; u[3 * (size_t)c + 1] = jy / r; u[3 * (size_t)c + 2] = jz / r;
 }
 
 }  // namespace fl
