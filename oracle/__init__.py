@@ -51,6 +51,8 @@ def lib():
         L.orc_spread.argtypes = [vp, i, P(d), P(d), P(d)]
         L.orc_collide_cell.argtypes = [P(d), P(d), P(d), P(d), d, P(d)]
         L.orc_frame_accel.argtypes = [P(d), d, d, d, P(d)]
+        L.orc_set_ib_iters.restype = i
+        L.orc_set_ib_iters.argtypes = [vp, i]
         _lib = L
     return _lib
 
@@ -103,7 +105,7 @@ def make_frame(acc=(0, 0, 0), omega=(0, 0, 0), domega=(0, 0, 0), origin=(0, 0, 0
 class Oracle:
     """One FP64 domain.  Fields use cell index x + nx*(y + ny*z)."""
 
-    def __init__(self, shape, tau, faces=(PERIODIC,) * 6, u_in=(0.0, 0.0, 0.0), rho_out=1.0):
+    def __init__(self, shape, tau, faces=(PERIODIC,) * 6, u_in=(0.0, 0.0, 0.0), rho_out=1.0, ib_iters=1):
         nx, ny, nz = shape
         self.shape = (nx, ny, nz)
         self.ncell = nx * ny * nz
@@ -112,6 +114,10 @@ class Oracle:
         self._h = lib().orc_create(nx, ny, nz, float(tau), _ip(faces), _dp(uin), float(rho_out))
         if not self._h:
             raise ValueError("oracle: invalid domain description")
+        if lib().orc_set_ib_iters(self._h, int(ib_iters)) != 0:
+            lib().orc_destroy(self._h)
+            self._h = None
+            raise ValueError("oracle: ib_iters must be in [1, 64]")
         self.tau = tau
         self.faces = tuple(int(f) for f in faces)
         self.nm = 0

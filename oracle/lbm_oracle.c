@@ -19,7 +19,9 @@
  *   - collision: regularized BGK with Guo forcing, i.e. the BGK-Guo
  *     post-collision moments (rho, j, Pi) projected on 2nd-order Hermite space;
  *   - delta kernel: Peskin's 4-point function;
- *   - marker force: one direct-forcing pass, F_l = 2 R_l (U_l - U~_l);
+ *   - marker force: direct forcing, F_l = 2 R_l (U_l - U~_l), in M passes
+ *     (multi-direct forcing; M = 1 by default), each pass interpolating the
+ *     velocity corrected by the force spread so far;
  *   - frame force (Eq. 3): dr/dt read as the frame angular velocity omega,
  *     d2r/dt2 as its rate domega, and x' measured from a caller-given origin;
  *     the Coriolis term is solved implicitly together with the Guo half-shift;
@@ -78,6 +80,7 @@ typedef struct {
     double *fs;          /* post-stream populations, [ncell][27] */
     double *rho, *j, *Pi;/* post-stream moments: rho, j[3], Pi[6] (xx,yy,zz,xy,xz,yz) */
     double *fib;         /* spread IB force density, [ncell][3] */
+    int ib_iters;        /* direct-forcing passes M (>= 1) */
     int nm, nseg;        /* markers */
     double *X, *U, *dV;  /* [nm][3], [nm][3], [nm] */
     int *seg;
@@ -114,6 +117,7 @@ void *orc_create(int nx, int ny, int nz, double tau, const int *face, const doub
     for (int k = 0; k < 6; ++k) o->face[k] = face[k];
     for (int a = 0; a < 3; ++a) o->u_in[a] = u_in ? u_in[a] : 0.0;
     o->rho_out = rho_out;
+    o->ib_iters = 1;
     o->f = (double *)calloc((size_t)o->ncell * Q, sizeof(double));
     o->fs = (double *)calloc((size_t)o->ncell * Q, sizeof(double));
     o->rho = (double *)calloc((size_t)o->ncell, sizeof(double));
@@ -360,15 +364,26 @@ int orc_set_markers(void *h, int n, const double *X, const double *U, const doub
 
 /* ------------------------------------------------ 4-5 interpolate, force */
 
-/* Direct forcing, one pass.  At every node the pre-IB velocity is
+/* Direct forcing.  At every node the pre-IB velocity is
  *   u~(x) = j/rho + a0(x)/2
  * (the Guo half-shift of the frame force; the small Coriolis part is left
  * out).  For each marker R_l = sum delta rho, U~_l = sum delta u~, and the
  * marker force density is F_l = 2 R_l (U_l - U~_l): with Guo's half-shift a
  * force density f moves the fluid velocity by f/(2 rho), so the factor 2
- * brings the interpolated velocity to U_l in one pass. */
-static void marker_forces(orc_t *o, const double *frame) {
+ * brings the interpolated velocity to U_l in one pass when the stencils of
+ * different markers do not overlap.
+ *
+ * Multi-direct forcing repeats the pass M = ib_iters times.  Pass m
+ * interpolates the velocity corrected by the force density spread so far,
+ *   u~_m(x) = u~(x) + fib_m(x) / (2 rho(x)),
+ * forms dF_l = 2 R_l (U_l - U~_m(X_l)) and spreads dF_l dV_l delta into fib;
+ * F_l is the sum of the passes' dF_l.  When the passes converge, the
+ * interpolated corrected velocity equals U_l at every marker.  M = 1 is the
+ * single pass above.  On return o->Fm holds F_l and o->fib the spread force
+ * density. */
+static void direct_forcing(orc_t *o, const double *frame) {
     const int n = o->nm;
+    memset(o->fib, 0, sizeof(double) * 3 * o->ncell);
     if (n == 0) return;
     double *ut = (double *)malloc(sizeof(double) * 3 * o->ncell);
     double *rr = (double *)malloc(sizeof(double) * 3 * o->ncell);
@@ -387,12 +402,35 @@ static void marker_forces(orc_t *o, const double *frame) {
             }
     double *Ui = (double *)malloc(sizeof(double) * 3 * n);
     double *Ri = (double *)malloc(sizeof(double) * 3 * n);
-    interp(o, ut, n, o->X, Ui);
+    double *dF = (double *)malloc(sizeof(double) * 3 * n);
+    double *dFdV = (double *)malloc(sizeof(double) * 3 * n);
+    double *dfib = (double *)malloc(sizeof(double) * 3 * o->ncell);
     interp(o, rr, n, o->X, Ri);
-    for (int l = 0; l < n; ++l)
-        for (int a = 0; a < 3; ++a)
-            o->Fm[3 * l + a] = 2.0 * Ri[3 * l] * (o->U[3 * l + a] - Ui[3 * l + a]);
-    free(ut); free(rr); free(Ui); free(Ri);
+    memset(o->Fm, 0, sizeof(double) * 3 * n);
+    for (int m = 0; m < o->ib_iters; ++m) {
+        interp(o, ut, n, o->X, Ui);
+        for (int l = 0; l < n; ++l)
+            for (int a = 0; a < 3; ++a) {
+                dF[3 * l + a] = 2.0 * Ri[3 * l] * (o->U[3 * l + a] - Ui[3 * l + a]);
+                o->Fm[3 * l + a] += dF[3 * l + a];
+                dFdV[3 * l + a] = dF[3 * l + a] * o->dV[l];
+            }
+        memset(dfib, 0, sizeof(double) * 3 * o->ncell);
+        spread(o, n, o->X, dFdV, dfib);
+        for (long c = 0; c < o->ncell; ++c)
+            for (int a = 0; a < 3; ++a) {
+                o->fib[3 * c + a] += dfib[3 * c + a];
+                ut[3 * c + a] += dfib[3 * c + a] / (2.0 * o->rho[c]);
+            }
+    }
+    free(ut); free(rr); free(Ui); free(Ri); free(dF); free(dFdV); free(dfib);
+}
+
+int orc_set_ib_iters(void *h, int m) {
+    orc_t *o = (orc_t *)h;
+    if (m < 1 || m > 64) return -1;
+    o->ib_iters = m;
+    return 0;
 }
 
 /* ------------------------------------------------------------ 6 collide */
@@ -530,15 +568,7 @@ int orc_step(void *h, const double *frame) {
     const int nx = o->n[0], ny = o->n[1], nz = o->n[2];
     stream(o);                 /* 1 */
     moments(o);                /* 2 */
-    marker_forces(o, frame);   /* 3-5 (a0 at the stencil nodes) */
-    memset(o->fib, 0, sizeof(double) * 3 * o->ncell);
-    if (o->nm > 0) {           /* 6a spread F_l dV_l */
-        double *FdV = (double *)malloc(sizeof(double) * 3 * o->nm);
-        for (int l = 0; l < o->nm; ++l)
-            for (int a = 0; a < 3; ++a) FdV[3 * l + a] = o->Fm[3 * l + a] * o->dV[l];
-        spread(o, o->nm, o->X, FdV, o->fib);
-        free(FdV);
-    }
+    direct_forcing(o, frame);  /* 3-5 and 6a: marker forces, spread F_l dV_l */
     const double *om = frame + 3;
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < nz; ++z)   /* 6b collide interior cells, 7 boundary cells */

@@ -51,8 +51,19 @@ MUTANTS = {
         "o->j[3 * c + a] / o->rho[c] + 0.0 * a0[a];",
         "test_comoving_markers_feel_no_force"),
     "direct_forcing_factor_1": (
-        "o->Fm[3 * l + a] = 2.0 * Ri[3 * l]", "o->Fm[3 * l + a] = 1.0 * Ri[3 * l]",
+        "dF[3 * l + a] = 2.0 * Ri[3 * l]", "dF[3 * l + a] = 1.0 * Ri[3 * l]",
         "test_stokes_drag_periodic_sphere_array"),
+    "mdf_velocity_not_corrected": (
+        "ut[3 * c + a] += dfib[3 * c + a] / (2.0 * o->rho[c]);",
+        "ut[3 * c + a] += 0.0 * dfib[3 * c + a] / (2.0 * o->rho[c]);",
+        "test_multi_direct_forcing_isolated_markers_closed_form"),
+    "mdf_full_velocity_shift": (
+        "ut[3 * c + a] += dfib[3 * c + a] / (2.0 * o->rho[c]);",
+        "ut[3 * c + a] += dfib[3 * c + a] / (1.0 * o->rho[c]);",
+        "test_multi_direct_forcing_isolated_markers_closed_form"),
+    "mdf_force_not_accumulated": (
+        "o->Fm[3 * l + a] += dF[3 * l + a];", "o->Fm[3 * l + a] = dF[3 * l + a];",
+        "test_multi_direct_forcing_isolated_markers_closed_form"),
     "freeslip_normal_kept": (
         "if (o->face[fa] == ORC_FREESLIP) ub[a] = 0.0;", "if (0) ub[a] = 0.0;",
         "test_nee_face_values_and_edge_precedence"),
