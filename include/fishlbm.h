@@ -72,11 +72,18 @@ typedef struct {
  * one thread per cell.  All compute the same step. */
 typedef enum { FG_KERNEL_AUTO = 0, FG_KERNEL_PLAIN = 1, FG_KERNEL_STAGED = 2, FG_KERNEL_STAGED512 = 3 } fg_kernel_variant;
 
+#define FG_MAX_IB_ITERS 8
+
 typedef struct {
     int storage;        /* fg_storage */
     int layout;         /* 0: two-buffer pull scheme (the only layout) */
     int deterministic;  /* 0 (reserved) */
-    int ib_iters;       /* direct-forcing passes per step; must be 1 */
+    int ib_iters;       /* direct-forcing passes per step, 1..FG_MAX_IB_ITERS
+                           (multi-direct forcing; each pass interpolates the
+                           velocity corrected by the force spread in the
+                           earlier passes, u~ + f_ib / (2 rho), and adds
+                           2 R (U - U~) to the marker force).  The adjoint
+                           takes 1 only. */
     int record_history; /* steps of (force, torque, mass) history kept on the
                            device per environment (0 = none), ring buffer */
     int kernel_variant; /* fg_kernel_variant */

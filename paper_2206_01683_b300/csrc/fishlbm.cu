@@ -113,6 +113,7 @@ struct fg_domain {
     float* adj_lut = nullptr;
     float* adj_gF = nullptr;
     float *X = nullptr, *U = nullptr, *dV = nullptr, *Fm = nullptr;
+    float* dF = nullptr;                 // per-pass force increments of multi-direct forcing
     int* seg = nullptr;
     int marker_slots = 0;                // allocated marker slots
     int total_markers = 0;
@@ -189,7 +190,7 @@ void free_all(fg_domain* d) {
         if (p) cudaFree(p);
     void* ptrs[] = {d->d_env, d->d_frame, d->pop[0], d->pop[1], d->fib, d->stamps, d->ib_nodes, d->ib_bar,
                     d->mass_part, d->red_partials, d->red_counters, d->d_state,
-                    d->X, d->U, d->dV, d->Fm, d->seg, d->ft, d->mass, d->hist, d->status};
+                    d->X, d->U, d->dV, d->Fm, d->dF, d->seg, d->ft, d->mass, d->hist, d->status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k < FG_K_COUNT; ++k)
@@ -235,7 +236,7 @@ fg_status grow_markers(fg_domain* d, int env, int n) {
         r.off = off;
         off += r.cap;
     }
-    float *X, *U, *dV, *Fm;
+    float *X, *U, *dV, *Fm, *dF;
     int* sg;
     fg_status s;
     if ((s = dalloc(&X, 3ull * off)) != FG_OK) return s;
@@ -244,6 +245,10 @@ fg_status grow_markers(fg_domain* d, int env, int n) {
     if ((s = dalloc(&Fm, 3ull * off)) != FG_OK) { cudaFree(X); cudaFree(U); cudaFree(dV); return s; }
     if ((s = dalloc(&sg, off)) != FG_OK) {
         cudaFree(X); cudaFree(U); cudaFree(dV); cudaFree(Fm);
+        return s;
+    }
+    if ((s = dalloc(&dF, 3ull * off)) != FG_OK) {
+        cudaFree(X); cudaFree(U); cudaFree(dV); cudaFree(Fm); cudaFree(sg);
         return s;
     }
     for (int e = 0; e < d->n_envs; ++e) {
@@ -261,8 +266,8 @@ fg_status grow_markers(fg_domain* d, int env, int n) {
                            cudaMemcpyDeviceToDevice, d->stream));
     }
     CK(cudaStreamSynchronize(d->stream));
-    if (d->X) { cudaFree(d->X); cudaFree(d->U); cudaFree(d->dV); cudaFree(d->Fm); cudaFree(d->seg); }
-    d->X = X; d->U = U; d->dV = dV; d->Fm = Fm; d->seg = sg;
+    if (d->X) { cudaFree(d->X); cudaFree(d->U); cudaFree(d->dV); cudaFree(d->Fm); cudaFree(d->seg); cudaFree(d->dF); }
+    d->X = X; d->U = U; d->dV = dV; d->Fm = Fm; d->seg = sg; d->dF = dF;
     d->marker_slots = off;
     d->mk = nr;
     return ensure_reduce_scratch(d);
@@ -323,7 +328,7 @@ fg_status enqueue_step(fg_domain* d, int parity, cudaStream_t s, cudaEvent_t* co
         CK(cudaLaunchKernelEx(&cfg, k_ib_step<S>, gin, (const EnvDev*)d->d_env, (const FrameDev*)d->d_frame,
                               d->n_envs, d->total_markers, (int)d->n_stamps, (const float*)d->X, (const float*)d->U,
                               (const float*)d->dV, d->Fm, d->fib, d->stamps, (const StepState*)d->d_state,
-                              d->ib_nodes, d->ib_bar, d->status));
+                              d->ib_nodes, d->ib_bar, d->opt.ib_iters, d->dF, d->status));
         if (ev) CK(cudaEventRecord(ev[FG_K_IB][1], s));
     }
     if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][0], s));
@@ -539,7 +544,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         return fail(FG_ERR_INVALID, "unknown kernel variant");
     if (o.storage < 0 || o.storage > 2) return fail(FG_ERR_INVALID, "unknown storage");
     if (o.layout != 0) return fail(FG_ERR_INVALID, "only the two-buffer pull layout (0) exists");
-    if (o.ib_iters != 1) return fail(FG_ERR_INVALID, "ib_iters must be 1");
+    if (o.ib_iters < 1 || o.ib_iters > FG_MAX_IB_ITERS) return fail(FG_ERR_INVALID, "ib_iters must be in [1, 8]");
     if (o.record_history < 0 || o.record_history > (1 << 20)) return fail(FG_ERR_INVALID, "record_history");
     unsigned long long cells = 0;
     for (int e = 0; e < n_envs; ++e) {
@@ -1086,6 +1091,7 @@ static fg_status adjoint_check(fg_domain* d) {
     if (!d) return fail(FG_ERR_INVALID, "null domain");
     if (d->n_envs != 1) return fail(FG_ERR_INVALID, "the adjoint takes a single environment");
     if (d->opt.storage != FG_F32) return fail(FG_ERR_INVALID, "the adjoint takes FP32 storage");
+    if (d->opt.ib_iters != 1) return fail(FG_ERR_INVALID, "the adjoint takes one direct-forcing pass");
     for (int k = 0; k < 6; ++k)
         if (d->desc[0].face[k] != FG_PERIODIC) return fail(FG_ERR_INVALID, "the adjoint takes periodic domains");
     if (d->poisoned) return fail(FG_ERR_STATE, "domain poisoned by a numeric fault; call fg_init_fields");

@@ -1,6 +1,6 @@
 // ib_kernels.cuh -- the immersed-boundary part of a step (arXiv 2206.01683,
 // Sec. III-B: direct-forcing IB with the 4-point Peskin delta) as one
-// persistent cooperative kernel in three phases separated by grid barriers.
+// persistent cooperative kernel in phases separated by grid barriers.
 // Neighbouring markers share most of their stencil nodes, so the post-stream
 // moments are computed once per node instead of once per (marker, node):
 //   mark    one half-warp per marker stamps the 32-slot tiles of its 4x4x4
@@ -11,7 +11,10 @@
 //           pulls), one float4 per cell
 //   force   one half-warp per marker: R, U~ from the 64 node float4s,
 //           F = 2 R (U - U~), spread F dV delta onto the nodes (vector
-//           reductions into the float4 force field)
+//           reductions into the float4 force field); with multi-direct
+//           forcing (ib_iters > 1) further passes interpolate the velocity
+//           corrected by the force spread so far, then (after a grid
+//           barrier) spread their increments
 //
 // The forces and the grid force density equal those of the single-pass k_ib
 // below (same per-node arithmetic, same delta weights), which the adjoint's
@@ -275,29 +278,48 @@ __device__ __forceinline__ MarkerRef load_marker(const EnvDev* __restrict__ envs
     return r;
 }
 
-// force: interpolate R, U~ from the node values, form F, spread F dV delta.
-// `active` is false for a half-warp without a (valid) marker, which still
-// takes part in the shuffles.
-__device__ __forceinline__ void ib_force(const EnvDev& E, const MarkerRef& r, bool active, int h,
-                                         float* __restrict__ Fm, float4* __restrict__ fib, const float4* nodes) {
-    float R = 0.f, Ux = 0.f, Uy = 0.f, Uz = 0.f;
+// Stencil nodes of half-lane h for one marker: the slots of its column's
+// four nodes and their delta weights.
+struct ColumnNodes {
     float dlt[4];
     uint32_t cell[4];
+};
+
+__device__ __forceinline__ ColumnNodes column_nodes(const EnvDev& E, const MarkerRef& r, int h) {
+    ColumnNodes cn;
+    const Column col = stencil_column(E, r.S, h);
+#pragma unroll
+    for (int kz = 0; kz < 4; ++kz) {
+        const int mz = r.S.base[2] + kz;
+        cn.cell[kz] = column_slot(E, col, mz);
+        cn.dlt[kz] = col.wxy * peskin4(r.S.xw[2] - (float)mz);
+    }
+    return cn;
+}
+
+// Direct-forcing increment of pass `pass`: R and U~ interpolated from the
+// node values, U~ of the velocity corrected by the force density spread in
+// the earlier passes (u~ + fib / (2 rho)); dF = 2 R (U - U~).  `active` is
+// false for a half-warp without a (valid) marker, which still takes part in
+// the shuffles; the result is valid in every lane of an active half.
+__device__ __forceinline__ float3 interp_force(const EnvDev& E, const MarkerRef& r, const ColumnNodes& cn,
+                                               bool active, int pass, const float4* fib, const float4* nodes) {
+    float R = 0.f, Ux = 0.f, Uy = 0.f, Uz = 0.f;
     if (active) {
-        const Column col = stencil_column(E, r.S, h);
 #pragma unroll
         for (int kz = 0; kz < 4; ++kz) {
-            const int mz = r.S.base[2] + kz;
-            cell[kz] = column_slot(E, col, mz);
-            dlt[kz] = col.wxy * peskin4(r.S.xw[2] - (float)mz);
-        }
-#pragma unroll
-        for (int kz = 0; kz < 4; ++kz) {
-            const float4 nd = __ldcg(nodes + E.slot_off + cell[kz]);
-            R += dlt[kz] * nd.x;
-            Ux += dlt[kz] * nd.y;
-            Uy += dlt[kz] * nd.z;
-            Uz += dlt[kz] * nd.w;
+            float4 nd = __ldcg(nodes + E.slot_off + cn.cell[kz]);
+            if (pass > 0) {   // the force field is zero when the step starts
+                const float4 f = __ldcg(fib + E.slot_off + cn.cell[kz]);
+                const float s = 0.5f / nd.x;
+                nd.y += f.x * s;
+                nd.z += f.y * s;
+                nd.w += f.z * s;
+            }
+            R += cn.dlt[kz] * nd.x;
+            Ux += cn.dlt[kz] * nd.y;
+            Uy += cn.dlt[kz] * nd.z;
+            Uz += cn.dlt[kz] * nd.w;
         }
     }
 #pragma unroll
@@ -307,19 +329,17 @@ __device__ __forceinline__ void ib_force(const EnvDev& E, const MarkerRef& r, bo
         Uy += __shfl_xor_sync(0xffffffffu, Uy, s);
         Uz += __shfl_xor_sync(0xffffffffu, Uz, s);
     }
-    if (!active) return;
-    // direct forcing: F_l = 2 R_l (U_l - U~_l); the grid receives F_l dV_l delta
-    const float Fx = 2.0f * R * (r.U[0] - Ux);
-    const float Fy = 2.0f * R * (r.U[1] - Uy);
-    const float Fz = 2.0f * R * (r.U[2] - Uz);
+    return make_float3(2.0f * R * (r.U[0] - Ux), 2.0f * R * (r.U[1] - Uy), 2.0f * R * (r.U[2] - Uz));
+}
+
+// Spread dF dV delta onto the column's nodes (one vector reduction per node).
+__device__ __forceinline__ void spread_force(const EnvDev& E, const MarkerRef& r, const ColumnNodes& cn, float3 F,
+                                             float4* fib) {
     float4* fb = fib + E.slot_off;
 #pragma unroll
     for (int kz = 0; kz < 4; ++kz) {
-        const float s = r.dV * dlt[kz];
-        atomicAdd(fb + cell[kz], make_float4(Fx * s, Fy * s, Fz * s, 0.f));   // one vector reduction
-    }
-    if (h == 0) {
-        Fm[3 * r.slot] = Fx; Fm[3 * r.slot + 1] = Fy; Fm[3 * r.slot + 2] = Fz;
+        const float s = r.dV * cn.dlt[kz];
+        atomicAdd(fb + cn.cell[kz], make_float4(F.x * s, F.y * s, F.z * s, 0.f));
     }
 }
 
@@ -332,8 +352,8 @@ __global__ void __launch_bounds__(IB_THREADS, 4)
 k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs,
           const FrameDev* __restrict__ frames, int n_envs, int total_markers, int n_stamps,
           const float* __restrict__ X, const float* __restrict__ U, const float* __restrict__ dV,
-          float* __restrict__ Fm, float4* __restrict__ fib, uint32_t* stamps, const StepState* __restrict__ st,
-          float4* nodes, unsigned* bar, int* status) {
+          float* __restrict__ Fm, float4* fib, uint32_t* stamps, const StepState* __restrict__ st,
+          float4* nodes, unsigned* bar, int ib_iters, float* dF, int* status) {
     const int lane = threadIdx.x & 31, h = lane & 15;
     const int gw = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -365,10 +385,12 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
             ib_nodes<S>(gin, envs, frames, n_envs, t0 + k * nw, lane, nodes);
         }
     }
+    // force, pass 0: interpolate, form F and spread it (nothing reads the
+    // force field in this pass)
     if (!grid_barrier(bar, base, 2, status)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) bar[1] = base + 2u * gridDim.x;   // the next launch's base
-    // force (both halves of a warp run the same number of iterations)
-    for (int mb = 2 * gw; mb < total_markers; mb += 2 * nw) {
+    const unsigned last_barrier = 2u * (unsigned)ib_iters;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && last_barrier == 2u) bar[1] = base + 2u * gridDim.x;
+    for (int mb = 2 * gw; mb < total_markers; mb += 2 * nw) {   // both halves iterate alike
         const int m = mb + (lane >> 4);
         const bool here = m < total_markers;
         MarkerRef r;
@@ -380,7 +402,51 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
             Fm[3 * r.slot] = 0.f; Fm[3 * r.slot + 1] = 0.f; Fm[3 * r.slot + 2] = 0.f;
             atomicOr(status, ST_BAD_MARKER);
         }
-        ib_force(envs[r.e], r, here && r.S.ok, h, Fm, fib, nodes);
+        const bool active = here && r.S.ok;
+        const EnvDev& E = envs[r.e];
+        ColumnNodes cn;
+        if (active) cn = column_nodes(E, r, h);
+        const float3 F = interp_force(E, r, cn, active, 0, fib, nodes);
+        if (active) {
+            spread_force(E, r, cn, F, fib);
+            if (h == 0) { Fm[3 * r.slot] = F.x; Fm[3 * r.slot + 1] = F.y; Fm[3 * r.slot + 2] = F.z; }
+        }
+    }
+    // multi-direct forcing, passes 1 .. ib_iters-1: every marker interpolates
+    // the corrected velocity before any spreads this pass's increment (two
+    // grid barriers per pass); the increments wait in dF.
+    for (int pass = 1; pass < ib_iters; ++pass) {
+        if (!grid_barrier(bar, base, 2u * (unsigned)pass + 1u, status)) return;
+        for (int mb = 2 * gw; mb < total_markers; mb += 2 * nw) {
+            const int m = mb + (lane >> 4);
+            const bool here = m < total_markers;
+            MarkerRef r;
+            r.e = 0;
+            r.slot = 0;
+            r.S.ok = false;
+            if (here) r = mb == 2 * gw ? first : load_marker(envs, n_envs, m, X, U, dV);
+            const bool active = here && r.S.ok;
+            const EnvDev& E = envs[r.e];
+            ColumnNodes cn;
+            if (active) cn = column_nodes(E, r, h);
+            const float3 F = interp_force(E, r, cn, active, pass, fib, nodes);
+            if (active && h == 0) {
+                float* Fl = Fm + 3 * r.slot;
+                Fl[0] += F.x; Fl[1] += F.y; Fl[2] += F.z;
+                float* d = dF + 3 * r.slot;
+                d[0] = F.x; d[1] = F.y; d[2] = F.z;
+            }
+        }
+        if (!grid_barrier(bar, base, 2u * (unsigned)pass + 2u, status)) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0 && 2u * (unsigned)pass + 2u == last_barrier)
+            bar[1] = base + last_barrier * gridDim.x;   // the next launch's base
+        for (int m = 2 * gw + (lane >> 4); m < total_markers; m += 2 * nw) {
+            const MarkerRef r = m < 2 * nw ? first : load_marker(envs, n_envs, m, X, U, dV);
+            if (!r.S.ok) continue;
+            const EnvDev& E = envs[r.e];
+            const float* d = dF + 3 * r.slot;
+            spread_force(E, r, column_nodes(E, r, h), make_float3(__ldcg(d), __ldcg(d + 1), __ldcg(d + 2)), fib);
+        }
     }
 }
 

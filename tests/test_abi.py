@@ -48,6 +48,21 @@ def test_lattice_is_d3q27():
     assert (c[26 - __import__("numpy").arange(27)] == -c).all()   # opposite of i is 26 - i
 
 
+def test_ib_iters_out_of_range_is_rejected_before_gpu_work():
+    env = fishlbm.env_desc((8, 8, 8), 0.6)
+    for m in (0, 9, -1):
+        opt = fishlbm.fg_options()
+        opt.storage = 0
+        opt.ib_iters = m
+        opt.use_graphs = 1
+        try:
+            fishlbm.fg_create_domain([env], opt)
+        except fishlbm.FgError as e:
+            assert e.status == fishlbm.FG_ERR_INVALID, m
+        else:
+            raise AssertionError("ib_iters = %d accepted" % m)
+
+
 def test_invalid_arguments_fail_without_gpu_work():
     bad = fishlbm.env_desc((8, 8, 8), 0.5)      # tau must exceed 1/2
     try:
