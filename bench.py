@@ -213,14 +213,15 @@ def _variant_kw(args):
 
 
 def storage_form(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, K, world, peak, vkw,
-                 ib_iters=1):
+                 ib_iters=1, deterministic=False):
     """The swimmer-channel step with populations stored as FP16 / BF16 (or
     FP32 with ib_iters direct-forcing passes)."""
     import torch
     from paper_2206_01683_b300 import fishlbm
     stream = torch.cuda.Stream()
     dom = fishlbm.Domain([fishlbm.env_desc(shape, tau, OPEN_X, (u_in, 0, 0), 1.0, (u_in, 0, 0))],
-                         storage=storage, stream=stream.cuda_stream, ib_iters=ib_iters, **vkw)
+                         storage=storage, stream=stream.cuda_stream, ib_iters=ib_iters,
+                         deterministic=deterministic, **vkw)
     dom.set_markers(Xd[0], Ud[0], dVd, segd, n_seg=5, ref=ref)
 
     def step(n):
@@ -238,7 +239,7 @@ def storage_form(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W,
     dom.close()
     return {"value": round(world * ncell * K / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
             "ms_per_step": round(ms / K, 5), "storage": storage, "kernel_variant": variant,
-            "ib_iters": ib_iters,
+            "ib_iters": ib_iters, "deterministic": bool(deterministic),
             "roofline": {"bound": "hbm", "kernel": "k_stream_collide", "achieved": round(gbs, 1),
                          "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
                          "algorithmic_bytes_per_cell": 216 if storage == "f32" else 108,
@@ -394,6 +395,8 @@ def run_ours(args):
                                  _variant_kw(args)),
             "mdf3": storage_form("f32", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world, peak,
                                  _variant_kw(args), ib_iters=3),
+            "deterministic": storage_form("f32", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world,
+                                          peak, _variant_kw(args), deterministic=True),
             "batched": batched_form(W, Kf, world, peak, _variant_kw(args)),
             "adjoint": adjoint_form(),
         }

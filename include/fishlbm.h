@@ -77,7 +77,11 @@ typedef enum { FG_KERNEL_AUTO = 0, FG_KERNEL_PLAIN = 1, FG_KERNEL_STAGED = 2, FG
 typedef struct {
     int storage;        /* fg_storage */
     int layout;         /* 0: two-buffer pull scheme (the only layout) */
-    int deterministic;  /* 0 (reserved) */
+    int deterministic;  /* 1: the IB spread sums each node's contributions as
+                           64-bit fixed-point integers (multiples of 2^-48,
+                           exact and order-independent), so every step is
+                           bit-reproducible; 0: FP32 vector atomics (the sum's
+                           rounding depends on arrival order) */
     int ib_iters;       /* direct-forcing passes per step, 1..FG_MAX_IB_ITERS
                            (multi-direct forcing; each pass interpolates the
                            velocity corrected by the force spread in the

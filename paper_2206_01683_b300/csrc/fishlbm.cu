@@ -87,6 +87,7 @@ struct fg_domain {
     uint32_t* stamps = nullptr;
     unsigned long long n_stamps = 0;
     float4* ib_nodes = nullptr;          // per slot: rho, u~ of the stamped tiles' cells
+    unsigned long long* fibq = nullptr;  // deterministic spread: fixed-point sums [slot][3]
     unsigned* ib_bar = nullptr;          // grid barrier of k_ib_step: arrival counter, base
     int ib_per_sm = 0;                   // resident blocks of k_ib_step per SM
     uint32_t stamp_host = 1;             // host mirror of StepState::stamp
@@ -189,7 +190,7 @@ void free_all(fg_domain* d) {
     for (void* p : adj)
         if (p) cudaFree(p);
     void* ptrs[] = {d->d_env, d->d_frame, d->pop[0], d->pop[1], d->fib, d->stamps, d->ib_nodes, d->ib_bar,
-                    d->mass_part, d->red_partials, d->red_counters, d->d_state,
+                    d->fibq, d->mass_part, d->red_partials, d->red_counters, d->d_state,
                     d->X, d->U, d->dV, d->Fm, d->dF, d->seg, d->ft, d->mass, d->hist, d->status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -328,7 +329,7 @@ fg_status enqueue_step(fg_domain* d, int parity, cudaStream_t s, cudaEvent_t* co
         CK(cudaLaunchKernelEx(&cfg, k_ib_step<S>, gin, (const EnvDev*)d->d_env, (const FrameDev*)d->d_frame,
                               d->n_envs, d->total_markers, (int)d->n_stamps, (const float*)d->X, (const float*)d->U,
                               (const float*)d->dV, d->Fm, d->fib, d->stamps, (const StepState*)d->d_state,
-                              d->ib_nodes, d->ib_bar, d->opt.ib_iters, d->dF, d->status));
+                              d->ib_nodes, d->ib_bar, d->opt.ib_iters, d->dF, d->fibq, d->status));
         if (ev) CK(cudaEventRecord(ev[FG_K_IB][1], s));
     }
     if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][0], s));
@@ -545,6 +546,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     if (o.storage < 0 || o.storage > 2) return fail(FG_ERR_INVALID, "unknown storage");
     if (o.layout != 0) return fail(FG_ERR_INVALID, "only the two-buffer pull layout (0) exists");
     if (o.ib_iters < 1 || o.ib_iters > FG_MAX_IB_ITERS) return fail(FG_ERR_INVALID, "ib_iters must be in [1, 8]");
+    if (o.deterministic != 0 && o.deterministic != 1) return fail(FG_ERR_INVALID, "deterministic must be 0 or 1");
     if (o.record_history < 0 || o.record_history > (1 << 20)) return fail(FG_ERR_INVALID, "record_history");
     unsigned long long cells = 0;
     for (int e = 0; e < n_envs; ++e) {
@@ -647,6 +649,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     DA(d->stamps, stamp_off);
     DA(d->ib_nodes, slot_off);
     DA(d->ib_bar, 2);
+    if (o.deterministic) DA(d->fibq, 3ull * slot_off);
     DA(d->red_counters, (size_t)n_envs * RED_ROWS);
     DA(d->d_state, 1);
     DA(d->ft, (size_t)n_envs * FT_ROW);   // compensated pairs, evaluated on the host
@@ -667,6 +670,8 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         (ce = cudaMemsetAsync(d->mass, 0, sizeof(Pair32) * n_envs, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->status, 0, sizeof(int), d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->ib_bar, 0, 2 * sizeof(unsigned), d->stream)) != cudaSuccess ||
+        (d->fibq && (ce = cudaMemsetAsync(d->fibq, 0, sizeof(unsigned long long) * 3ull * slot_off,
+                                          d->stream)) != cudaSuccess) ||
         (ce = cudaMemsetAsync(d->red_counters, 0, sizeof(int) * n_envs * RED_ROWS, d->stream)) != cudaSuccess ||
         (ce = cudaMemcpyAsync(d->d_state, &initial_state, sizeof(StepState), cudaMemcpyHostToDevice,
                               d->stream)) != cudaSuccess) {

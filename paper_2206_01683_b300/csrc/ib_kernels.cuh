@@ -297,20 +297,56 @@ __device__ __forceinline__ ColumnNodes column_nodes(const EnvDev& E, const Marke
     return cn;
 }
 
+// Deterministic spread: every contribution is rounded to a multiple of 2^-48
+// and summed as a 64-bit integer.  Integer addition is exact and associative,
+// so the sum does not depend on the order in which the reductions land; it
+// is converted back to FP32 once.  |contributions| and |sums| must stay below
+// 2^15 (force densities here are far smaller); larger contributions are
+// flagged as a numeric fault.
+constexpr float FIX_SCALE = 281474976710656.0f;        // 2^48
+constexpr float FIX_INV = 3.5527136788005009294e-15f;  // 2^-48
+
+__device__ __forceinline__ void spread_force_fixed(const EnvDev& E, const MarkerRef& r, const ColumnNodes& cn,
+                                                   float3 F, unsigned long long* fibq, int* status) {
+    unsigned long long* q = fibq + 3ull * E.slot_off;
+#pragma unroll
+    for (int kz = 0; kz < 4; ++kz) {
+        const float s = r.dV * cn.dlt[kz];
+        const float v[3] = {F.x * s, F.y * s, F.z * s};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (!(fabsf(v[a]) < 16384.0f)) atomicOr(status, ST_NUMERIC);
+            atomicAdd(q + 3ull * cn.cell[kz] + a, (unsigned long long)__float2ll_rn(v[a] * FIX_SCALE));
+        }
+    }
+}
+
+__device__ __forceinline__ float fixed_to_float(unsigned long long q) {
+    return __ll2float_rn((long long)q) * FIX_INV;
+}
+
 // Direct-forcing increment of pass `pass`: R and U~ interpolated from the
 // node values, U~ of the velocity corrected by the force density spread in
 // the earlier passes (u~ + fib / (2 rho)); dF = 2 R (U - U~).  `active` is
 // false for a half-warp without a (valid) marker, which still takes part in
 // the shuffles; the result is valid in every lane of an active half.
 __device__ __forceinline__ float3 interp_force(const EnvDev& E, const MarkerRef& r, const ColumnNodes& cn,
-                                               bool active, int pass, const float4* fib, const float4* nodes) {
+                                               bool active, int pass, const float4* fib,
+                                               const unsigned long long* fibq, const float4* nodes) {
     float R = 0.f, Ux = 0.f, Uy = 0.f, Uz = 0.f;
     if (active) {
 #pragma unroll
         for (int kz = 0; kz < 4; ++kz) {
             float4 nd = __ldcg(nodes + E.slot_off + cn.cell[kz]);
             if (pass > 0) {   // the force field is zero when the step starts
-                const float4 f = __ldcg(fib + E.slot_off + cn.cell[kz]);
+                float4 f;
+                if (fibq) {   // deterministic spread: the fixed-point sums
+                    const unsigned long long* q = fibq + 3ull * (E.slot_off + cn.cell[kz]);
+                    f = make_float4(fixed_to_float(__ldcg(q)), fixed_to_float(__ldcg(q + 1)),
+                                    fixed_to_float(__ldcg(q + 2)), 0.f);
+                } else {
+                    f = __ldcg(fib + E.slot_off + cn.cell[kz]);
+                }
                 const float s = 0.5f / nd.x;
                 nd.y += f.x * s;
                 nd.z += f.y * s;
@@ -346,19 +382,32 @@ __device__ __forceinline__ void spread_force(const EnvDev& E, const MarkerRef& r
 // The IB part of one step.  Launched cooperatively with at most as many
 // blocks as fit on the device at once; half-warps stride over markers (the
 // first marker of each half-warp stays in registers from the mark phase to
-// the force phase), warps over tile stamps.
+// the force phase), warps over tile stamps.  fibq != nullptr selects the
+// deterministic spread (fixed-point sums, converted to fib in a last phase).
 template <class S>
 __global__ void __launch_bounds__(IB_THREADS, 4)
 k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs,
           const FrameDev* __restrict__ frames, int n_envs, int total_markers, int n_stamps,
           const float* __restrict__ X, const float* __restrict__ U, const float* __restrict__ dV,
           float* __restrict__ Fm, float4* fib, uint32_t* stamps, const StepState* __restrict__ st,
-          float4* nodes, unsigned* bar, int ib_iters, float* dF, int* status) {
+          float4* nodes, unsigned* bar, int ib_iters, float* dF, unsigned long long* fibq, int* status) {
     const int lane = threadIdx.x & 31, h = lane & 15;
     const int gw = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int nw = (int)((gridDim.x * blockDim.x) >> 5);
     const uint32_t stamp = st->stamp;
     const unsigned base = __ldcg(bar + 1);
+    // barriers of this launch: mark, nodes, two per extra pass, the conversion
+    const unsigned n_bar = 2u * (unsigned)ib_iters + (fibq ? 1u : 0u);
+    unsigned nb = 0;
+    auto barrier = [&]() -> bool {
+        if (!grid_barrier(bar, base, ++nb, status)) return false;
+        if (nb == n_bar && blockIdx.x == 0 && threadIdx.x == 0) bar[1] = base + n_bar * gridDim.x;
+        return true;
+    };
+    auto spread = [&](const EnvDev& E, const MarkerRef& r, const ColumnNodes& cn, float3 F) {
+        if (fibq) spread_force_fixed(E, r, cn, F, fibq, status);
+        else spread_force(E, r, cn, F, fib);
+    };
     const int m0 = 2 * gw + (lane >> 4);
     // mark
     MarkerRef first;
@@ -373,7 +422,7 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
         const Stencil Sm = marker_stencil(E, X, E.marker_off + (m - E.mk_begin));
         if (Sm.ok) ib_mark(E, Sm, h, stamp, stamps);   // invalid markers are reported by the force phase
     }
-    if (!grid_barrier(bar, base, 1, status)) return;
+    if (!barrier()) return;
     // nodes: lane k of warp gw reads the stamp of tile gw + nw (k + 32 j)
     for (int t0 = gw; t0 < n_stamps; t0 += 32 * nw) {
         const long long t = (long long)t0 + (long long)lane * nw;
@@ -385,11 +434,9 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
             ib_nodes<S>(gin, envs, frames, n_envs, t0 + k * nw, lane, nodes);
         }
     }
+    if (!barrier()) return;
     // force, pass 0: interpolate, form F and spread it (nothing reads the
     // force field in this pass)
-    if (!grid_barrier(bar, base, 2, status)) return;
-    const unsigned last_barrier = 2u * (unsigned)ib_iters;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && last_barrier == 2u) bar[1] = base + 2u * gridDim.x;
     for (int mb = 2 * gw; mb < total_markers; mb += 2 * nw) {   // both halves iterate alike
         const int m = mb + (lane >> 4);
         const bool here = m < total_markers;
@@ -406,9 +453,9 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
         const EnvDev& E = envs[r.e];
         ColumnNodes cn;
         if (active) cn = column_nodes(E, r, h);
-        const float3 F = interp_force(E, r, cn, active, 0, fib, nodes);
+        const float3 F = interp_force(E, r, cn, active, 0, fib, fibq, nodes);
         if (active) {
-            spread_force(E, r, cn, F, fib);
+            spread(E, r, cn, F);
             if (h == 0) { Fm[3 * r.slot] = F.x; Fm[3 * r.slot + 1] = F.y; Fm[3 * r.slot + 2] = F.z; }
         }
     }
@@ -416,7 +463,7 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
     // the corrected velocity before any spreads this pass's increment (two
     // grid barriers per pass); the increments wait in dF.
     for (int pass = 1; pass < ib_iters; ++pass) {
-        if (!grid_barrier(bar, base, 2u * (unsigned)pass + 1u, status)) return;
+        if (!barrier()) return;
         for (int mb = 2 * gw; mb < total_markers; mb += 2 * nw) {
             const int m = mb + (lane >> 4);
             const bool here = m < total_markers;
@@ -429,7 +476,7 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
             const EnvDev& E = envs[r.e];
             ColumnNodes cn;
             if (active) cn = column_nodes(E, r, h);
-            const float3 F = interp_force(E, r, cn, active, pass, fib, nodes);
+            const float3 F = interp_force(E, r, cn, active, pass, fib, fibq, nodes);
             if (active && h == 0) {
                 float* Fl = Fm + 3 * r.slot;
                 Fl[0] += F.x; Fl[1] += F.y; Fl[2] += F.z;
@@ -437,15 +484,36 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
                 d[0] = F.x; d[1] = F.y; d[2] = F.z;
             }
         }
-        if (!grid_barrier(bar, base, 2u * (unsigned)pass + 2u, status)) return;
-        if (blockIdx.x == 0 && threadIdx.x == 0 && 2u * (unsigned)pass + 2u == last_barrier)
-            bar[1] = base + last_barrier * gridDim.x;   // the next launch's base
-        for (int m = 2 * gw + (lane >> 4); m < total_markers; m += 2 * nw) {
-            const MarkerRef r = m < 2 * nw ? first : load_marker(envs, n_envs, m, X, U, dV);
+        if (!barrier()) return;
+        for (int m = m0; m < total_markers; m += 2 * nw) {
+            const MarkerRef r = m == m0 ? first : load_marker(envs, n_envs, m, X, U, dV);
             if (!r.S.ok) continue;
             const EnvDev& E = envs[r.e];
             const float* d = dF + 3 * r.slot;
-            spread_force(E, r, column_nodes(E, r, h), make_float3(__ldcg(d), __ldcg(d + 1), __ldcg(d + 2)), fib);
+            spread(E, r, column_nodes(E, r, h), make_float3(__ldcg(d), __ldcg(d + 1), __ldcg(d + 2)));
+        }
+    }
+    if (!fibq) return;
+    // deterministic spread: convert the fixed-point sums of every stamped tile
+    // to the FP32 force field and clear them
+    if (!barrier()) return;
+    for (int t0 = gw; t0 < n_stamps; t0 += 32 * nw) {
+        const long long t = (long long)t0 + (long long)lane * nw;
+        const bool hit = t < n_stamps && __ldcg(stamps + t) == stamp;
+        unsigned hits = __ballot_sync(0xffffffffu, hit);
+        while (hits) {
+            const int k = __ffs(hits) - 1;
+            hits &= hits - 1u;
+            const int tt = t0 + k * nw;
+            const int e = n_envs > 1 ? env_of<&EnvDev::stamp_off>(envs, n_envs, tt) : 0;
+            const EnvDev& E = envs[e];
+            const uint32_t c = (uint32_t)(tt - E.stamp_off) * 32u + (uint32_t)lane;
+            if (c < E.nslot) {
+                unsigned long long* q = fibq + 3ull * (E.slot_off + c);
+                const unsigned long long qx = __ldcg(q), qy = __ldcg(q + 1), qz = __ldcg(q + 2);
+                fib[E.slot_off + c] = make_float4(fixed_to_float(qx), fixed_to_float(qy), fixed_to_float(qz), 0.f);
+                q[0] = 0ull; q[1] = 0ull; q[2] = 0ull;
+            }
         }
     }
 }

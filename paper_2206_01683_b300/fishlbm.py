@@ -216,12 +216,12 @@ class Domain:
     """Owns one fg_domain (one or many environments)."""
 
     def __init__(self, envs, storage="f32", record_history=0, stream=None, variant="auto",
-                 graphs=True, autotune=False, ib_iters=1):
+                 graphs=True, autotune=False, ib_iters=1, deterministic=False):
         self.envs = list(envs)
         opt = fg_options()
         opt.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
         opt.layout = 0
-        opt.deterministic = 0
+        opt.deterministic = 1 if deterministic else 0
         opt.ib_iters = int(ib_iters)
         opt.record_history = int(record_history)
         opt.kernel_variant = VARIANT[variant] if isinstance(variant, str) else int(variant)

@@ -41,11 +41,11 @@ class Pair:
     """One GPU domain (single environment) and one oracle, stepped together."""
 
     def __init__(self, shape, tau, faces=(0,) * 6, u_in=(0.0, 0.0, 0.0), rho0=1.0, storage="f32",
-                 variant="auto", ib_iters=1):
+                 variant="auto", ib_iters=1, deterministic=False):
         self.shape = tuple(shape)
         self.o = oracle.Oracle(shape, tau, faces=faces, u_in=f32(u_in), rho_out=rho0, ib_iters=ib_iters)
         self.g = fishlbm.Domain([fishlbm.env_desc(shape, tau, faces, f32(u_in), rho0)], storage=storage,
-                                variant=variant, ib_iters=ib_iters)
+                                variant=variant, ib_iters=ib_iters, deterministic=deterministic)
         self.perm = gpu_to_oracle_perm()
         _, self.w = oracle.lattice()
         self.nseg = 1

@@ -125,6 +125,48 @@ def test_multi_direct_forcing_reduces_gpu_marker_slip():
     assert all(b > a for a, b in zip(drag, drag[1:])), drag
 
 
+@pytest.mark.parametrize("M", [1, 3])
+def test_deterministic_spread_parity(M):
+    """The fixed-point (deterministic) spread against the oracle: sphere box,
+    60 steps, one and three direct-forcing passes."""
+    cfg = inputs.SPHERE_BOX
+    p = Pair(cfg["shape"], cfg["tau"], ib_iters=M, deterministic=True)
+    for n in range(60):
+        X, U, dV = inputs.translating_sphere(cfg["n_markers"], cfg["radius"], cfg["center"],
+                                             cfg["velocity"], n)
+        p.markers(X, U, dV)
+        p.step()
+    assert_parity(p.errors(), keys=("rho", "u", "pop", "force", "torque"))
+
+
+def _swimmer_run(deterministic, ib_iters, steps=30, variant="staged"):
+    shape = (96, 48, 48)
+    fish = inputs.fish_for_grid(shape, 24.0, 900)
+    traj = inputs.FrameTrajectory(inputs.seed_for(2), inputs.domain_centre(shape))
+    d = fishlbm.Domain([fishlbm.env_desc(shape, 0.52, OPEN_X, (0.02, 0, 0), 1.0, (0.02, 0, 0))],
+                       record_history=steps, variant=variant, ib_iters=ib_iters, deterministic=deterministic)
+    for n in range(steps):
+        X, U = fish.pose(n)
+        d.set_markers(np.float32(X), np.float32(U), np.float32(fish.dV), seg=fish.seg, n_seg=5,
+                      ref=fish.joints_rest[0])
+        d.step(1, [fishlbm.frame_from_array(traj.at(n))])
+    return d.populations(), d.history(steps)
+
+
+@pytest.mark.parametrize("M", [1, 3])
+def test_deterministic_spread_is_bit_reproducible(M):
+    """Two fresh runs of the swimmer channel (30 steps, moving frame, open
+    faces) with the deterministic spread give identical populations and force
+    histories, bit for bit; they agree with the atomic spread to rounding."""
+    f1, h1 = _swimmer_run(True, M)
+    f2, h2 = _swimmer_run(True, M)
+    assert np.array_equal(f1, f2)
+    assert np.array_equal(h1, h2)
+    fa, ha = _swimmer_run(False, M)
+    assert rel_l2(f1, fa) < 1e-6
+    assert rel_l2(h1, ha) < 1e-5
+
+
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_ragged_grid_mixed_faces_rotating_frame(variant):
     """37x23x11 (rows padded to a pitch of 40, not a multiple of 32 or 256):
