@@ -53,6 +53,8 @@ def lib():
         L.orc_frame_accel.argtypes = [P(d), d, d, d, P(d)]
         L.orc_set_ib_iters.restype = i
         L.orc_set_ib_iters.argtypes = [vp, i]
+        L.orc_set_slip.restype = i
+        L.orc_set_slip.argtypes = [vp, i, i, P(d)]
         _lib = L
     return _lib
 
@@ -105,7 +107,8 @@ def make_frame(acc=(0, 0, 0), omega=(0, 0, 0), domega=(0, 0, 0), origin=(0, 0, 0
 class Oracle:
     """One FP64 domain.  Fields use cell index x + nx*(y + ny*z)."""
 
-    def __init__(self, shape, tau, faces=(PERIODIC,) * 6, u_in=(0.0, 0.0, 0.0), rho_out=1.0, ib_iters=1):
+    def __init__(self, shape, tau, faces=(PERIODIC,) * 6, u_in=(0.0, 0.0, 0.0), rho_out=1.0, ib_iters=1,
+                 slip=False):
         nx, ny, nz = shape
         self.shape = (nx, ny, nz)
         self.ncell = nx * ny * nz
@@ -118,6 +121,7 @@ class Oracle:
             lib().orc_destroy(self._h)
             self._h = None
             raise ValueError("oracle: ib_iters must be in [1, 64]")
+        self.slip = bool(slip)
         self.tau = tau
         self.faces = tuple(int(f) for f in faces)
         self.nm = 0
@@ -136,7 +140,8 @@ class Oracle:
         lib().orc_init_fields(self._h, _dp(r) if r is not None else None,
                               _dp(v) if v is not None else None)
 
-    def set_markers(self, X, U, dV, seg=None, nseg=1, ref=(0.0, 0.0, 0.0)):
+    def set_markers(self, X, U, dV, seg=None, nseg=1, ref=(0.0, 0.0, 0.0), normals=None):
+        """normals: unit surface normals (n, 3), required with slip=True."""
         X = _f64(X).reshape(-1, 3)
         n = X.shape[0]
         U = _f64(U, (n, 3))
@@ -149,11 +154,18 @@ class Oracle:
             raise ValueError("oracle: invalid markers")
         self.nm = n
         self.nseg = max(int(nseg), 1)
+        if self.slip:
+            if normals is None:
+                raise ValueError("oracle: slip forcing needs marker normals")
+            N = _f64(normals, (n, 3))
+            if lib().orc_set_slip(self._h, 1, n, _dp(N)) != 0:
+                raise ValueError("oracle: invalid normals")
 
     def step(self, frame=None, n=1):
         fr = make_frame() if frame is None else _f64(frame, (12,))
         for _ in range(n):
-            lib().orc_step(self._h, _dp(fr))
+            if lib().orc_step(self._h, _dp(fr)) != 0:
+                raise ValueError("oracle: step refused (slip forcing without normals)")
 
     def populations(self):
         f = np.zeros((self.ncell, 27))

@@ -21,7 +21,8 @@
  *   - delta kernel: Peskin's 4-point function;
  *   - marker force: direct forcing, F_l = 2 R_l (U_l - U~_l), in M passes
  *     (multi-direct forcing; M = 1 by default), each pass interpolating the
- *     velocity corrected by the force spread so far;
+ *     velocity corrected by the force spread so far; optionally only the
+ *     normal component of the slip (the paper's slipping wall, Sec. III-B);
  *   - frame force (Eq. 3): dr/dt read as the frame angular velocity omega,
  *     d2r/dt2 as its rate domega, and x' measured from a caller-given origin;
  *     the Coriolis term is solved implicitly together with the Guo half-shift;
@@ -81,6 +82,8 @@ typedef struct {
     double *rho, *j, *Pi;/* post-stream moments: rho, j[3], Pi[6] (xx,yy,zz,xy,xz,yz) */
     double *fib;         /* spread IB force density, [ncell][3] */
     int ib_iters;        /* direct-forcing passes M (>= 1) */
+    int slip;            /* 1: enforce only the normal velocity component */
+    double *Nrm;         /* unit marker normals [nm][3] (slip) */
     int nm, nseg;        /* markers */
     double *X, *U, *dV;  /* [nm][3], [nm][3], [nm] */
     int *seg;
@@ -136,7 +139,7 @@ void orc_destroy(void *h) {
     orc_t *o = (orc_t *)h;
     if (!o) return;
     free(o->f); free(o->fs); free(o->rho); free(o->j); free(o->Pi); free(o->fib);
-    free(o->X); free(o->U); free(o->dV); free(o->seg); free(o->Fm);
+    free(o->X); free(o->U); free(o->dV); free(o->seg); free(o->Fm); free(o->Nrm);
     free(o);
 }
 
@@ -346,7 +349,8 @@ int orc_set_markers(void *h, int n, const double *X, const double *U, const doub
         if (!marker_ok(o, X + 3 * l)) return -1;
         if (seg && (seg[l] < 0 || seg[l] >= (nseg > 0 ? nseg : 1))) return -1;
     }
-    free(o->X); free(o->U); free(o->dV); free(o->seg); free(o->Fm);
+    free(o->X); free(o->U); free(o->dV); free(o->seg); free(o->Fm); free(o->Nrm);
+    o->Nrm = NULL;
     o->nm = n;
     o->nseg = nseg;
     o->X = (double *)malloc(sizeof(double) * 3 * (n ? n : 1));
@@ -409,12 +413,18 @@ static void direct_forcing(orc_t *o, const double *frame) {
     memset(o->Fm, 0, sizeof(double) * 3 * n);
     for (int m = 0; m < o->ib_iters; ++m) {
         interp(o, ut, n, o->X, Ui);
-        for (int l = 0; l < n; ++l)
+        for (int l = 0; l < n; ++l) {
+            for (int a = 0; a < 3; ++a) dF[3 * l + a] = 2.0 * Ri[3 * l] * (o->U[3 * l + a] - Ui[3 * l + a]);
+            if (o->slip) {   /* keep the normal component: dF <- (dF.n) n */
+                const double *nl = o->Nrm + 3 * l;
+                const double dn = dF[3 * l] * nl[0] + dF[3 * l + 1] * nl[1] + dF[3 * l + 2] * nl[2];
+                for (int a = 0; a < 3; ++a) dF[3 * l + a] = dn * nl[a];
+            }
             for (int a = 0; a < 3; ++a) {
-                dF[3 * l + a] = 2.0 * Ri[3 * l] * (o->U[3 * l + a] - Ui[3 * l + a]);
                 o->Fm[3 * l + a] += dF[3 * l + a];
                 dFdV[3 * l + a] = dF[3 * l + a] * o->dV[l];
             }
+        }
         memset(dfib, 0, sizeof(double) * 3 * o->ncell);
         spread(o, n, o->X, dFdV, dfib);
         for (long c = 0; c < o->ncell; ++c)
@@ -424,6 +434,28 @@ static void direct_forcing(orc_t *o, const double *frame) {
             }
     }
     free(ut); free(rr); free(Ui); free(Ri); free(dF); free(dFdV); free(dfib);
+}
+
+/* Slip (Neumann) direct forcing: only the normal component of the marker
+ * slip is enforced, dF_l = 2 R_l ((U_l - U~_l).n_l) n_l, so the fluid may
+ * slide along the surface.  N: unit normals [n][3] of the current markers
+ * (n must equal their count; normalised here). */
+int orc_set_slip(void *h, int on, int n, const double *N) {
+    orc_t *o = (orc_t *)h;
+    if (!on) {
+        o->slip = 0;
+        return 0;
+    }
+    if (n != o->nm || (n > 0 && !N)) return -1;
+    free(o->Nrm);
+    o->Nrm = (double *)malloc(sizeof(double) * 3 * (n ? n : 1));
+    for (int l = 0; l < n; ++l) {
+        double s = sqrt(N[3 * l] * N[3 * l] + N[3 * l + 1] * N[3 * l + 1] + N[3 * l + 2] * N[3 * l + 2]);
+        if (!(s > 0.0)) return -1;
+        for (int a = 0; a < 3; ++a) o->Nrm[3 * l + a] = N[3 * l + a] / s;
+    }
+    o->slip = 1;
+    return 0;
 }
 
 int orc_set_ib_iters(void *h, int m) {
@@ -566,6 +598,7 @@ static void force_torque(orc_t *o) {
 int orc_step(void *h, const double *frame) {
     orc_t *o = (orc_t *)h;
     const int nx = o->n[0], ny = o->n[1], nz = o->n[2];
+    if (o->slip && o->nm > 0 && !o->Nrm) return -1;   /* normals of the current markers */
     stream(o);                 /* 1 */
     moments(o);                /* 2 */
     direct_forcing(o, frame);  /* 3-5 and 6a: marker forces, spread F_l dV_l */

@@ -61,6 +61,14 @@ MUTANTS = {
         "ut[3 * c + a] += dfib[3 * c + a] / (2.0 * o->rho[c]);",
         "ut[3 * c + a] += dfib[3 * c + a] / (1.0 * o->rho[c]);",
         "test_multi_direct_forcing_isolated_markers_closed_form"),
+    "slip_projection_dropped": (
+        "for (int a = 0; a < 3; ++a) dF[3 * l + a] = dn * nl[a];",
+        "for (int a = 0; a < 3; ++a) dF[3 * l + a] = dF[3 * l + a] + 0.0 * dn * nl[a];",
+        "test_slip_forcing_isolated_markers_closed_form"),
+    "slip_tangential_kept": (
+        "for (int a = 0; a < 3; ++a) dF[3 * l + a] = dn * nl[a];",
+        "for (int a = 0; a < 3; ++a) dF[3 * l + a] = dn * nl[a] + 0.01 * (dF[3 * l + a] - dn * nl[a]);",
+        "test_slip_sheet_leaves_tangential_shear_untouched"),
     "mdf_force_not_accumulated": (
         "o->Fm[3 * l + a] += dF[3 * l + a];", "o->Fm[3 * l + a] = dF[3 * l + a];",
         "test_multi_direct_forcing_isolated_markers_closed_form"),

@@ -22,7 +22,10 @@ a shifted stencil, a transposed cross product) fails one of them:
 * frame force of Eq. 3 for a pure rotation (centrifugal and Euler terms);
 * multi-direct forcing: for isolated markers in fluid at rest the force after
   M passes has a closed form; on a marker shell the interpolated slip falls
-  with every pass.
+  with every pass;
+* slip (Neumann) forcing: the normal-only closed form for isolated markers,
+  exact invariance of a tangential shear past a flat slip sheet, and the drag
+  of a slip sphere between a bubble's and a no-slip sphere's.
 """
 import math
 import os
@@ -568,3 +571,98 @@ def test_multi_direct_forcing_reduces_marker_slip():
     o1.set_markers(X, U, dV)
     o1.step()
     assert np.array_equal(o1.marker_force(), forces[1])
+
+
+@pytest.mark.parametrize("M", [1, 3])
+def test_slip_forcing_isolated_markers_closed_form(M):
+    """Slip (Neumann) forcing enforces only the normal component of the
+    marker velocity: for markers with disjoint stencils in fluid at rest,
+    F_l = 2 (U_l.n_l) n_l (1 - (1 - k_l)^M) / k_l (the multi-direct-forcing
+    closed form restricted to the normal direction); a purely tangential
+    U_l gives exactly zero force."""
+    shape = (24, 24, 24)
+    rng = np.random.default_rng(23)
+    base = np.array([[x, y, z] for x in (4.0, 12.0) for y in (4.0, 13.0) for z in (3.0, 12.0)])
+    X = base + rng.uniform(0, 1, base.shape)
+    n = X.shape[0]
+    N = rng.standard_normal((n, 3))
+    N /= np.linalg.norm(N, axis=1, keepdims=True)
+    U = rng.uniform(-0.02, 0.02, (n, 3))
+    dV = rng.uniform(0.5, 3.0, n)
+    o = oracle.Oracle(shape, 0.8, ib_iters=M, slip=True)
+    o.set_markers(X, U, dV, normals=N)
+    o.step()
+    F = o.marker_force()
+    for l in range(n):
+        s2 = 1.0
+        for a in range(3):
+            m0 = math.floor(X[l, a]) - 1
+            s2 *= sum(_peskin(X[l, a] - (m0 + k)) ** 2 for k in range(4))
+        kap = dV[l] * s2
+        expect = 2.0 * (U[l] @ N[l]) * N[l] * (1.0 - (1.0 - kap) ** M) / kap
+        assert np.allclose(F[l], expect, rtol=1e-12, atol=1e-16), (l, F[l], expect)
+    Ut = U - (U * N).sum(axis=1, keepdims=True) * N          # tangential part only
+    o = oracle.Oracle(shape, 0.8, ib_iters=M, slip=True)
+    o.set_markers(X, Ut, dV, normals=N)
+    o.step()
+    assert np.max(np.abs(o.marker_force())) < 1e-17
+
+
+def test_slip_sheet_leaves_tangential_shear_untouched():
+    """A flat sheet of markers (normal z, spanning the periodic xy plane) in a
+    shear wave u_x(z): with slip forcing nothing is enforced along the sheet,
+    so after 50 steps the flow equals the flow without markers (to rounding:
+    the normal velocity the sheet sees is zero up to rounding); the no-slip
+    sheet changes it by far more."""
+    shape = (16, 12, 24)
+    nx, ny, nz = shape
+    z = np.arange(nz)
+    u = np.zeros((nx * ny * nz, 3))
+    u[:, 0] = np.repeat(0.01 * np.sin(2 * math.pi * z / nz), nx * ny)
+    rho = np.ones(nx * ny * nz)
+    xs, ys = np.meshgrid(np.arange(0.0, nx, 0.8), np.arange(0.0, ny, 0.8), indexing="ij")
+    X = np.stack([xs.ravel(), ys.ravel(), np.full(xs.size, 9.3)], axis=1)
+    n = X.shape[0]
+    N = np.tile([0.0, 0.0, 1.0], (n, 1))
+    dV = np.full(n, 0.64)
+
+    def run(markers, slip):
+        o = oracle.Oracle(shape, 0.8, slip=slip)
+        o.init_fields(rho, u)
+        for _ in range(50):
+            if markers:
+                o.set_markers(X, np.zeros((n, 3)), dV, normals=N)
+            o.step()
+        return o.populations()
+
+    free = run(False, False)
+    # w is zero up to rounding, so the slip sheet's forces are rounding-sized
+    assert np.max(np.abs(run(True, True) - free)) < 1e-15
+    assert np.max(np.abs(run(True, False) - free)) > 1e-5
+
+
+@pytest.mark.slow
+def test_slip_sphere_drag_between_bubble_and_no_slip():
+    """The periodic translating sphere of the Stokes pin with slip forcing:
+    the drag opposes the motion and lies between half and 0.85 of the
+    no-slip drag (a shear-free surface; Hadamard-Rybczynski gives 4/6 for a
+    bubble and 5/6 for a drop of equal viscosity in unbounded flow)."""
+    L, R, tau, Us = 40, 5.0, 1.0, 1e-3
+    Mb = float(L ** 3)
+    n = int(round(4 * math.pi * R * R))
+    c0 = np.array([(L - 1) / 2 - 2] * 3)
+    X0, dV = inputs.fibonacci_sphere(n, R, c0)
+
+    def drag(slip):
+        o = oracle.Oracle((L, L, L), tau, slip=slip)
+        Fb = 0.0
+        for step in range(1200):
+            shift = np.array([Us * step, 0.0, 0.0])
+            o.set_markers(X0 + shift, np.tile([Us, 0, 0], (n, 1)), dV, normals=(X0 - c0) / R)
+            o.step(oracle.make_frame(acc=(-Fb / Mb, 0, 0)))
+            Fb = o.force_torque()[-1, 0]
+        return -Fb
+
+    d_ns, d_s = drag(False), drag(True)
+    assert d_s > 0
+    assert 0.5 < d_s / d_ns < 0.85, (d_s, d_ns)
