@@ -92,6 +92,11 @@ typedef struct {
                            device per environment (0 = none), ring buffer */
     int kernel_variant; /* fg_kernel_variant */
     int autotune;       /* 1 (with kernel_variant AUTO): run fg_autotune at creation */
+    int ib_slip;        /* 1: slip (Neumann) direct forcing: only the normal
+                           component of the marker slip is enforced,
+                           dF = 2 R ((U - U~).n) n, with the unit normals given
+                           by fg_set_marker_normals; 0: no-slip (default).  The
+                           adjoint takes 0 only. */
     int use_graphs;     /* 1: each step is replayed from a captured CUDA graph
                            (captured on first use and whenever the marker count or
                            marker storage changes); 0: direct launches.  Steps taken
@@ -133,6 +138,15 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
 fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const float* U,
                          const float* dV, const int* seg, int n_seg, const double ref[3],
                          int device_ptrs);
+
+/* Unit surface normals of env's current markers for slip forcing
+ * (fg_options.ib_slip = 1): N[n][3] float, host or device (device_ptrs), n
+ * equal to the count given to the last fg_set_markers (normalised by the
+ * caller; not rescaled).  They are copied and kept until replaced; a step of
+ * a slip domain whose markers have no normals fails with FG_ERR_STATE, and
+ * fg_set_markers with a new marker count drops them.  The paper applies a
+ * slipping condition on immersed solids (Sec. III-B). */
+fg_status fg_set_marker_normals(fg_domain* d, int env, int n, const float* N, int device_ptrs);
 
 /* Advance every environment by n_steps time steps (asynchronous on the
  * domain's stream).  frames: NULL keeps the previous frames, else n_envs

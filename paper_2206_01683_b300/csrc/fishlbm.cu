@@ -64,6 +64,7 @@ enum { K1_PLAIN = 0, K1_STAGED256 = 1, K1_STAGED512 = 2, K1_NVARIANTS = 3 };
 struct MarkerRegion {
     int n = 0, cap = 0, off = 0, nseg = 1;
     bool has_dv = false;
+    bool has_normals = false;            // slip forcing: normals of the current markers
     double ref[3] = {0, 0, 0};
 };
 
@@ -115,6 +116,7 @@ struct fg_domain {
     float* adj_gF = nullptr;
     float *X = nullptr, *U = nullptr, *dV = nullptr, *Fm = nullptr;
     float* dF = nullptr;                 // per-pass force increments of multi-direct forcing
+    float* Nrm = nullptr;                // unit marker normals (slip forcing)
     int* seg = nullptr;
     int marker_slots = 0;                // allocated marker slots
     int total_markers = 0;
@@ -191,7 +193,7 @@ void free_all(fg_domain* d) {
         if (p) cudaFree(p);
     void* ptrs[] = {d->d_env, d->d_frame, d->pop[0], d->pop[1], d->fib, d->stamps, d->ib_nodes, d->ib_bar,
                     d->fibq, d->mass_part, d->red_partials, d->red_counters, d->d_state,
-                    d->X, d->U, d->dV, d->Fm, d->dF, d->seg, d->ft, d->mass, d->hist, d->status};
+                    d->X, d->U, d->dV, d->Fm, d->dF, d->Nrm, d->seg, d->ft, d->mass, d->hist, d->status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k < FG_K_COUNT; ++k)
@@ -237,7 +239,7 @@ fg_status grow_markers(fg_domain* d, int env, int n) {
         r.off = off;
         off += r.cap;
     }
-    float *X, *U, *dV, *Fm, *dF;
+    float *X, *U, *dV, *Fm, *dF, *Nr;
     int* sg;
     fg_status s;
     if ((s = dalloc(&X, 3ull * off)) != FG_OK) return s;
@@ -250,6 +252,10 @@ fg_status grow_markers(fg_domain* d, int env, int n) {
     }
     if ((s = dalloc(&dF, 3ull * off)) != FG_OK) {
         cudaFree(X); cudaFree(U); cudaFree(dV); cudaFree(Fm); cudaFree(sg);
+        return s;
+    }
+    if ((s = dalloc(&Nr, 3ull * off)) != FG_OK) {
+        cudaFree(X); cudaFree(U); cudaFree(dV); cudaFree(Fm); cudaFree(sg); cudaFree(dF);
         return s;
     }
     for (int e = 0; e < d->n_envs; ++e) {
@@ -265,10 +271,15 @@ fg_status grow_markers(fg_domain* d, int env, int n) {
                            cudaMemcpyDeviceToDevice, d->stream));
         CK(cudaMemcpyAsync(sg + nr[e].off, d->seg + o.off, sizeof(int) * o.n,
                            cudaMemcpyDeviceToDevice, d->stream));
+        CK(cudaMemcpyAsync(Nr + 3ull * nr[e].off, d->Nrm + 3ull * o.off, sizeof(float) * 3 * o.n,
+                           cudaMemcpyDeviceToDevice, d->stream));
     }
     CK(cudaStreamSynchronize(d->stream));
-    if (d->X) { cudaFree(d->X); cudaFree(d->U); cudaFree(d->dV); cudaFree(d->Fm); cudaFree(d->seg); cudaFree(d->dF); }
-    d->X = X; d->U = U; d->dV = dV; d->Fm = Fm; d->seg = sg; d->dF = dF;
+    if (d->X) {
+        cudaFree(d->X); cudaFree(d->U); cudaFree(d->dV); cudaFree(d->Fm); cudaFree(d->seg); cudaFree(d->dF);
+        cudaFree(d->Nrm);
+    }
+    d->X = X; d->U = U; d->dV = dV; d->Fm = Fm; d->seg = sg; d->dF = dF; d->Nrm = Nr;
     d->marker_slots = off;
     d->mk = nr;
     return ensure_reduce_scratch(d);
@@ -329,7 +340,8 @@ fg_status enqueue_step(fg_domain* d, int parity, cudaStream_t s, cudaEvent_t* co
         CK(cudaLaunchKernelEx(&cfg, k_ib_step<S>, gin, (const EnvDev*)d->d_env, (const FrameDev*)d->d_frame,
                               d->n_envs, d->total_markers, (int)d->n_stamps, (const float*)d->X, (const float*)d->U,
                               (const float*)d->dV, d->Fm, d->fib, d->stamps, (const StepState*)d->d_state,
-                              d->ib_nodes, d->ib_bar, d->opt.ib_iters, d->dF, d->fibq, d->status));
+                              d->ib_nodes, d->ib_bar, d->opt.ib_iters, d->dF, d->fibq,
+                              (const float*)(d->opt.ib_slip ? d->Nrm : nullptr), d->status));
         if (ev) CK(cudaEventRecord(ev[FG_K_IB][1], s));
     }
     if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][0], s));
@@ -536,7 +548,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     g_err.clear();
     if (!envs || !out || n_envs < 1 || n_envs > 4096) return fail(FG_ERR_INVALID, "bad environment list");
     fg_options o{};
-    o.storage = FG_F32; o.layout = 0; o.deterministic = 0; o.ib_iters = 1; o.record_history = 0;
+    o.storage = FG_F32; o.layout = 0; o.deterministic = 0; o.ib_iters = 1; o.record_history = 0; o.ib_slip = 0;
     o.kernel_variant = FG_KERNEL_AUTO;
     o.use_graphs = 1;
     o.autotune = 0;
@@ -547,6 +559,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     if (o.layout != 0) return fail(FG_ERR_INVALID, "only the two-buffer pull layout (0) exists");
     if (o.ib_iters < 1 || o.ib_iters > FG_MAX_IB_ITERS) return fail(FG_ERR_INVALID, "ib_iters must be in [1, 8]");
     if (o.deterministic != 0 && o.deterministic != 1) return fail(FG_ERR_INVALID, "deterministic must be 0 or 1");
+    if (o.ib_slip != 0 && o.ib_slip != 1) return fail(FG_ERR_INVALID, "ib_slip must be 0 or 1");
     if (o.record_history < 0 || o.record_history > (1 << 20)) return fail(FG_ERR_INVALID, "record_history");
     unsigned long long cells = 0;
     for (int e = 0; e < n_envs; ++e) {
@@ -813,6 +826,7 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
     const bool table_changed = m.n != n || m.nseg != n_seg ||
                                (ref && (ref[0] != m.ref[0] || ref[1] != m.ref[1] || ref[2] != m.ref[2])) ||
                                (!ref && (m.ref[0] != 0 || m.ref[1] != 0 || m.ref[2] != 0));
+    if (m.n != n) m.has_normals = false;
     m.n = n;
     m.nseg = n_seg;
     if (dV) m.has_dv = true;
@@ -821,6 +835,23 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
         refresh_marker_table(d);
         if ((st = upload_env(d)) != FG_OK) return st;
     }
+    return FG_OK;
+}
+
+fg_status fg_set_marker_normals(fg_domain* d, int env, int n, const float* N, int device_ptrs) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    MarkerRegion& m = d->mk[env];
+    if (n != m.n) return fail(FG_ERR_INVALID, "normals count differs from the marker count");
+    if (n > 0 && !N) return fail(FG_ERR_INVALID, "null normals");
+    if (!device_ptrs) {
+        for (int k = 0; k < 3 * n; ++k)
+            if (!std::isfinite(N[k])) return fail(FG_ERR_INVALID, "normal not finite");
+    }
+    if (n > 0)
+        CK(cudaMemcpyAsync(d->Nrm + 3ull * m.off, N, sizeof(float) * 3 * n,
+                           device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, d->stream));
+    m.has_normals = true;
     return FG_OK;
 }
 
@@ -848,6 +879,10 @@ fg_status fg_step(fg_domain* d, int n_steps, const fg_frame* frames) {
         fg_status st = upload_frames(d);
         if (st != FG_OK) return st;
     }
+    if (d->opt.ib_slip)
+        for (int e = 0; e < d->n_envs; ++e)
+            if (d->mk[e].n > 0 && !d->mk[e].has_normals)
+                return fail(FG_ERR_STATE, "slip forcing needs the markers' normals (fg_set_marker_normals)");
     const bool graphs = d->opt.use_graphs && !d->profiling;
     for (int s = 0; s < n_steps; ++s) {
         fg_status st = dispatch(d->opt.storage, [&](auto tag) {
@@ -1097,6 +1132,7 @@ static fg_status adjoint_check(fg_domain* d) {
     if (d->n_envs != 1) return fail(FG_ERR_INVALID, "the adjoint takes a single environment");
     if (d->opt.storage != FG_F32) return fail(FG_ERR_INVALID, "the adjoint takes FP32 storage");
     if (d->opt.ib_iters != 1) return fail(FG_ERR_INVALID, "the adjoint takes one direct-forcing pass");
+    if (d->opt.ib_slip) return fail(FG_ERR_INVALID, "the adjoint takes no-slip forcing");
     for (int k = 0; k < 6; ++k)
         if (d->desc[0].face[k] != FG_PERIODIC) return fail(FG_ERR_INVALID, "the adjoint takes periodic domains");
     if (d->poisoned) return fail(FG_ERR_STATE, "domain poisoned by a numeric fault; call fg_init_fields");

@@ -327,12 +327,14 @@ __device__ __forceinline__ float fixed_to_float(unsigned long long q) {
 
 // Direct-forcing increment of pass `pass`: R and U~ interpolated from the
 // node values, U~ of the velocity corrected by the force density spread in
-// the earlier passes (u~ + fib / (2 rho)); dF = 2 R (U - U~).  `active` is
+// the earlier passes (u~ + fib / (2 rho)); dF = 2 R (U - U~), or with slip
+// forcing (Nrm != nullptr) its normal component (dF.n) n.  `active` is
 // false for a half-warp without a (valid) marker, which still takes part in
 // the shuffles; the result is valid in every lane of an active half.
 __device__ __forceinline__ float3 interp_force(const EnvDev& E, const MarkerRef& r, const ColumnNodes& cn,
                                                bool active, int pass, const float4* fib,
-                                               const unsigned long long* fibq, const float4* nodes) {
+                                               const unsigned long long* fibq, const float4* nodes,
+                                               const float* __restrict__ Nrm) {
     float R = 0.f, Ux = 0.f, Uy = 0.f, Uz = 0.f;
     if (active) {
 #pragma unroll
@@ -365,7 +367,13 @@ __device__ __forceinline__ float3 interp_force(const EnvDev& E, const MarkerRef&
         Uy += __shfl_xor_sync(0xffffffffu, Uy, s);
         Uz += __shfl_xor_sync(0xffffffffu, Uz, s);
     }
-    return make_float3(2.0f * R * (r.U[0] - Ux), 2.0f * R * (r.U[1] - Uy), 2.0f * R * (r.U[2] - Uz));
+    float3 F = make_float3(2.0f * R * (r.U[0] - Ux), 2.0f * R * (r.U[1] - Uy), 2.0f * R * (r.U[2] - Uz));
+    if (Nrm && active) {   // slip forcing: keep the normal component, (F.n) n
+        const float nx = __ldg(Nrm + 3 * r.slot), ny = __ldg(Nrm + 3 * r.slot + 1), nz = __ldg(Nrm + 3 * r.slot + 2);
+        const float dn = F.x * nx + F.y * ny + F.z * nz;
+        F = make_float3(dn * nx, dn * ny, dn * nz);
+    }
+    return F;
 }
 
 // Spread dF dV delta onto the column's nodes (one vector reduction per node).
@@ -390,7 +398,8 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
           const FrameDev* __restrict__ frames, int n_envs, int total_markers, int n_stamps,
           const float* __restrict__ X, const float* __restrict__ U, const float* __restrict__ dV,
           float* __restrict__ Fm, float4* fib, uint32_t* stamps, const StepState* __restrict__ st,
-          float4* nodes, unsigned* bar, int ib_iters, float* dF, unsigned long long* fibq, int* status) {
+          float4* nodes, unsigned* bar, int ib_iters, float* dF, unsigned long long* fibq,
+          const float* __restrict__ Nrm, int* status) {
     const int lane = threadIdx.x & 31, h = lane & 15;
     const int gw = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -453,7 +462,7 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
         const EnvDev& E = envs[r.e];
         ColumnNodes cn;
         if (active) cn = column_nodes(E, r, h);
-        const float3 F = interp_force(E, r, cn, active, 0, fib, fibq, nodes);
+        const float3 F = interp_force(E, r, cn, active, 0, fib, fibq, nodes, Nrm);
         if (active) {
             spread(E, r, cn, F);
             if (h == 0) { Fm[3 * r.slot] = F.x; Fm[3 * r.slot + 1] = F.y; Fm[3 * r.slot + 2] = F.z; }
@@ -476,7 +485,7 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
             const EnvDev& E = envs[r.e];
             ColumnNodes cn;
             if (active) cn = column_nodes(E, r, h);
-            const float3 F = interp_force(E, r, cn, active, pass, fib, fibq, nodes);
+            const float3 F = interp_force(E, r, cn, active, pass, fib, fibq, nodes, Nrm);
             if (active && h == 0) {
                 float* Fl = Fm + 3 * r.slot;
                 Fl[0] += F.x; Fl[1] += F.y; Fl[2] += F.z;

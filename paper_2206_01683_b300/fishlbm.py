@@ -46,7 +46,7 @@ class fg_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("layout", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("ib_iters", ctypes.c_int),
                 ("record_history", ctypes.c_int), ("kernel_variant", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("ib_slip", ctypes.c_int), ("use_graphs", ctypes.c_int)]
 
 
 class fg_frame(ctypes.Structure):
@@ -60,6 +60,7 @@ _P = ctypes.POINTER
 SIGNATURES = {
     "fg_create_domain": (_I, [_P(fg_env_desc), _I, _P(fg_options), _V, _P(_V)]),
     "fg_set_markers": (_I, [_V, _I, _I, _V, _V, _V, _V, _I, _P(_D), _I]),
+    "fg_set_marker_normals": (_I, [_V, _I, _I, _V, _I]),
     "fg_step": (_I, [_V, _I, _P(fg_frame)]),
     "fg_get_body_force_torque": (_I, [_V, _I, _P(_D)]),
     "fg_destroy": (None, [_V]),
@@ -216,7 +217,7 @@ class Domain:
     """Owns one fg_domain (one or many environments)."""
 
     def __init__(self, envs, storage="f32", record_history=0, stream=None, variant="auto",
-                 graphs=True, autotune=False, ib_iters=1, deterministic=False):
+                 graphs=True, autotune=False, ib_iters=1, deterministic=False, slip=False):
         self.envs = list(envs)
         opt = fg_options()
         opt.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
@@ -225,6 +226,7 @@ class Domain:
         opt.ib_iters = int(ib_iters)
         opt.record_history = int(record_history)
         opt.kernel_variant = VARIANT[variant] if isinstance(variant, str) else int(variant)
+        opt.ib_slip = 1 if slip else 0
         opt.use_graphs = 1 if graphs else 0
         opt.autotune = 1 if autotune else 0
         self.storage = opt.storage
@@ -258,6 +260,14 @@ class Domain:
         self._keep = (kX, kU, kd, ks)
         self.nseg[env] = int(n_seg)
         self.nmark[env] = n
+
+    def set_marker_normals(self, N, env=0):
+        """Unit normals (n, 3) of env's current markers (slip forcing);
+        numpy, torch CPU or CUDA tensors."""
+        n = int(N.shape[0])
+        p, dev, keep = _ptr_and_keep(N, np.float32)
+        _check(lib().fg_set_marker_normals(self.h, env, n, p, 1 if dev else 0))
+        self._keep_n = keep
 
     def step(self, n=1, frames=None):
         if frames is not None and not isinstance(frames, (list, tuple)):

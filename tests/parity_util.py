@@ -41,11 +41,12 @@ class Pair:
     """One GPU domain (single environment) and one oracle, stepped together."""
 
     def __init__(self, shape, tau, faces=(0,) * 6, u_in=(0.0, 0.0, 0.0), rho0=1.0, storage="f32",
-                 variant="auto", ib_iters=1, deterministic=False):
+                 variant="auto", ib_iters=1, deterministic=False, slip=False):
         self.shape = tuple(shape)
-        self.o = oracle.Oracle(shape, tau, faces=faces, u_in=f32(u_in), rho_out=rho0, ib_iters=ib_iters)
+        self.o = oracle.Oracle(shape, tau, faces=faces, u_in=f32(u_in), rho_out=rho0, ib_iters=ib_iters,
+                               slip=slip)
         self.g = fishlbm.Domain([fishlbm.env_desc(shape, tau, faces, f32(u_in), rho0)], storage=storage,
-                                variant=variant, ib_iters=ib_iters, deterministic=deterministic)
+                                variant=variant, ib_iters=ib_iters, deterministic=deterministic, slip=slip)
         self.perm = gpu_to_oracle_perm()
         _, self.w = oracle.lattice()
         self.nseg = 1
@@ -56,11 +57,18 @@ class Pair:
         self.o.init_fields(rho, u)
         self.g.init_fields(rho, u)
 
-    def markers(self, X, U, dV, seg=None, nseg=1, ref=(0.0, 0.0, 0.0)):
+    def markers(self, X, U, dV, seg=None, nseg=1, ref=(0.0, 0.0, 0.0), normals=None):
         X32, U32, dV32 = (np.asarray(a, dtype=np.float32) for a in (X, U, dV))
+        N32 = None
+        if normals is not None:
+            N32 = np.asarray(normals, dtype=np.float64)
+            N32 = (N32 / np.linalg.norm(N32, axis=1, keepdims=True)).astype(np.float32)
         self.o.set_markers(X32.astype(np.float64), U32.astype(np.float64), dV32.astype(np.float64),
-                           seg=seg, nseg=nseg, ref=ref)
+                           seg=seg, nseg=nseg, ref=ref,
+                           normals=None if N32 is None else N32.astype(np.float64))
         self.g.set_markers(X32, U32, dV32, seg=seg, n_seg=nseg, ref=ref)
+        if N32 is not None:
+            self.g.set_marker_normals(N32)
         self.nseg = nseg
 
     def step(self, frame=None, record=True):

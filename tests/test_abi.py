@@ -38,7 +38,7 @@ def test_binding_signatures_match_header():
 def test_struct_layouts():
     assert ctypes.sizeof(fishlbm.fg_env_desc) == 4 * 3 + 4 + 8 + 4 * 6 + 8 * 3 + 8 + 8 * 3
     assert ctypes.sizeof(fishlbm.fg_frame) == 12 * 8
-    assert ctypes.sizeof(fishlbm.fg_options) == 8 * 4
+    assert ctypes.sizeof(fishlbm.fg_options) == 9 * 4
 
 
 def test_lattice_is_d3q27():

@@ -139,6 +139,39 @@ def test_deterministic_spread_parity(M):
     assert_parity(p.errors(), keys=("rho", "u", "pop", "force", "torque"))
 
 
+@pytest.mark.parametrize("M", [1, 3])
+def test_slip_forcing_parity(M):
+    """Slip (normal-only) forcing on the translating sphere in the periodic
+    box, 60 steps, with the sphere's outward normals."""
+    cfg = inputs.SPHERE_BOX
+    p = Pair(cfg["shape"], cfg["tau"], ib_iters=M, slip=True)
+    c0 = np.asarray(cfg["center"], dtype=np.float64)
+    for n in range(60):
+        X, U, dV = inputs.translating_sphere(cfg["n_markers"], cfg["radius"], cfg["center"],
+                                             cfg["velocity"], n)
+        centre = c0 + np.asarray(cfg["velocity"]) * n
+        p.markers(X, U, dV, normals=X - centre)
+        p.step()
+    assert_parity(p.errors(), keys=("rho", "u", "pop", "force", "torque"))
+    assert rel_l2(p.g.marker_force().astype(np.float64), p.o.marker_force()) <= TOL_F32
+
+
+def test_slip_forcing_needs_normals():
+    d = fishlbm.Domain([fishlbm.env_desc((16, 16, 16), 0.7)], slip=True)
+    X, dV = inputs.fibonacci_sphere(60, 3.0, (8.0, 8.0, 8.0))
+    d.set_markers(np.float32(X), np.zeros((60, 3), np.float32), np.float32(dV))
+    with pytest.raises(fishlbm.FgError) as ei:
+        d.step(1)
+    assert ei.value.status == fishlbm.FG_ERR_STATE
+    with pytest.raises(fishlbm.FgError):
+        d.set_marker_normals(np.ones((59, 3), np.float32))        # wrong count
+    d.set_marker_normals(np.float32((X - 8.0) / 3.0))
+    d.step(1)
+    d.set_markers(np.float32(X[:50]), np.zeros((50, 3), np.float32), np.float32(dV[:50]))
+    with pytest.raises(fishlbm.FgError):                         # a new count drops the normals
+        d.step(1)
+
+
 def _swimmer_run(deterministic, ib_iters, steps=30, variant="staged"):
     shape = (96, 48, 48)
     fish = inputs.fish_for_grid(shape, 24.0, 900)
