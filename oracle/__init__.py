@@ -53,6 +53,8 @@ def lib():
         L.orc_frame_accel.argtypes = [P(d), d, d, d, P(d)]
         L.orc_set_ib_iters.restype = i
         L.orc_set_ib_iters.argtypes = [vp, i]
+        L.orc_set_segment_refs.restype = i
+        L.orc_set_segment_refs.argtypes = [vp, i, P(d)]
         L.orc_set_slip.restype = i
         L.orc_set_slip.argtypes = [vp, i, i, P(d)]
         _lib = L
@@ -160,6 +162,15 @@ class Oracle:
             N = _f64(normals, (n, 3))
             if lib().orc_set_slip(self._h, 1, n, _dp(N)) != 0:
                 raise ValueError("oracle: invalid normals")
+
+    def set_segment_refs(self, refs):
+        """Torque reference point per segment row (nseg, 3); None: common ref."""
+        if refs is None:
+            lib().orc_set_segment_refs(self._h, 0, None)
+            return
+        r = _f64(refs).reshape(-1, 3)
+        if lib().orc_set_segment_refs(self._h, r.shape[0], _dp(r)) != 0:
+            raise ValueError("oracle: one reference point per segment")
 
     def step(self, frame=None, n=1):
         fr = make_frame() if frame is None else _f64(frame, (12,))

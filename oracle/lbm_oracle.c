@@ -87,7 +87,9 @@ typedef struct {
     int nm, nseg;        /* markers */
     double *X, *U, *dV;  /* [nm][3], [nm][3], [nm] */
     int *seg;
-    double ref[3];
+    double ref[3];       /* torque reference point of the total row */
+    double seg_ref[64][3];   /* torque reference point of each segment row */
+    int has_seg_ref;     /* 0: segment rows use ref as well */
     double *Fm;          /* marker force density F_l, [nm][3] */
     double force[64 * 6];/* per segment + total: F(3), T(3) */
     double mass, mass_dev;   /* sum rho and sum (rho - 1) after the last step */
@@ -363,6 +365,23 @@ int orc_set_markers(void *h, int n, const double *X, const double *U, const doub
     memcpy(o->dV, dV, sizeof(double) * n);
     for (int l = 0; l < n; ++l) o->seg[l] = seg ? seg[l] : 0;
     for (int a = 0; a < 3; ++a) o->ref[a] = ref ? ref[a] : 0.0;
+    o->has_seg_ref = 0;
+    return 0;
+}
+
+/* Torque reference points of the segment rows (several bodies in one marker
+ * set: each body's segments about that body's own point); NULL returns to
+ * the common reference point.  The total row always uses ref. */
+int orc_set_segment_refs(void *h, int nseg, const double *refs) {
+    orc_t *o = (orc_t *)h;
+    if (!refs) {
+        o->has_seg_ref = 0;
+        return 0;
+    }
+    if (nseg != (o->nseg > 0 ? o->nseg : 1) || nseg > 64) return -1;
+    for (int s = 0; s < nseg; ++s)
+        for (int a = 0; a < 3; ++a) o->seg_ref[s][a] = refs[3 * s + a];
+    o->has_seg_ref = 1;
     return 0;
 }
 
@@ -572,22 +591,27 @@ static void boundary_cell(const orc_t *o, int x, int y, int z, const int side[3]
 
 /* F = -sum_l F_l dV_l and T = -sum_l (X_l - X_ref) x F_l dV_l, the force and
  * torque the fluid exerts on the body (the tau_ext of Eq. 1), per segment and
- * in total (last row). */
+ * in total (last row).  Segment rows take their torque about the segment's
+ * reference point when one is set, the total row about ref. */
 static void force_torque(orc_t *o) {
     int ns = o->nseg > 0 ? o->nseg : 1;
     memset(o->force, 0, sizeof(o->force));
     for (int l = 0; l < o->nm; ++l) {
-        double F[3], r[3], T[3];
+        const int sg = o->seg[l];
+        const double *rs = o->has_seg_ref ? o->seg_ref[sg] : o->ref;
+        double F[3], r[3], rt[3], T[3], Tt[3];
         for (int a = 0; a < 3; ++a) {
             F[a] = -o->Fm[3 * l + a] * o->dV[l];
-            r[a] = o->X[3 * l + a] - o->ref[a];
+            r[a] = o->X[3 * l + a] - rs[a];
+            rt[a] = o->X[3 * l + a] - o->ref[a];
         }
         cross(r, F, T);
+        cross(rt, F, Tt);
         for (int a = 0; a < 3; ++a) {
-            o->force[6 * o->seg[l] + a] += F[a];
-            o->force[6 * o->seg[l] + 3 + a] += T[a];
+            o->force[6 * sg + a] += F[a];
+            o->force[6 * sg + 3 + a] += T[a];
             o->force[6 * ns + a] += F[a];
-            o->force[6 * ns + 3 + a] += T[a];
+            o->force[6 * ns + 3 + a] += Tt[a];
         }
     }
 }

@@ -61,6 +61,10 @@ MUTANTS = {
         "ut[3 * c + a] += dfib[3 * c + a] / (2.0 * o->rho[c]);",
         "ut[3 * c + a] += dfib[3 * c + a] / (1.0 * o->rho[c]);",
         "test_multi_direct_forcing_isolated_markers_closed_form"),
+    "segment_ref_ignored": (
+        "const double *rs = o->has_seg_ref ? o->seg_ref[sg] : o->ref;",
+        "const double *rs = o->ref;",
+        "test_segment_reference_points_transport_the_moment"),
     "slip_projection_dropped": (
         "for (int a = 0; a < 3; ++a) dF[3 * l + a] = dn * nl[a];",
         "for (int a = 0; a < 3; ++a) dF[3 * l + a] = dF[3 * l + a] + 0.0 * dn * nl[a];",

@@ -25,7 +25,8 @@ a shifted stencil, a transposed cross product) fails one of them:
   with every pass;
 * slip (Neumann) forcing: the normal-only closed form for isolated markers,
   exact invariance of a tangential shear past a flat slip sheet, and the drag
-  of a slip sphere between a bubble's and a no-slip sphere's.
+  of a slip sphere between a bubble's and a no-slip sphere's;
+* per-segment torque reference points obey the transport of a moment.
 """
 import math
 import os
@@ -666,3 +667,33 @@ def test_slip_sphere_drag_between_bubble_and_no_slip():
     d_ns, d_s = drag(False), drag(True)
     assert d_s > 0
     assert 0.5 < d_s / d_ns < 0.85, (d_s, d_ns)
+
+
+def test_segment_reference_points_transport_the_moment():
+    """Per-segment torque reference points (several bodies in one marker set)
+    obey the transport of a moment: about a point p the torque of a segment
+    is T(p) = T(q) + (q - p) x F for its torque T(q) about q and its force F.
+    The total row keeps the common reference point."""
+    shape = (24, 20, 20)
+    rho, u = inputs.random_fields(shape, seed=31, u_amp=0.02, rho_amp=0.01)
+    X, dV = inputs.fibonacci_sphere(240, 4.0, (11.0, 9.5, 10.0))
+    rng = np.random.default_rng(5)
+    U = 0.01 * rng.standard_normal((240, 3))
+    seg = (np.arange(240) % 3).astype(np.int32)
+    q = np.array([10.0, 9.0, 9.5])
+    P = np.array([[4.0, 2.0, 3.0], [15.0, 11.0, 12.5], [11.0, 9.5, 10.0]])
+
+    def run(refs):
+        o = oracle.Oracle(shape, 0.7)
+        o.init_fields(rho, u)
+        o.set_markers(X, U, dV, seg=seg, nseg=3, ref=q)
+        o.set_segment_refs(refs)
+        o.step()
+        return o.force_torque()
+
+    common, own = run(None), run(P)
+    for s in range(3):
+        F = common[s, :3]
+        assert np.allclose(own[s, :3], F, rtol=0, atol=1e-17)
+        assert np.allclose(own[s, 3:], common[s, 3:] + np.cross(q - P[s], F), rtol=1e-12, atol=1e-16)
+    assert np.array_equal(own[3], common[3])
