@@ -246,6 +246,55 @@ def storage_form(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W,
                          "kernel_ms": round(k[1], 5), "ib_ms": round(k[0], 5)}}
 
 
+def school_form(W, K, world, peak, vkw):
+    """Two fish in tandem in one 150x50x100 open channel (the paper's
+    two-fish schooling domain), one marker set of 2 x 2500 markers with ten
+    segments, each fish's torque about its own first joint, in the leader's
+    moving frame."""
+    import torch
+    from paper_2206_01683_b300 import fishlbm, inputs
+    cfg = inputs.SCHOOL_CHANNEL
+    shape, tau, u_in = cfg["shape"], cfg["tau"], cfg["u_in"]
+    school = inputs.School(shape, cfg["length"], cfg["n_markers"], cfg["gap"], cfg["phase_lag"])
+    traj = inputs.FrameTrajectory(inputs.seed_for(6), inputs.domain_centre(shape))
+    T = W + 2 * K
+    X = np.zeros((T, school.n, 3), np.float32)
+    U = np.zeros((T, school.n, 3), np.float32)
+    fr = []
+    for n in range(T):
+        X[n], U[n] = school.pose(n)
+        fr.append(fishlbm.frame_from_array(traj.at(n)))
+    Xd, Ud = torch.from_numpy(X).cuda(), torch.from_numpy(U).cuda()
+    dVd = torch.from_numpy(school.dV.astype(np.float32)).cuda()
+    segd = torch.from_numpy(school.seg).cuda()
+    stream = torch.cuda.Stream()
+    dom = fishlbm.Domain([fishlbm.env_desc(shape, tau, OPEN_X, (u_in, 0, 0), 1.0, (u_in, 0, 0))],
+                         stream=stream.cuda_stream, **vkw)
+    dom.set_markers(Xd[0], Ud[0], dVd, segd, n_seg=school.n_seg, ref=tuple(school.ref))
+    dom.set_segment_refs(school.seg_refs)
+
+    def step(n):
+        dom.set_markers(Xd[n], Ud[n], None, None, n_seg=school.n_seg, ref=tuple(school.ref))
+        dom.step(1, [fr[n]])
+
+    for n in range(W):
+        step(n)
+    ms = _max_over_ranks(_timed(stream, world, step, range(W, W + K)), world)
+    ft = dom.get_body_force_torque()
+    k = _kernel_ms(dom, step, range(W + K, W + 2 * K))
+    ncell = shape[0] * shape[1] * shape[2]
+    gbs = dom.stream_collide_bytes() / (k[1] * 1e-3) / 1e9
+    variant = dom.stream_collide_variant()
+    dom.close()
+    return {"value": round(world * ncell * K / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+            "ms_per_step": round(ms / K, 5), "workload": "two_fish_school_150x50x100",
+            "markers": int(school.n), "segments": int(school.n_seg), "kernel_variant": variant,
+            "leader_fx": round(float(ft[:5, 0].sum()), 8), "follower_fx": round(float(ft[5:10, 0].sum()), 8),
+            "roofline": {"bound": "hbm", "kernel": "k_stream_collide", "achieved": round(gbs, 1),
+                         "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+                         "kernel_ms": round(k[1], 5), "ib_ms": round(k[0], 5)}}
+
+
 def batched_form(W, K, world, peak, vkw, n_envs=64):
     """64 independent single-fish environments, grid sizes drawn by seed from
     {96x64x64, 128x64x64, 160x80x80, 192x96x96}, fish of 0.4 x grid length
@@ -397,6 +446,7 @@ def run_ours(args):
                                  _variant_kw(args), ib_iters=3),
             "deterministic": storage_form("f32", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world,
                                           peak, _variant_kw(args), deterministic=True),
+            "school": school_form(W, Kf, world, peak, _variant_kw(args)),
             "batched": batched_form(W, Kf, world, peak, _variant_kw(args)),
             "adjoint": adjoint_form(),
         }

@@ -139,6 +139,15 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
                          const float* dV, const int* seg, int n_seg, const double ref[3],
                          int device_ptrs);
 
+/* Torque reference points of env's segment rows, refs[n_seg][3] (host),
+ * n_seg equal to that of the last fg_set_markers: segment s reports its
+ * torque about refs[s], so several bodies can share one marker set (each
+ * body's segments about its own point, e.g. two fish of a school).  The
+ * total row keeps the reference point of fg_set_markers.  refs = NULL returns
+ * to that common point; fg_set_markers with a different n_seg does too.  The
+ * call synchronises the stream. */
+fg_status fg_set_segment_refs(fg_domain* d, int env, int n_seg, const double* refs);
+
 /* Unit surface normals of env's current markers for slip forcing
  * (fg_options.ib_slip = 1): N[n][3] float, host or device (device_ptrs), n
  * equal to the count given to the last fg_set_markers (normalised by the

@@ -353,6 +353,7 @@ int orc_set_markers(void *h, int n, const double *X, const double *U, const doub
     }
     free(o->X); free(o->U); free(o->dV); free(o->seg); free(o->Fm); free(o->Nrm);
     o->Nrm = NULL;
+    if (nseg != o->nseg) o->has_seg_ref = 0;   /* segment points belong to a segmentation */
     o->nm = n;
     o->nseg = nseg;
     o->X = (double *)malloc(sizeof(double) * 3 * (n ? n : 1));
@@ -365,13 +366,13 @@ int orc_set_markers(void *h, int n, const double *X, const double *U, const doub
     memcpy(o->dV, dV, sizeof(double) * n);
     for (int l = 0; l < n; ++l) o->seg[l] = seg ? seg[l] : 0;
     for (int a = 0; a < 3; ++a) o->ref[a] = ref ? ref[a] : 0.0;
-    o->has_seg_ref = 0;
     return 0;
 }
 
 /* Torque reference points of the segment rows (several bodies in one marker
  * set: each body's segments about that body's own point); NULL returns to
- * the common reference point.  The total row always uses ref. */
+ * the common reference point, and so does a later orc_set_markers with a
+ * different segment count.  The total row always uses ref. */
 int orc_set_segment_refs(void *h, int nseg, const double *refs) {
     orc_t *o = (orc_t *)h;
     if (!refs) {

@@ -66,6 +66,8 @@ struct MarkerRegion {
     bool has_dv = false;
     bool has_normals = false;            // slip forcing: normals of the current markers
     double ref[3] = {0, 0, 0};
+    bool has_seg_ref = false;            // segment rows about their own points
+    double seg_ref[MAX_SEG][3] = {};
 };
 
 }  // namespace
@@ -117,6 +119,7 @@ struct fg_domain {
     float *X = nullptr, *U = nullptr, *dV = nullptr, *Fm = nullptr;
     float* dF = nullptr;                 // per-pass force increments of multi-direct forcing
     float* Nrm = nullptr;                // unit marker normals (slip forcing)
+    float* seg_ref = nullptr;            // torque points of the segment rows [n_envs][MAX_SEG][3]
     int* seg = nullptr;
     int marker_slots = 0;                // allocated marker slots
     int total_markers = 0;
@@ -146,6 +149,21 @@ struct fg_domain {
 };
 
 namespace {
+
+// Torque points of every environment's segment rows: its own points when
+// set, else the environment's reference point (device copy in FP32, like the
+// marker positions the reduction subtracts them from).
+fg_status upload_seg_refs(fg_domain* d) {
+    std::vector<float> h((size_t)d->n_envs * MAX_SEG * 3);
+    for (int e = 0; e < d->n_envs; ++e)
+        for (int sg = 0; sg < MAX_SEG; ++sg)
+            for (int a = 0; a < 3; ++a)
+                h[((size_t)e * MAX_SEG + sg) * 3 + a] =
+                    (float)(d->mk[e].has_seg_ref ? d->mk[e].seg_ref[sg][a] : d->mk[e].ref[a]);
+    CK(cudaMemcpyAsync(d->seg_ref, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, d->stream));
+    CK(cudaStreamSynchronize(d->stream));   // h is released on return
+    return FG_OK;
+}
 
 fg_status upload_env(fg_domain* d) {
     CK(cudaMemcpyAsync(d->d_env, d->env.data(), sizeof(EnvDev) * d->n_envs, cudaMemcpyHostToDevice,
@@ -193,7 +211,8 @@ void free_all(fg_domain* d) {
         if (p) cudaFree(p);
     void* ptrs[] = {d->d_env, d->d_frame, d->pop[0], d->pop[1], d->fib, d->stamps, d->ib_nodes, d->ib_bar,
                     d->fibq, d->mass_part, d->red_partials, d->red_counters, d->d_state,
-                    d->X, d->U, d->dV, d->Fm, d->dF, d->Nrm, d->seg, d->ft, d->mass, d->hist, d->status};
+                    d->X, d->U, d->dV, d->Fm, d->dF, d->Nrm, d->seg, d->seg_ref, d->ft, d->mass, d->hist,
+                    d->status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k < FG_K_COUNT; ++k)
@@ -349,8 +368,8 @@ fg_status enqueue_step(fg_domain* d, int parity, cudaStream_t s, cudaEvent_t* co
     if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][1], s));
     if (ev) CK(cudaEventRecord(ev[FG_K_REDUCE][0], s));
     k_reduce<<<dim3(d->n_envs, RED_ROWS, d->red_z), RED_THREADS, 0, s>>>(
-        d->d_env, d->X, d->Fm, d->dV, d->seg, d->mass_part, d->red_partials, d->red_counters, d->n_envs,
-        d->red_z, d->ft, d->mass, d->hist, d->opt.record_history, d->d_state, d->status);
+        d->d_env, d->X, d->Fm, d->dV, d->seg, d->seg_ref, d->mass_part, d->red_partials, d->red_counters,
+        d->n_envs, d->red_z, d->ft, d->mass, d->hist, d->opt.record_history, d->d_state, d->status);
     if (ev) CK(cudaEventRecord(ev[FG_K_REDUCE][1], s));
     CK(cudaGetLastError());
     return FG_OK;
@@ -662,6 +681,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     DA(d->stamps, stamp_off);
     DA(d->ib_nodes, slot_off);
     DA(d->ib_bar, 2);
+    DA(d->seg_ref, (size_t)n_envs * MAX_SEG * 3);
     if (o.deterministic) DA(d->fibq, 3ull * slot_off);
     DA(d->red_counters, (size_t)n_envs * RED_ROWS);
     DA(d->d_state, 1);
@@ -715,7 +735,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
             return st;
         }
     }
-    if ((st = upload_env(d)) != FG_OK || (st = upload_frames(d)) != FG_OK) {
+    if ((st = upload_env(d)) != FG_OK || (st = upload_frames(d)) != FG_OK || (st = upload_seg_refs(d)) != FG_OK) {
         free_all(d);
         delete d;
         return st;
@@ -827,6 +847,7 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
                                (ref && (ref[0] != m.ref[0] || ref[1] != m.ref[1] || ref[2] != m.ref[2])) ||
                                (!ref && (m.ref[0] != 0 || m.ref[1] != 0 || m.ref[2] != 0));
     if (m.n != n) m.has_normals = false;
+    if (m.nseg != n_seg) m.has_seg_ref = false;
     m.n = n;
     m.nseg = n_seg;
     if (dV) m.has_dv = true;
@@ -834,8 +855,26 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
     if (table_changed) {
         refresh_marker_table(d);
         if ((st = upload_env(d)) != FG_OK) return st;
+        if ((st = upload_seg_refs(d)) != FG_OK) return st;
     }
     return FG_OK;
+}
+
+fg_status fg_set_segment_refs(fg_domain* d, int env, int n_seg, const double* refs) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    MarkerRegion& m = d->mk[env];
+    if (!refs) {
+        m.has_seg_ref = false;
+        return upload_seg_refs(d);
+    }
+    if (n_seg != m.nseg) return fail(FG_ERR_INVALID, "one reference point per segment of the last fg_set_markers");
+    for (int k = 0; k < 3 * n_seg; ++k)
+        if (!std::isfinite(refs[k])) return fail(FG_ERR_INVALID, "reference point not finite");
+    for (int sg = 0; sg < n_seg; ++sg)
+        for (int a = 0; a < 3; ++a) m.seg_ref[sg][a] = refs[3 * sg + a];
+    m.has_seg_ref = true;
+    return upload_seg_refs(d);
 }
 
 fg_status fg_set_marker_normals(fg_domain* d, int env, int n, const float* N, int device_ptrs) {

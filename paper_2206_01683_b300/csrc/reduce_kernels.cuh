@@ -42,8 +42,9 @@ constexpr int MASS_PER_THREAD = 8;
 constexpr int RED_ROWS = MAX_SEG + 2;   // force/torque rows 0..MAX_SEG, then the mass
 
 // Grid (n_envs, RED_ROWS, chunks).  Block (e, y, z) sums chunk z of row y of
-// environment e: y <= nseg is force/torque row y (segment y; y == nseg is
-// the total over all markers), one marker per thread; y == RED_ROWS - 1 is
+// environment e: y <= nseg is force/torque row y (segment y, its torque
+// about seg_ref[e][y]; y == nseg is the total over all markers, its torque
+// about the environment's ref), one marker per thread; y == RED_ROWS - 1 is
 // the mass, MASS_PER_THREAD partials per thread.  Force on the body
 // F = -sum F_l dV_l, torque T = -sum (X_l - ref) x F_l dV_l, mass = ncell +
 // sum (rho - 1).  Chunk sums are compensated FP32 pairs (all components of a
@@ -58,7 +59,8 @@ constexpr int RED_ROWS = MAX_SEG + 2;   // force/torque rows 0..MAX_SEG, then th
 // state.
 static __global__ void __launch_bounds__(RED_THREADS)
 k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const float* __restrict__ Fm,
-         const float* __restrict__ dV, const int* __restrict__ seg, const Pair32* __restrict__ mass_part,
+         const float* __restrict__ dV, const int* __restrict__ seg, const float* __restrict__ seg_ref,
+         const Pair32* __restrict__ mass_part,
          Pair32* __restrict__ partials, int* __restrict__ counters, int n_envs, int zmax,
          Pair32* __restrict__ ft, Pair32* __restrict__ mass, Pair32* __restrict__ hist, int hist_cap,
          StepState* __restrict__ st, int* __restrict__ status) {
@@ -91,8 +93,11 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
             if (y == ns || seg[q] == y) {
                 const float v = -dV[q];
                 const float Fx = Fm[3 * q] * v, Fy = Fm[3 * q + 1] * v, Fz = Fm[3 * q + 2] * v;
-                const float rx = X[3 * q] - (float)E.ref[0], ry = X[3 * q + 1] - (float)E.ref[1],
-                            rz = X[3 * q + 2] - (float)E.ref[2];
+                // segment rows about the segment's point, the total row about ref
+                const float* rp = seg_ref + ((size_t)e * MAX_SEG + (y < ns ? y : 0)) * 3;
+                const float px = y < ns ? rp[0] : (float)E.ref[0], py = y < ns ? rp[1] : (float)E.ref[1],
+                            pz = y < ns ? rp[2] : (float)E.ref[2];
+                const float rx = X[3 * q] - px, ry = X[3 * q + 1] - py, rz = X[3 * q + 2] - pz;
                 acc[0].add(Fx); acc[1].add(Fy); acc[2].add(Fz);
                 acc[3].add(ry * Fz - rz * Fy);
                 acc[4].add(rz * Fx - rx * Fz);

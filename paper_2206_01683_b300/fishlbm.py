@@ -61,6 +61,7 @@ SIGNATURES = {
     "fg_create_domain": (_I, [_P(fg_env_desc), _I, _P(fg_options), _V, _P(_V)]),
     "fg_set_markers": (_I, [_V, _I, _I, _V, _V, _V, _V, _I, _P(_D), _I]),
     "fg_set_marker_normals": (_I, [_V, _I, _I, _V, _I]),
+    "fg_set_segment_refs": (_I, [_V, _I, _I, _P(_D)]),
     "fg_step": (_I, [_V, _I, _P(fg_frame)]),
     "fg_get_body_force_torque": (_I, [_V, _I, _P(_D)]),
     "fg_destroy": (None, [_V]),
@@ -260,6 +261,14 @@ class Domain:
         self._keep = (kX, kU, kd, ks)
         self.nseg[env] = int(n_seg)
         self.nmark[env] = n
+
+    def set_segment_refs(self, refs, env=0):
+        """Torque point per segment row (n_seg, 3); None: the common point."""
+        if refs is None:
+            _check(lib().fg_set_segment_refs(self.h, env, 0, None))
+            return
+        r = np.ascontiguousarray(refs, dtype=np.float64).reshape(-1, 3)
+        _check(lib().fg_set_segment_refs(self.h, env, r.shape[0], _dp(r)))
 
     def set_marker_normals(self, N, env=0):
         """Unit normals (n, 3) of env's current markers (slip forcing);

@@ -29,6 +29,9 @@ BATCH_SHAPES = ((96, 64, 64), (128, 64, 64), (160, 80, 80), (192, 96, 96))
 ADJOINT_CHANNEL = dict(shape=(128, 64, 64), tau=0.52, length=32.0, n_markers=1500,
                        steps=200, checkpoint=20)
 
+SCHOOL_CHANNEL = dict(shape=(150, 50, 100), tau=0.52, u_in=0.02, length=36.0, n_markers=2500,
+                      gap=54.0, phase_lag=math.pi / 2.0, steps=2000)
+
 WAVE_PERIOD = 400.0
 N_SEGMENTS = 5
 
@@ -208,6 +211,33 @@ def fish_for_grid(shape, length, n_markers, amplitudes=None, phases=None):
     nx, ny, nz = shape
     head = (nx / 4.0, (ny - 1) / 2.0, (nz - 1) / 2.0)
     return Fish(length, n_markers, head, amplitudes, phases)
+
+
+class School:
+    """Two fish in tandem along x in one marker set: the leader's head tip at
+    x = nx/5, the follower's ``gap`` cells behind it, both centred in y and z;
+    the follower's joint wave lags the leader's by ``phase_lag``.  Segments
+    0-4 are the leader's, 5-9 the follower's; ``seg_refs`` gives each
+    segment's torque point (its fish's first joint) and ``ref`` the leader's
+    first joint for the total row."""
+
+    def __init__(self, shape, length, n_each, gap, phase_lag=math.pi / 2.0):
+        nx, ny, nz = shape
+        y0, z0 = (ny - 1) / 2.0, (nz - 1) / 2.0
+        j = np.arange(1, 5, dtype=np.float64)
+        self.fish = [Fish(length, n_each, (nx / 5.0, y0, z0)),
+                     Fish(length, n_each, (nx / 5.0 + gap, y0, z0), phases=0.8 * j + phase_lag)]
+        self.n = 2 * int(n_each)
+        self.n_seg = 2 * N_SEGMENTS
+        self.dV = np.concatenate([f.dV for f in self.fish])
+        self.seg = np.concatenate([self.fish[0].seg, self.fish[1].seg + N_SEGMENTS]).astype(np.int32)
+        self.seg_refs = np.concatenate([np.tile(f.joints_rest[0], (N_SEGMENTS, 1)) for f in self.fish])
+        self.ref = self.fish[0].joints_rest[0].copy()
+
+    def pose(self, t):
+        XA, UA = self.fish[0].pose(t)
+        XB, UB = self.fish[1].pose(t)
+        return np.concatenate([XA, XB]), np.concatenate([UA, UB])
 
 
 # ------------------------------------------------------------------- frame

@@ -139,6 +139,44 @@ def test_deterministic_spread_parity(M):
     assert_parity(p.errors(), keys=("rho", "u", "pop", "force", "torque"))
 
 
+@pytest.mark.parametrize("variant", ["plain", "staged"])
+def test_two_fish_school_parity(variant):
+    """Two fish in tandem (one marker set, ten segments, each fish's segments
+    about its own first joint) in an open channel with the leader's moving
+    frame: 75x25x50, body length 18, 2 x 600 markers, 60 steps; fields,
+    populations, the total and the ten per-segment force/torque rows."""
+    shape = (75, 25, 50)
+    school = inputs.School(shape, 18.0, 600, 27.0)
+    traj = inputs.FrameTrajectory(inputs.seed_for(6), inputs.domain_centre(shape))
+    p = Pair(shape, 0.52, faces=OPEN_X, u_in=(0.02, 0.0, 0.0), variant=variant)
+    p.init(None, np.tile([0.02, 0.0, 0.0], (p.o.ncell, 1)))
+    for n in range(60):
+        X, U = school.pose(n)
+        p.markers(X, U, school.dV, seg=school.seg, nseg=school.n_seg, ref=school.ref)
+        if n == 0:
+            p.o.set_segment_refs(school.seg_refs)
+            p.g.set_segment_refs(school.seg_refs)
+        p.step(traj.at(n))
+    assert_parity(p.errors(), keys=("rho", "u", "pop", "force", "torque", "seg_force"))
+    ft = p.g.get_body_force_torque()
+    assert ft.shape == (11, 6)
+    # per-fish sums of the segment rows give each fish's force
+    lead, follow = ft[:5, :3].sum(axis=0), ft[5:10, :3].sum(axis=0)
+    assert np.allclose(lead + follow, ft[10, :3], rtol=1e-5, atol=1e-9)
+
+
+def test_segment_refs_validation_and_reset():
+    d = fishlbm.Domain([fishlbm.env_desc((16, 16, 16), 0.7)])
+    X, dV = inputs.fibonacci_sphere(60, 3.0, (8.0, 8.0, 8.0))
+    seg = (np.arange(60) % 2).astype(np.int32)
+    d.set_markers(np.float32(X), np.zeros((60, 3), np.float32), np.float32(dV), seg=seg, n_seg=2)
+    with pytest.raises(fishlbm.FgError):
+        d.set_segment_refs(np.zeros((3, 3)))               # one point per segment
+    d.set_segment_refs(np.array([[1.0, 2.0, 3.0], [4.0, 5.0, 6.0]]))
+    d.set_segment_refs(None)
+    d.step(1)
+
+
 @pytest.mark.parametrize("M", [1, 3])
 def test_slip_forcing_parity(M):
     """Slip (normal-only) forcing on the translating sphere in the periodic
