@@ -53,6 +53,7 @@ def lib():
         L.orc_frame_accel.argtypes = [P(d), d, d, d, P(d)]
         L.orc_set_ib_iters.restype = i
         L.orc_set_ib_iters.argtypes = [vp, i]
+        L.orc_region_momentum.argtypes = [vp, P(d), d, P(d), P(d)]
         L.orc_set_segment_refs.restype = i
         L.orc_set_segment_refs.argtypes = [vp, i, P(d)]
         L.orc_set_slip.restype = i
@@ -162,6 +163,14 @@ class Oracle:
             N = _f64(normals, (n, 3))
             if lib().orc_set_slip(self._h, 1, n, _dp(N)) != 0:
                 raise ValueError("oracle: invalid normals")
+
+    def region_momentum(self, center, radius):
+        """(P[3], L[3], sum alpha) of the fluid inside the sphere."""
+        out = np.zeros(6)
+        a = ctypes.c_double()
+        c = _f64(center, (3,))
+        lib().orc_region_momentum(self._h, _dp(c), float(radius), _dp(out), ctypes.byref(a))
+        return out[:3].copy(), out[3:].copy(), a.value
 
     def set_segment_refs(self, refs):
         """Torque reference point per segment row (nseg, 3); None: common ref."""

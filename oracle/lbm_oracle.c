@@ -692,6 +692,45 @@ void orc_get_fields(void *h, double *rho, double *u) {
     }
 }
 
+/* Momentum and angular momentum of the fluid inside a sphere (centre c,
+ * radius R) in the stored state: P = sum_x alpha(x) j(x), L = sum_x alpha(x)
+ * (x - c) x j(x), j = sum_i c_i f*_i, with the cell's volume fraction
+ * approximated by alpha = clamp(R + 1/2 - |x - c|, 0, 1) and x - c the
+ * minimal image on periodic axes.  This is the internal-fluid term of a free
+ * body's Newton-Euler equations (Kempe & Froehlich 2012, J. Comput. Phys.
+ * 231).  out: P[3], L[3]; alpha_sum: sum alpha (the discrete volume). */
+void orc_region_momentum(void *h, const double *c, double R, double *out, double *alpha_sum) {
+    orc_t *o = (orc_t *)h;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int z = 0; z < o->n[2]; ++z)
+        for (int y = 0; y < o->n[1]; ++y)
+            for (int x = 0; x < o->n[0]; ++x) {
+                int p[3] = {x, y, z};
+                double r[3];
+                for (int a = 0; a < 3; ++a) {
+                    r[a] = p[a] - c[a];
+                    if (periodic(o, a)) r[a] -= o->n[a] * floor(r[a] / o->n[a] + 0.5);
+                }
+                double d = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+                double al = R + 0.5 - d;
+                if (al <= 0.0) continue;
+                if (al > 1.0) al = 1.0;
+                const double *f = o->f + cidx(o, x, y, z) * Q;
+                double j[3] = {0, 0, 0};
+                for (int i = 0; i < Q; ++i)
+                    for (int a = 0; a < 3; ++a) j[a] += C[i][a] * f[i];
+                double t[3];
+                cross(r, j, t);
+                for (int a = 0; a < 3; ++a) {
+                    acc[a] += al * j[a];
+                    acc[3 + a] += al * t[a];
+                }
+                acc[6] += al;
+            }
+    for (int k = 0; k < 6; ++k) out[k] = acc[k];
+    if (alpha_sum) *alpha_sum = acc[6];
+}
+
 void orc_get_force_torque(void *h, double *out) {
     orc_t *o = (orc_t *)h;
     int ns = o->nseg > 0 ? o->nseg : 1;

@@ -65,6 +65,9 @@ MUTANTS = {
         "const double *rs = o->has_seg_ref ? o->seg_ref[sg] : o->ref;",
         "const double *rs = o->ref;",
         "test_segment_reference_points_transport_the_moment"),
+    "region_momentum_alpha_unclamped": (
+        "if (al > 1.0) al = 1.0;", "if (al > 2.0) al = 1.0;",
+        "test_region_momentum_volume_and_inertia"),
     "slip_projection_dropped": (
         "for (int a = 0; a < 3; ++a) dF[3 * l + a] = dn * nl[a];",
         "for (int a = 0; a < 3; ++a) dF[3 * l + a] = dF[3 * l + a] + 0.0 * dn * nl[a];",
