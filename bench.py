@@ -295,6 +295,29 @@ def school_form(W, K, world, peak, vkw):
                          "kernel_ms": round(k[1], 5), "ib_ms": round(k[0], 5)}}
 
 
+def free_sphere_form(W, K, world, vkw):
+    """A free sphere (R = 8, density ratio 1.08, gravity 1e-4 along -z) in a
+    128^3 periodic box, two-way coupled every step: the body update reads the
+    force/torque and the inner-fluid momentum back to the host each step, so
+    the timed step includes those two synchronisations."""
+    import torch
+    from paper_2206_01683_b300 import fishlbm, rigid
+    shape = (128, 128, 128)
+    stream = torch.cuda.Stream()
+    dom = fishlbm.Domain([fishlbm.env_desc(shape, 0.6)], stream=stream.cuda_stream, **vkw)
+    body = rigid.FreeSphere(dom, 8.0, (63.5, 63.5, 80.0), 1.08, (0.0, 0.0, -1e-4))
+    for _ in range(W):
+        body.step()
+    ms = _max_over_ranks(_timed(stream, world, lambda n: body.step(), range(K)), world)
+    ncell = shape[0] * shape[1] * shape[2]
+    out = {"value": round(world * ncell * K / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+           "ms_per_step": round(ms / K, 5), "workload": "free_sphere_128cube_R8_ratio1.08",
+           "markers": int(len(body.dirs)), "velocity_z": round(float(body.vel[2]), 8),
+           "host_syncs_per_step": 2}
+    dom.close()
+    return out
+
+
 def batched_form(W, K, world, peak, vkw, n_envs=64):
     """64 independent single-fish environments, grid sizes drawn by seed from
     {96x64x64, 128x64x64, 160x80x80, 192x96x96}, fish of 0.4 x grid length
@@ -447,6 +470,7 @@ def run_ours(args):
             "deterministic": storage_form("f32", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world,
                                           peak, _variant_kw(args), deterministic=True),
             "school": school_form(W, Kf, world, peak, _variant_kw(args)),
+            "free_sphere": free_sphere_form(W, Kf, world, _variant_kw(args)),
             "batched": batched_form(W, Kf, world, peak, _variant_kw(args)),
             "adjoint": adjoint_form(),
         }

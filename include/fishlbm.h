@@ -139,6 +139,18 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
                          const float* dV, const int* seg, int n_seg, const double ref[3],
                          int device_ptrs);
 
+/* Momentum and angular momentum of the fluid inside a sphere (centre,
+ * radius; lattice units) in env's current state: out[0..2] = sum alpha j,
+ * out[3..5] = sum alpha (x - centre) x j, with j = sum_i c_i f_i,
+ * alpha = clamp(radius + 1/2 - |x - centre|, 0, 1) the cell's volume
+ * fraction and x - centre the minimal image on periodic axes; *alpha_sum
+ * (nullable) = sum alpha.  A free body's Newton-Euler equations need this
+ * inner-fluid momentum every step (Eq. 1's tau_ext with the fluid inside the
+ * immersed shell, Kempe & Froehlich 2012).  Compensated FP32 sums on the
+ * device, added in FP64 on the host; synchronises. */
+fg_status fg_region_momentum(fg_domain* d, int env, const double center[3], double radius, double* out,
+                             double* alpha_sum);
+
 /* Torque reference points of env's segment rows, refs[n_seg][3] (host),
  * n_seg equal to that of the last fg_set_markers: segment s reports its
  * torque about refs[s], so several bodies can share one marker set (each

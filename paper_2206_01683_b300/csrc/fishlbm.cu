@@ -120,6 +120,8 @@ struct fg_domain {
     float* dF = nullptr;                 // per-pass force increments of multi-direct forcing
     float* Nrm = nullptr;                // unit marker normals (slip forcing)
     float* seg_ref = nullptr;            // torque points of the segment rows [n_envs][MAX_SEG][3]
+    Pair32* region_part = nullptr;       // block partials of fg_region_momentum
+    int region_cap = 0;
     int* seg = nullptr;
     int marker_slots = 0;                // allocated marker slots
     int total_markers = 0;
@@ -211,8 +213,8 @@ void free_all(fg_domain* d) {
         if (p) cudaFree(p);
     void* ptrs[] = {d->d_env, d->d_frame, d->pop[0], d->pop[1], d->fib, d->stamps, d->ib_nodes, d->ib_bar,
                     d->fibq, d->mass_part, d->red_partials, d->red_counters, d->d_state,
-                    d->X, d->U, d->dV, d->Fm, d->dF, d->Nrm, d->seg, d->seg_ref, d->ft, d->mass, d->hist,
-                    d->status};
+                    d->X, d->U, d->dV, d->Fm, d->dF, d->Nrm, d->seg, d->seg_ref, d->region_part, d->ft, d->mass,
+                    d->hist, d->status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k < FG_K_COUNT; ++k)
@@ -857,6 +859,57 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
         if ((st = upload_env(d)) != FG_OK) return st;
         if ((st = upload_seg_refs(d)) != FG_OK) return st;
     }
+    return FG_OK;
+}
+
+fg_status fg_region_momentum(fg_domain* d, int env, const double* center, double radius, double* out,
+                             double* alpha_sum) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    if (!center || !out) return fail(FG_ERR_INVALID, "null argument");
+    if (!(radius > 0.0) || !std::isfinite(radius)) return fail(FG_ERR_INVALID, "radius must be positive");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(center[a]) || std::fabs(center[a]) > 1e6) return fail(FG_ERR_INVALID, "centre not finite");
+    const EnvDev& E = d->env[env];
+    int lo[3], ext[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (int)std::floor(center[a] - radius - 1.0);
+        ext[a] = (int)std::ceil(center[a] + radius + 1.0) - lo[a] + 1;
+        if (!E.per[a]) {   // open axis: clamp the box to the domain
+            const int hi = std::min(lo[a] + ext[a], E.n[a]);
+            lo[a] = std::max(lo[a], 0);
+            ext[a] = std::max(hi - lo[a], 0);
+        } else if (ext[a] > E.n[a]) {   // periodic axis: each cell once
+            lo[a] = 0;
+            ext[a] = E.n[a];
+        }
+    }
+    const long long n_box = (long long)ext[0] * ext[1] * ext[2];
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((n_box + RED_THREADS - 1) / RED_THREADS,
+                                                                       4ll * d->n_sms));
+    if (d->region_cap < blocks) {
+        if (d->region_part) cudaFree(d->region_part);
+        d->region_part = nullptr;
+        if ((st = dalloc(&d->region_part, (size_t)blocks * 7)) != FG_OK) return st;
+        d->region_cap = blocks;
+    }
+    st = dispatch(d->opt.storage, [&](auto tag) -> fg_status {
+        typedef decltype(tag) S;
+        k_region_momentum<S><<<blocks, RED_THREADS, 0, d->stream>>>(
+            (const typename S::raw*)d->pop[d->cur], d->d_env, env, (float)center[0], (float)center[1],
+            (float)center[2], (float)radius, lo[0], lo[1], lo[2], ext[0], ext[1], ext[2], d->region_part);
+        CK(cudaGetLastError());
+        return FG_OK;
+    });
+    if (st != FG_OK) return st;
+    std::vector<Pair32> h((size_t)blocks * 7);
+    CK(cudaMemcpyAsync(h.data(), d->region_part, sizeof(Pair32) * h.size(), cudaMemcpyDeviceToHost, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < blocks; ++b)
+        for (int q = 0; q < 7; ++q) acc[q] += pair_value(h[(size_t)b * 7 + q]);
+    for (int q = 0; q < 6; ++q) out[q] = acc[q];
+    if (alpha_sum) *alpha_sum = acc[6];
     return FG_OK;
 }
 

@@ -200,4 +200,78 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
     st->stamp = st->stamp == 0xffffffffu ? 1u : st->stamp + 1u;
 }
 
+// Momentum and angular momentum of the fluid inside a sphere (centre c,
+// radius R) in the stored state g of environment e: P = sum alpha j,
+// L = sum alpha (x - c) x j, j = sum_i c_i g_i (the rest populations w_i
+// carry no momentum), alpha = clamp(R + 1/2 - |x - c|, 0, 1), x - c the
+// minimal image on periodic axes.  The free-body coupling needs it every step
+// (the inner fluid's momentum change, Kempe & Froehlich 2012).  Threads walk
+// the cells of the sphere's bounding box [lo, lo + ext); every block writes
+// seven compensated pairs (P, L, sum alpha) to part[block]; the host adds
+// them in block order.
+template <class S>
+__global__ void __launch_bounds__(RED_THREADS)
+k_region_momentum(const typename S::raw* __restrict__ g, const EnvDev* __restrict__ envs, int e, float cx_,
+                  float cy_, float cz_, float R, int lo_x, int lo_y, int lo_z, int ext_x, int ext_y, int ext_z,
+                  Pair32* __restrict__ part) {
+    __shared__ Pair32 sh[RED_THREADS / 32][7];
+    const EnvDev& E = envs[e];
+    const typename S::raw* G = g + E.pop_off;
+    const float c[3] = {cx_, cy_, cz_};
+    Pair32 acc[7];
+    const long long n_box = (long long)ext_x * ext_y * ext_z;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n_box;
+         k += (long long)gridDim.x * blockDim.x) {
+        int p[3] = {lo_x + (int)(k % ext_x), lo_y + (int)((k / ext_x) % ext_y), lo_z + (int)(k / ((long long)ext_x * ext_y))};
+        float r[3];
+        bool inside = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int n = E.n[a];
+            r[a] = (float)p[a] - c[a];
+            if (E.per[a]) {
+                p[a] = ((p[a] % n) + n) % n;
+                r[a] -= (float)n * floorf(r[a] / (float)n + 0.5f);
+            } else if (p[a] < 0 || p[a] >= n) {
+                inside = false;
+            }
+        }
+        if (!inside) continue;
+        const float al = fminf(R + 0.5f - sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]), 1.0f);
+        if (al <= 0.0f) continue;
+        const uint32_t slot = (uint32_t)p[0] + (uint32_t)E.P * ((uint32_t)p[1] + (uint32_t)E.n[1] * (uint32_t)p[2]);
+        float j[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const float v = S::decode(G[(size_t)i * E.nslot + slot], i);
+            j[0] += cx(i) * v;
+            j[1] += cy(i) * v;
+            j[2] += cz(i) * v;
+        }
+        acc[0].add(al * j[0]); acc[1].add(al * j[1]); acc[2].add(al * j[2]);
+        acc[3].add(al * (r[1] * j[2] - r[2] * j[1]));
+        acc[4].add(al * (r[2] * j[0] - r[0] * j[2]));
+        acc[5].add(al * (r[0] * j[1] - r[1] * j[0]));
+        acc[6].add(al);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) {
+            Pair32 o;
+            o.hi = __shfl_xor_sync(0xffffffffu, acc[q].hi, s);
+            o.lo = __shfl_xor_sync(0xffffffffu, acc[q].lo, s);
+            acc[q].add(o);
+        }
+        if (lane == 0) sh[w][q] = acc[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        Pair32 t;
+        for (int i = 0; i < RED_THREADS / 32; ++i) t.add(sh[i][threadIdx.x]);
+        part[(size_t)blockIdx.x * 7 + threadIdx.x] = t;
+    }
+}
+
 }  // namespace fl

@@ -62,6 +62,7 @@ SIGNATURES = {
     "fg_set_markers": (_I, [_V, _I, _I, _V, _V, _V, _V, _I, _P(_D), _I]),
     "fg_set_marker_normals": (_I, [_V, _I, _I, _V, _I]),
     "fg_set_segment_refs": (_I, [_V, _I, _I, _P(_D)]),
+    "fg_region_momentum": (_I, [_V, _I, _P(_D), _D, _P(_D), _P(_D)]),
     "fg_step": (_I, [_V, _I, _P(fg_frame)]),
     "fg_get_body_force_torque": (_I, [_V, _I, _P(_D)]),
     "fg_destroy": (None, [_V]),
@@ -261,6 +262,14 @@ class Domain:
         self._keep = (kX, kU, kd, ks)
         self.nseg[env] = int(n_seg)
         self.nmark[env] = n
+
+    def region_momentum(self, center, radius, env=0):
+        """(P[3], L[3], sum alpha) of the fluid inside a sphere."""
+        c = np.ascontiguousarray(center, dtype=np.float64).reshape(3)
+        out = np.zeros(6)
+        a = _D()
+        _check(lib().fg_region_momentum(self.h, env, _dp(c), float(radius), _dp(out), ctypes.byref(a)))
+        return out[:3].copy(), out[3:].copy(), a.value
 
     def set_segment_refs(self, refs, env=0):
         """Torque point per segment row (n_seg, 3); None: the common point."""
