@@ -322,7 +322,8 @@ def batched_form(W, K, world, peak, vkw, n_envs=64):
     """64 independent single-fish environments, grid sizes drawn by seed from
     {96x64x64, 128x64x64, 160x80x80, 192x96x96}, fish of 0.4 x grid length
     with 1500-4000 markers and its own wave amplitude and frame trajectory,
-    all advanced by the same launches (one graph replay per step)."""
+    all advanced by the same launches: one marker update for all
+    environments and one graph replay per step."""
     import torch
     from paper_2206_01683_b300 import fishlbm, inputs
     draws = inputs.batch_envs(n_envs, inputs.seed_for(4))
@@ -338,19 +339,22 @@ def batched_form(W, K, world, peak, vkw, n_envs=64):
     ts = np.arange(T)
     stream = torch.cuda.Stream()
     dom = fishlbm.Domain(descs, stream=stream.cuda_stream, **vkw)
-    XU = []
+    Xs, Us = [], []
     for e, f in enumerate(fishes):
         X, U = f.poses(ts)
-        XU.append((torch.from_numpy(X.astype(np.float32)).cuda(), torch.from_numpy(U.astype(np.float32)).cuda()))
+        Xs.append(X.astype(np.float32))
+        Us.append(U.astype(np.float32))
         ref = tuple(float(v) for v in f.joints_rest[0])
-        dom.set_markers(XU[e][0][0], XU[e][1][0], torch.from_numpy(f.dV.astype(np.float32)).cuda(),
-                        torch.from_numpy(f.seg).cuda(), n_seg=5, ref=ref, env=e)
-    refs = [tuple(float(v) for v in f.joints_rest[0]) for f in fishes]
+        dom.set_markers(torch.from_numpy(Xs[e][0]).cuda(), torch.from_numpy(Us[e][0]).cuda(),
+                        torch.from_numpy(f.dV.astype(np.float32)).cuda(), torch.from_numpy(f.seg).cuda(),
+                        n_seg=5, ref=ref, env=e)
+    # every step's markers of all environments, resident in HBM in the compact order
+    Xall = torch.from_numpy(np.concatenate(Xs, axis=1)).cuda()
+    Uall = torch.from_numpy(np.concatenate(Us, axis=1)).cuda()
     frames = [[fishlbm.frame_from_array(t.at(n)) for t in trajs] for n in range(T)]
 
     def step(n):
-        for e in range(n_envs):
-            dom.set_markers(XU[e][0][n], XU[e][1][n], None, None, n_seg=5, ref=refs[e], env=e)
+        dom.set_markers_all(Xall[n], Uall[n])
         dom.step(1, frames[n])
 
     for n in range(W):

@@ -139,6 +139,14 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
                          const float* dV, const int* seg, int n_seg, const double ref[3],
                          int device_ptrs);
 
+/* New positions and velocities for the markers of all environments at once
+ * (the per-step update of a batch): X, U float [n][3], environment after
+ * environment in the counts of each environment's last fg_set_markers, n their
+ * total; host or device (device_ptrs).  Weights, segments and reference
+ * points are unchanged.  One scatter launch (plus two copies for host
+ * arrays) instead of one call per environment; asynchronous. */
+fg_status fg_set_markers_all(fg_domain* d, int n, const float* X, const float* U, int device_ptrs);
+
 /* Momentum and angular momentum of the fluid inside a sphere (centre,
  * radius; lattice units) in env's current state: out[0..2] = sum alpha j,
  * out[3..5] = sum alpha (x - centre) x j, with j = sum_i c_i f_i,

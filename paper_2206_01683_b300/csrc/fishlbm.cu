@@ -23,6 +23,23 @@
 
 using namespace fl;
 
+// Marker positions and velocities of every environment from caller-owned
+// device arrays in the compact marker order (environment after environment),
+// scattered to each environment's marker region in one launch.
+__global__ void k_scatter_markers(const fl::EnvDev* __restrict__ envs, int n_envs, int total,
+                                  const float* __restrict__ Xs, const float* __restrict__ Us,
+                                  float* __restrict__ X, float* __restrict__ U) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+        const int e = n_envs > 1 ? fl::env_of<&fl::EnvDev::mk_begin>(envs, n_envs, k) : 0;
+        const int slot = envs[e].marker_off + (k - envs[e].mk_begin);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            X[3 * slot + a] = Xs[3 * k + a];
+            U[3 * slot + a] = Us[3 * k + a];
+        }
+    }
+}
+
 // Marker positions and velocities of one environment from caller-owned
 // device arrays (count values each), in one launch.
 __global__ void k_copy_markers(float* __restrict__ X, float* __restrict__ U, const float* __restrict__ Xs,
@@ -120,6 +137,8 @@ struct fg_domain {
     float* dF = nullptr;                 // per-pass force increments of multi-direct forcing
     float* Nrm = nullptr;                // unit marker normals (slip forcing)
     float* seg_ref = nullptr;            // torque points of the segment rows [n_envs][MAX_SEG][3]
+    float* mk_stage = nullptr;           // host marker arrays of fg_set_markers_all, staged
+    size_t mk_stage_cap = 0;             // floats
     Pair32* region_part = nullptr;       // block partials of fg_region_momentum
     int region_cap = 0;
     int* seg = nullptr;
@@ -213,7 +232,7 @@ void free_all(fg_domain* d) {
         if (p) cudaFree(p);
     void* ptrs[] = {d->d_env, d->d_frame, d->pop[0], d->pop[1], d->fib, d->stamps, d->ib_nodes, d->ib_bar,
                     d->fibq, d->mass_part, d->red_partials, d->red_counters, d->d_state,
-                    d->X, d->U, d->dV, d->Fm, d->dF, d->Nrm, d->seg, d->seg_ref, d->region_part, d->ft, d->mass,
+                    d->X, d->U, d->dV, d->Fm, d->dF, d->Nrm, d->seg, d->seg_ref, d->region_part, d->mk_stage, d->ft, d->mass,
                     d->hist, d->status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -928,6 +947,46 @@ fg_status fg_set_segment_refs(fg_domain* d, int env, int n_seg, const double* re
         for (int a = 0; a < 3; ++a) m.seg_ref[sg][a] = refs[3 * sg + a];
     m.has_seg_ref = true;
     return upload_seg_refs(d);
+}
+
+fg_status fg_set_markers_all(fg_domain* d, int n, const float* X, const float* U, int device_ptrs) {
+    if (!d) return fail(FG_ERR_INVALID, "null domain");
+    if (n != d->total_markers) return fail(FG_ERR_INVALID, "n must equal the markers of all environments");
+    if (n == 0) return FG_OK;
+    if (!X || !U) return fail(FG_ERR_INVALID, "null marker array");
+    const float* xs = X;
+    const float* us = U;
+    if (!device_ptrs) {
+        int k = 0;
+        for (int e = 0; e < d->n_envs; ++e) {   // the checks of fg_set_markers, environment by environment
+            const EnvDev& E = d->env[e];
+            for (int l = 0; l < d->mk[e].n; ++l, ++k)
+                for (int a = 0; a < 3; ++a) {
+                    const float x = X[3 * k + a];
+                    if (!std::isfinite(x) || std::fabs(x) > 1.0e6f) return fail(FG_ERR_INVALID, "marker position not finite");
+                    if (!E.per[a] && !(x >= 2.0f && x < (float)E.n[a] - 3.0f))
+                        return fail(FG_ERR_INVALID, "marker within 2 cells of a non-periodic face");
+                    if (!std::isfinite(U[3 * k + a])) return fail(FG_ERR_INVALID, "marker velocity not finite");
+                }
+        }
+        const size_t need = 6ull * n;
+        if (d->mk_stage_cap < need) {
+            if (d->mk_stage) cudaFree(d->mk_stage);
+            d->mk_stage = nullptr;
+            d->mk_stage_cap = 0;
+            fg_status st = dalloc(&d->mk_stage, need);
+            if (st != FG_OK) return st;
+            d->mk_stage_cap = need;
+        }
+        CK(cudaMemcpyAsync(d->mk_stage, X, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, d->stream));
+        CK(cudaMemcpyAsync(d->mk_stage + 3ull * n, U, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, d->stream));
+        xs = d->mk_stage;
+        us = d->mk_stage + 3ull * n;
+    }
+    const int blocks = std::min((n + 255) / 256, 8 * d->n_sms);
+    k_scatter_markers<<<blocks, 256, 0, d->stream>>>(d->d_env, d->n_envs, n, xs, us, d->X, d->U);
+    CK(cudaGetLastError());
+    return FG_OK;
 }
 
 fg_status fg_set_marker_normals(fg_domain* d, int env, int n, const float* N, int device_ptrs) {

@@ -62,6 +62,7 @@ SIGNATURES = {
     "fg_set_markers": (_I, [_V, _I, _I, _V, _V, _V, _V, _I, _P(_D), _I]),
     "fg_set_marker_normals": (_I, [_V, _I, _I, _V, _I]),
     "fg_set_segment_refs": (_I, [_V, _I, _I, _P(_D)]),
+    "fg_set_markers_all": (_I, [_V, _I, _V, _V, _I]),
     "fg_region_momentum": (_I, [_V, _I, _P(_D), _D, _P(_D), _P(_D)]),
     "fg_step": (_I, [_V, _I, _P(fg_frame)]),
     "fg_get_body_force_torque": (_I, [_V, _I, _P(_D)]),
@@ -270,6 +271,17 @@ class Domain:
         a = _D()
         _check(lib().fg_region_momentum(self.h, env, _dp(c), float(radius), _dp(out), ctypes.byref(a)))
         return out[:3].copy(), out[3:].copy(), a.value
+
+    def set_markers_all(self, X, U):
+        """Positions and velocities (n_total, 3) of all environments' markers,
+        environment after environment (numpy, torch CPU or CUDA tensors)."""
+        n = int(X.shape[0])
+        pX, devX, kX = _ptr_and_keep(X, np.float32)
+        pU, devU, kU = _ptr_and_keep(U, np.float32)
+        if devX != devU:
+            raise ValueError("X and U must both be host or both be device arrays")
+        _check(lib().fg_set_markers_all(self.h, n, pX, pU, 1 if devX else 0))
+        self._keep_all = (kX, kU)
 
     def set_segment_refs(self, refs, env=0):
         """Torque point per segment row (n_seg, 3); None: the common point."""

@@ -507,3 +507,39 @@ def test_free_sphere_matches_oracle_reference():
     assert np.linalg.norm(s_g.vel - s_o.V) <= 2e-4 * np.linalg.norm(s_o.V)
     assert np.linalg.norm(s_g.centre - s_o.c) <= 1e-6 * L
     assert np.linalg.norm(s_g.spin - s_o.W) <= 2e-3 * np.linalg.norm(s_o.W) + 1e-10
+
+
+def test_set_markers_all_equals_per_environment_updates():
+    """One fg_set_markers_all call (device and host arrays) moves the markers
+    of three environments exactly as three fg_set_markers calls do."""
+    torch = pytest.importorskip("torch")
+    shapes = [(32, 24, 20), (40, 16, 24), (24, 24, 24)]
+    fishes = [inputs.fish_for_grid(s, 0.4 * s[0], 300 + 50 * k) for k, s in enumerate(shapes)]
+
+    def make():
+        d = fishlbm.Domain([fishlbm.env_desc(s, 0.6, OPEN_X, (0.02, 0, 0), 1.0, (0.02, 0, 0)) for s in shapes],
+                           deterministic=True)   # bit-reproducible, so the runs compare exactly
+        for e, f in enumerate(fishes):
+            X, U = f.pose(0)
+            d.set_markers(np.float32(X), np.float32(U), np.float32(f.dV), seg=f.seg, n_seg=5,
+                          ref=f.joints_rest[0], env=e)
+        return d
+
+    a, b, c = make(), make(), make()
+    for n in range(1, 6):
+        poses = [f.pose(n) for f in fishes]
+        for e, f in enumerate(fishes):
+            a.set_markers(np.float32(poses[e][0]), np.float32(poses[e][1]), None, None, n_seg=5,
+                          ref=f.joints_rest[0], env=e)
+        Xall = np.concatenate([p[0] for p in poses]).astype(np.float32)
+        Uall = np.concatenate([p[1] for p in poses]).astype(np.float32)
+        b.set_markers_all(torch.from_numpy(Xall).cuda(), torch.from_numpy(Uall).cuda())
+        c.set_markers_all(Xall, Uall)
+        for d in (a, b, c):
+            d.step(1)
+    for e in range(3):
+        fa = a.populations(e)
+        assert np.array_equal(fa, b.populations(e)) and np.array_equal(fa, c.populations(e))
+        assert np.array_equal(a.get_body_force_torque(e), b.get_body_force_torque(e))
+    with pytest.raises(fishlbm.FgError):
+        b.set_markers_all(Xall[:-1], Uall[:-1])             # wrong total
