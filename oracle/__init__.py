@@ -49,7 +49,9 @@ def lib():
         L.orc_interp.argtypes = [vp, P(d), i, P(d), P(d)]
         L.orc_spread.restype = i
         L.orc_spread.argtypes = [vp, i, P(d), P(d), P(d)]
-        L.orc_collide_cell.argtypes = [P(d), P(d), P(d), P(d), d, P(d)]
+        L.orc_collide_cell.argtypes = [P(d), P(d), P(d), P(d), d, i, P(d)]
+        L.orc_set_eq_order.restype = i
+        L.orc_set_eq_order.argtypes = [vp, i]
         L.orc_frame_accel.argtypes = [P(d), d, d, d, P(d)]
         L.orc_set_ib_iters.restype = i
         L.orc_set_ib_iters.argtypes = [vp, i]
@@ -96,10 +98,10 @@ def frame_accel(frame, x):
     return out
 
 
-def collide_cell(fs, a0, fib, omega, tau):
+def collide_cell(fs, a0, fib, omega, tau, eq_order=2):
     out = np.zeros(27)
     fs, a0, fib, om = _f64(fs, (27,)), _f64(a0, (3,)), _f64(fib, (3,)), _f64(omega, (3,))
-    lib().orc_collide_cell(_dp(fs), _dp(a0), _dp(fib), _dp(om), float(tau), _dp(out))
+    lib().orc_collide_cell(_dp(fs), _dp(a0), _dp(fib), _dp(om), float(tau), int(eq_order), _dp(out))
     return out
 
 
@@ -111,7 +113,7 @@ class Oracle:
     """One FP64 domain.  Fields use cell index x + nx*(y + ny*z)."""
 
     def __init__(self, shape, tau, faces=(PERIODIC,) * 6, u_in=(0.0, 0.0, 0.0), rho_out=1.0, ib_iters=1,
-                 slip=False):
+                 slip=False, eq_order=2):
         nx, ny, nz = shape
         self.shape = (nx, ny, nz)
         self.ncell = nx * ny * nz
@@ -125,6 +127,8 @@ class Oracle:
             self._h = None
             raise ValueError("oracle: ib_iters must be in [1, 64]")
         self.slip = bool(slip)
+        if lib().orc_set_eq_order(self._h, int(eq_order)) != 0:
+            raise ValueError("oracle: eq_order must be 2 or 3")
         self.tau = tau
         self.faces = tuple(int(f) for f in faces)
         self.nm = 0

@@ -82,6 +82,7 @@ typedef struct {
     double *rho, *j, *Pi;/* post-stream moments: rho, j[3], Pi[6] (xx,yy,zz,xy,xz,yz) */
     double *fib;         /* spread IB force density, [ncell][3] */
     int ib_iters;        /* direct-forcing passes M (>= 1) */
+    int eq_order;        /* 2, or 3: add the lattice's third-order equilibrium terms */
     int slip;            /* 1: enforce only the normal velocity component */
     double *Nrm;         /* unit marker normals [nm][3] (slip) */
     int nm, nseg;        /* markers */
@@ -123,6 +124,7 @@ void *orc_create(int nx, int ny, int nz, double tau, const int *face, const doub
     for (int a = 0; a < 3; ++a) o->u_in[a] = u_in ? u_in[a] : 0.0;
     o->rho_out = rho_out;
     o->ib_iters = 1;
+    o->eq_order = 2;
     o->f = (double *)calloc((size_t)o->ncell * Q, sizeof(double));
     o->fs = (double *)calloc((size_t)o->ncell * Q, sizeof(double));
     o->rho = (double *)calloc((size_t)o->ncell, sizeof(double));
@@ -157,6 +159,46 @@ static void equilibrium(double rho, const double u[3], double out[Q]) {
     }
 }
 
+/* The third-order Hermite terms of the equilibrium that D3Q27 can carry,
+ *   f3_i = w_i / (6 cs2^3) sum_abc rho u_a u_b u_c H_abc(c_i),
+ *   H_abc(c) = c_a c_b c_c - cs2 (c_a d_bc + c_b d_ac + c_c d_ab),
+ * summed over the index triples that are not all equal: on D3Q27
+ * c_a^3 = c_a and 3 cs2 = 1, so H_aaa(c) = c_a^3 - 3 cs2 c_a vanishes on every
+ * lattice velocity -- the lattice cannot carry rho u_a^3 (the loop skips
+ * these terms, which are zero anyway). */
+static void hermite3_eq(double rho, const double u[3], double out[Q]) {
+    for (int i = 0; i < Q; ++i) {
+        const int *c = C[i];
+        double s = 0.0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                for (int g = 0; g < 3; ++g) {
+                    if (a == b && b == g) continue;
+                    double H = c[a] * c[b] * c[g] -
+                               CS2 * (c[a] * (b == g) + c[b] * (a == g) + c[g] * (a == b));
+                    s += rho * u[a] * u[b] * u[g] * H;
+                }
+        out[i] = W[i] * s / (6.0 * CS2 * CS2 * CS2);
+    }
+}
+
+/* Equilibrium of the configured order: second order, plus hermite3_eq. */
+static void equilibrium_n(const orc_t *o, double rho, const double u[3], double out[Q]) {
+    equilibrium(rho, u, out);
+    if (o->eq_order == 3) {
+        double t[Q];
+        hermite3_eq(rho, u, t);
+        for (int i = 0; i < Q; ++i) out[i] += t[i];
+    }
+}
+
+int orc_set_eq_order(void *h, int order) {
+    orc_t *o = (orc_t *)h;
+    if (order != 2 && order != 3) return -1;
+    o->eq_order = order;
+    return 0;
+}
+
 /* Rebuild populations from (rho, J, Qt) on the 2nd-order Hermite basis,
  *   f_i = w_i [rho + c_i.J/cs2 + (c_i c_i - cs2 I):Qt/(2 cs2^2)],
  * Qt = Pi - rho cs2 I given as (xx,yy,zz,xy,xz,yz). */
@@ -177,7 +219,7 @@ void orc_init_fields(void *h, const double *rho, const double *u) {
         double r = rho ? rho[c] : 1.0;
         double uu[3] = {0, 0, 0};
         if (u) { uu[0] = u[3 * c]; uu[1] = u[3 * c + 1]; uu[2] = u[3 * c + 2]; }
-        equilibrium(r, uu, o->f + c * Q);
+        equilibrium_n(o, r, uu, o->f + c * Q);
     }
     o->step = 0;
 }
@@ -499,7 +541,7 @@ int orc_set_ib_iters(void *h, int m) {
  * with Pi_eq = rho u u + rho cs2 I.  These are the moments that BGK with
  * Guo's source term produces, rebuilt on the 2nd-order Hermite basis. */
 static void collide(const double fs[Q], const double a0[3], const double fib[3],
-                    const double om[3], double tau, double out[Q]) {
+                    const double om[3], double tau, int eq_order, double out[Q]) {
     double rho = 0, j[3] = {0, 0, 0}, Pi[3][3] = {{0}};
     for (int i = 0; i < Q; ++i) {
         rho += fs[i];
@@ -527,12 +569,17 @@ static void collide(const double fs[Q], const double a0[3], const double fib[3],
     double Qt[6] = {Pst[0][0] - rho * CS2, Pst[1][1] - rho * CS2, Pst[2][2] - rho * CS2,
                     Pst[0][1], Pst[0][2], Pst[1][2]};
     hermite2(rho, J, Qt, out);
+    if (eq_order == 3) {   /* the post-collision state carries the equilibrium's third moments */
+        double t[Q];
+        hermite3_eq(rho, u, t);
+        for (int i = 0; i < Q; ++i) out[i] += t[i];
+    }
 }
 
 void orc_collide_cell(const double *fs, const double *a0, const double *fib, const double *om,
-                      double tau, double *out) {
+                      double tau, int eq_order, double *out) {
     lattice_init();
-    collide(fs, a0, fib, om, tau, out);
+    collide(fs, a0, fib, om, tau, eq_order == 3 ? 3 : 2, out);
 }
 
 /* ------------------------------------------------------ 7 boundary (NEE) */
@@ -582,7 +629,7 @@ static void boundary_cell(const orc_t *o, int x, int y, int z, const int side[3]
         }
     }
     double feq[Q], zero3[3] = {0, 0, 0}, fneq[Q];
-    equilibrium(rb, ub, feq);
+    equilibrium_n(o, rb, ub, feq);
     hermite2(0.0, zero3, Pneq, fneq);
     long cb = cidx(o, x, y, z);
     for (int i = 0; i < Q; ++i) o->f[cb * Q + i] = feq[i] + (1.0 - 1.0 / o->tau) * fneq[i];
@@ -645,7 +692,7 @@ int orc_step(void *h, const double *frame) {
                     long c = cidx(o, x, y, z);
                     double a0[3];
                     frame_accel(frame, x, y, z, a0);
-                    collide(o->fs + c * Q, a0, o->fib + 3 * c, om, o->tau, o->f + c * Q);
+                    collide(o->fs + c * Q, a0, o->fib + 3 * c, om, o->tau, o->eq_order, o->f + c * Q);
                 }
             }
     force_torque(o);           /* 8 */

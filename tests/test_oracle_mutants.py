@@ -68,6 +68,14 @@ MUTANTS = {
     "region_momentum_alpha_unclamped": (
         "if (al > 1.0) al = 1.0;", "if (al > 2.0) al = 1.0;",
         "test_region_momentum_volume_and_inertia"),
+    "eq3_wrong_hermite_shift": (
+        "CS2 * (c[a] * (b == g) + c[b] * (a == g) + c[g] * (a == b));",
+        "CS2 * (c[a] * (b == g) + c[b] * (a == g));",
+        "test_third_order_equilibrium_moments"),
+    "eq3_post_collision_dropped": (
+        "if (eq_order == 3) {   /* the post-collision state carries the equilibrium's third moments */",
+        "if (0) {   /* the post-collision state carries the equilibrium's third moments */",
+        "test_third_order_equilibrium_restores_galilean_invariance_of_shear_decay"),
     "slip_projection_dropped": (
         "for (int a = 0; a < 3; ++a) dF[3 * l + a] = dn * nl[a];",
         "for (int a = 0; a < 3; ++a) dF[3 * l + a] = dF[3 * l + a] + 0.0 * dn * nl[a];",

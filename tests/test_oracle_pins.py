@@ -27,6 +27,9 @@ a shifted stencil, a transposed cross product) fails one of them:
   exact invariance of a tangential shear past a flat slip sheet, and the drag
   of a slip sphere between a bubble's and a no-slip sphere's;
 * per-segment torque reference points obey the transport of a moment;
+* third-order equilibrium: the Maxwellian's third moments on every index
+  triple the lattice carries, and an advected shear wave decaying at the same
+  rate for any carrier speed (the second order loses 3 U0^2);
 * free rigid sphere: the region momentum integral approaches the sphere's
   volume and moment of inertia; body plus outer-fluid momentum is conserved
   to rounding; the settling velocity matches the periodic Stokes drag.
@@ -801,3 +804,72 @@ def test_free_sphere_invariant_rejects_a_dropped_inner_fluid_term():
         total = s.mp * s.V + (rho[:, None] * u).sum(axis=0) - s.P_in
         worst = max(worst, np.max(np.abs(total)))
     assert worst > 1e-6 * s.mp * 1e-3
+
+
+def test_third_order_equilibrium_moments():
+    """With eq_order = 3 the equilibrium keeps the moments of order 0-2 and
+    gains the Maxwellian's third moments rho u_a u_b u_c + cs2 rho (u_a d_bc +
+    u_b d_ac + u_c d_ab) for every index triple that is not all equal (on
+    D3Q27, c_a^3 = c_a, so sum f c_a^3 stays rho u_a)."""
+    shape = (6, 5, 4)
+    rng = np.random.default_rng(71)
+    n = 120
+    rho = 1.0 + 0.05 * rng.standard_normal(n)
+    u = 0.08 * rng.standard_normal((n, 3))
+    c, _ = oracle.lattice()
+    o2, o3 = oracle.Oracle(shape, 0.8), oracle.Oracle(shape, 0.8, eq_order=3)
+    o2.init_fields(rho, u)
+    o3.init_fields(rho, u)
+    f2, f3 = o2.populations(), o3.populations()
+    cs2 = 1.0 / 3.0
+    for q in range(n):
+        assert abs(f3[q].sum() - rho[q]) < 1e-14
+        assert np.allclose(f3[q] @ c, rho[q] * u[q], atol=1e-15)
+        P3 = np.einsum("i,ia,ib->ab", f3[q], c, c)
+        assert np.allclose(P3, rho[q] * np.outer(u[q], u[q]) + cs2 * rho[q] * np.eye(3), atol=1e-15)
+        for a in range(3):
+            for b in range(3):
+                for g in range(3):
+                    m3 = np.sum(f3[q] * c[:, a] * c[:, b] * c[:, g])
+                    if a == b == g:
+                        assert abs(m3 - rho[q] * u[q, a]) < 1e-15
+                        continue
+                    want = rho[q] * u[q, a] * u[q, b] * u[q, g] + cs2 * rho[q] * (
+                        u[q, a] * (b == g) + u[q, b] * (a == g) + u[q, g] * (a == b))
+                    assert abs(m3 - want) < 1e-15, (q, a, b, g, m3, want)
+    assert not np.allclose(f2, f3)
+
+
+def _advected_shear_decay(order, U0, tau=0.8, L=64, steps=400, A=1e-3):
+    shape = (L, 4, 4)
+    o = oracle.Oracle(shape, tau, eq_order=order)
+    n = L * 16
+    x = np.tile(np.arange(L), 16).astype(float)
+    u = np.zeros((n, 3))
+    u[:, 0] = U0
+    u[:, 1] = A * np.sin(2 * math.pi * x / L)
+
+    def amp():
+        _, uu = o.fields()
+        v = uu[:, 1].reshape(4, 4, L).mean(axis=(0, 1))
+        return abs(np.fft.rfft(v)[1])
+
+    o.init_fields(np.ones(n), u)
+    a0 = amp()
+    o.step(n=steps)
+    nu, k = (tau - 0.5) / 3.0, 2 * math.pi / L
+    return -math.log(amp() / a0) / steps / (nu * k * k)
+
+
+def test_third_order_equilibrium_restores_galilean_invariance_of_shear_decay():
+    """A shear wave u_y = A sin(k x) carried along x at U0 decays at nu k^2
+    whatever U0 in a Galilean-invariant fluid.  With the second-order
+    equilibrium the lattice misses rho u_x^2 u_y in the third moment that
+    feeds the xy stress, and the decay rate drops by 3 U0^2 (U0^2 / cs2); the
+    third-order equilibrium supplies it and the rate stops depending on U0."""
+    r0 = _advected_shear_decay(2, 0.0)
+    assert abs(r0 - 1.0) < 3e-3                       # lattice viscosity at rest
+    for U0 in (0.05, 0.1):
+        r2, r3 = _advected_shear_decay(2, U0), _advected_shear_decay(3, U0)
+        assert abs((r2 - r0) / (-3 * U0 * U0) - 1.0) < 0.1, (U0, r2, r0)
+        assert abs(r3 - r0) < 1e-4 * r0, (U0, r3, r0)
