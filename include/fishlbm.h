@@ -97,6 +97,13 @@ typedef struct {
                            dF = 2 R ((U - U~).n) n, with the unit normals given
                            by fg_set_marker_normals; 0: no-slip (default).  The
                            adjoint takes 0 only. */
+    int eq_order;       /* 2: second-order (Hermite-2) equilibrium (default);
+                           3: also the third-order terms D3Q27 carries,
+                           4.5 w_i rho (c.u)((c.u)^2 - |u|^2), in the initial
+                           state, the post-collision rebuild and the open-face
+                           rule (removes the 3 u^2 error of the viscous
+                           stress for shear along the flow).  The adjoint takes
+                           2 only. */
     int use_graphs;     /* 1: each step is replayed from a captured CUDA graph
                            (captured on first use and whenever the marker count or
                            marker storage changes); 0: direct launches.  Steps taken

@@ -339,21 +339,29 @@ void refresh_marker_table(fg_domain* d) {
     d->total_markers = begin;
 }
 
-// The stream-collide launch of the variant in use (gin -> gout).
-template <class S>
-void enqueue_k1(fg_domain* d, const typename S::raw* gin, typename S::raw* gout, cudaStream_t s) {
+// The stream-collide launch of the variant in use (gin -> gout), with the
+// equilibrium order of the domain.
+template <class S, bool EQ3>
+void enqueue_k1_order(fg_domain* d, const typename S::raw* gin, typename S::raw* gout, cudaStream_t s) {
     if (d->k1 == K1_STAGED256) {
-        k_stream_collide_staged<S, 256, 4><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
+        k_stream_collide_staged<S, 256, 4, EQ3><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
             gin, gout, d->d_env, d->d_frame, d->n_envs, d->total_groups, d->fib, d->stamps, d->d_state,
             d->mass_part, d->status);
     } else if (d->k1 == K1_STAGED512) {
-        k_stream_collide_staged<S, 512, 2><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
+        k_stream_collide_staged<S, 512, 2, EQ3><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
             gin, gout, d->d_env, d->d_frame, d->n_envs, d->total_groups, d->fib, d->stamps, d->d_state,
             d->mass_part, d->status);
     } else {
-        k_stream_collide<S><<<d->total_blocks, K1_THREADS, 0, s>>>(gin, gout, d->d_env, d->d_frame, d->n_envs,
-                                                                   d->fib, d->stamps, d->d_state, d->mass_part);
+        k_stream_collide<S, EQ3><<<d->total_blocks, K1_THREADS, 0, s>>>(gin, gout, d->d_env, d->d_frame,
+                                                                        d->n_envs, d->fib, d->stamps, d->d_state,
+                                                                        d->mass_part);
     }
+}
+
+template <class S>
+void enqueue_k1(fg_domain* d, const typename S::raw* gin, typename S::raw* gout, cudaStream_t s) {
+    if (d->opt.eq_order == 3) enqueue_k1_order<S, true>(d, gin, gout, s);
+    else enqueue_k1_order<S, false>(d, gin, gout, s);
 }
 
 // Launch the kernels of one step reading buffer `parity` on stream s; with
@@ -483,10 +491,17 @@ fg_status dispatch(int storage, F&& f) {
 // Shared memory, occupancy and persistent grid of the staged kernel.
 template <class S, int GC, int MINB>
 fg_status staged_occupancy(fg_domain* d, int* per_sm) {
-    CK(cudaFuncSetAttribute(k_stream_collide_staged<S, GC, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // both equilibrium orders; the occupancy of the one in use
+    CK(cudaFuncSetAttribute(k_stream_collide_staged<S, GC, MINB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)d->staged_smem));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_stream_collide_staged<S, GC, MINB>, K1_THREADS,
-                                                     d->staged_smem));
+    CK(cudaFuncSetAttribute(k_stream_collide_staged<S, GC, MINB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)d->staged_smem));
+    if (d->opt.eq_order == 3)
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_stream_collide_staged<S, GC, MINB, true>,
+                                                         K1_THREADS, d->staged_smem));
+    else
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_stream_collide_staged<S, GC, MINB, false>,
+                                                         K1_THREADS, d->staged_smem));
     return FG_OK;
 }
 
@@ -588,7 +603,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     g_err.clear();
     if (!envs || !out || n_envs < 1 || n_envs > 4096) return fail(FG_ERR_INVALID, "bad environment list");
     fg_options o{};
-    o.storage = FG_F32; o.layout = 0; o.deterministic = 0; o.ib_iters = 1; o.record_history = 0; o.ib_slip = 0;
+    o.storage = FG_F32; o.layout = 0; o.deterministic = 0; o.ib_iters = 1; o.record_history = 0; o.ib_slip = 0; o.eq_order = 2;
     o.kernel_variant = FG_KERNEL_AUTO;
     o.use_graphs = 1;
     o.autotune = 0;
@@ -600,6 +615,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     if (o.ib_iters < 1 || o.ib_iters > FG_MAX_IB_ITERS) return fail(FG_ERR_INVALID, "ib_iters must be in [1, 8]");
     if (o.deterministic != 0 && o.deterministic != 1) return fail(FG_ERR_INVALID, "deterministic must be 0 or 1");
     if (o.ib_slip != 0 && o.ib_slip != 1) return fail(FG_ERR_INVALID, "ib_slip must be 0 or 1");
+    if (o.eq_order != 2 && o.eq_order != 3) return fail(FG_ERR_INVALID, "eq_order must be 2 or 3");
     if (o.record_history < 0 || o.record_history > (1 << 20)) return fail(FG_ERR_INVALID, "record_history");
     unsigned long long cells = 0;
     for (int e = 0; e < n_envs; ++e) {
@@ -797,7 +813,7 @@ fg_status fg_init_fields(fg_domain* d, int env, const double* rho, const double*
     st = dispatch(d->opt.storage, [&](auto tag) -> fg_status {
         typedef decltype(tag) S;
         k_init_eq<S><<<blocks, 256, 0, d->stream>>>((typename S::raw*)d->pop[d->cur], d->d_env, env, drho, du,
-                                                    s.rho0, s.u0[0], s.u0[1], s.u0[2]);
+                                                    s.rho0, s.u0[0], s.u0[1], s.u0[2], d->opt.eq_order == 3 ? 1 : 0);
         return FG_OK;
     });
     cudaError_t e1 = cudaGetLastError();
@@ -1284,6 +1300,7 @@ static fg_status adjoint_check(fg_domain* d) {
     if (d->opt.storage != FG_F32) return fail(FG_ERR_INVALID, "the adjoint takes FP32 storage");
     if (d->opt.ib_iters != 1) return fail(FG_ERR_INVALID, "the adjoint takes one direct-forcing pass");
     if (d->opt.ib_slip) return fail(FG_ERR_INVALID, "the adjoint takes no-slip forcing");
+    if (d->opt.eq_order != 2) return fail(FG_ERR_INVALID, "the adjoint takes the second-order equilibrium");
     for (int k = 0; k < 6; ++k)
         if (d->desc[0].face[k] != FG_PERIODIC) return fail(FG_ERR_INVALID, "the adjoint takes periodic domains");
     if (d->poisoned) return fail(FG_ERR_STATE, "domain poisoned by a numeric fault; call fg_init_fields");

@@ -15,11 +15,12 @@ __device__ __forceinline__ uint32_t cell_to_slot(const EnvDev& E, uint32_t c) {
     return row * (uint32_t)E.P + (c - row * nx);
 }
 
-// f_eq(rho, u) - w on the Hermite-2 basis, computed in FP64.
+// f_eq(rho, u) - w on the Hermite-2 basis (plus, with eq3, the third-order
+// terms 4.5 w rho (c.u)((c.u)^2 - |u|^2)), computed in FP64.
 template <class S>
 __global__ void k_init_eq(typename S::raw* __restrict__ g, const EnvDev* __restrict__ envs, int e,
                           const double* __restrict__ rho, const double* __restrict__ u,
-                          double rho0, double u0x, double u0y, double u0z) {
+                          double rho0, double u0x, double u0y, double u0z, int eq3) {
     const EnvDev& E = envs[e];
     const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t ncell = (uint32_t)E.n[0] * E.n[1] * E.n[2];
@@ -33,7 +34,8 @@ __global__ void k_init_eq(typename S::raw* __restrict__ g, const EnvDev* __restr
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-        const double f = wd(i) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+        double f = wd(i) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+        if (eq3) f += wd(i) * r * 4.5 * cu * (cu * cu - uu);
         G[(size_t)i * E.nslot + s] = S::encode((float)(f - wd(i)), i);
     }
 }

@@ -262,8 +262,12 @@ __device__ __forceinline__ int face_kind(int bc, int face) { return (bc >> (2 * 
 // Collision (interior) or open-face rule (boundary) from the pulled moments
 // m, then the Hermite-2 rebuild of all 27 outputs.  (sx, sy, sz) is the
 // inward normal of the non-periodic faces the cell lies on (0 for interior
-// cells).  Returns rho_out - 1 for the mass sum.
-template <class S>
+// cells).  EQ3 adds the third-order equilibrium terms the lattice carries,
+// w_i rho [(c.u)^3 - (c.u)|u|^2] / (2 cs2^3) = 4.5 w_i rho (c.u)((c.u)^2 - |u|^2)
+// (the Hermite sum over the index triples that are not all equal: H_aaa
+// vanishes on D3Q27), with the collision's (rho, u) inside and (rho_b, u_b)
+// on the open faces.  Returns rho_out - 1 for the mass sum.
+template <class S, bool EQ3 = false>
 __device__ __forceinline__ float update_cell(const CellConsts& F, const Moments& m, int x, int y, int z, int sx,
                                              int sy, int sz, float fx, float fy, float fz,
                                              typename S::raw* __restrict__ Go, uint32_t slot) {
@@ -271,6 +275,7 @@ __device__ __forceinline__ float update_cell(const CellConsts& F, const Moments&
     const float rho = 1.0f + m.dr;
     const float inv = 1.0f / rho;
     float drout, Jx, Jy, Jz, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz;
+    float r3 = 0.f, u3x = 0.f, u3y = 0.f, u3z = 0.f;   // (rho, u) of the third-order terms
     if ((sx | sy | sz) == 0) {
         // a0 = c0 - M p (the affine form of Eq. 3 without Coriolis)
         const float px = (float)x, py = (float)y, pz = (float)z;
@@ -303,6 +308,9 @@ __device__ __forceinline__ float update_cell(const CellConsts& F, const Moments&
         Qxz = ruxz + k * (m.sxz - ruxz) + gq * (ux * Gz + Gx * uz);
         Qyz = ruyz + k * (m.syz - ruyz) + gq * (uy * Gz + Gy * uz);
         drout = m.dr;
+        if constexpr (EQ3) {
+            r3 = rho; u3x = ux; u3y = uy; u3z = uz;
+        }
     } else {
         // non-equilibrium extrapolation (m are the moments of x_f = x + n):
         // f* = f_eq(rho_b, u_b) + (1 - 1/tau) f_neq(x_f); x-faces govern on edges
@@ -330,7 +338,11 @@ __device__ __forceinline__ float update_cell(const CellConsts& F, const Moments&
         Qxy = rb * ubx * uby + k * (m.sxy - rho * ufx * ufy);
         Qxz = rb * ubx * ubz + k * (m.sxz - rho * ufx * ufz);
         Qyz = rb * uby * ubz + k * (m.syz - rho * ufy * ufz);
+        if constexpr (EQ3) {
+            r3 = rb; u3x = ubx; u3y = uby; u3z = ubz;
+        }
     }
+    const float k3 = S::POLY * 4.5f * r3, uu3 = u3x * u3x + u3y * u3y + u3z * u3z;
     // Hermite-2 rebuild of the deviation: g*_i = w_i [dr + 3 c.J + 4.5 c c : Q - 1.5 tr Q],
     // organised by x-lines (cy, cz):  v(cx) = E + cx^2 dxx + O + cx B  with
     //   E = A + cy^2 dyy + cz^2 dzz + cy cz oyz,  O = cy ty + cz tz,  B = tx + cy oxy + cz oxz.
@@ -350,11 +362,21 @@ __device__ __forceinline__ float update_cell(const CellConsts& F, const Moments&
         if (lz == 1) O += tz; else if (lz == -1) O -= tz;
         if (ly == 1) B += oxy; else if (ly == -1) B -= oxy;
         if (lz == 1) B += oxz; else if (lz == -1) B -= oxz;
-        const float v0 = E + O;
+        float v0 = E + O;
         const float v1 = v0 + dxx;
+        float vp = v1 + B, vm = v1 - B;
+        if constexpr (EQ3) {   // c.u = cx u_x + b on this line
+            float b = 0.0f;
+            if (ly == 1) b += u3y; else if (ly == -1) b -= u3y;
+            if (lz == 1) b += u3z; else if (lz == -1) b -= u3z;
+            const float cp = b + u3x, cm = b - u3x;
+            v0 += k3 * b * (b * b - uu3);
+            vp += k3 * cp * (cp * cp - uu3);
+            vm += k3 * cm * (cm * cm - uu3);
+        }
         S::emit(Go + (size_t)(3 * l + 1) * F.nslot + slot, v0, 3 * l + 1);   // cx = 0
-        S::emit(Go + (size_t)(3 * l + 2) * F.nslot + slot, v1 + B, 3 * l + 2); // cx = +1
-        S::emit(Go + (size_t)(3 * l) * F.nslot + slot, v1 - B, 3 * l);        // cx = -1
+        S::emit(Go + (size_t)(3 * l + 2) * F.nslot + slot, vp, 3 * l + 2);   // cx = +1
+        S::emit(Go + (size_t)(3 * l) * F.nslot + slot, vm, 3 * l);           // cx = -1
     }
     return drout;
 }
@@ -393,7 +415,7 @@ __device__ __forceinline__ float block_sum_f32(float v, float* wsum) {
 }
 
 // Plain variant: one thread per slot, direct loads.
-template <class S>
+template <class S, bool EQ3 = false>
 __global__ void __launch_bounds__(K1_THREADS)
 k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __restrict__ gout,
                  const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, int n_envs,
@@ -421,7 +443,8 @@ k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __res
             const uint32_t p = (uint32_t)((int)c + sx + (sy + sz * E.n[1]) * E.P);
             const PullOffsets o = pull_offsets(E, px, py, pz);
             const Moments m = pull_moments<S, true>(gin + E.pop_off, E.nslot, p, o);
-            drout = update_cell<S>(load_consts(E, frames[e]), m, x, y, z, sx, sy, sz, fx, fy, fz, gout + E.pop_off, c);
+            drout = update_cell<S, EQ3>(load_consts(E, frames[e]), m, x, y, z, sx, sy, sz, fx, fy, fz,
+                                        gout + E.pop_off, c);
         }
     }
     const float t = block_sum_f32(drout, wsum);
@@ -478,7 +501,7 @@ struct EnvRegs {
     int group0, rpg, rows;
 };
 
-template <class S, int GC, int MINB>
+template <class S, int GC, int MINB, bool EQ3 = false>
 __global__ void __launch_bounds__(K1_THREADS, MINB)
 k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw* __restrict__ gout,
                         const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, int n_envs,
@@ -570,7 +593,7 @@ k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw
             }
             Moments m = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             accumulate<true>(m, gv);
-            drsum += update_cell<S>(C, m, x, y, z, sx, sy, sz, fx, fy, fz, gout + R.pop_off, slot);
+            drsum += update_cell<S, EQ3>(C, m, x, y, z, sx, sy, sz, fx, fy, fz, gout + R.pop_off, slot);
         }
 #pragma unroll
         for (int s = 16; s >= 1; s >>= 1) drsum += __shfl_xor_sync(0xffffffffu, drsum, s);

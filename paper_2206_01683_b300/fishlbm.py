@@ -46,7 +46,8 @@ class fg_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("layout", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("ib_iters", ctypes.c_int),
                 ("record_history", ctypes.c_int), ("kernel_variant", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("ib_slip", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("ib_slip", ctypes.c_int), ("eq_order", ctypes.c_int),
+                ("use_graphs", ctypes.c_int)]
 
 
 class fg_frame(ctypes.Structure):
@@ -220,7 +221,7 @@ class Domain:
     """Owns one fg_domain (one or many environments)."""
 
     def __init__(self, envs, storage="f32", record_history=0, stream=None, variant="auto",
-                 graphs=True, autotune=False, ib_iters=1, deterministic=False, slip=False):
+                 graphs=True, autotune=False, ib_iters=1, deterministic=False, slip=False, eq_order=2):
         self.envs = list(envs)
         opt = fg_options()
         opt.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
@@ -230,6 +231,7 @@ class Domain:
         opt.record_history = int(record_history)
         opt.kernel_variant = VARIANT[variant] if isinstance(variant, str) else int(variant)
         opt.ib_slip = 1 if slip else 0
+        opt.eq_order = int(eq_order)
         opt.use_graphs = 1 if graphs else 0
         opt.autotune = 1 if autotune else 0
         self.storage = opt.storage

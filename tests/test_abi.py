@@ -38,7 +38,7 @@ def test_binding_signatures_match_header():
 def test_struct_layouts():
     assert ctypes.sizeof(fishlbm.fg_env_desc) == 4 * 3 + 4 + 8 + 4 * 6 + 8 * 3 + 8 + 8 * 3
     assert ctypes.sizeof(fishlbm.fg_frame) == 12 * 8
-    assert ctypes.sizeof(fishlbm.fg_options) == 9 * 4
+    assert ctypes.sizeof(fishlbm.fg_options) == 10 * 4
 
 
 def test_lattice_is_d3q27():
@@ -54,6 +54,7 @@ def test_ib_iters_out_of_range_is_rejected_before_gpu_work():
         opt = fishlbm.fg_options()
         opt.storage = 0
         opt.ib_iters = m
+        opt.eq_order = 2
         opt.use_graphs = 1
         try:
             fishlbm.fg_create_domain([env], opt)

@@ -543,3 +543,56 @@ def test_set_markers_all_equals_per_environment_updates():
         assert np.array_equal(a.get_body_force_torque(e), b.get_body_force_torque(e))
     with pytest.raises(fishlbm.FgError):
         b.set_markers_all(Xall[:-1], Uall[:-1])             # wrong total
+
+
+@pytest.mark.parametrize("variant", ["plain", "staged"])
+def test_third_order_equilibrium_parity(variant):
+    """eq_order = 3 against the oracle: a perturbed Taylor-Green field with a
+    uniform carrier velocity (periodic, 100 steps) and the swimmer channel
+    (open faces, moving frame, 60 steps)."""
+    shape = (32, 24, 8)
+    rho, u = inputs.taylor_green(shape, (0, 1), U0=0.02)
+    r2, u2 = inputs.random_fields(shape, seed=13, u_amp=0.01, rho_amp=0.005)
+    p = Pair(shape, 0.56, variant=variant, eq_order=3)
+    p.init(rho + r2 - 1.0, u + u2 + np.array([0.05, -0.03, 0.02]))
+    for _ in range(100):
+        p.step(record=False)
+    assert_parity(p.errors(), keys=("rho", "u", "pop"))
+    fish = inputs.fish_for_grid((96, 48, 48), 24.0, 900)
+    traj = inputs.FrameTrajectory(inputs.seed_for(2), inputs.domain_centre((96, 48, 48)))
+    p = Pair((96, 48, 48), 0.52, faces=OPEN_X, u_in=(0.02, 0.0, 0.0), variant=variant, eq_order=3)
+    p.init(None, np.tile([0.02, 0.0, 0.0], (p.o.ncell, 1)))
+    for n in range(60):
+        X, U = fish.pose(n)
+        p.markers(X, U, fish.dV, seg=fish.seg, nseg=5, ref=fish.joints_rest[0])
+        p.step(traj.at(n))
+    assert_parity(p.errors(), keys=("rho", "u", "pop", "force", "torque", "seg_force"))
+
+
+def test_third_order_equilibrium_galilean_shear_on_gpu():
+    """The advected shear wave of the oracle pin, on the GPU: with eq_order = 3
+    the decay rate at U0 = 0.1 equals the one at rest; with 2 it drops by
+    about 3 U0^2."""
+    L, tau, steps = 64, 0.8, 400
+
+    def rate(order, U0):
+        d = fishlbm.Domain([fishlbm.env_desc((L, 4, 4), tau)], eq_order=order)
+        n = L * 16
+        x = np.tile(np.arange(L), 16).astype(float)
+        u = np.zeros((n, 3))
+        u[:, 0] = U0
+        u[:, 1] = 1e-3 * np.sin(2 * math.pi * x / L)
+        d.init_fields(np.ones(n), u)
+
+        def amp():
+            _, uu = d.fields()
+            return abs(np.fft.rfft(uu[:, 1].reshape(4, 4, L).mean(axis=(0, 1)))[1])
+
+        a0 = amp()
+        d.step(steps)
+        nu, k = (tau - 0.5) / 3.0, 2 * math.pi / L
+        return -math.log(amp() / a0) / steps / (nu * k * k)
+
+    r0 = rate(3, 0.0)
+    assert abs(rate(3, 0.1) - r0) < 2e-4 * r0
+    assert abs((rate(2, 0.1) - r0) / (-0.03) - 1.0) < 0.15
