@@ -42,6 +42,9 @@ NCU_TRAFFIC = {
 }
 
 
+NOMINAL_HBM_GBS = 8000.0   # B300 HBM3e, nominal (context only; the fraction that counts is of measured)
+
+
 def kernel_source_hash():
     """sha256 over the sources the stream-collide kernel is compiled from."""
     h = hashlib.sha256()
@@ -512,6 +515,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": "k_stream_collide", "achieved": round(achieved, 1),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
+                     "nominal_peak": NOMINAL_HBM_GBS, "frac_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                      "traffic": (round(bpc * ncell) if bpc else None),
                      "algorithmic_bytes": int(algo_bytes),
                      "kernel_ms": round(k1_ms, 5), "ib_ms": round(ib_ms, 5),
@@ -551,13 +555,19 @@ def oracle_steps(shape, tau, u_in, fish, X, U, frames, steps):
 
 
 def cpu_baseline(fish, X, U, frames, shape, tau, u_in, steps):
+    import oracle
     ncell = shape[0] * shape[1] * shape[2]
+    cores = oracle.set_threads(0)
     times = oracle_steps(shape, tau, u_in, fish, X, U, frames, steps)
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    oracle.set_threads(1)
+    t1 = oracle_steps(shape, tau, u_in, fish, X, U, frames, 1)
+    oracle.set_threads(cores)
     return {"value": round(ncell * steps / sum(times) / 1e6, 3), "unit": "MLUPS", "cores": cores,
             "kind": "oracle",
             "sample": "%d steps of the full %dx%dx%d swimmer channel (FP64 C oracle, OpenMP)"
-                      % (steps, *shape)}
+                      % (steps, *shape),
+            "single_thread": {"value": round(ncell / t1[0] / 1e6, 3), "unit": "MLUPS", "cores": 1,
+                              "sample": "1 step of the same channel"}}
 
 
 def run_reference(args):

@@ -53,6 +53,8 @@ def lib():
         L.orc_set_eq_order.restype = i
         L.orc_set_eq_order.argtypes = [vp, i]
         L.orc_frame_accel.argtypes = [P(d), d, d, d, P(d)]
+        L.orc_set_threads.restype = i
+        L.orc_set_threads.argtypes = [i]
         L.orc_set_ib_iters.restype = i
         L.orc_set_ib_iters.argtypes = [vp, i]
         L.orc_region_momentum.argtypes = [vp, P(d), d, P(d), P(d)]
@@ -77,6 +79,11 @@ def _f64(a, shape=None):
     if shape is not None:
         a = a.reshape(shape)
     return a
+
+
+def set_threads(n):
+    """OpenMP threads of the oracle's loops (0: keep); returns the count in use."""
+    return lib().orc_set_threads(int(n))
 
 
 def lattice():

@@ -34,6 +34,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define Q 27
 #define CS2 (1.0 / 3.0)
@@ -60,6 +63,18 @@ static void lattice_init(void) {
                         ++n;
                     }
     lattice_ready = 1;
+}
+
+/* Threads of the OpenMP loops (timing only; results do not depend on it
+ * except for the summation order of the mass).  Returns the count in use. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 void orc_lattice(int *c, double *w) {
