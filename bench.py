@@ -396,7 +396,7 @@ def run_ours(args):
     fr = [fishlbm.frame_from_array(f) for f in frames]
     stream = torch.cuda.Stream()
     dom = fishlbm.Domain([fishlbm.env_desc(shape, tau, OPEN_X, (u_in, 0, 0), 1.0, (u_in, 0, 0))],
-                         stream=stream.cuda_stream, **_variant_kw(args))
+                         stream=stream.cuda_stream, storage=args.storage, **_variant_kw(args))
     Xd = torch.from_numpy(X).cuda()
     Ud = torch.from_numpy(U).cuda()
     dVd = torch.from_numpy(fish.dV.astype(np.float32)).cuda()
@@ -488,7 +488,7 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return None
     achieved = algo_bytes / (k1_ms * 1e-3) / 1e9
-    bpc = NCU_TRAFFIC.get(kernel_source_hash())
+    bpc = NCU_TRAFFIC.get(kernel_source_hash()) if args.storage == "f32" else None
     mlups = world * ncell * K / (ms * 1e-3) / 1e6
     h2d = 2 * X[0].nbytes + 64   # X, U and the frame
     d2h = out.nbytes
@@ -507,7 +507,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": "swimmer_channel_256x128x128", "grid": list(shape), "tau": tau,
                    "faces": "inlet -x (u=0.02), outflow +x, free-slip y/z",
-                   "markers": int(X.shape[1]), "segments": 5, "storage": "f32",
+                   "markers": int(X.shape[1]), "segments": 5, "storage": args.storage,
                    "frame": "seeded accelerating + rotating (Eq. 3)",
                    "l2": "inputs exceed L2 (populations 453 MB per buffer, 2 buffers)",
                    "parallelism": "replicas" if world > 1 else "single",
@@ -618,6 +618,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16/batched forms")
     ap.add_argument("--form-steps", type=int, default=50)
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="population storage of the main workload (f32 is the headline; the others for profiling)")
     ap.add_argument("--variant", default="autotune", choices=["autotune", "plain", "staged", "staged512"],
                     help="stream-collide kernel: autotuned at creation (default) or fixed")
     args = ap.parse_args()

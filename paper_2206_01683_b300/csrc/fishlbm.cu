@@ -78,6 +78,13 @@ constexpr int MAX_STAGED_P = 512;   // longest row pitch the staged kernel takes
 // population in shared memory (compiled for 4 and 2 resident blocks per SM).
 enum { K1_PLAIN = 0, K1_STAGED256 = 1, K1_STAGED512 = 2, K1_NVARIANTS = 3 };
 
+// Blocks per SM the 512-slot staged kernel is compiled for: its row buffers
+// take 2 x 27 x 512 x sizeof(raw) bytes of shared memory, 110.6 KB in FP32
+// (two blocks fit) and 55.3 KB in FP16/BF16 (four fit, as for the 256-slot
+// kernel in FP32).
+template <class S>
+constexpr int staged512_minb() { return sizeof(typename S::raw) == 2 ? 4 : 2; }
+
 struct MarkerRegion {
     int n = 0, cap = 0, off = 0, nseg = 1;
     bool has_dv = false;
@@ -348,7 +355,7 @@ void enqueue_k1_order(fg_domain* d, const typename S::raw* gin, typename S::raw*
             gin, gout, d->d_env, d->d_frame, d->n_envs, d->total_groups, d->fib, d->stamps, d->d_state,
             d->mass_part, d->status);
     } else if (d->k1 == K1_STAGED512) {
-        k_stream_collide_staged<S, 512, 2, EQ3><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
+        k_stream_collide_staged<S, 512, staged512_minb<S>(), EQ3><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
             gin, gout, d->d_env, d->d_frame, d->n_envs, d->total_groups, d->fib, d->stamps, d->d_state,
             d->mass_part, d->status);
     } else {
@@ -539,7 +546,7 @@ fg_status configure_k1(fg_domain* d, int v, bool allocate) {
         fg_status st = dispatch(d->opt.storage, [&](auto tag) -> fg_status {
             typedef decltype(tag) S;
             return v == K1_STAGED256 ? staged_occupancy<S, 256, 4>(d, &per_sm)
-                                     : staged_occupancy<S, 512, 2>(d, &per_sm);
+                                     : staged_occupancy<S, 512, staged512_minb<S>()>(d, &per_sm);
         });
         if (st != FG_OK) return st;
         if (per_sm < 1) return fail(FG_ERR_INVALID, "staged kernel does not fit on an SM");

@@ -26,7 +26,7 @@ TOL = {"f16": 2e-3, "bf16": 5e-2}
 OPEN_X = (1, 2, 3, 3, 3, 3)
 
 
-@pytest.mark.parametrize("variant", ["plain", "staged"])
+@pytest.mark.parametrize("variant", ["plain", "staged", "staged512"])
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 def test_sphere_box_reduced_storage(storage, variant):
     cfg = inputs.SPHERE_BOX
