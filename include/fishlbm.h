@@ -146,6 +146,18 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
                          const float* dV, const int* seg, int n_seg, const double ref[3],
                          int device_ptrs);
 
+/* Failure-detection self test of the library's bounded device waits (the
+ * mbarrier waits of the staged stream-collide kernel and the grid barrier of
+ * the IB kernel), run on conditions that never come: an mbarrier nobody
+ * arrives on and a grid barrier whose target is never reached.  Each wait
+ * gives up after `limit` polls (the step kernels use 2^22) and reports
+ * instead of hanging or trapping: result[0] = 1 if the mbarrier wait gave up,
+ * result[1] = 1 if the grid barrier gave up, result[2] = 1 if the timeout bit
+ * was set in the status word.  Runs on the current device, allocates and
+ * frees its own 12 bytes, synchronises; the context stays usable.  The paper
+ * has no counterpart. */
+fg_status fg_selftest_waits(unsigned int limit, int* result);
+
 /* New positions and velocities for the markers of all environments at once
  * (the per-step update of a batch): X, U float [n][3], environment after
  * environment in the counts of each environment's last fg_set_markers, n their

@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/fishlbm.h"
 #include "step_kernels.cuh"
 #include "adjoint_kernels.cuh"
@@ -49,6 +51,17 @@ __global__ void k_copy_markers(float* __restrict__ X, float* __restrict__ U, con
         else U[i - count] = Us[i - count];
     }
 }
+
+namespace {
+
+// NVTX range over a C-ABI call (named in profiler timelines; free when no
+// tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
+}  // namespace
 
 namespace {
 
@@ -843,6 +856,7 @@ fg_status fg_init_fields(fg_domain* d, int env, const double* rho, const double*
 
 fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const float* U, const float* dV,
                          const int* seg, int n_seg, const double ref[3], int device_ptrs) {
+    NvtxRange nvtx_range("fg_set_markers");
     fg_status st = check_env(d, env);
     if (st != FG_OK) return st;
     if (n < 0) return fail(FG_ERR_INVALID, "negative marker count");
@@ -906,6 +920,7 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
 
 fg_status fg_region_momentum(fg_domain* d, int env, const double* center, double radius, double* out,
                              double* alpha_sum) {
+    NvtxRange nvtx_range("fg_region_momentum");
     fg_status st = check_env(d, env);
     if (st != FG_OK) return st;
     if (!center || !out) return fail(FG_ERR_INVALID, "null argument");
@@ -972,7 +987,40 @@ fg_status fg_set_segment_refs(fg_domain* d, int env, int n_seg, const double* re
     return upload_seg_refs(d);
 }
 
+fg_status fg_selftest_waits(unsigned int limit, int* result) {
+    if (!result) return fail(FG_ERR_INVALID, "null result");
+    if (limit == 0) return fail(FG_ERR_INVALID, "limit must be positive");
+    unsigned* bar = nullptr;
+    int *out = nullptr, *status = nullptr;
+    fg_status st = dalloc(&bar, 1);
+    if (st == FG_OK) st = dalloc(&out, 2);
+    if (st == FG_OK) st = dalloc(&status, 1);
+    cudaError_t e = cudaSuccess;
+    if (st == FG_OK) {
+        e = cudaMemset(bar, 0, sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemset(out, 0, 2 * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(status, 0, sizeof(int));
+        if (e == cudaSuccess) {
+            k_selftest_waits<<<1, 64>>>(bar, limit, out, status);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        int h[3] = {0, 0, 0};
+        if (e == cudaSuccess) e = cudaMemcpy(h, out, 2 * sizeof(int), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(h + 2, status, sizeof(int), cudaMemcpyDeviceToHost);
+        result[0] = h[0];
+        result[1] = h[1];
+        result[2] = (h[2] & ST_TIMEOUT) ? 1 : 0;
+        if (e != cudaSuccess) st = cuda_fail(e, "k_selftest_waits");
+    }
+    if (bar) cudaFree(bar);
+    if (out) cudaFree(out);
+    if (status) cudaFree(status);
+    return st;
+}
+
 fg_status fg_set_markers_all(fg_domain* d, int n, const float* X, const float* U, int device_ptrs) {
+    NvtxRange nvtx_range("fg_set_markers_all");
     if (!d) return fail(FG_ERR_INVALID, "null domain");
     if (n != d->total_markers) return fail(FG_ERR_INVALID, "n must equal the markers of all environments");
     if (n == 0) return FG_OK;
@@ -1039,6 +1087,7 @@ static fg_status note_stamp_advance(fg_domain* d) {
 }
 
 fg_status fg_step(fg_domain* d, int n_steps, const fg_frame* frames) {
+    NvtxRange nvtx_range("fg_step");
     if (!d) return fail(FG_ERR_INVALID, "null domain");
     if (n_steps < 0) return fail(FG_ERR_INVALID, "negative step count");
     if (d->poisoned) return fail(FG_ERR_STATE, "domain poisoned by a numeric fault; call fg_init_fields");
@@ -1096,6 +1145,7 @@ static fg_status status_to_error(fg_domain* d) {
 }
 
 fg_status fg_get_body_force_torque(fg_domain* d, int env, double* out) {
+    NvtxRange nvtx_range("fg_get_body_force_torque");
     fg_status st = check_env(d, env);
     if (st != FG_OK) return st;
     if (!out) return fail(FG_ERR_INVALID, "null output");
@@ -1337,6 +1387,7 @@ fg_status fg_adjoint_reset(fg_domain* d) {
 }
 
 fg_status fg_adjoint_step(fg_domain* d, const fg_frame* frames, const double* gF, float* gX, float* gU) {
+    NvtxRange nvtx_range("fg_adjoint_step");
     fg_status st = adjoint_check(d);
     if (st != FG_OK) return st;
     const int n = d->mk[0].n;
@@ -1424,6 +1475,7 @@ fg_status fg_copy_state(fg_domain* d, int env, void* buf, int to_buf) {
 }
 
 fg_status fg_autotune(fg_domain* d, int* choice, double* ms) {
+    NvtxRange nvtx_range("fg_autotune");
     if (!d) return fail(FG_ERR_INVALID, "null domain");
     if (d->poisoned) return fail(FG_ERR_STATE, "domain poisoned by a numeric fault; call fg_init_fields");
     CK(cudaStreamSynchronize(d->stream));

@@ -180,7 +180,8 @@ __device__ __forceinline__ void red_add_release_gpu(unsigned* p, unsigned v) {
 // acquire loads.  Polls are bounded: a block that gives up records
 // ST_TIMEOUT and returns false; the host then poisons the domain and zeroes
 // both words.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned base, unsigned k, int* status) {
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned base, unsigned k, int* status,
+                                             uint32_t limit = GRID_WAIT_LIMIT) {
     __shared__ int pass;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -189,7 +190,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned base, unsig
         red_add_release_gpu(bar, 1u);
         uint32_t i = 0;
         while ((int)(ld_acquire_gpu(bar) - target) < 0) {
-            if (++i == GRID_WAIT_LIMIT) {
+            if (++i == limit) {
                 ok = 0;
                 atomicOr(status, ST_TIMEOUT);
                 break;
@@ -525,6 +526,25 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
             }
         }
     }
+}
+
+// Failure-detection self test of the bounded waits above, on conditions
+// that never come: (1) an mbarrier that expects one arrival nobody makes,
+// (2) the grid barrier with a target the counter never reaches.  Each wait
+// gives up after `limit` polls; out[0], out[1] = 1 when wait (1), (2) gave up.
+// One block; no copy is in flight and nothing is left waiting.
+static __global__ void k_selftest_waits(unsigned* bar, uint32_t limit, int* out, int* status) {
+    __shared__ __align__(8) uint64_t mb;
+    if (threadIdx.x == 0) {
+        mbar_init(&mb, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) out[0] = mbar_wait_bounded(&mb, 0, limit) ? 0 : 1;
+    __syncthreads();
+    const unsigned unreachable = __ldcg(bar) + (1u << 30);   // base far beyond any arrival
+    const bool passed = grid_barrier(bar, unreachable, 1, status, limit);
+    if (threadIdx.x == 0) out[1] = passed ? 0 : 1;
 }
 
 }  // namespace fl

@@ -64,6 +64,7 @@ SIGNATURES = {
     "fg_set_marker_normals": (_I, [_V, _I, _I, _V, _I]),
     "fg_set_segment_refs": (_I, [_V, _I, _I, _P(_D)]),
     "fg_set_markers_all": (_I, [_V, _I, _V, _V, _I]),
+    "fg_selftest_waits": (_I, [ctypes.c_uint, _P(_I)]),
     "fg_region_momentum": (_I, [_V, _I, _P(_D), _D, _P(_D), _P(_D)]),
     "fg_step": (_I, [_V, _I, _P(fg_frame)]),
     "fg_get_body_force_torque": (_I, [_V, _I, _P(_D)]),
@@ -215,6 +216,14 @@ def _ptr_and_keep(a, dtype):
         return _V(a.data_ptr()), bool(a.is_cuda), a
     arr = np.ascontiguousarray(a, dtype=dtype)
     return arr.ctypes.data_as(_V), False, arr
+
+
+def selftest_waits(limit=4096):
+    """Run the bounded device waits on conditions that never come; returns
+    (mbarrier wait gave up, grid barrier gave up, status timeout bit)."""
+    out = (_I * 3)()
+    _check(lib().fg_selftest_waits(int(limit), out))
+    return bool(out[0]), bool(out[1]), bool(out[2])
 
 
 class Domain:
