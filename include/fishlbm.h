@@ -146,6 +146,15 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
                          const float* dV, const int* seg, int n_seg, const double ref[3],
                          int device_ptrs);
 
+/* Index-check flags of a debug build (libfishlbm_debug.so, compiled with
+ * -DFG_DEBUG_BOUNDS): bit set = some kernel computed an index outside its
+ * array and skipped the access (1 pulled population, 2 emitted slot, 4 staged
+ * bulk copy, 8 staged-row read, 16 IB stencil node, 32 reduction chunk,
+ * 64 region cell).  reset != 0 clears them after reading.  Synchronises the
+ * device.  A release build reports FG_ERR_STATE.  The paper has no
+ * counterpart. */
+fg_status fg_debug_flags(unsigned int* flags, int reset);
+
 /* Failure-detection self test of the library's bounded device waits (the
  * mbarrier waits of the staged stream-collide kernel and the grid barrier of
  * the IB kernel), run on conditions that never come: an mbarrier nobody

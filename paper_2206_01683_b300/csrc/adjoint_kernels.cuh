@@ -216,7 +216,7 @@ k_adj_ib(const float* __restrict__ f, const EnvDev* __restrict__ envs, const Fra
     // per-lane partial sums
     float R = 0.f, Ut[3] = {0.f, 0.f, 0.f}, Lf[3] = {0.f, 0.f, 0.f};
     float Dr[3] = {0.f, 0.f, 0.f}, Du[3][3] = {{0.f}}, Dl[3][3] = {{0.f}};
-    float dlt[2], rho_n[2], ut_n[2][3], grad_n[2][3];
+    float dlt[2];
     uint32_t cell[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -245,11 +245,8 @@ k_adj_ib(const float* __restrict__ f, const EnvDev* __restrict__ envs, const Fra
                 Du[b][a] += gd[a] * ut[b];   // sum grad_a(delta) u~_b
                 Dl[b][a] += gd[a] * lf[b];   // sum grad_a(delta) lfib_b
             }
-            grad_n[h][a] = gd[a];
-            ut_n[h][a] = ut[a];
         }
         dlt[h] = d;
-        rho_n[h] = rho;
         cell[h] = c;
     }
     // warp sums (all lanes end with the totals)

@@ -987,6 +987,23 @@ fg_status fg_set_segment_refs(fg_domain* d, int env, int n_seg, const double* re
     return upload_seg_refs(d);
 }
 
+fg_status fg_debug_flags(unsigned int* flags, int reset) {
+    if (!flags) return fail(FG_ERR_INVALID, "null flags");
+#ifdef FG_DEBUG_BOUNDS
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpyFromSymbol(flags, fl::g_debug_flags, sizeof(unsigned int)));
+    if (reset) {
+        const unsigned int zero = 0;
+        CK(cudaMemcpyToSymbol(fl::g_debug_flags, &zero, sizeof(unsigned int)));
+    }
+    return FG_OK;
+#else
+    (void)reset;
+    *flags = 0;
+    return fail(FG_ERR_STATE, "not a debug build (compile with -DFG_DEBUG_BOUNDS)");
+#endif
+}
+
 fg_status fg_selftest_waits(unsigned int limit, int* result) {
     if (!result) return fail(FG_ERR_INVALID, "null result");
     if (limit == 0) return fail(FG_ERR_INVALID, "limit must be positive");

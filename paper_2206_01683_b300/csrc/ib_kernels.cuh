@@ -229,7 +229,10 @@ __device__ __forceinline__ void ib_mark(const EnvDev& E, const Stencil& S, int h
                                         uint32_t* stamps) {
     const Column col = stencil_column(E, S, h);
 #pragma unroll
-    for (int kz = 0; kz < 4; ++kz) stamps[E.stamp_off + (column_slot(E, col, S.base[2] + kz) >> 5)] = stamp;
+    for (int kz = 0; kz < 4; ++kz) {
+        const uint32_t c = column_slot(E, col, S.base[2] + kz);
+        if (FG_IN_RANGE(DBG_NODE, c, E.nslot)) stamps[E.stamp_off + (c >> 5)] = stamp;
+    }
 }
 
 // nodes: post-stream rho and u~ of the 32 cells of tile t (one warp).
@@ -294,6 +297,10 @@ __device__ __forceinline__ ColumnNodes column_nodes(const EnvDev& E, const Marke
         const int mz = r.S.base[2] + kz;
         cn.cell[kz] = column_slot(E, col, mz);
         cn.dlt[kz] = col.wxy * peskin4(r.S.xw[2] - (float)mz);
+        if (!FG_IN_RANGE(DBG_NODE, cn.cell[kz], E.nslot)) {   // skip the node
+            cn.cell[kz] = 0;
+            cn.dlt[kz] = 0.0f;
+        }
     }
     return cn;
 }

@@ -95,6 +95,32 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t n, FastDiv f) {
     return (__umulhi(n, f.m) + n) >> f.l;
 }
 
+// Debug builds (-DFG_DEBUG_BOUNDS, libfishlbm_debug.so) check the indices
+// the kernels compute before using them: a failed check sets its bit in a
+// device flag word (read with fg_debug_flags) and the access is skipped, so
+// an indexing error is reported instead of faulting.  In release builds the
+// checks compile to nothing.
+enum {
+    DBG_PULL = 1,       // stream-collide: pulled population outside the plane
+    DBG_STORE = 2,      // stream-collide: emitted slot outside the plane
+    DBG_COPY = 4,       // staged kernel: source row or buffer range of a bulk copy
+    DBG_SMEM = 8,       // staged kernel: staged-row read outside the buffer
+    DBG_NODE = 16,      // IB: stencil node outside the plane
+    DBG_REDUCE = 32,    // reduction: chunk outside the partial buffer
+    DBG_REGION = 64     // region momentum: cell outside the plane
+};
+#ifdef FG_DEBUG_BOUNDS
+static __device__ unsigned int g_debug_flags;
+__device__ __forceinline__ bool debug_in_range(unsigned bit, long long idx, long long n) {
+    const bool ok = idx >= 0 && idx < n;
+    if (!ok) atomicOr(&g_debug_flags, bit);
+    return ok;
+}
+#define FG_IN_RANGE(bit, idx, n) ::fl::debug_in_range((bit), (long long)(idx), (long long)(n))
+#else
+#define FG_IN_RANGE(bit, idx, n) true
+#endif
+
 // Peskin's 4-point function (Peskin 2002, Acta Numerica 11, Sec. 6).
 __device__ __forceinline__ float peskin4(float r) {
     r = fabsf(r);

@@ -124,7 +124,7 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
     if (tid < ncomp) {
         Pair32 t;
         for (int i = 0; i < NW; ++i) t.add(sh[i][tid]);
-        slot[(size_t)z * 6 + tid] = t;
+        if (FG_IN_RANGE(DBG_REDUCE, z, zmax)) slot[(size_t)z * 6 + tid] = t;
         __threadfence();
     }
     __syncthreads();
@@ -240,6 +240,7 @@ k_region_momentum(const typename S::raw* __restrict__ g, const EnvDev* __restric
         const float al = fminf(R + 0.5f - sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]), 1.0f);
         if (al <= 0.0f) continue;
         const uint32_t slot = (uint32_t)p[0] + (uint32_t)E.P * ((uint32_t)p[1] + (uint32_t)E.n[1] * (uint32_t)p[2]);
+        if (!FG_IN_RANGE(DBG_REGION, slot, E.nslot)) continue;
         float j[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int i = 0; i < Q; ++i) {

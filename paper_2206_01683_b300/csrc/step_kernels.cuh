@@ -195,8 +195,10 @@ __device__ __forceinline__ Moments pull_moments(const typename S::raw* __restric
     Moments m = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float g[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-        g[i] = S::load(G + (size_t)i * nslot + (uint32_t)((int)p + pull_off(o, i)), i);
+    for (int i = 0; i < Q; ++i) {
+        const int idx = (int)p + pull_off(o, i);
+        g[i] = FG_IN_RANGE(DBG_PULL, idx, nslot) ? S::load(G + (size_t)i * nslot + (uint32_t)idx, i) : 0.0f;
+    }
     accumulate<SECOND>(m, g);
     return m;
 }
@@ -374,9 +376,11 @@ __device__ __forceinline__ float update_cell(const CellConsts& F, const Moments&
             vp += k3 * cp * (cp * cp - uu3);
             vm += k3 * cm * (cm * cm - uu3);
         }
-        S::emit(Go + (size_t)(3 * l + 1) * F.nslot + slot, v0, 3 * l + 1);   // cx = 0
-        S::emit(Go + (size_t)(3 * l + 2) * F.nslot + slot, vp, 3 * l + 2);   // cx = +1
-        S::emit(Go + (size_t)(3 * l) * F.nslot + slot, vm, 3 * l);           // cx = -1
+        if (FG_IN_RANGE(DBG_STORE, slot, F.nslot)) {
+            S::emit(Go + (size_t)(3 * l + 1) * F.nslot + slot, v0, 3 * l + 1);   // cx = 0
+            S::emit(Go + (size_t)(3 * l + 2) * F.nslot + slot, vp, 3 * l + 2);   // cx = +1
+            S::emit(Go + (size_t)(3 * l) * F.nslot + slot, vm, 3 * l);           // cx = -1
+        }
     }
     return drout;
 }
@@ -485,7 +489,10 @@ __device__ __forceinline__ void issue_group(const EnvDev& E, int g_local, const 
         zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
         const raw* src = G + (size_t)i * E.nslot + (size_t)(ys + ny * zs) * E.P;
         raw* dst = buf + (size_t)i * GC + (size_t)r * E.P;
-        bulk_g2s(dst, src, row_bytes, bar);
+        // (a skipped copy leaves the group's barrier short: its wait gives up)
+        if (FG_IN_RANGE(DBG_COPY, ys, ny) && FG_IN_RANGE(DBG_COPY, zs, nz) &&
+            FG_IN_RANGE(DBG_COPY, (r + 1) * E.P - 1, GC))
+            bulk_g2s(dst, src, row_bytes, bar);
     }
 }
 
@@ -589,7 +596,7 @@ k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const int xi = cx(i) == 1 ? xm : (cx(i) == -1 ? xp : xs);
-                gv[i] = S::decode(rb[i * GC + xi], i);
+                gv[i] = FG_IN_RANGE(DBG_SMEM, r * R.P + xi, GC) ? S::decode(rb[i * GC + xi], i) : 0.0f;
             }
             Moments m = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             accumulate<true>(m, gv);

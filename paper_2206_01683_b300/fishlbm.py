@@ -14,7 +14,8 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libfishlbm.so")
+# FISHLBM_LIB selects another build of the library (the debug build in tests)
+LIB_PATH = os.environ.get("FISHLBM_LIB") or os.path.join(HERE, "libfishlbm.so")
 
 FG_OK, FG_ERR_INVALID, FG_ERR_CUDA, FG_ERR_OOM = 0, -1, -2, -3
 FG_ERR_TIMEOUT, FG_ERR_NUMERIC, FG_ERR_STATE = -4, -5, -6
@@ -65,6 +66,7 @@ SIGNATURES = {
     "fg_set_segment_refs": (_I, [_V, _I, _I, _P(_D)]),
     "fg_set_markers_all": (_I, [_V, _I, _V, _V, _I]),
     "fg_selftest_waits": (_I, [ctypes.c_uint, _P(_I)]),
+    "fg_debug_flags": (_I, [_P(ctypes.c_uint), _I]),
     "fg_region_momentum": (_I, [_V, _I, _P(_D), _D, _P(_D), _P(_D)]),
     "fg_step": (_I, [_V, _I, _P(fg_frame)]),
     "fg_get_body_force_torque": (_I, [_V, _I, _P(_D)]),
@@ -216,6 +218,13 @@ def _ptr_and_keep(a, dtype):
         return _V(a.data_ptr()), bool(a.is_cuda), a
     arr = np.ascontiguousarray(a, dtype=dtype)
     return arr.ctypes.data_as(_V), False, arr
+
+
+def debug_flags(reset=True):
+    """Index-check flags of the debug build (see fg_debug_flags)."""
+    f = ctypes.c_uint()
+    _check(lib().fg_debug_flags(ctypes.byref(f), 1 if reset else 0))
+    return f.value
 
 
 def selftest_waits(limit=4096):
