@@ -854,6 +854,39 @@ fg_status fg_init_fields(fg_domain* d, int env, const double* rho, const double*
     return FG_OK;
 }
 
+// Host checks of marker positions and velocities: |x| <= 1e6 and finite,
+// 2 <= x < n - 3 along non-periodic axes, finite velocities.  The bulk check
+// has no early exit so that it vectorises (it runs every step for host
+// arrays); the slow pass names the first problem only when one exists.
+static bool markers_valid(const EnvDev& E, int n, const float* X, const float* U) {
+    float lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = E.per[a] ? -1.0e6f : 2.0f;
+        hi[a] = E.per[a] ? 1.0e6f : (float)E.n[a] - 3.0f;
+    }
+    int bad = 0;
+    for (int l = 0; l < n; ++l)
+        for (int a = 0; a < 3; ++a) {
+            const float x = X[3 * l + a], u = U[3 * l + a];
+            // NaN fails every comparison; +-inf fails the bounds
+            bad |= !(x >= lo[a] && x <= hi[a] && (E.per[a] || x < hi[a]));
+            bad |= !(u - u == 0.0f);
+        }
+    return bad == 0;
+}
+
+static const char* first_marker_problem(const EnvDev& E, int n, const float* X, const float* U) {
+    for (int l = 0; l < n; ++l)
+        for (int a = 0; a < 3; ++a) {
+            const float x = X[3 * l + a];
+            if (!std::isfinite(x) || std::fabs(x) > 1.0e6f) return "marker position not finite";
+            if (!E.per[a] && !(x >= 2.0f && x < (float)E.n[a] - 3.0f))
+                return "marker within 2 cells of a non-periodic face";
+            if (!std::isfinite(U[3 * l + a])) return "marker velocity not finite";
+        }
+    return "invalid marker";
+}
+
 fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const float* U, const float* dV,
                          const int* seg, int n_seg, const double ref[3], int device_ptrs) {
     NvtxRange nvtx_range("fg_set_markers");
@@ -866,15 +899,9 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
     if (n > 0 && !dV && !(r.has_dv && r.n == n))
         return fail(FG_ERR_INVALID, "dV is required when the marker count changes");
     if (!device_ptrs && n > 0) {
-        const EnvDev& E = d->env[env];
+        if (!markers_valid(d->env[env], n, X, U))
+            return fail(FG_ERR_INVALID, first_marker_problem(d->env[env], n, X, U));
         for (int l = 0; l < n; ++l) {
-            for (int a = 0; a < 3; ++a) {
-                const float x = X[3 * l + a];
-                if (!std::isfinite(x) || std::fabs(x) > 1.0e6f) return fail(FG_ERR_INVALID, "marker position not finite");
-                if (!E.per[a] && !(x >= 2.0f && x < (float)E.n[a] - 3.0f))
-                    return fail(FG_ERR_INVALID, "marker within 2 cells of a non-periodic face");
-                if (!std::isfinite(U[3 * l + a])) return fail(FG_ERR_INVALID, "marker velocity not finite");
-            }
             if (dV && !std::isfinite(dV[l])) return fail(FG_ERR_INVALID, "marker weight not finite");
             if (seg && (seg[l] < 0 || seg[l] >= n_seg)) return fail(FG_ERR_INVALID, "segment id out of range");
         }
@@ -1045,17 +1072,12 @@ fg_status fg_set_markers_all(fg_domain* d, int n, const float* X, const float* U
     const float* xs = X;
     const float* us = U;
     if (!device_ptrs) {
-        int k = 0;
+        size_t k = 0;
         for (int e = 0; e < d->n_envs; ++e) {   // the checks of fg_set_markers, environment by environment
-            const EnvDev& E = d->env[e];
-            for (int l = 0; l < d->mk[e].n; ++l, ++k)
-                for (int a = 0; a < 3; ++a) {
-                    const float x = X[3 * k + a];
-                    if (!std::isfinite(x) || std::fabs(x) > 1.0e6f) return fail(FG_ERR_INVALID, "marker position not finite");
-                    if (!E.per[a] && !(x >= 2.0f && x < (float)E.n[a] - 3.0f))
-                        return fail(FG_ERR_INVALID, "marker within 2 cells of a non-periodic face");
-                    if (!std::isfinite(U[3 * k + a])) return fail(FG_ERR_INVALID, "marker velocity not finite");
-                }
+            const int m = d->mk[e].n;
+            if (!markers_valid(d->env[e], m, X + 3 * k, U + 3 * k))
+                return fail(FG_ERR_INVALID, first_marker_problem(d->env[e], m, X + 3 * k, U + 3 * k));
+            k += m;
         }
         const size_t need = 6ull * n;
         if (d->mk_stage_cap < need) {
