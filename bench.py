@@ -249,6 +249,29 @@ def storage_form(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W,
                          "kernel_ms": round(k[1], 5), "ib_ms": round(k[0], 5)}}
 
 
+def storage_accuracy(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, steps, vkw):
+    """Velocity rel-L2 of the step with populations stored as `storage`
+    against the same steps in FP32 (same inputs, same initial state)."""
+    import torch
+    from paper_2206_01683_b300 import fishlbm
+    us = []
+    for st in ("f32", storage):
+        dom = fishlbm.Domain([fishlbm.env_desc(shape, tau, OPEN_X, (u_in, 0, 0), 1.0, (u_in, 0, 0))],
+                             storage=st, **vkw)
+        dom.set_markers(Xd[0], Ud[0], dVd, segd, n_seg=5, ref=ref)
+        for n in range(steps):
+            dom.set_markers(Xd[n], Ud[n], None, None, n_seg=5, ref=ref)
+            dom.step(1, [fr[n]])
+        torch.cuda.synchronize()
+        us.append(dom.fields()[1])
+        dom.close()
+    return float(np.linalg.norm(us[1] - us[0]) / np.linalg.norm(us[0]))
+
+
+# rel-L2 bars of u and F against the FP64 oracle (frozen in the precision tests)
+STORAGE_BAR = {"f16": 2e-3, "bf16": 5e-2}
+
+
 def school_form(W, K, world, peak, vkw):
     """Two fish in tandem in one 150x50x100 open channel (the paper's
     two-fish schooling domain), one marker set of 2 x 2500 markers with ten
@@ -530,6 +553,16 @@ def run_ours(args):
             f32={"value": line["value"], "unit": "MLUPS", "ms_per_step": line["ms_per_step"],
                  "roofline": {"achieved": line["roofline"]["achieved"], "frac": line["roofline"]["frac"],
                               "algorithmic_bytes_per_cell": 216}}, **forms)
+    if forms is not None:
+        for name, form in line["forms"].items():
+            if name != "f32" and isinstance(form, dict) and form.get("unit") == "MLUPS" and form.get("value"):
+                form["speedup_vs_f32"] = round(form["value"] / line["value"], 3)
+        na = min(60, len(fr))
+        for st in ("f16", "bf16"):
+            line["forms"][st]["accuracy"] = {
+                "u_rel_l2_vs_f32": round(storage_accuracy(st, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr,
+                                                          na, _variant_kw(args)), 8),
+                "steps": na, "bar_vs_fp64_oracle": STORAGE_BAR[st]}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(fish, X, U, frames, shape, tau, u_in, steps=args.cpu_steps)
     if world > 1:

@@ -177,6 +177,49 @@ def test_segment_refs_validation_and_reset():
     d.step(1)
 
 
+def test_maximum_segment_count_parity():
+    """16 segments (the most a marker set may have), each with its own torque
+    point: a rotating, translating sphere cut into 16 longitude sectors in the
+    periodic box, 40 steps; every segment's force and torque row against the
+    oracle."""
+    cfg = inputs.SPHERE_BOX
+    nseg = 16
+    p = Pair(cfg["shape"], cfg["tau"])
+    c0 = np.asarray(cfg["center"], dtype=np.float64)
+    X0, dV = inputs.fibonacci_sphere(cfg["n_markers"], cfg["radius"], c0)
+    phi = np.arctan2(X0[:, 1] - c0[1], X0[:, 0] - c0[0])
+    seg = np.minimum(((phi + np.pi) / (2 * np.pi) * nseg).astype(np.int32), nseg - 1)
+    assert set(seg.tolist()) == set(range(nseg))
+    om = np.array([0.0, 0.0, 4e-3])
+    v = np.asarray(cfg["velocity"], dtype=np.float64)
+    for n in range(40):
+        c = c0 + v * n
+        X = X0 - c0 + c
+        U = v + np.cross(om, X - c)
+        p.markers(X, U, dV, seg=seg, nseg=nseg, ref=tuple(c))
+        refs = np.array([c + 2.0 * np.array([np.cos(a), np.sin(a), 0.0])
+                         for a in (np.arange(nseg) + 0.5) * 2 * np.pi / nseg - np.pi])
+        p.o.set_segment_refs(f32(refs))
+        p.g.set_segment_refs(f32(refs))
+        p.step()
+    err = p.errors()
+    assert_parity(err, keys=("rho", "u", "pop", "force", "torque", "seg_force"))
+    assert p.force_hist_g[-1].shape == (nseg + 1, 6)
+
+
+def test_segment_count_and_ids_are_checked():
+    d = fishlbm.Domain([fishlbm.env_desc((16, 16, 16), 0.7)])
+    X, dV = inputs.fibonacci_sphere(40, 3.0, (8.0, 8.0, 8.0))
+    X, U, dV = np.float32(X), np.zeros((40, 3), np.float32), np.float32(dV)
+    for n_seg, seg in ((17, np.arange(40) % 17), (0, None), (4, np.full(40, 4)), (4, np.full(40, -1))):
+        with pytest.raises(fishlbm.FgError) as ei:
+            d.set_markers(X, U, dV, seg=None if seg is None else seg.astype(np.int32), n_seg=n_seg)
+        assert ei.value.status == fishlbm.FG_ERR_INVALID
+    d.set_markers(X, U, dV, seg=(np.arange(40) % 16).astype(np.int32), n_seg=16)
+    d.step(1)
+    assert d.get_body_force_torque().shape == (17, 6)
+
+
 @pytest.mark.parametrize("M", [1, 3])
 def test_slip_forcing_parity(M):
     """Slip (normal-only) forcing on the translating sphere in the periodic
