@@ -88,15 +88,20 @@ constexpr int MAX_STAGED_P = 512;   // longest row pitch the staged kernel takes
 
 // Stream-collide variants the domain can run (and the autotuner times):
 // the plain kernel, and the staged kernel with 256 or 512 slots per
-// population in shared memory (compiled for 4 and 2 resident blocks per SM).
+// population in shared memory.
 enum { K1_PLAIN = 0, K1_STAGED256 = 1, K1_STAGED512 = 2, K1_NVARIANTS = 3 };
 
-// Blocks per SM the 512-slot staged kernel is compiled for: its row buffers
+// Blocks per SM the staged kernel is compiled for.  The 512-slot row buffers
 // take 2 x 27 x 512 x sizeof(raw) bytes of shared memory, 110.6 KB in FP32
 // (two blocks fit) and 55.3 KB in FP16/BF16 (four fit, as for the 256-slot
-// kernel in FP32).
-template <class S>
-constexpr int staged512_minb() { return sizeof(typename S::raw) == 2 ? 4 : 2; }
+// kernel in FP32).  With two cells per thread the 16-bit kernels are compiled
+// for three: at four their 64 registers spill, and on the swimmer channel
+// the 512-slot kernel measured 100.3 us at three against 110.9 us at four and
+// 113.5 us at two.
+template <class S, int GC, bool PAIR>
+constexpr int staged_minb() {
+    return sizeof(typename S::raw) == 2 ? (PAIR ? 3 : 4) : (GC == 256 ? 4 : 2);
+}
 
 struct MarkerRegion {
     int n = 0, cap = 0, off = 0, nseg = 1;
@@ -142,6 +147,7 @@ struct fg_domain {
     bool staged = false;                 // k1 != K1_PLAIN
     int staged_grid = 0;                 // persistent blocks of the staged kernel
     int staged_gc = 256;                 // staged: slots per population in shared memory
+    bool staged_pair = false;            // staged: two neighbouring cells per thread
     size_t staged_smem = 0;
     size_t mass_part_cap = 0;
     int max_P = 8;
@@ -370,16 +376,26 @@ void refresh_marker_table(fg_domain* d) {
 
 // The stream-collide launch of the variant in use (gin -> gout), with the
 // equilibrium order of the domain.
+template <class S, int GC, bool EQ3>
+void enqueue_staged(fg_domain* d, const typename S::raw* gin, typename S::raw* gout, cudaStream_t s) {
+    if (d->staged_pair)
+        k_stream_collide_staged<S, GC, staged_minb<S, GC, true>(), EQ3, true>
+            <<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(gin, gout, d->d_env, d->d_frame, d->n_envs,
+                                                                d->total_groups, d->fib, d->stamps, d->d_state,
+                                                                d->mass_part, d->status);
+    else
+        k_stream_collide_staged<S, GC, staged_minb<S, GC, false>(), EQ3, false>
+            <<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(gin, gout, d->d_env, d->d_frame, d->n_envs,
+                                                                d->total_groups, d->fib, d->stamps, d->d_state,
+                                                                d->mass_part, d->status);
+}
+
 template <class S, bool EQ3>
 void enqueue_k1_order(fg_domain* d, const typename S::raw* gin, typename S::raw* gout, cudaStream_t s) {
     if (d->k1 == K1_STAGED256) {
-        k_stream_collide_staged<S, 256, 4, EQ3><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
-            gin, gout, d->d_env, d->d_frame, d->n_envs, d->total_groups, d->fib, d->stamps, d->d_state,
-            d->mass_part, d->status);
+        enqueue_staged<S, 256, EQ3>(d, gin, gout, s);
     } else if (d->k1 == K1_STAGED512) {
-        k_stream_collide_staged<S, 512, staged512_minb<S>(), EQ3><<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(
-            gin, gout, d->d_env, d->d_frame, d->n_envs, d->total_groups, d->fib, d->stamps, d->d_state,
-            d->mass_part, d->status);
+        enqueue_staged<S, 512, EQ3>(d, gin, gout, s);
     } else {
         k_stream_collide<S, EQ3><<<d->total_blocks, K1_THREADS, 0, s>>>(gin, gout, d->d_env, d->d_frame,
                                                                         d->n_envs, d->fib, d->stamps, d->d_state,
@@ -518,20 +534,26 @@ fg_status dispatch(int storage, F&& f) {
 
 
 // Shared memory, occupancy and persistent grid of the staged kernel.
-template <class S, int GC, int MINB>
-fg_status staged_occupancy(fg_domain* d, int* per_sm) {
-    // both equilibrium orders; the occupancy of the one in use
-    CK(cudaFuncSetAttribute(k_stream_collide_staged<S, GC, MINB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)d->staged_smem));
-    CK(cudaFuncSetAttribute(k_stream_collide_staged<S, GC, MINB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)d->staged_smem));
-    if (d->opt.eq_order == 3)
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_stream_collide_staged<S, GC, MINB, true>,
-                                                         K1_THREADS, d->staged_smem));
-    else
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_stream_collide_staged<S, GC, MINB, false>,
-                                                         K1_THREADS, d->staged_smem));
+template <class S, int GC, bool EQ3, bool PAIR>
+fg_status staged_occupancy_of(fg_domain* d, int* per_sm) {
+    constexpr int MINB = staged_minb<S, GC, PAIR>();
+    CK(cudaFuncSetAttribute(k_stream_collide_staged<S, GC, MINB, EQ3, PAIR>,
+                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->staged_smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_stream_collide_staged<S, GC, MINB, EQ3, PAIR>,
+                                                     K1_THREADS, d->staged_smem));
     return FG_OK;
+}
+
+// The shared-memory limit of the instantiation in use is raised and its
+// occupancy returned.
+template <class S, int GC>
+fg_status staged_occupancy(fg_domain* d, int* per_sm) {
+    const bool eq3 = d->opt.eq_order == 3;
+    if (d->staged_pair)
+        return eq3 ? staged_occupancy_of<S, GC, true, true>(d, per_sm)
+                   : staged_occupancy_of<S, GC, false, true>(d, per_sm);
+    return eq3 ? staged_occupancy_of<S, GC, true, false>(d, per_sm)
+               : staged_occupancy_of<S, GC, false, false>(d, per_sm);
 }
 
 bool k1_runnable(const fg_domain* d, int v) {
@@ -548,6 +570,14 @@ fg_status configure_k1(fg_domain* d, int v, bool allocate) {
     d->k1 = v;
     d->staged = v != K1_PLAIN;
     d->staged_gc = v == K1_STAGED512 ? 512 : 256;
+    // 16-bit storage is bound by instruction issue, not by DRAM: two cells
+    // per thread share the per-cell index work and store their outputs as
+    // 32-bit pairs (needs every row length even).  FP32 is bound by DRAM and
+    // measured no faster paired (153.6 against 154.8 us with 512 slots,
+    // slower with 256, whose 64 registers then spill).
+    d->staged_pair = d->staged && d->esize == 2;
+    for (int e = 0; e < d->n_envs; ++e)
+        if (d->env[e].n[0] % 2 != 0) d->staged_pair = false;
     int group0 = 0;
     for (int e = 0; e < d->n_envs; ++e) {
         EnvDev& E = d->env[e];
@@ -567,8 +597,8 @@ fg_status configure_k1(fg_domain* d, int v, bool allocate) {
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         fg_status st = dispatch(d->opt.storage, [&](auto tag) -> fg_status {
             typedef decltype(tag) S;
-            return v == K1_STAGED256 ? staged_occupancy<S, 256, 4>(d, &per_sm)
-                                     : staged_occupancy<S, 512, staged512_minb<S>()>(d, &per_sm);
+            return v == K1_STAGED256 ? staged_occupancy<S, 256>(d, &per_sm)
+                                     : staged_occupancy<S, 512>(d, &per_sm);
         });
         if (st != FG_OK) return st;
         if (per_sm < 1) return fail(FG_ERR_INVALID, "staged kernel does not fit on an SM");

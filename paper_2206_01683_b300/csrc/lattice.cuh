@@ -34,11 +34,16 @@ __host__ __device__ constexpr float store_scale(int i) { return (float)(4 << (2 
 // emit(v, i) stores the population whose Hermite polynomial value is v
 // (g_i = w_i v) given coefficients pre-multiplied by POLY: FP32 stores w_i v;
 // the reduced formats store s_i g_i = (32/27) v, so with POLY = 32/27 they
-// store v itself and need no per-population multiply.
+// store v itself and need no per-population multiply.  emit2 stores the
+// values of two neighbouring slots (the first at p, which is aligned to
+// twice the element size) with one access.
 struct StoreF32 {
     typedef float raw;
     static constexpr float POLY = 1.0f;
     static __device__ __forceinline__ void emit(raw* p, float v, int i) { *p = wf(i) * v; }
+    static __device__ __forceinline__ void emit2(raw* p, float a, float b, int i) {
+        *reinterpret_cast<float2*>(p) = make_float2(wf(i) * a, wf(i) * b);
+    }
     static __device__ __forceinline__ float load(const raw* p, int) { return __ldg(p); }
     static __device__ __forceinline__ void store(raw* p, float v, int) { *p = v; }
     static __device__ __forceinline__ float decode(raw v, int) { return v; }
@@ -49,6 +54,9 @@ struct StoreF16 {
     typedef __half raw;
     static constexpr float POLY = 32.0f / 27.0f;
     static __device__ __forceinline__ void emit(raw* p, float v, int) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ void emit2(raw* p, float a, float b, int) {
+        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
+    }
     static __device__ __forceinline__ float decode(raw v, int i) {
         return __half2float(v) * (1.0f / store_scale(i));
     }
@@ -63,6 +71,9 @@ struct StoreBF16 {
     typedef __nv_bfloat16 raw;
     static constexpr float POLY = 32.0f / 27.0f;
     static __device__ __forceinline__ void emit(raw* p, float v, int) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ void emit2(raw* p, float a, float b, int) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+    }
     static __device__ __forceinline__ float decode(raw v, int i) {
         return __bfloat162float(v) * (1.0f / store_scale(i));
     }

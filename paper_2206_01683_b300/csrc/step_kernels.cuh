@@ -261,18 +261,26 @@ __device__ __forceinline__ int face_kind(int bc, int face) { return (bc >> (2 * 
 
 // ------------------------------------------------ the per-cell update
 
+// Hermite coefficients of one cell's post-collision deviation, pre-multiplied
+// by S::POLY (see line_values), and rho_out - 1.
+struct Herm {
+    float A, dxx, dyy, dzz, oxy, oxz, oyz, tx, ty, tz;
+    float k3, u3x, u3y, u3z, uu3;   // third-order terms (EQ3 only)
+    float drout;
+};
+
 // Collision (interior) or open-face rule (boundary) from the pulled moments
-// m, then the Hermite-2 rebuild of all 27 outputs.  (sx, sy, sz) is the
-// inward normal of the non-periodic faces the cell lies on (0 for interior
-// cells).  EQ3 adds the third-order equilibrium terms the lattice carries,
+// m, as the coefficients of the Hermite-2 rebuild of all 27 outputs.
+// (sx, sy, sz) is the inward normal of the non-periodic faces the cell lies
+// on (0 for interior cells).  EQ3 adds the third-order equilibrium terms the
+// lattice carries,
 // w_i rho [(c.u)^3 - (c.u)|u|^2] / (2 cs2^3) = 4.5 w_i rho (c.u)((c.u)^2 - |u|^2)
 // (the Hermite sum over the index triples that are not all equal: H_aaa
 // vanishes on D3Q27), with the collision's (rho, u) inside and (rho_b, u_b)
-// on the open faces.  Returns rho_out - 1 for the mass sum.
+// on the open faces.
 template <class S, bool EQ3 = false>
-__device__ __forceinline__ float update_cell(const CellConsts& F, const Moments& m, int x, int y, int z, int sx,
-                                             int sy, int sz, float fx, float fy, float fz,
-                                             typename S::raw* __restrict__ Go, uint32_t slot) {
+__device__ __forceinline__ Herm cell_coeffs(const CellConsts& F, const Moments& m, int x, int y, int z, int sx,
+                                            int sy, int sz, float fx, float fy, float fz) {
     const float cs2 = 1.0f / 3.0f;
     const float rho = 1.0f + m.dr;
     const float inv = 1.0f / rho;
@@ -344,45 +352,86 @@ __device__ __forceinline__ float update_cell(const CellConsts& F, const Moments&
             r3 = rb; u3x = ubx; u3y = uby; u3z = ubz;
         }
     }
-    const float k3 = S::POLY * 4.5f * r3, uu3 = u3x * u3x + u3y * u3y + u3z * u3z;
-    // Hermite-2 rebuild of the deviation: g*_i = w_i [dr + 3 c.J + 4.5 c c : Q - 1.5 tr Q],
-    // organised by x-lines (cy, cz):  v(cx) = E + cx^2 dxx + O + cx B  with
-    //   E = A + cy^2 dyy + cz^2 dzz + cy cz oyz,  O = cy ty + cz tz,  B = tx + cy oxy + cz oxz.
+    Herm h;
+    h.k3 = S::POLY * 4.5f * r3;
+    h.u3x = u3x; h.u3y = u3y; h.u3z = u3z;
+    h.uu3 = u3x * u3x + u3y * u3y + u3z * u3z;
+    // Hermite-2 rebuild of the deviation: g*_i = w_i [dr + 3 c.J + 4.5 c c : Q - 1.5 tr Q]
     const float sc = S::POLY;
-    const float A = sc * (drout - 1.5f * (Qxx + Qyy + Qzz));
-    const float dxx = sc * 4.5f * Qxx, dyy = sc * 4.5f * Qyy, dzz = sc * 4.5f * Qzz;
-    const float oxy = sc * 9.0f * Qxy, oxz = sc * 9.0f * Qxz, oyz = sc * 9.0f * Qyz;
-    const float tx = sc * 3.0f * Jx, ty = sc * 3.0f * Jy, tz = sc * 3.0f * Jz;
+    h.A = sc * (drout - 1.5f * (Qxx + Qyy + Qzz));
+    h.dxx = sc * 4.5f * Qxx; h.dyy = sc * 4.5f * Qyy; h.dzz = sc * 4.5f * Qzz;
+    h.oxy = sc * 9.0f * Qxy; h.oxz = sc * 9.0f * Qxz; h.oyz = sc * 9.0f * Qyz;
+    h.tx = sc * 3.0f * Jx; h.ty = sc * 3.0f * Jy; h.tz = sc * 3.0f * Jz;
+    h.drout = drout;
+    return h;
+}
+
+// The three outputs of x-line l (cy = l % 3 - 1, cz = l / 3 - 1), organised
+// as v(cx) = E + cx^2 dxx + O + cx B with
+//   E = A + cy^2 dyy + cz^2 dzz + cy cz oyz,  O = cy ty + cz tz,  B = tx + cy oxy + cz oxz;
+// v0, vp, vm for cx = 0, +1, -1 (population 3 l + 1, 3 l + 2, 3 l).
+template <bool EQ3>
+__device__ __forceinline__ void line_values(const Herm& h, int l, float& v0, float& vp, float& vm) {
+    const int ly = l % 3 - 1, lz = l / 3 - 1;      // this line's cy, cz
+    float E = h.A, O = 0.0f, B = h.tx;
+    if (ly != 0) E += h.dyy;
+    if (lz != 0) E += h.dzz;
+    if (ly * lz == 1) E += h.oyz; else if (ly * lz == -1) E -= h.oyz;
+    if (ly == 1) O += h.ty; else if (ly == -1) O -= h.ty;
+    if (lz == 1) O += h.tz; else if (lz == -1) O -= h.tz;
+    if (ly == 1) B += h.oxy; else if (ly == -1) B -= h.oxy;
+    if (lz == 1) B += h.oxz; else if (lz == -1) B -= h.oxz;
+    v0 = E + O;
+    const float v1 = v0 + h.dxx;
+    vp = v1 + B;
+    vm = v1 - B;
+    if constexpr (EQ3) {   // c.u = cx u_x + b on this line
+        float b = 0.0f;
+        if (ly == 1) b += h.u3y; else if (ly == -1) b -= h.u3y;
+        if (lz == 1) b += h.u3z; else if (lz == -1) b -= h.u3z;
+        const float cp = b + h.u3x, cm = b - h.u3x;
+        v0 += h.k3 * b * (b * b - h.uu3);
+        vp += h.k3 * cp * (cp * cp - h.uu3);
+        vm += h.k3 * cm * (cm * cm - h.uu3);
+    }
+}
+
+// Collision and rebuild of one cell, all 27 outputs stored at slot.
+// Returns rho_out - 1 for the mass sum.
+template <class S, bool EQ3 = false>
+__device__ __forceinline__ float update_cell(const CellConsts& F, const Moments& m, int x, int y, int z, int sx,
+                                             int sy, int sz, float fx, float fy, float fz,
+                                             typename S::raw* __restrict__ Go, uint32_t slot) {
+    const Herm h = cell_coeffs<S, EQ3>(F, m, x, y, z, sx, sy, sz, fx, fy, fz);
 #pragma unroll
     for (int l = 0; l < 9; ++l) {
-        const int ly = l % 3 - 1, lz = l / 3 - 1;      // this line's cy, cz
-        float E = A, O = 0.0f, B = tx;
-        if (ly != 0) E += dyy;
-        if (lz != 0) E += dzz;
-        if (ly * lz == 1) E += oyz; else if (ly * lz == -1) E -= oyz;
-        if (ly == 1) O += ty; else if (ly == -1) O -= ty;
-        if (lz == 1) O += tz; else if (lz == -1) O -= tz;
-        if (ly == 1) B += oxy; else if (ly == -1) B -= oxy;
-        if (lz == 1) B += oxz; else if (lz == -1) B -= oxz;
-        float v0 = E + O;
-        const float v1 = v0 + dxx;
-        float vp = v1 + B, vm = v1 - B;
-        if constexpr (EQ3) {   // c.u = cx u_x + b on this line
-            float b = 0.0f;
-            if (ly == 1) b += u3y; else if (ly == -1) b -= u3y;
-            if (lz == 1) b += u3z; else if (lz == -1) b -= u3z;
-            const float cp = b + u3x, cm = b - u3x;
-            v0 += k3 * b * (b * b - uu3);
-            vp += k3 * cp * (cp * cp - uu3);
-            vm += k3 * cm * (cm * cm - uu3);
-        }
+        float v0, vp, vm;
+        line_values<EQ3>(h, l, v0, vp, vm);
         if (FG_IN_RANGE(DBG_STORE, slot, F.nslot)) {
             S::emit(Go + (size_t)(3 * l + 1) * F.nslot + slot, v0, 3 * l + 1);   // cx = 0
             S::emit(Go + (size_t)(3 * l + 2) * F.nslot + slot, vp, 3 * l + 2);   // cx = +1
             S::emit(Go + (size_t)(3 * l) * F.nslot + slot, vm, 3 * l);           // cx = -1
         }
     }
-    return drout;
+    return h.drout;
+}
+
+// The outputs of two neighbouring cells a (at an even slot) and b (slot + 1),
+// stored as pairs.
+template <class S, bool EQ3>
+__device__ __forceinline__ void emit_pair(const Herm& a, const Herm& b, typename S::raw* __restrict__ Go,
+                                          uint32_t nslot, uint32_t slot) {
+#pragma unroll
+    for (int l = 0; l < 9; ++l) {
+        float a0, ap, am, b0, bp, bm;
+        line_values<EQ3>(a, l, a0, ap, am);
+        line_values<EQ3>(b, l, b0, bp, bm);
+        if (FG_IN_RANGE(DBG_STORE, slot + 1, nslot)) {
+            S::emit2(Go + (size_t)(3 * l + 1) * nslot + slot, a0, b0, 3 * l + 1);
+            S::emit2(Go + (size_t)(3 * l + 2) * nslot + slot, ap, bp, 3 * l + 2);
+            S::emit2(Go + (size_t)(3 * l) * nslot + slot, am, bm, 3 * l);
+        }
+    }
 }
 
 // Inward normal along one axis for coordinate v (0 on periodic axes).
@@ -499,6 +548,24 @@ __device__ __forceinline__ void issue_group(const EnvDev& E, int g_local, const 
     }
 }
 
+// Moments of the cell at x of staged row r (rb: that row's first slot in
+// population 0 of the group buffer), sx its inward x normal.
+template <class S, int GC>
+__device__ __forceinline__ Moments staged_moments(const typename S::raw* rb, int r, int P, int nx, int x, int sx) {
+    const int xs = x + sx;
+    const int xm = xs == 0 ? nx - 1 : xs - 1;      // source of c_x = +1
+    const int xp = xs == nx - 1 ? 0 : xs + 1;      // source of c_x = -1
+    float gv[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int xi = cx(i) == 1 ? xm : (cx(i) == -1 ? xp : xs);
+        gv[i] = FG_IN_RANGE(DBG_SMEM, r * P + xi, GC) ? S::decode(rb[i * GC + xi], i) : 0.0f;
+    }
+    Moments m = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    accumulate<true>(m, gv);
+    return m;
+}
+
 // Environment scalars a cell update needs, held in registers while a block
 // works through groups of one environment.
 struct EnvRegs {
@@ -511,7 +578,7 @@ struct EnvRegs {
     int group0, rpg, rows;
 };
 
-template <class S, int GC, int MINB, bool EQ3 = false>
+template <class S, int GC, int MINB, bool EQ3 = false, bool PAIR = false>
 __global__ void __launch_bounds__(K1_THREADS, MINB)
 k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw* __restrict__ gout,
                         const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, int n_envs,
@@ -574,38 +641,61 @@ k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw
         const int r0 = (g - R.group0) * R.rpg;
         const int span = ok ? min(R.rpg, R.rows - r0) * R.P : 0;
         float drsum = 0.f;
-        for (int t = threadIdx.x; t < span; t += K1_THREADS) {
-            const int r = (int)fdiv((uint32_t)t, R.div_P);
-            const int x = t - r * R.P;
-            if (x >= R.nx) continue;
-            const int row = r0 + r;
-            const int z = (int)fdiv((uint32_t)row, R.div_ny);
-            const int y = row - z * R.ny;
-            const uint32_t slot = (uint32_t)row * (uint32_t)R.P + (uint32_t)x;
-            // IB force density of a stamped tile (cleared after use)
-            float fx = 0.f, fy = 0.f, fz = 0.f;
-            if (__ldg(stamps + R.stamp_off + (slot >> 5)) == stamp) {
-                float4* fb = fib + R.slot_off + slot;
-                const float4 f = *fb;
-                fx = f.x; fy = f.y; fz = f.z;
-                *fb = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (PAIR) {
+            // two neighbouring cells (x even, x + 1) per thread, outputs stored
+            // as pairs; every row length is even, so both cells are real
+            // cells, share a 32-slot tile and are never both on an x face
+            for (int t = threadIdx.x; 2 * t < span; t += K1_THREADS) {
+                const int r = (int)fdiv((uint32_t)(2 * t), R.div_P);
+                const int x = 2 * t - r * R.P;
+                if (x >= R.nx) continue;
+                const int row = r0 + r;
+                const int z = (int)fdiv((uint32_t)row, R.div_ny);
+                const int y = row - z * R.ny;
+                const uint32_t slot = (uint32_t)row * (uint32_t)R.P + (uint32_t)x;
+                float4 fa = make_float4(0.f, 0.f, 0.f, 0.f), fb2 = fa;
+                if (__ldg(stamps + R.stamp_off + (slot >> 5)) == stamp) {
+                    float4* fb = fib + R.slot_off + slot;
+                    fa = fb[0];
+                    fb2 = fb[1];
+                    fb[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    fb[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                const int sxa = R.per_x ? 0 : (x == 0 ? 1 : 0);
+                const int sxb = R.per_x ? 0 : (x + 1 == R.nx - 1 ? -1 : 0);
+                const int sy = R.per_y ? 0 : (y == 0 ? 1 : (y == R.ny - 1 ? -1 : 0));
+                const int sz = R.per_z ? 0 : (z == 0 ? 1 : (z == R.nz - 1 ? -1 : 0));
+                const raw* rb = sb + r * R.P;
+                const Herm ha = cell_coeffs<S, EQ3>(C, staged_moments<S, GC>(rb, r, R.P, R.nx, x, sxa), x, y, z,
+                                                    sxa, sy, sz, fa.x, fa.y, fa.z);
+                const Herm hb = cell_coeffs<S, EQ3>(C, staged_moments<S, GC>(rb, r, R.P, R.nx, x + 1, sxb), x + 1,
+                                                    y, z, sxb, sy, sz, fb2.x, fb2.y, fb2.z);
+                drsum += ha.drout + hb.drout;
+                emit_pair<S, EQ3>(ha, hb, gout + R.pop_off, R.nslot, slot);
             }
-            const int sx = R.per_x ? 0 : (x == 0 ? 1 : (x == R.nx - 1 ? -1 : 0));
-            const int sy = R.per_y ? 0 : (y == 0 ? 1 : (y == R.ny - 1 ? -1 : 0));
-            const int sz = R.per_z ? 0 : (z == 0 ? 1 : (z == R.nz - 1 ? -1 : 0));
-            const int xs = x + sx;
-            const int xm = xs == 0 ? R.nx - 1 : xs - 1;      // source of c_x = +1
-            const int xp = xs == R.nx - 1 ? 0 : xs + 1;      // source of c_x = -1
-            const raw* rb = sb + r * R.P;
-            float gv[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int xi = cx(i) == 1 ? xm : (cx(i) == -1 ? xp : xs);
-                gv[i] = FG_IN_RANGE(DBG_SMEM, r * R.P + xi, GC) ? S::decode(rb[i * GC + xi], i) : 0.0f;
+        } else {
+            for (int t = threadIdx.x; t < span; t += K1_THREADS) {
+                const int r = (int)fdiv((uint32_t)t, R.div_P);
+                const int x = t - r * R.P;
+                if (x >= R.nx) continue;
+                const int row = r0 + r;
+                const int z = (int)fdiv((uint32_t)row, R.div_ny);
+                const int y = row - z * R.ny;
+                const uint32_t slot = (uint32_t)row * (uint32_t)R.P + (uint32_t)x;
+                // IB force density of a stamped tile (cleared after use)
+                float fx = 0.f, fy = 0.f, fz = 0.f;
+                if (__ldg(stamps + R.stamp_off + (slot >> 5)) == stamp) {
+                    float4* fb = fib + R.slot_off + slot;
+                    const float4 f = *fb;
+                    fx = f.x; fy = f.y; fz = f.z;
+                    *fb = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                const int sx = R.per_x ? 0 : (x == 0 ? 1 : (x == R.nx - 1 ? -1 : 0));
+                const int sy = R.per_y ? 0 : (y == 0 ? 1 : (y == R.ny - 1 ? -1 : 0));
+                const int sz = R.per_z ? 0 : (z == 0 ? 1 : (z == R.nz - 1 ? -1 : 0));
+                const Moments m = staged_moments<S, GC>(sb + r * R.P, r, R.P, R.nx, x, sx);
+                drsum += update_cell<S, EQ3>(C, m, x, y, z, sx, sy, sz, fx, fy, fz, gout + R.pop_off, slot);
             }
-            Moments m = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            accumulate<true>(m, gv);
-            drsum += update_cell<S, EQ3>(C, m, x, y, z, sx, sy, sz, fx, fy, fz, gout + R.pop_off, slot);
         }
 #pragma unroll
         for (int s = 16; s >= 1; s >>= 1) drsum += __shfl_xor_sync(0xffffffffu, drsum, s);

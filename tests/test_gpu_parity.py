@@ -492,6 +492,53 @@ def test_graph_replay_matches_direct_launches():
     assert rel_l2(h0, h1) < 1e-6
 
 
+@pytest.mark.parametrize("storage", ["f16", "bf16", "f32"])
+@pytest.mark.parametrize("nx", [64, 63])
+def test_stream_collide_variants_agree(storage, nx):
+    """One cell per thread (plain kernel) and the staged kernels -- which take
+    two neighbouring cells per thread with 16-bit storage when every row
+    length is even (nx = 64), one otherwise (nx = 63) -- agree to rounding:
+    the kernels inline the same per-cell arithmetic, and the compiler's
+    choice of fused multiply-adds may differ between them (measured: FP32
+    deviations differ by at most a few 1e-9, FP16 stores in about 1e-4 of the
+    entries).  Open x faces, a moving frame, markers with the deterministic
+    spread, 12 steps."""
+    shape = (nx, 20, 18)
+    rho, u = inputs.random_fields(shape, seed=61, u_amp=0.02, rho_amp=0.01)
+    c = np.array([nx / 2.0, 10.0, 9.0])
+    X0, dV = inputs.fibonacci_sphere(150, 4.0, c)
+    frame = fishlbm.make_frame(acc=(1e-5, 2e-6, 0.0), omega=(0.0, 1e-4, 2e-4), domega=(1e-6, 0.0, 0.0),
+                               origin=tuple(c))
+    doms = [fishlbm.Domain([fishlbm.env_desc(shape, 0.56, OPEN_X, (0.02, 0, 0), 1.0, (0.02, 0, 0))],
+                           storage=storage, variant=v, deterministic=True) for v in ("plain", "staged", "staged512")]
+    for d in doms:
+        d.init_fields(rho, u)
+    for n in range(12):
+        U = np.tile([0.01, 0.003 * math.sin(0.3 * n), 0.0], (150, 1))
+        for d in doms:
+            d.set_markers(np.float32(X0 + U * n), np.float32(U), np.float32(dV))
+            d.step(1, [frame])
+    cl, w = fishlbm.fg_lattice()                   # library velocity order
+    scale = 4.0 ** (1 + (cl ** 2).sum(axis=1))     # the 16-bit stores keep s_i g_i
+    ref = doms[0].populations() - w
+    for d in doms[1:]:
+        g = d.populations() - w
+        v = d.stream_collide_variant()
+        if storage == "f32":
+            assert rel_l2(g, ref) < 1e-6 and np.abs(g - ref).max() < 1e-7, v
+        else:
+            # the stored values s_i g_i differ by at most a few units in the
+            # last place of the cell's largest stored value (a rounding of a
+            # moment moves every output of the cell), in a small fraction of
+            # the entries; one unit is 2^-10 (FP16) or 2^-7 (BF16) relative
+            ulp = 2.0 ** -10 if storage == "f16" else 2.0 ** -7
+            dh = np.abs(g - ref) * scale
+            hmax = np.abs(ref * scale).max(axis=1, keepdims=True)
+            ratio = (dh / (ulp * hmax + 2.0 ** -24)).max()
+            assert ratio <= 4.0, (v, float(ratio))
+            assert np.mean(g != ref) < 1e-2, (v, float(np.mean(g != ref)))
+
+
 def test_autotune_keeps_a_runnable_variant_and_the_state():
     """The autotuner times the candidates on the domain's own buffers without
     changing the state, keeps the fastest, and steps continue identically."""
