@@ -182,6 +182,10 @@ struct fg_domain {
         Pair32 mass;
         int status;
     }* rb = nullptr;
+    Pair32* rb_ft_all = nullptr;         // pinned: the force/torque rows of all environments
+    // device addresses of the mapped pinned copies k_reduce writes every step
+    Pair32* rb_ft_all_dev = nullptr;
+    int* rb_status_dev = nullptr;
     long long steps = 0;
     StepState* d_state = nullptr;        // stamp / step / completion count on the device
     bool poisoned = false;
@@ -271,6 +275,7 @@ void free_all(fg_domain* d) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (d->rb) cudaFreeHost(d->rb);
+    if (d->rb_ft_all) cudaFreeHost(d->rb_ft_all);
     for (int k = 0; k < FG_K_COUNT; ++k)
         for (cudaEvent_t e : d->ev[k]) cudaEventDestroy(e);
 }
@@ -443,7 +448,8 @@ fg_status enqueue_step(fg_domain* d, int parity, cudaStream_t s, cudaEvent_t* co
     if (ev) CK(cudaEventRecord(ev[FG_K_REDUCE][0], s));
     k_reduce<<<dim3(d->n_envs, RED_ROWS, d->red_z), RED_THREADS, 0, s>>>(
         d->d_env, d->X, d->Fm, d->dV, d->seg, d->seg_ref, d->mass_part, d->red_partials, d->red_counters,
-        d->n_envs, d->red_z, d->ft, d->mass, d->hist, d->opt.record_history, d->d_state, d->status);
+        d->n_envs, d->red_z, d->ft, d->mass, d->hist, d->opt.record_history, d->d_state, d->status,
+        d->rb_ft_all_dev, d->rb_status_dev);
     if (ev) CK(cudaEventRecord(ev[FG_K_REDUCE][1], s));
     CK(cudaGetLastError());
     return FG_OK;
@@ -787,9 +793,15 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     DA(d->status, 1);
 #undef DA
     {
-        const cudaError_t e = cudaHostAlloc((void**)&d->rb, sizeof(*d->rb), cudaHostAllocDefault);
+        cudaError_t e = cudaHostAlloc((void**)&d->rb, sizeof(*d->rb), cudaHostAllocMapped);
+        if (e != cudaSuccess) d->rb = nullptr;
+        if (e == cudaSuccess) {
+            e = cudaHostAlloc((void**)&d->rb_ft_all, sizeof(Pair32) * n_envs * FT_ROW, cudaHostAllocMapped);
+            if (e != cudaSuccess) d->rb_ft_all = nullptr;
+        }
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&d->rb_ft_all_dev, d->rb_ft_all, 0);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&d->rb_status_dev, &d->rb->status, 0);
         if (e != cudaSuccess) {
-            d->rb = nullptr;
             free_all(d);
             delete d;
             return cuda_fail(e, "cudaHostAlloc");
@@ -906,6 +918,18 @@ fg_status fg_init_fields(fg_domain* d, int env, const double* rho, const double*
 // 2 <= x < n - 3 along non-periodic axes, finite velocities.  The bulk check
 // has no early exit so that it vectorises (it runs every step for host
 // arrays); the slow pass names the first problem only when one exists.
+// The device address of a host pointer into pinned (page-locked, mapped)
+// memory, nullptr for pageable memory.  Kernels read such arrays directly,
+// which costs one launch instead of one copy call per array.
+static const float* mapped_device_ptr(const float* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // not a CUDA pointer: clear the error
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? static_cast<const float*>(a.devicePointer) : nullptr;
+}
+
 static bool markers_valid(const EnvDev& E, int n, const float* X, const float* U) {
     // closed bounds per axis: [-1e6, 1e6] on a periodic axis, [2, n - 3) on
     // an open one (the largest float below n - 3 as the closed upper bound)
@@ -964,10 +988,14 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
     MarkerRegion& m = d->mk[env];
     const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (n > 0) {
-        if (device_ptrs) {
+        // pinned host arrays are read by the copy kernel in place
+        const float* Xm = device_ptrs ? X : mapped_device_ptr(X);
+        const float* Um = device_ptrs ? U : (Xm ? mapped_device_ptr(U) : nullptr);
+        if (Xm && Um) {
             // one launch for both arrays (the per-step marker update)
             const int blocks = (int)std::min<long long>((6ll * n + 255) / 256, 4096);
-            k_copy_markers<<<blocks, 256, 0, d->stream>>>(d->X + 3ull * m.off, d->U + 3ull * m.off, X, U, 3 * n);
+            k_copy_markers<<<blocks, 256, 0, d->stream>>>(d->X + 3ull * m.off, d->U + 3ull * m.off, Xm, Um,
+                                                          3 * n);
             CK(cudaGetLastError());
         } else {
             CK(cudaMemcpyAsync(d->X + 3ull * m.off, X, sizeof(float) * 3 * n, kind, d->stream));
@@ -1123,6 +1151,7 @@ fg_status fg_set_markers_all(fg_domain* d, int n, const float* X, const float* U
     if (!X || !U) return fail(FG_ERR_INVALID, "null marker array");
     const float* xs = X;
     const float* us = U;
+    bool stage = false;   // pageable host arrays: copied to device scratch first
     if (!device_ptrs) {
         size_t k = 0;
         for (int e = 0; e < d->n_envs; ++e) {   // the checks of fg_set_markers, environment by environment
@@ -1131,6 +1160,23 @@ fg_status fg_set_markers_all(fg_domain* d, int n, const float* X, const float* U
                 return fail(FG_ERR_INVALID, first_marker_problem(d->env[e], m, X + 3 * k, U + 3 * k));
             k += m;
         }
+        const float* Xm = mapped_device_ptr(X);
+        const float* Um = Xm ? mapped_device_ptr(U) : nullptr;
+        if (Xm && Um) {
+            // pinned host arrays: the kernels below read them in place
+            xs = Xm;
+            us = Um;
+        } else if (d->n_envs == 1) {   // already in the compact order: copy in place
+            CK(cudaMemcpyAsync(d->X + 3ull * d->mk[0].off, X, sizeof(float) * 3 * n, cudaMemcpyHostToDevice,
+                               d->stream));
+            CK(cudaMemcpyAsync(d->U + 3ull * d->mk[0].off, U, sizeof(float) * 3 * n, cudaMemcpyHostToDevice,
+                               d->stream));
+            return FG_OK;
+        } else {
+            stage = true;
+        }
+    }
+    if (stage) {
         const size_t need = 6ull * n;
         if (d->mk_stage_cap < need) {
             if (d->mk_stage) cudaFree(d->mk_stage);
@@ -1230,6 +1276,39 @@ static fg_status status_to_error(fg_domain* d, int s) {
     if (s & ST_TIMEOUT) {
         d->poisoned = true;
         return fail(FG_ERR_TIMEOUT, "a bounded device wait gave up; call fg_init_fields");
+    }
+    return FG_OK;
+}
+
+fg_status fg_step_io(fg_domain* d, const float* X, const float* U, int device_ptrs, const fg_frame* frames,
+                     double* out) {
+    NvtxRange nvtx_range("fg_step_io");
+    if (!d) return fail(FG_ERR_INVALID, "null domain");
+    if (!out) return fail(FG_ERR_INVALID, "null output");
+    if ((X == nullptr) != (U == nullptr)) return fail(FG_ERR_INVALID, "X and U must both be given or both NULL");
+    // fg_step's own checks first, so that a failing step launches no marker copy
+    if (d->poisoned) return fail(FG_ERR_STATE, "domain poisoned by a numeric fault; call fg_init_fields");
+    if (frames)
+        for (int e = 0; e < d->n_envs; ++e)
+            for (int a = 0; a < 3; ++a)
+                if (!std::isfinite(frames[e].acc[a]) || !std::isfinite(frames[e].omega[a]) ||
+                    !std::isfinite(frames[e].domega[a]) || !std::isfinite(frames[e].origin[a]))
+                    return fail(FG_ERR_INVALID, "frame not finite");
+    if (d->opt.ib_slip)
+        for (int e = 0; e < d->n_envs; ++e)
+            if (d->mk[e].n > 0 && !d->mk[e].has_normals)
+                return fail(FG_ERR_STATE, "slip forcing needs the markers' normals (fg_set_marker_normals)");
+    fg_status st = FG_OK;
+    if (X && (st = fg_set_markers_all(d, d->total_markers, X, U, device_ptrs)) != FG_OK) return st;
+    if ((st = fg_step(d, 1, frames)) != FG_OK) return st;
+    // the step's k_reduce wrote the rows and the status word to mapped pinned
+    // memory: no copy to issue, the synchronisation makes them visible
+    CK(cudaStreamSynchronize(d->stream));
+    if ((st = status_to_error(d, d->rb->status)) != FG_OK) return st;
+    size_t o = 0;
+    for (int e = 0; e < d->n_envs; ++e) {
+        const int vals = 6 * (d->mk[e].nseg + 1);
+        for (int k = 0; k < vals; ++k) out[o++] = pair_value(d->rb_ft_all[(size_t)e * FT_ROW + k]);
     }
     return FG_OK;
 }

@@ -51,19 +51,22 @@ constexpr int RED_ROWS = MAX_SEG + 2;   // force/torque rows 0..MAX_SEG, then th
 // block reduced together: one shuffle tree per component, then the warp
 // totals in warp order).  One counter per environment counts its blocks; the
 // last one adds, for every row and component, the chunk pairs in chunk order
-// (a warp per component) and evaluates the result in FP64, so the result does
-// not depend on which block finished last.  Results stay compensated FP32
-// pairs on the device (ft, the mass without the cell count, the history row);
-// the host evaluates hi + lo in FP64 when it reads them (FP64 arithmetic is
-// slow on this part).  The last environment to finish advances the step
-// state.
+// (a warp per component), so the result does not depend on which block
+// finished last.  Results stay compensated FP32 pairs on the device (ft, the
+// mass without the cell count, the history row); the host evaluates hi + lo
+// in FP64 when it reads them (FP64 arithmetic is slow on this part).  The
+// force/torque rows are also written to host_ft and, by the last environment
+// to finish (which advances the step state), the status word to host_status:
+// pinned host memory mapped into the device's address space, so a coupled
+// step reads them back with no copy (either may be NULL).
 static __global__ void __launch_bounds__(RED_THREADS)
 k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const float* __restrict__ Fm,
          const float* __restrict__ dV, const int* __restrict__ seg, const float* __restrict__ seg_ref,
          const Pair32* __restrict__ mass_part,
          Pair32* __restrict__ partials, int* __restrict__ counters, int n_envs, int zmax,
          Pair32* __restrict__ ft, Pair32* __restrict__ mass, Pair32* __restrict__ hist, int hist_cap,
-         StepState* __restrict__ st, int* __restrict__ status) {
+         StepState* __restrict__ st, int* __restrict__ status, Pair32* __restrict__ host_ft,
+         int* __restrict__ host_status) {
     constexpr int NW = RED_THREADS / 32;
     __shared__ Pair32 sh[NW][6];
     __shared__ int is_last;
@@ -177,8 +180,12 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
             }
             const int k = k0 + j * NW;
             if (lane == 0 && k < items) {
-                if (k == items - 1) mass[e] = t[j];
-                else ft[(size_t)e * FT_ROW + k] = t[j];
+                if (k == items - 1) {
+                    mass[e] = t[j];
+                } else {
+                    ft[(size_t)e * FT_ROW + k] = t[j];
+                    if (host_ft) host_ft[(size_t)e * FT_ROW + k] = t[j];   // host-mapped copy
+                }
                 if (!(isfinite(t[j].hi) && isfinite(t[j].lo))) atomicOr(status, ST_NUMERIC);
             }
         }
@@ -198,6 +205,9 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
     }
     st->step += 1;
     st->stamp = st->stamp == 0xffffffffu ? 1u : st->stamp + 1u;
+    // the step's status word (every kernel of the step, and every
+    // environment's combine, has set its bits by now) to the host-mapped copy
+    if (host_status) *host_status = atomicOr(status, 0);
 }
 
 // Momentum and angular momentum of the fluid inside a sphere (centre c,

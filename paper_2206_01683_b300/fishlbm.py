@@ -70,6 +70,7 @@ SIGNATURES = {
     "fg_region_momentum": (_I, [_V, _I, _P(_D), _D, _P(_D), _P(_D)]),
     "fg_step": (_I, [_V, _I, _P(fg_frame)]),
     "fg_get_body_force_torque": (_I, [_V, _I, _P(_D)]),
+    "fg_step_io": (_I, [_V, _V, _V, _I, _P(fg_frame), _P(_D)]),
     "fg_destroy": (None, [_V]),
     "fg_last_error": (ctypes.c_char_p, []),
     "fg_lattice": (_I, [_P(_I), _P(_D)]),
@@ -328,6 +329,35 @@ class Domain:
 
     def get_body_force_torque(self, env=0):
         return fg_get_body_force_torque(self.h, env, self.nseg[env])
+
+    def step_io(self, X=None, U=None, frames=None):
+        """One coupled step in one call (fg_step_io): new positions and
+        velocities of all environments' markers (numpy, torch CPU/pinned or
+        CUDA tensors, environment after environment; None keeps them), one
+        step, and the force/torque rows read back.  Returns the (n_seg + 1, 6)
+        rows of a single environment, else a list of them."""
+        if (X is None) != (U is None):
+            raise ValueError("X and U must both be given or both be None")
+        pX = pU = None
+        dev = False
+        if X is not None:
+            pX, devX, kX = _ptr_and_keep(X, np.float32)
+            pU, devU, kU = _ptr_and_keep(U, np.float32)
+            if devX != devU:
+                raise ValueError("X and U must both be host or both be device arrays")
+            dev = bool(devX)
+            self._keep_io = (kX, kU)
+        fr = None
+        if frames is not None:
+            if not isinstance(frames, (list, tuple)):
+                frames = [frames]
+            fr = (fg_frame * len(frames))(*[f if isinstance(f, fg_frame) else frame_from_array(f) for f in frames])
+        rows = [self.nseg[e] + 1 for e in range(len(self.nseg))]
+        out = np.zeros((sum(rows), 6))
+        _check(lib().fg_step_io(self.h, pX, pU, 1 if dev else 0, fr, _dp(out)))
+        if len(rows) == 1:
+            return out
+        return np.split(out, np.cumsum(rows)[:-1])
 
     def init_fields(self, rho=None, u=None, env=0):
         r = np.ascontiguousarray(rho, dtype=np.float64) if rho is not None else None

@@ -635,6 +635,71 @@ def test_set_markers_all_equals_per_environment_updates():
         b.set_markers_all(Xall[:-1], Uall[:-1])             # wrong total
 
 
+@pytest.mark.parametrize("n_envs", [1, 3])
+def test_step_io_equals_separate_calls(n_envs):
+    """fg_step_io (markers in, one step, force/torque out, one call) gives
+    exactly what fg_set_markers_all + fg_step + fg_get_body_force_torque
+    give, with pageable, pinned and device marker arrays, for one environment
+    and for three, and so do per-environment fg_set_markers calls with pinned
+    arrays (read in place by the copy kernel); a failing check (a frame that
+    is not finite) launches nothing, so the steps that follow are
+    unchanged."""
+    torch = pytest.importorskip("torch")
+    shapes = [(32, 24, 20), (40, 16, 24), (24, 24, 24)][:n_envs]
+    fishes = [inputs.fish_for_grid(s, 0.4 * s[0], 300 + 50 * k) for k, s in enumerate(shapes)]
+    trajs = [inputs.FrameTrajectory(inputs.seed_for(2) + k, inputs.domain_centre(s)) for k, s in enumerate(shapes)]
+
+    def make():
+        d = fishlbm.Domain([fishlbm.env_desc(s, 0.6, OPEN_X, (0.02, 0, 0), 1.0, (0.02, 0, 0)) for s in shapes],
+                           deterministic=True)   # bit-reproducible, so the runs compare exactly
+        for e, f in enumerate(fishes):
+            X, U = f.pose(0)
+            d.set_markers(np.float32(X), np.float32(U), np.float32(f.dV), seg=f.seg, n_seg=5,
+                          ref=f.joints_rest[0], env=e)
+        return d
+
+    a, b, c, p, q = make(), make(), make(), make(), make()
+    bad = fishlbm.make_frame(acc=(float("nan"), 0.0, 0.0))
+    for n in range(1, 6):
+        poses = [f.pose(n) for f in fishes]
+        frames = [fishlbm.frame_from_array(t.at(n)) for t in trajs]
+        Xall = np.concatenate([p[0] for p in poses]).astype(np.float32)
+        Uall = np.concatenate([p[1] for p in poses]).astype(np.float32)
+        keep = n == 3   # this step keeps the previous markers
+        if not keep:
+            a.set_markers_all(Xall, Uall)
+        a.step(1, frames)
+        ref = [a.get_body_force_torque(e) for e in range(n_envs)]
+        if keep:
+            # valid markers with a bad frame: refused before any copy
+            with pytest.raises(fishlbm.FgError) as ei:
+                b.step_io(Xall + 0.25, Uall, [bad] * n_envs)
+            assert ei.value.status == fishlbm.FG_ERR_INVALID
+            got_b, got_c = b.step_io(None, None, frames), c.step_io(None, None, frames)
+            got_p = p.step_io(None, None, frames)
+        else:
+            got_b = b.step_io(Xall, Uall, frames)
+            got_c = c.step_io(torch.from_numpy(Xall).cuda(), torch.from_numpy(Uall).cuda(), frames)
+            got_p = p.step_io(torch.from_numpy(Xall).pin_memory(), torch.from_numpy(Uall).pin_memory(), frames)
+            for e, f in enumerate(fishes):
+                q.set_markers(torch.from_numpy(np.float32(poses[e][0])).pin_memory(),
+                              torch.from_numpy(np.float32(poses[e][1])).pin_memory(), None, None, n_seg=5,
+                              ref=f.joints_rest[0], env=e)
+        q.step(1, frames)
+        got_q = [q.get_body_force_torque(e) for e in range(n_envs)]
+        if n_envs == 1:
+            got_b, got_c, got_p = [got_b], [got_c], [got_p]
+        for e in range(n_envs):
+            assert got_b[e].shape == (6, 6)
+            for got in (got_b, got_c, got_p, got_q):
+                assert np.array_equal(got[e], ref[e])
+    for e in range(n_envs):
+        for d in (b, c, p, q):
+            assert np.array_equal(a.populations(e), d.populations(e))
+    with pytest.raises(ValueError):
+        b.step_io(Xall, None)
+
+
 @pytest.mark.parametrize("variant", ["plain", "staged"])
 def test_third_order_equilibrium_parity(variant):
     """eq_order = 3 against the oracle: a perturbed Taylor-Green field with a
