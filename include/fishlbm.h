@@ -124,8 +124,11 @@ typedef struct {
  * every environment advances in the same kernel launches).  opt may be NULL
  * (FP32, one pass, automatic kernel choice, graphs on).  cuda_stream is a cudaStream_t or NULL.  Populations are
  * initialised at equilibrium with (rho0, u0); the frame is at rest with its
- * origin at the domain centre.  Errors: FG_ERR_INVALID (sizes, tau, faces,
- * options), FG_ERR_OOM, FG_ERR_CUDA.  *out is set only on FG_OK. */
+ * origin at the domain centre.  Limits: 1 <= n_envs <= 4096; 1 <= cells
+ * per axis <= 65536; P ny nz < 2^31 slots per environment (P = nx rounded up
+ * to a multiple of 8).  Errors: FG_ERR_INVALID (sizes, limits, tau, rho0,
+ * faces, options; checked before any GPU work), FG_ERR_OOM, FG_ERR_CUDA.
+ * *out is set only on FG_OK. */
 fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options* opt,
                            void* cuda_stream, fg_domain** out);
 

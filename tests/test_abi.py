@@ -79,3 +79,31 @@ def test_invalid_arguments_fail_without_gpu_work():
         assert e.status == fishlbm.FG_ERR_INVALID
     else:
         raise AssertionError("2-cell open axis accepted")
+
+
+def test_domain_limits_are_rejected_before_gpu_work():
+    """Every documented limit of fg_create_domain fails with FG_ERR_INVALID
+    before any GPU work (so these run without a GPU)."""
+    ok = fishlbm.env_desc((8, 8, 8), 0.6)
+    cases = {
+        "no environments": [],
+        "4097 environments": [ok] * 4097,
+        "zero cells": [fishlbm.env_desc((0, 8, 8), 0.6)],
+        "65537 cells on an axis": [fishlbm.env_desc((8, 65537, 1), 0.6)],
+        "2^31 slots": [fishlbm.env_desc((2048, 1024, 1024), 0.6)],
+        "unknown face": [fishlbm.env_desc((8, 8, 8), 0.6, faces=(0, 0, 0, 0, 4, 4))],
+        "unpaired periodic face": [fishlbm.env_desc((8, 8, 8), 0.6, faces=(0, 2, 0, 0, 0, 0))],
+        "tau not finite": [fishlbm.env_desc((8, 8, 8), float("nan"))],
+        "rho0 <= 0": [fishlbm.env_desc((8, 8, 8), 0.6, rho0=0.0)],
+    }
+    for name, envs in cases.items():
+        try:
+            if envs:
+                fishlbm.fg_create_domain(envs)
+            else:
+                out = fishlbm._V()
+                fishlbm._check(fishlbm.lib().fg_create_domain(None, 0, None, None, ctypes.byref(out)))
+        except fishlbm.FgError as e:
+            assert e.status == fishlbm.FG_ERR_INVALID, name
+        else:
+            raise AssertionError(name + " accepted")
