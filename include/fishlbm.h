@@ -139,7 +139,11 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
  *   id in [0, n_seg) (NULL: all 0), 1 <= n_seg <= 16, ref[3] the point
  *   torques are taken about (NULL: origin).
  * device_ptrs = 0: host arrays; 1: device arrays (copied on the stream,
- * asynchronously).  dV and seg may be NULL on later calls with the same n to
+ * asynchronously).  Host arrays in pinned (page-locked) memory are read in
+ * place by a copy kernel on the stream, pageable ones are copied at the
+ * call; either way the library keeps its own copy, and pinned or device
+ * arrays must stay unchanged until the stream has reached the copy (as for
+ * any asynchronous copy).  dV and seg may be NULL on later calls with the same n to
  * keep the previous values.  Periodic axes wrap X; along a non-periodic
  * axis every marker must satisfy 2 <= X < n-3 so its 4-point stencil stays
  * off the boundary layer: host arrays are checked here (FG_ERR_INVALID),
