@@ -293,6 +293,15 @@ fg_status fg_load_state(fg_domain* d, int env, const void* host_buf);
  * caller device buffer, asynchronous on the stream (checkpoints). */
 fg_status fg_copy_state(fg_domain* d, int env, void* buf, int to_buf);
 
+/* One step of a single-environment domain from the caller's device state
+ * buffer `in` into `out` (each fg_state_bytes bytes in the layout of
+ * fg_copy_state; distinct): the step fg_step takes with the domain's markers,
+ * frame (frames: NULL keeps the last) and options, force/torque, mass and
+ * history recorded as by fg_step, but the domain's own populations are
+ * neither read nor written.  Asynchronous on the stream.  Checkpoint
+ * recompute steps from buffer to buffer with it, so no state is copied. */
+fg_status fg_step_state(fg_domain* d, const void* in, void* out, const fg_frame* frames);
+
 /* Device status word (bit 0 numeric, bit 1 invalid marker, bit 2 timeout)
  * without clearing it.  Synchronises. */
 fg_status fg_get_status(fg_domain* d, int* status);
@@ -308,10 +317,11 @@ fg_status fg_step_count(fg_domain* d, long long* steps);
  * adjoint state lam = dL/df* (all zero after fg_adjoint_reset, the terminal
  * condition of a loss that does not read the final state).  The caller
  * replays the steps backwards: before the adjoint of step n it puts the
- * state f*^n into the domain (fg_copy_state / checkpoint + recompute) and the
- * step's markers (fg_set_markers); then fg_adjoint_step turns lam^{n+1} into
- * lam^n and writes the step's marker gradients.  The forward state is not
- * changed. */
+ * state f*^n into the domain (fg_copy_state / checkpoint + recompute), or
+ * passes it in a buffer (fg_step_state / fg_adjoint_step_state), and sets
+ * the step's markers (fg_set_markers); then fg_adjoint_step turns lam^{n+1}
+ * into lam^n and writes the step's marker gradients.  The forward state is
+ * not changed. */
 fg_status fg_adjoint_reset(fg_domain* d);
 
 /* frames: the step's frame (NULL keeps the last one); gF: host, (n_seg + 1) * 6
@@ -319,6 +329,12 @@ fg_status fg_adjoint_reset(fg_domain* d);
  * reports them (NULL: none); gX, gU: device float [n][3] outputs, dL/dX_l and
  * dL/dU_l of this step.  Asynchronous on the stream. */
 fg_status fg_adjoint_step(fg_domain* d, const fg_frame* frames, const double* gF, float* gX, float* gU);
+
+/* fg_adjoint_step with the step's forward state f*^n read from the caller's
+ * device buffer `state` (fg_state_bytes, the layout of fg_copy_state) instead
+ * of the domain's populations. */
+fg_status fg_adjoint_step_state(fg_domain* d, const void* state, const fg_frame* frames, const double* gF,
+                                float* gX, float* gU);
 
 /* The adjoint state lam as host FP64 [ncell][27] (library velocity order):
  * read it, or overwrite it (tests).  Both synchronise. */

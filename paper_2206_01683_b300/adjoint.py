@@ -10,8 +10,9 @@ autograd maps dL/dX, dL/dU of every step to dL/dA, dL/dphi.
 
 The forward pass runs the CUDA step and keeps the state every `checkpoint`
 steps; the backward pass walks the segments in reverse, recomputes the states
-of a segment from its checkpoint, and runs the library's adjoint step
-(fg_adjoint_step) from the last step of the segment to its first.  Only the
+of a segment from its checkpoint (fg_step_state, from buffer to buffer, so no
+state is copied), and runs the library's adjoint step on each of them
+(fg_adjoint_step_state) from the last step of the segment to its first.  Only the
 skinning (a small dense map) is differentiated by torch; the fluid's adjoint
 is the library's.
 """
@@ -143,16 +144,17 @@ class ThrustProblem:
         d.adjoint_reset()
         for s in reversed(range(0, N, self.C)):
             e = min(s + self.C, N)
-            d.copy_state(self.ckpt[s // self.C], False)
-            for n in range(s, e):                  # recompute f*^s .. f*^{e-1}
-                d.copy_state(self.seg_states[n - s], True)
-                if n < e - 1:
-                    self._markers(X, U, n)
-                    d.step(1, self._frame(n))
-            for n in reversed(range(s, e)):
-                d.copy_state(self.seg_states[n - s], False)
+            # the input state of step n: the checkpoint for n = s, else the
+            # recomputed seg_states[n - s]; each recompute step writes the
+            # next buffer directly (no state copies)
+            state = [self.ckpt[s // self.C]] + [self.seg_states[k] for k in range(1, e - s)]
+            for n in range(s, e - 1):              # recompute f*^{s+1} .. f*^{e-1}
                 self._markers(X, U, n)
-                d.adjoint_step(self._frame(n)[0] if self.frames is not None else None, gF, gX[n], gU[n])
+                d.step_state(state[n - s], state[n - s + 1], self._frame(n))
+            for n in reversed(range(s, e)):
+                self._markers(X, U, n)
+                d.adjoint_step_state(state[n - s], self._frame(n)[0] if self.frames is not None else None, gF,
+                                     gX[n], gU[n])
         ev[1].record()
         torch.cuda.synchronize()
         self.backward_ms = ev[0].elapsed_time(ev[1])

@@ -417,10 +417,8 @@ void enqueue_k1(fg_domain* d, const typename S::raw* gin, typename S::raw* gout,
 // Launch the kernels of one step reading buffer `parity` on stream s; with
 // ev != nullptr an event pair is recorded around each kernel.
 template <class S>
-fg_status enqueue_step(fg_domain* d, int parity, cudaStream_t s, cudaEvent_t* const* ev) {
-    typedef typename S::raw raw;
-    const raw* gin = (const raw*)d->pop[parity];
-    raw* gout = (raw*)d->pop[parity ^ 1];
+fg_status enqueue_step_io(fg_domain* d, const typename S::raw* gin, typename S::raw* gout, cudaStream_t s,
+                          cudaEvent_t* const* ev) {
     if (d->total_markers > 0) {
         if (ev) CK(cudaEventRecord(ev[FG_K_IB][0], s));
         // all resident blocks: the scan phase covers every tile stamp
@@ -453,6 +451,12 @@ fg_status enqueue_step(fg_domain* d, int parity, cudaStream_t s, cudaEvent_t* co
     if (ev) CK(cudaEventRecord(ev[FG_K_REDUCE][1], s));
     CK(cudaGetLastError());
     return FG_OK;
+}
+
+template <class S>
+fg_status enqueue_step(fg_domain* d, int parity, cudaStream_t s, cudaEvent_t* const* ev) {
+    typedef typename S::raw raw;
+    return enqueue_step_io<S>(d, (const raw*)d->pop[parity], (raw*)d->pop[parity ^ 1], s, ev);
 }
 
 // One step with direct launches (and per-kernel events when profiling).
@@ -1254,6 +1258,32 @@ fg_status fg_step(fg_domain* d, int n_steps, const fg_frame* frames) {
     return FG_OK;
 }
 
+fg_status fg_step_state(fg_domain* d, const void* in, void* out, const fg_frame* frames) {
+    NvtxRange nvtx_range("fg_step_state");
+    if (!d) return fail(FG_ERR_INVALID, "null domain");
+    if (d->n_envs != 1) return fail(FG_ERR_INVALID, "fg_step_state takes a single environment");
+    if (!in || !out || in == out) return fail(FG_ERR_INVALID, "in and out must be distinct device buffers");
+    if (d->poisoned) return fail(FG_ERR_STATE, "domain poisoned by a numeric fault; call fg_init_fields");
+    if (frames) {
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(frames[0].acc[a]) || !std::isfinite(frames[0].omega[a]) ||
+                !std::isfinite(frames[0].domega[a]) || !std::isfinite(frames[0].origin[a]))
+                return fail(FG_ERR_INVALID, "frame not finite");
+        set_frame(d->frame[0], frames[0]);
+        fg_status st = upload_frames(d);
+        if (st != FG_OK) return st;
+    }
+    if (d->opt.ib_slip && d->mk[0].n > 0 && !d->mk[0].has_normals)
+        return fail(FG_ERR_STATE, "slip forcing needs the markers' normals (fg_set_marker_normals)");
+    fg_status st = dispatch(d->opt.storage, [&](auto tag) {
+        typedef typename decltype(tag)::raw raw;
+        return enqueue_step_io<decltype(tag)>(d, (const raw*)in, (raw*)out, d->stream, nullptr);
+    });
+    if (st != FG_OK) return st;
+    d->steps += 1;
+    return note_stamp_advance(d);
+}
+
 fg_status fg_get_status(fg_domain* d, int* status) {
     if (!d || !status) return fail(FG_ERR_INVALID, "null argument");
     CK(cudaMemcpyAsync(&d->rb->status, d->status, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
@@ -1556,10 +1586,9 @@ fg_status fg_adjoint_reset(fg_domain* d) {
     return FG_OK;
 }
 
-fg_status fg_adjoint_step(fg_domain* d, const fg_frame* frames, const double* gF, float* gX, float* gU) {
-    NvtxRange nvtx_range("fg_adjoint_step");
-    fg_status st = adjoint_check(d);
-    if (st != FG_OK) return st;
+static fg_status adjoint_step_from(fg_domain* d, const float* f, const fg_frame* frames, const double* gF,
+                                   float* gX, float* gU) {
+    fg_status st = FG_OK;
     const int n = d->mk[0].n;
     if (n > 0 && (!gX || !gU)) return fail(FG_ERR_INVALID, "gX and gU are required");
     if (frames) {
@@ -1571,7 +1600,6 @@ fg_status fg_adjoint_step(fg_domain* d, const fg_frame* frames, const double* gF
     if (gF)
         for (int k = 0; k < 6 * rows; ++k) g[k] = (float)gF[k];
     CK(cudaMemcpyAsync(d->adj_gF, g.data(), sizeof(float) * FT_ROW, cudaMemcpyHostToDevice, d->stream));
-    const float* f = (const float*)d->pop[d->cur];
     const float* lam_in = d->adj_lam[d->adj_cur];
     float* lam_out = d->adj_lam[d->adj_cur ^ 1];
     const EnvDev& E = d->env[0];
@@ -1594,6 +1622,22 @@ fg_status fg_adjoint_step(fg_domain* d, const fg_frame* frames, const double* gF
     CK(cudaGetLastError());
     d->adj_cur ^= 1;
     return note_stamp_advance(d);
+}
+
+fg_status fg_adjoint_step(fg_domain* d, const fg_frame* frames, const double* gF, float* gX, float* gU) {
+    NvtxRange nvtx_range("fg_adjoint_step");
+    fg_status st = adjoint_check(d);
+    if (st != FG_OK) return st;
+    return adjoint_step_from(d, (const float*)d->pop[d->cur], frames, gF, gX, gU);
+}
+
+fg_status fg_adjoint_step_state(fg_domain* d, const void* state, const fg_frame* frames, const double* gF,
+                                float* gX, float* gU) {
+    NvtxRange nvtx_range("fg_adjoint_step_state");
+    fg_status st = adjoint_check(d);
+    if (st != FG_OK) return st;
+    if (!state) return fail(FG_ERR_INVALID, "null state buffer");
+    return adjoint_step_from(d, (const float*)state, frames, gF, gX, gU);
 }
 
 fg_status fg_get_adjoint(fg_domain* d, double* lam) {

@@ -91,8 +91,10 @@ SIGNATURES = {
     "fg_stream_collide_bytes": (_I, [_V, _P(_ULL)]),
     "fg_autotune": (_I, [_V, _P(_I), _P(_D)]),
     "fg_copy_state": (_I, [_V, _I, _V, _I]),
+    "fg_step_state": (_I, [_V, _V, _V, _P(fg_frame)]),
     "fg_adjoint_reset": (_I, [_V]),
     "fg_adjoint_step": (_I, [_V, _P(fg_frame), _P(_D), _V, _V]),
+    "fg_adjoint_step_state": (_I, [_V, _V, _P(fg_frame), _P(_D), _V, _V]),
     "fg_get_adjoint": (_I, [_V, _P(_D)]),
     "fg_set_adjoint": (_I, [_V, _P(_D)]),
     "fg_stream_collide_variant": (_I, [_V, _P(_I)]),
@@ -437,6 +439,19 @@ class Domain:
         p = buf.data_ptr() if hasattr(buf, "data_ptr") else int(buf)
         _check(lib().fg_copy_state(self.h, env, _V(p), 1 if to_buf else 0))
 
+    def step_state(self, src, dst, frames=None):
+        """One step from the device state buffer src into dst (CUDA tensors
+        or int pointers of state_bytes() bytes), leaving the domain's own
+        populations alone (fg_step_state)."""
+        fr = None
+        if frames is not None:
+            if not isinstance(frames, (list, tuple)):
+                frames = [frames]
+            fr = (fg_frame * len(frames))(*[f if isinstance(f, fg_frame) else frame_from_array(f) for f in frames])
+        ps = src.data_ptr() if hasattr(src, "data_ptr") else int(src)
+        pd = dst.data_ptr() if hasattr(dst, "data_ptr") else int(dst)
+        _check(lib().fg_step_state(self.h, _V(ps), _V(pd), fr))
+
     def adjoint_reset(self):
         _check(lib().fg_adjoint_reset(self.h))
 
@@ -451,6 +466,20 @@ class Domain:
         _check(lib().fg_adjoint_step(self.h, fr, _dp(g) if g is not None else None,
                                      _V(gX.data_ptr()) if gX is not None else None,
                                      _V(gU.data_ptr()) if gU is not None else None))
+
+    def adjoint_step_state(self, state, frame=None, gF=None, gX=None, gU=None):
+        """adjoint_step with the step's forward state read from a device
+        buffer (CUDA tensor or int pointer of state_bytes() bytes)."""
+        fr = None
+        if frame is not None:
+            fr = ctypes.byref(frame if isinstance(frame, fg_frame) else frame_from_array(frame))
+        g = None
+        if gF is not None:
+            g = np.ascontiguousarray(gF, dtype=np.float64).ravel()
+        p = state.data_ptr() if hasattr(state, "data_ptr") else int(state)
+        _check(lib().fg_adjoint_step_state(self.h, _V(p), fr, _dp(g) if g is not None else None,
+                                           _V(gX.data_ptr()) if gX is not None else None,
+                                           _V(gU.data_ptr()) if gU is not None else None))
 
     def adjoint(self):
         lam = np.zeros((self.ncell(0), 27))

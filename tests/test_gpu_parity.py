@@ -751,3 +751,38 @@ def test_third_order_equilibrium_galilean_shear_on_gpu():
     r0 = rate(3, 0.0)
     assert abs(rate(3, 0.1) - r0) < 2e-4 * r0
     assert abs((rate(2, 0.1) - r0) / (-0.03) - 1.0) < 0.15
+
+
+def test_step_state_steps_between_buffers():
+    """fg_step_state from a state buffer into another gives exactly the step
+    fg_step takes from the same state (deterministic spread, markers, moving
+    frame), records the same force/torque, and leaves the domain's own
+    populations untouched; in == out and several environments are refused."""
+    torch = pytest.importorskip("torch")
+    shape = (40, 24, 20)
+    rho, u = inputs.random_fields(shape, seed=71, u_amp=0.02)
+    X, dV = inputs.fibonacci_sphere(200, 4.0, (20, 12, 10))
+    frame = fishlbm.make_frame(acc=(1e-5, 0, 2e-6), omega=(0, 1e-4, 0), origin=(20, 12, 10))
+    a, b = (fishlbm.Domain([fishlbm.env_desc(shape, 0.6)], deterministic=True) for _ in range(2))
+    for d in (a, b):
+        d.init_fields(rho, u)
+        d.set_markers(np.float32(X), np.tile(np.float32([0.01, 0, 0]), (200, 1)), np.float32(dV))
+    nb = b.state_bytes()
+    bufs = [torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(3)]
+    b.copy_state(bufs[0], True)
+    before = b.populations()
+    for n in range(3):
+        U = np.tile(np.float32([0.01, 0.002 * n, 0]), (200, 1))
+        for d in (a, b):
+            d.set_markers(np.float32(X + U * n), U, None)
+        a.step(1, [frame])
+        b.step_state(bufs[n], bufs[n + 1] if n < 2 else bufs[0], [frame])
+        assert np.array_equal(a.get_body_force_torque(), b.get_body_force_torque())
+    assert np.array_equal(b.populations(), before)            # the domain's state is untouched
+    b.copy_state(bufs[0], False)
+    assert np.array_equal(a.populations(), b.populations())
+    with pytest.raises(fishlbm.FgError):
+        b.step_state(bufs[1], bufs[1])
+    two = fishlbm.Domain([fishlbm.env_desc(shape, 0.6)] * 2)
+    with pytest.raises(fishlbm.FgError):
+        two.step_state(bufs[1], bufs[2])
