@@ -276,6 +276,16 @@ fg_status fg_get_marker_force(fg_domain* d, int env, float* F);
  * compensated FP32 pair on the device, evaluated in FP64.  Synchronises. */
 fg_status fg_get_mass(fg_domain* d, int env, double* mass);
 
+/* Mass-drift watchdog of env.  rel_tol > 0 takes env's current mass M0 as
+ * the reference and makes the reduction of every later step check
+ * |M - M0| <= rel_tol M0; a step that exceeds it sets status bit 3, and the
+ * next call that reads results returns FG_ERR_NUMERIC ("mass drift") and
+ * poisons the domain as a NaN does.  rel_tol <= 0 switches it off (the
+ * default).  Periodic domains conserve mass to rounding; open faces exchange
+ * mass, so there the tolerance bounds the net flux.  fg_init_fields keeps the
+ * reference.  Synchronises. */
+fg_status fg_watch_mass(fg_domain* d, int env, double rel_tol);
+
 /* Copy up to max_steps rows of env's recorded history, oldest first; each row
  * is (n_seg + 1) * 6 force/torque values followed by the mass.  *n_rows gets
  * the number of rows written.  Synchronises. */
@@ -302,7 +312,8 @@ fg_status fg_copy_state(fg_domain* d, int env, void* buf, int to_buf);
  * recompute steps from buffer to buffer with it, so no state is copied. */
 fg_status fg_step_state(fg_domain* d, const void* in, void* out, const fg_frame* frames);
 
-/* Device status word (bit 0 numeric, bit 1 invalid marker, bit 2 timeout)
+/* Device status word (bit 0 numeric, bit 1 invalid marker, bit 2 timeout,
+ * bit 3 mass drift)
  * without clearing it.  Synchronises. */
 fg_status fg_get_status(fg_domain* d, int* status);
 

@@ -1303,6 +1303,10 @@ static fg_status status_to_error(fg_domain* d, int s) {
         CK(cudaStreamSynchronize(d->stream));
         return fail(FG_ERR_INVALID, "a marker was outside the domain or within 2 cells of a non-periodic face");
     }
+    if (s & ST_MASS_DRIFT) {
+        d->poisoned = true;
+        return fail(FG_ERR_NUMERIC, "mass drift beyond the fg_watch_mass tolerance");
+    }
     if (s & ST_TIMEOUT) {
         d->poisoned = true;
         return fail(FG_ERR_TIMEOUT, "a bounded device wait gave up; call fg_init_fields");
@@ -1369,6 +1373,24 @@ fg_status fg_get_mass(fg_domain* d, int env, double* mass) {
     if ((st = status_to_error(d, d->rb->status)) != FG_OK) return st;
     *mass = (double)env_cells(d, env) + pair_value(d->rb->mass);
     return FG_OK;
+}
+
+fg_status fg_watch_mass(fg_domain* d, int env, double rel_tol) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    if (!std::isfinite(rel_tol)) return fail(FG_ERR_INVALID, "rel_tol not finite");
+    EnvDev& E = d->env[env];
+    if (rel_tol <= 0.0) {
+        E.mass_tol = 0.0f;
+        E.mass_ref = 0.0f;
+        return upload_env(d);
+    }
+    double m = 0.0;
+    if ((st = fg_get_mass(d, env, &m)) != FG_OK) return st;   // synchronises
+    const double cells = (double)env_cells(d, env);
+    E.mass_ref = (float)(m - cells);
+    E.mass_tol = (float)(rel_tol * m);
+    return upload_env(d);
 }
 
 fg_status fg_get_marker_force(fg_domain* d, int env, float* F) {

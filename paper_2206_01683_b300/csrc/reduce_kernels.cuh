@@ -182,6 +182,10 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
             if (lane == 0 && k < items) {
                 if (k == items - 1) {
                     mass[e] = t[j];
+                    // mass-drift watchdog (the reference and tolerance are
+                    // set by fg_watch_mass)
+                    if (E.mass_tol > 0.0f && !(fabsf((t[j].hi - E.mass_ref) + t[j].lo) <= E.mass_tol))
+                        atomicOr(status, ST_MASS_DRIFT);
                 } else {
                     ft[(size_t)e * FT_ROW + k] = t[j];
                     if (host_ft) host_ft[(size_t)e * FT_ROW + k] = t[j];   // host-mapped copy

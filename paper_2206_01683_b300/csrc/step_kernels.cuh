@@ -34,7 +34,7 @@ constexpr int HIST_ROW = FT_ROW + 1;       // + mass
 constexpr uint32_t WAIT_LIMIT = 1u << 22;  // mbarrier polls before giving up
 
 enum { BC_PERIODIC = 0, BC_VELOCITY = 1, BC_OUTFLOW = 2, BC_FREESLIP = 3 };
-enum { ST_NUMERIC = 1, ST_BAD_MARKER = 2, ST_TIMEOUT = 4 };
+enum { ST_NUMERIC = 1, ST_BAD_MARKER = 2, ST_TIMEOUT = 4, ST_MASS_DRIFT = 8 };
 
 // Static description of one environment on the device.
 struct EnvDev {
@@ -61,6 +61,8 @@ struct EnvDev {
     int marker_off;           // first marker slot in the marker arrays
     int nseg;
     double ref[3];            // torque reference point
+    float mass_ref;           // mass watchdog: reference sum (rho - 1) and the
+    float mass_tol;           // largest allowed |change| (<= 0: off)
 };
 
 // Frame motion of one environment (Eq. 3), refreshed by fg_step.  Besides

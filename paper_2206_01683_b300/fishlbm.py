@@ -79,6 +79,7 @@ SIGNATURES = {
     "fg_get_populations": (_I, [_V, _I, _P(_D)]),
     "fg_set_populations": (_I, [_V, _I, _P(_D)]),
     "fg_get_marker_force": (_I, [_V, _I, _P(ctypes.c_float)]),
+    "fg_watch_mass": (_I, [_V, _I, _D]),
     "fg_get_mass": (_I, [_V, _I, _P(_D)]),
     "fg_get_history": (_I, [_V, _I, _P(_D), _I, _P(_I)]),
     "fg_state_bytes": (_I, [_V, _I, _P(_ULL)]),
@@ -387,6 +388,11 @@ class Domain:
         F = np.zeros((max(self.nmark[env], 1), 3), dtype=np.float32)
         _check(lib().fg_get_marker_force(self.h, env, F.ctypes.data_as(_P(ctypes.c_float))))
         return F[: self.nmark[env]]
+
+    def watch_mass(self, rel_tol, env=0):
+        """Mass-drift watchdog (fg_watch_mass): the current mass becomes the
+        reference; rel_tol <= 0 switches it off."""
+        _check(lib().fg_watch_mass(self.h, env, float(rel_tol)))
 
     def mass(self, env=0):
         m = _D()

@@ -418,6 +418,47 @@ def test_numeric_watchdog_poison_and_reset():
     assert abs(d.mass() - 512.0) < 1e-9
 
 
+def test_mass_drift_watchdog():
+    """fg_watch_mass: a periodic box with a translating sphere conserves mass
+    to rounding, so a tight watch stays quiet for 60 steps; mass injected
+    into the state trips it (FG_ERR_NUMERIC, domain poisoned); switched off,
+    the same injection passes; an open channel passes a tolerance that bounds
+    its net inflow."""
+    cfg = inputs.SPHERE_BOX
+    d = fishlbm.Domain([fishlbm.env_desc(cfg["shape"], cfg["tau"])])
+    d.step(1)
+    d.watch_mass(1e-9)
+    m0 = d.mass()
+    for n in range(60):
+        X, U, dV = inputs.translating_sphere(cfg["n_markers"], cfg["radius"], cfg["center"], cfg["velocity"], n)
+        d.set_markers(np.float32(X), np.float32(U), np.float32(dV))
+        d.step(1)
+    d.get_body_force_torque()
+    assert abs(d.mass() - m0) <= 1e-9 * m0
+    f = d.populations()
+    f[:, 13] += 1e-6                      # +1e-6 per cell in the rest population: relative drift 1e-6
+    d.set_populations(f)
+    d.step(1)
+    with pytest.raises(fishlbm.FgError) as ei:
+        d.get_body_force_torque()
+    assert ei.value.status == fishlbm.FG_ERR_NUMERIC and "mass" in str(ei.value)
+    with pytest.raises(fishlbm.FgError) as ei:
+        d.step(1)
+    assert ei.value.status == fishlbm.FG_ERR_STATE
+    d.watch_mass(0.0)
+    d.init_fields(None, None)
+    d.set_populations(f)
+    d.step(2)
+    d.get_body_force_torque()
+    ch = fishlbm.Domain([fishlbm.env_desc((48, 24, 24), 0.6, OPEN_X, (0.02, 0, 0), 1.0, (0.02, 0, 0))])
+    ch.step(1)
+    ch.watch_mass(0.05)
+    ch.step(50)
+    ch.get_body_force_torque()
+    with pytest.raises(fishlbm.FgError):
+        ch.watch_mass(float("nan"))
+
+
 def test_history_checkpoint_and_profile():
     shape = (24, 16, 16)
     d = fishlbm.Domain([fishlbm.env_desc(shape, 0.6)], record_history=8)
