@@ -243,6 +243,13 @@ fg_status fg_step_io(fg_domain* d, const float* X, const float* U, int device_pt
 /* Release all device memory of the domain; NULL is ignored. */
 void fg_destroy(fg_domain* d);
 
+/* Largest single device allocation the library may make, in bytes (0, the
+ * default: no limit), process-wide.  A larger request fails with FG_ERR_OOM
+ * as an exhausted device would, and the call that made it leaves its domain
+ * unchanged (a failed fg_create_domain frees what it had allocated).  For
+ * testing the out-of-memory paths without filling the device. */
+fg_status fg_set_alloc_cap(unsigned long long bytes);
+
 /* Thread-local message describing the last failed call ("" if none). */
 const char* fg_last_error(void);
 

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -71,6 +72,11 @@ fg_status fail(fg_status s, const std::string& msg) {
     g_err = msg;
     return s;
 }
+
+// Largest single device allocation the library makes (0: no limit), set by
+// fg_set_alloc_cap so that the out-of-memory paths can be exercised without
+// filling the device.
+std::atomic<unsigned long long> g_alloc_cap{0};
 
 fg_status cuda_fail(cudaError_t e, const char* what) {
     g_err = std::string(what) + ": " + cudaGetErrorString(e);
@@ -284,6 +290,8 @@ template <class T>
 fg_status dalloc(T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
+    const unsigned long long cap = g_alloc_cap.load(std::memory_order_relaxed);
+    if (cap != 0 && sizeof(T) * count > cap) return fail(FG_ERR_OOM, "allocation above the fg_set_alloc_cap limit");
     cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -1372,6 +1380,11 @@ fg_status fg_get_mass(fg_domain* d, int env, double* mass) {
     CK(cudaStreamSynchronize(d->stream));
     if ((st = status_to_error(d, d->rb->status)) != FG_OK) return st;
     *mass = (double)env_cells(d, env) + pair_value(d->rb->mass);
+    return FG_OK;
+}
+
+fg_status fg_set_alloc_cap(unsigned long long bytes) {
+    g_alloc_cap.store(bytes, std::memory_order_relaxed);
     return FG_OK;
 }
 

@@ -80,6 +80,7 @@ SIGNATURES = {
     "fg_set_populations": (_I, [_V, _I, _P(_D)]),
     "fg_get_marker_force": (_I, [_V, _I, _P(ctypes.c_float)]),
     "fg_watch_mass": (_I, [_V, _I, _D]),
+    "fg_set_alloc_cap": (_I, [_ULL]),
     "fg_get_mass": (_I, [_V, _I, _P(_D)]),
     "fg_get_history": (_I, [_V, _I, _P(_D), _I, _P(_I)]),
     "fg_state_bytes": (_I, [_V, _I, _P(_ULL)]),
@@ -222,6 +223,12 @@ def _ptr_and_keep(a, dtype):
         return _V(a.data_ptr()), bool(a.is_cuda), a
     arr = np.ascontiguousarray(a, dtype=dtype)
     return arr.ctypes.data_as(_V), False, arr
+
+
+def set_alloc_cap(nbytes):
+    """Largest single device allocation the library may make (0: no limit);
+    larger requests fail with FG_ERR_OOM (fg_set_alloc_cap)."""
+    _check(lib().fg_set_alloc_cap(int(nbytes)))
 
 
 def debug_flags(reset=True):

@@ -459,6 +459,44 @@ def test_mass_drift_watchdog():
         ch.watch_mass(float("nan"))
 
 
+def test_out_of_memory_paths_leave_domains_usable():
+    """With a per-allocation cap (fg_set_alloc_cap) standing in for a full
+    device: creating a domain whose population buffers exceed it fails with
+    FG_ERR_OOM and frees what it had allocated; growing a live domain's
+    marker buffers past it fails with FG_ERR_OOM and leaves the domain's
+    markers and state as they were, so it steps on exactly like a twin that
+    never saw the failure."""
+    torch = pytest.importorskip("torch")
+    shape = (64, 64, 64)
+    try:
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        fishlbm.set_alloc_cap(1 << 20)
+        with pytest.raises(fishlbm.FgError) as ei:
+            fishlbm.Domain([fishlbm.env_desc(shape, 0.6)])
+        assert ei.value.status == fishlbm.FG_ERR_OOM
+        torch.cuda.synchronize()
+        assert abs(torch.cuda.mem_get_info()[0] - free0) < (64 << 20)
+        fishlbm.set_alloc_cap(0)
+        a, b = (fishlbm.Domain([fishlbm.env_desc((32, 24, 20), 0.6)], deterministic=True) for _ in range(2))
+        X, dV = inputs.fibonacci_sphere(100, 4.0, (16, 12, 10))
+        U = np.tile(np.float32([0.01, 0, 0]), (100, 1))
+        for d in (a, b):
+            d.set_markers(np.float32(X), U, np.float32(dV))
+            d.step(2)
+        fishlbm.set_alloc_cap(16 << 10)
+        X2, dV2 = inputs.fibonacci_sphere(20000, 6.0, (16, 12, 10))
+        with pytest.raises(fishlbm.FgError) as ei:
+            b.set_markers(np.float32(X2), np.tile(np.float32([0.01, 0, 0]), (20000, 1)), np.float32(dV2))
+        assert ei.value.status == fishlbm.FG_ERR_OOM
+    finally:
+        fishlbm.set_alloc_cap(0)
+    for d in (a, b):
+        d.step(3)
+    assert np.array_equal(a.populations(), b.populations())
+    assert np.array_equal(a.get_body_force_torque(), b.get_body_force_torque())
+
+
 def test_history_checkpoint_and_profile():
     shape = (24, 16, 16)
     d = fishlbm.Domain([fishlbm.env_desc(shape, 0.6)], record_history=8)
