@@ -57,6 +57,7 @@ def lib():
         L.orc_set_threads.argtypes = [i]
         L.orc_set_ib_iters.restype = i
         L.orc_set_ib_iters.argtypes = [vp, i]
+        L.orc_set_body_force.argtypes = [vp, P(d)]
         L.orc_region_momentum.argtypes = [vp, P(d), d, P(d), P(d)]
         L.orc_set_segment_refs.restype = i
         L.orc_set_segment_refs.argtypes = [vp, i, P(d)]
@@ -182,6 +183,17 @@ class Oracle:
         c = _f64(center, (3,))
         lib().orc_region_momentum(self._h, _dp(c), float(radius), _dp(out), ctypes.byref(a))
         return out[:3].copy(), out[3:].copy(), a.value
+
+    def set_body_force(self, G):
+        """External body-force density G (ncell, 3), cell order x fastest,
+        entering the Guo forcing as the IB force does (pins only); None
+        removes it."""
+        if G is None:
+            lib().orc_set_body_force(self._h, None)
+            return
+        g = _f64(G).reshape(self.ncell, 3)
+        if lib().orc_set_body_force(self._h, _dp(g)) != 0:
+            raise MemoryError("oracle: body force")
 
     def set_segment_refs(self, refs):
         """Torque reference point per segment row (nseg, 3); None: common ref."""

@@ -96,6 +96,7 @@ typedef struct {
     double *fs;          /* post-stream populations, [ncell][27] */
     double *rho, *j, *Pi;/* post-stream moments: rho, j[3], Pi[6] (xx,yy,zz,xy,xz,yz) */
     double *fib;         /* spread IB force density, [ncell][3] */
+    double *gext;        /* external body-force density added to fib (pins only), [ncell][3] or NULL */
     int ib_iters;        /* direct-forcing passes M (>= 1) */
     int eq_order;        /* 2, or 3: add the lattice's third-order equilibrium terms */
     int slip;            /* 1: enforce only the normal velocity component */
@@ -158,7 +159,7 @@ void orc_destroy(void *h) {
     orc_t *o = (orc_t *)h;
     if (!o) return;
     free(o->f); free(o->fs); free(o->rho); free(o->j); free(o->Pi); free(o->fib);
-    free(o->X); free(o->U); free(o->dV); free(o->seg); free(o->Fm); free(o->Nrm);
+    free(o->X); free(o->U); free(o->dV); free(o->seg); free(o->Fm); free(o->Nrm); free(o->gext);
     free(o);
 }
 
@@ -517,6 +518,23 @@ static void direct_forcing(orc_t *o, const double *frame) {
  * slip is enforced, dF_l = 2 R_l ((U_l - U~_l).n_l) n_l, so the fluid may
  * slide along the surface.  N: unit normals [n][3] of the current markers
  * (n must equal their count; normalised here). */
+/* External body-force density G[ncell][3] (cell order x fastest), added to
+ * the spread IB force density before the collision, so that it enters the
+ * Guo forcing exactly as the IB force does; NULL removes it.  Not part of
+ * the method: the oracle's pins use it (Kolmogorov flow). */
+int orc_set_body_force(void *h, const double *G) {
+    orc_t *o = (orc_t *)h;
+    if (!G) {
+        free(o->gext);
+        o->gext = NULL;
+        return 0;
+    }
+    if (!o->gext) o->gext = (double *)malloc(sizeof(double) * 3 * o->ncell);
+    if (!o->gext) return -1;
+    memcpy(o->gext, G, sizeof(double) * 3 * o->ncell);
+    return 0;
+}
+
 int orc_set_slip(void *h, int on, int n, const double *N) {
     orc_t *o = (orc_t *)h;
     if (!on) {
@@ -689,6 +707,8 @@ int orc_step(void *h, const double *frame) {
     stream(o);                 /* 1 */
     moments(o);                /* 2 */
     direct_forcing(o, frame);  /* 3-5 and 6a: marker forces, spread F_l dV_l */
+    if (o->gext)               /* an external force density enters like the IB force */
+        for (long c = 0; c < 3 * o->ncell; ++c) o->fib[c] += o->gext[c];
     const double *om = frame + 3;
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < nz; ++z)   /* 6b collide interior cells, 7 boundary cells */

@@ -60,6 +60,30 @@ def test_sphere_in_periodic_box_full_run(variant):
     assert drag[-1] < 0          # the fluid resists the motion
 
 
+def test_fixed_sphere_in_oncoming_flow_parity_and_frame_equivalence():
+    """The fixed sphere in fluid that starts at -U against the oracle, and on
+    the GPU the frame equivalence the oracle pins: its mean drag equals that
+    of the sphere translating at U through fluid at rest."""
+    shape, tau, U, nm = (48, 32, 32), 0.6, 0.02, 400
+    c0 = np.array([20.0, 15.5, 15.5])
+    X0, dV = inputs.fibonacci_sphere(nm, 5.0, c0)
+    p = Pair(shape, tau)
+    p.init(None, np.tile([-U, 0.0, 0.0], (p.o.ncell, 1)))
+    moving = fishlbm.Domain([fishlbm.env_desc(shape, tau)])
+    Fm = []
+    for n in range(120):
+        p.markers(X0, np.zeros((nm, 3)), dV)
+        p.step()
+        moving.set_markers(np.float32(X0 + np.array([U * n, 0.0, 0.0])), np.tile(np.float32([U, 0, 0]), (nm, 1)),
+                           np.float32(dV))
+        moving.step(1)
+        Fm.append(moving.get_body_force_torque()[-1, 0])
+    assert_parity(p.errors(), keys=("rho", "u", "pop", "force", "torque"))
+    Ff = np.array([h[-1, 0] for h in p.force_hist_g])[40:]
+    Fm = np.array(Fm[40:])
+    assert abs(Fm.mean() - Ff.mean()) < 2e-4 * abs(Ff.mean())
+
+
 def _fish_case(shape, tau, length, n_markers, steps, seed, amps=None, variant="auto", ib_iters=1):
     fish = inputs.fish_for_grid(shape, length, n_markers, amplitudes=amps)
     traj = inputs.FrameTrajectory(seed, inputs.domain_centre(shape))

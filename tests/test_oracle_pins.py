@@ -266,6 +266,64 @@ def test_mass_conserved_periodic_with_ib_and_frame():
     assert abs(o.mass_deviation() - m1) < 1e-9
 
 
+@pytest.mark.parametrize("tau", [0.6, 0.8])
+def test_kolmogorov_flow_steady_amplitude(tau):
+    """Kolmogorov flow: a body force G_x = G0 sin(k y) in a periodic box
+    drives, at steady state, u_x = G0 / (rho nu k^2) sin(k y) with
+    nu = (tau - 1/2)/3 (the Navier-Stokes solution of unidirectional shear
+    flow).  The oracle's profile is exactly sinusoidal, u_y and rho stay
+    uniform, and the amplitude approaches the closed form at second order in
+    k (measured: relative error 6.4e-4 -> 1.7e-4 at tau = 0.8, 4.5e-3 ->
+    1.1e-3 at tau = 0.6 from 32 to 64 cells per wavelength).  A wrong
+    viscosity, force factor or sign fails by orders of magnitude."""
+    G0 = 1e-5
+    nu = (tau - 0.5) / 3.0
+    errs = []
+    for N in (32, 64):
+        k = 2.0 * math.pi / N
+        o = oracle.Oracle((1, N, 1), tau)
+        y = np.arange(N)
+        G = np.zeros((N, 3))
+        G[:, 0] = G0 * np.sin(k * y)
+        o.set_body_force(G)
+        o.step(n=int(12.0 / (nu * k * k)))          # transients decay as exp(-nu k^2 t)
+        rho, u = o.fields()
+        A = 2.0 / N * np.sum(u[:, 0] * np.sin(k * y))
+        assert np.abs(u[:, 0] - A * np.sin(k * y)).max() <= 1e-9 * A
+        assert np.abs(u[:, 1:]).max() < 1e-12 and np.abs(rho - 1.0).max() < 1e-10
+        errs.append(A / (G0 / (nu * k * k)) - 1.0)
+    assert abs(errs[1]) < 2e-3
+    assert 3.5 < errs[0] / errs[1] < 4.5
+
+
+def test_moving_sphere_and_oncoming_flow_feel_the_same_drag():
+    """Frame equivalence (the paper's Fig. 3 argument, in its Galilean form):
+    a sphere translating at U through fluid at rest, and the same sphere held
+    fixed in fluid that starts at -U, are the same flow seen from two frames,
+    so the drag on the body agrees.  In the oracle it does so to 1e-5
+    relative on average over steps 40..120; step by step the moving sphere's
+    sub-cell offset changes the delta-kernel weights, a fluctuation of well
+    under 1%.  A sign or frame error in the marker velocity breaks the
+    agreement by orders of magnitude."""
+    shape, tau, U, nm = (48, 32, 32), 0.6, 0.02, 400
+    c0 = np.array([20.0, 15.5, 15.5])
+    X0, dV = inputs.fibonacci_sphere(nm, 5.0, c0)
+    a, b = oracle.Oracle(shape, tau), oracle.Oracle(shape, tau)
+    b.init_fields(None, np.tile([-U, 0.0, 0.0], (a.ncell, 1)))
+    Fa, Fb = [], []
+    for n in range(120):
+        a.set_markers(X0 + np.array([U * n, 0.0, 0.0]), np.tile([U, 0.0, 0.0], (nm, 1)), dV)
+        a.step()
+        b.set_markers(X0, np.zeros((nm, 3)), dV)
+        b.step()
+        Fa.append(a.force_torque()[-1, 0])
+        Fb.append(b.force_torque()[-1, 0])
+    Fa, Fb = np.array(Fa[40:]), np.array(Fb[40:])
+    assert np.all(Fb < 0)                                   # drag along -x, against the relative motion
+    assert abs(Fa.mean() - Fb.mean()) < 1e-4 * abs(Fb.mean())
+    assert np.abs(Fa - Fb).max() < 1e-2 * abs(Fb.mean())
+
+
 def test_uniform_body_force_momentum_gain():
     """A uniform frame acceleration p'' is the uniform body force -rho p'':
     the total momentum grows by exactly -p'' M per step."""
