@@ -17,7 +17,8 @@
 // deviation from the fluid at rest) in storage type S; slot = x + P (y + ny z)
 // with the row pitch P = nx rounded up to a multiple of 8, so every row starts
 // on a 32-byte (FP32) / 16-byte (FP16) boundary.  Slots x >= nx are padding
-// and never read.  Arithmetic is FP32; reductions end in FP64.
+// and never read.  Arithmetic is FP32; the force/torque and mass sums are
+// compensated FP32 pairs, evaluated in FP64 on the host.
 #pragma once
 
 #include "async_copy.cuh"
