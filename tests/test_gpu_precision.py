@@ -1,8 +1,8 @@
 """Reduced-precision population storage (FP16, BF16) against the FP64 oracle.
 
 Populations are stored as h_i = s_i (f_i - w_i) with a fixed power-of-two
-scale per velocity class; all arithmetic stays FP32 and the reductions end in
-FP64.  The tolerances below were predeclared as FP16 <= 1e-2 and BF16 <= 1e-1
+scale per velocity class; all arithmetic stays FP32 and the force/torque
+reductions are compensated FP32 pairs evaluated in FP64.  The tolerances below were predeclared as FP16 <= 1e-2 and BF16 <= 1e-1
 (relative L2 of velocity and of the body-force history), then refined once
 from the measured errors and frozen before the large-sphere run:
 
@@ -89,3 +89,44 @@ def test_large_sphere_reduced_storage_tracks_fp32():
         u, F = large_sphere_run(storage, 1000)
         assert rel_l2(u, u32) <= TOL[storage], (storage, rel_l2(u, u32))
         assert rel_l2(F, F32) <= TOL[storage], (storage, rel_l2(F, F32))
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("odd", [False, True])
+def test_batched_reduced_storage_matches_separate_oracles(storage, odd):
+    """Three environments of different sizes, faces, tau and frames in one
+    16-bit domain against their own FP64 oracles, with the per-dtype bars:
+    every row length even (the staged kernel updates two cells per thread and
+    switches environment between row groups), or one odd (one cell per
+    thread)."""
+    import oracle
+    from oracle import FREESLIP, PERIODIC
+    shapes = [(40, 24, 24), (32, 32, 16), (21 if odd else 22, 20, 28)]
+    taus = [0.52, 0.6, 0.8]
+    faces = [OPEN_X, (PERIODIC,) * 6, (PERIODIC, PERIODIC, FREESLIP, FREESLIP, PERIODIC, PERIODIC)]
+    u_in = np.float32([0.02, 0.0, 0.0]).astype(np.float64)
+    envs = [fishlbm.env_desc(sh, t, f, u_in, 1.0, u_in) for sh, t, f in zip(shapes, taus, faces)]
+    dom = fishlbm.Domain(envs, storage=storage, variant="staged512")
+    ors = [oracle.Oracle(sh, t, faces=f, u_in=u_in) for sh, t, f in zip(shapes, taus, faces)]
+    for o in ors:
+        o.init_fields(None, np.tile(u_in, (o.ncell, 1)))
+    for e, sh in enumerate(shapes):
+        X, dV = inputs.fibonacci_sphere(80 + 20 * e, 3.0, (sh[0] / 2, sh[1] / 2, sh[2] / 2))
+        U = np.tile([0.01 * (e + 1), 0.0, -0.005], (X.shape[0], 1))
+        X32, U32, dV32 = (np.asarray(a, np.float32) for a in (X, U, dV))
+        dom.set_markers(X32, U32, dV32, env=e)
+        ors[e].set_markers(X32.astype(float), U32.astype(float), dV32.astype(float))
+    trajs = [inputs.FrameTrajectory(200 + e, inputs.domain_centre(sh)) for e, sh in enumerate(shapes)]
+    Fg, Fo = [[] for _ in shapes], [[] for _ in shapes]
+    for n in range(60):
+        frs = [np.float32(t.at(n)).astype(np.float64) for t in trajs]
+        dom.step(1, [fishlbm.frame_from_array(f) for f in frs])
+        for e in range(3):
+            ors[e].step(frs[e])
+            Fg[e].append(dom.get_body_force_torque(env=e)[-1])
+            Fo[e].append(ors[e].force_torque()[-1])
+    for e in range(3):
+        _, uo = ors[e].fields()
+        _, ug = dom.fields(env=e)
+        assert rel_l2(ug, uo) <= TOL[storage], (e, rel_l2(ug, uo))
+        assert rel_l2(np.array(Fg[e]), np.array(Fo[e])) <= TOL[storage], e
