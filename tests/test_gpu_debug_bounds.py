@@ -6,8 +6,9 @@ kernel checks the indices it computes and records a flag instead of making
 an out-of-range access.  A child process loads it (FISHLBM_LIB) and runs
 tiny periodic and open domains through every stream-collide variant and
 option (multi-direct forcing, deterministic spread, slip forcing, third-order
-equilibrium, FP16 storage, several environments, region momentum, 1- and
-2-cell domains) against the oracle; no flag may be set and the FP32 cases
+equilibrium, FP16/BF16 storage with two cells per thread and one, several
+environments, fg_step_io, region momentum, 1- and 2-cell domains) against
+the oracle; no flag may be set and the FP32 cases
 must stay within the parity bar.
 """
 import json
@@ -69,6 +70,16 @@ for st in ("f16", "bf16"):
     g = fishlbm.Domain([fishlbm.env_desc((8, 8, 8), 0.7)], storage=st, variant="staged512")
     g.set_markers(np.float32(X), np.zeros((4, 3), np.float32), np.float32(dV))
     g.step(10)
+    # two cells per thread with open x faces and environment switches (even
+    # rows), and one cell per thread (an odd row)
+    for nx in (10, 9):
+        h = fishlbm.Domain([fishlbm.env_desc((8, 8, 8), 0.7),
+                            fishlbm.env_desc((nx, 7, 6), 0.7, OPEN, (0.01, 0, 0), 1.0, (0.01, 0, 0))],
+                           storage=st, variant="staged512")
+        h.set_markers(np.float32(X), np.zeros((4, 3), np.float32), np.float32(dV), env=0)
+        h.set_markers(np.float32([[4.3, 3.1, 2.6]]), np.zeros((1, 3), np.float32), np.float32([1.0]), env=1)
+        h.step_io(np.float32(np.concatenate([X, [[4.4, 3.1, 2.6]]])), np.zeros((5, 3), np.float32))
+        h.step(5, [fishlbm.make_frame(acc=(1e-5, 0, 0), omega=(0, 1e-4, 0))] * 2)
 for shape in ((1, 1, 1), (2, 1, 1)):
     t = fishlbm.Domain([fishlbm.env_desc(shape, 0.8)])
     t.step(3)
