@@ -93,6 +93,14 @@ MUTANTS = {
     "outflow_density_extrapolated": (
         "rb = o->rho_out;", "rb = rf;",
         "test_nee_reaches_uniform_inflow_from_rest"),
+    "collision_force_shift_dropped": (
+        "v[a] = j[a] / rho + 0.5 * a0[a] + fib[a] / (2.0 * rho);",
+        "v[a] = j[a] / rho + 0.5 * a0[a] + 0.0 * fib[a] / (2.0 * rho);",
+        "test_moving_sphere_and_oncoming_flow_feel_the_same_drag"),
+    "marker_velocity_halved": (
+        "dF[3 * l + a] = 2.0 * Ri[3 * l] * (o->U[3 * l + a] - Ui[3 * l + a]);",
+        "dF[3 * l + a] = 2.0 * Ri[3 * l] * (0.5 * o->U[3 * l + a] - Ui[3 * l + a]);",
+        "test_moving_sphere_and_oncoming_flow_feel_the_same_drag"),
     "nee_nonequilibrium_dropped": (
         "o->f[cb * Q + i] = feq[i] + (1.0 - 1.0 / o->tau) * fneq[i];",
         "o->f[cb * Q + i] = feq[i];",
