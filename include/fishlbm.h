@@ -229,14 +229,17 @@ fg_status fg_get_body_force_torque(fg_domain* d, int env, double* out);
 
 /* One two-way coupled step in one call, for a loop in which the body's next
  * pose depends on the force just computed (Eq. 1): the new positions and
- * velocities of all environments' markers (as fg_set_markers_all; X and U
- * NULL keep the current ones), one step with `frames` (as fg_step with
+ * velocities of all environments' markers (as fg_set_markers_all: X and U
+ * float [n][3], n the total of the counts of each environment's last
+ * fg_set_markers, environment after environment; NULL keeps the current
+ * ones), one step with `frames` (as fg_step with
  * n_steps = 1), then the force/torque rows of every environment read back
  * (as fg_get_body_force_torque, environment after environment: (n_seg_e + 1)
  * x 6 FP64 values each, so out holds sum_e (n_seg_e + 1) * 6).  X, U: host
  * or device (device_ptrs); frames, out: host.  The same checks and errors as
  * those calls; nothing is launched when a check fails.  One synchronisation
- * at the end (the readback lands in pinned memory). */
+ * at the end (the step's reduction writes the rows to mapped pinned memory,
+ * so no copy is issued). */
 fg_status fg_step_io(fg_domain* d, const float* X, const float* U, int device_ptrs, const fg_frame* frames,
                      double* out);
 

@@ -351,6 +351,9 @@ class Domain:
         pX = pU = None
         dev = False
         if X is not None:
+            n = sum(self.nmark)
+            if tuple(X.shape) != (n, 3) or tuple(U.shape) != (n, 3):
+                raise ValueError("X and U must be (%d, 3): every environment's markers, in order" % n)
             pX, devX, kX = _ptr_and_keep(X, np.float32)
             pU, devU, kU = _ptr_and_keep(U, np.float32)
             if devX != devU:

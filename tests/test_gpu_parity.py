@@ -801,6 +801,8 @@ def test_step_io_equals_separate_calls(n_envs):
             assert np.array_equal(a.populations(e), d.populations(e))
     with pytest.raises(ValueError):
         b.step_io(Xall, None)
+    with pytest.raises(ValueError):
+        b.step_io(Xall[:-1], Uall[:-1])                    # the binding checks the marker count
 
 
 @pytest.mark.parametrize("variant", ["plain", "staged"])
