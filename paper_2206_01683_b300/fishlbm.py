@@ -211,6 +211,13 @@ def env_desc(shape, tau, faces=(FG_PERIODIC,) * 6, u_in=(0.0, 0.0, 0.0), rho0=1.
     return e
 
 
+def _check_shape(name, a, shape):
+    """The C ABI takes bare pointers: a wrong shape would make it read past
+    the caller's array, so the binding refuses it."""
+    if a is not None and tuple(a.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, not %s" % (name, tuple(shape), tuple(a.shape)))
+
+
 def _ptr_and_keep(a, dtype):
     """(pointer, is_device, keepalive) for a numpy array or a torch tensor
     (a CUDA tensor is passed as a device pointer, a CPU tensor, e.g. pinned,
@@ -282,6 +289,10 @@ class Domain:
 
     def set_markers(self, X, U, dV=None, seg=None, n_seg=1, ref=None, env=0):
         n = int(X.shape[0])
+        _check_shape("X", X, (n, 3))
+        _check_shape("U", U, (n, 3))
+        _check_shape("dV", dV, (n,))
+        _check_shape("seg", seg, (n,))
         pX, devX, kX = _ptr_and_keep(X, np.float32)
         pU, devU, kU = _ptr_and_keep(U, np.float32)
         pd, devd, kd = _ptr_and_keep(dV, np.float32)
@@ -307,6 +318,8 @@ class Domain:
         """Positions and velocities (n_total, 3) of all environments' markers,
         environment after environment (numpy, torch CPU or CUDA tensors)."""
         n = int(X.shape[0])
+        _check_shape("X", X, (n, 3))
+        _check_shape("U", U, (n, 3))
         pX, devX, kX = _ptr_and_keep(X, np.float32)
         pU, devU, kU = _ptr_and_keep(U, np.float32)
         if devX != devU:
@@ -326,6 +339,7 @@ class Domain:
         """Unit normals (n, 3) of env's current markers (slip forcing);
         numpy, torch CPU or CUDA tensors."""
         n = int(N.shape[0])
+        _check_shape("N", N, (n, 3))
         p, dev, keep = _ptr_and_keep(N, np.float32)
         _check(lib().fg_set_marker_normals(self.h, env, n, p, 1 if dev else 0))
         self._keep_n = keep

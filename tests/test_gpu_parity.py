@@ -242,6 +242,12 @@ def test_segment_count_and_ids_are_checked():
     d.set_markers(X, U, dV, seg=(np.arange(40) % 16).astype(np.int32), n_seg=16)
     d.step(1)
     assert d.get_body_force_torque().shape == (17, 6)
+    # shapes the bare-pointer ABI cannot check are refused by the binding
+    for bad in ((X[:, :2], U, dV), (X, U[:39], dV), (X, U, dV[:39])):
+        with pytest.raises(ValueError):
+            d.set_markers(*bad)
+    with pytest.raises(ValueError):
+        d.set_markers_all(X.reshape(-1), U.reshape(-1))
 
 
 @pytest.mark.parametrize("M", [1, 3])
