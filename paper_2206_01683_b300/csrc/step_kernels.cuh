@@ -478,10 +478,13 @@ k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __res
                  float4* __restrict__ fib, const uint32_t* __restrict__ stamps, const StepState* __restrict__ st,
                  Pair32* __restrict__ mass_part) {
     __shared__ float wsum[K1_THREADS / 32];
+    __shared__ CellConsts C;   // the block's environment constants, read by every cell
     const uint32_t stamp = st->stamp;
     const int b = blockIdx.x;
     const int e = n_envs > 1 ? env_of<&EnvDev::block0>(envs, n_envs, b) : 0;
     const EnvDev& E = envs[e];
+    if (threadIdx.x == 0) C = load_consts(E, frames[e]);
+    __syncthreads();
     const uint32_t c = (uint32_t)(b - E.block0) * K1_THREADS + threadIdx.x;
     float drout = 0.0f;
     if (c < E.nslot) {
@@ -499,8 +502,7 @@ k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __res
             const uint32_t p = (uint32_t)((int)c + sx + (sy + sz * E.n[1]) * E.P);
             const PullOffsets o = pull_offsets(E, px, py, pz);
             const Moments m = pull_moments<S, true>(gin + E.pop_off, E.nslot, p, o);
-            drout = update_cell<S, EQ3>(load_consts(E, frames[e]), m, x, y, z, sx, sy, sz, fx, fy, fz,
-                                        gout + E.pop_off, c);
+            drout = update_cell<S, EQ3>(C, m, x, y, z, sx, sy, sz, fx, fy, fz, gout + E.pop_off, c);
         }
     }
     const float t = block_sum_f32(drout, wsum);
