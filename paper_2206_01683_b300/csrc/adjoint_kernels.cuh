@@ -152,13 +152,15 @@ k_adj_tiles(const float* __restrict__ f, const float* __restrict__ lam, const En
             const FrameDev* __restrict__ frames, const float4* __restrict__ fib, const uint32_t* __restrict__ stamps,
             const StepState* __restrict__ st, float* __restrict__ lfib) {
     const EnvDev& E = envs[0];
+    __shared__ CellConsts C;   // loaded once per block, read by every cell
+    if (threadIdx.x == 0) C = load_consts(E, frames[0]);
+    __syncthreads();
     const uint32_t c = blockIdx.x * K1_THREADS + threadIdx.x;
     if (c >= E.nslot) return;
     if (__ldg(stamps + E.stamp_off + (c >> 5)) != st->stamp) return;
     int x, y, z;
     slot_xyz(E, c, x, y, z);
     if (x >= E.n[0]) return;
-    const CellConsts C = load_consts(E, frames[0]);
     const Moments m = adj_forward_moments(E, f, c, x, y, z);
     const float4 f4 = fib[c];
     const float fb[3] = {f4.x, f4.y, f4.z};
@@ -317,12 +319,14 @@ k_adj_stream_collide(const float* __restrict__ f, const float* __restrict__ lam_
                      const uint32_t* __restrict__ stamps, const StepState* __restrict__ st,
                      float* __restrict__ lfib, float* __restrict__ lrho, float* __restrict__ lut) {
     const EnvDev& E = envs[0];
+    __shared__ CellConsts C;   // loaded once per block, read by every cell
+    if (threadIdx.x == 0) C = load_consts(E, frames[0]);
+    __syncthreads();
     const uint32_t c = blockIdx.x * K1_THREADS + threadIdx.x;
     if (c >= E.nslot) return;
     int x, y, z;
     slot_xyz(E, c, x, y, z);
     if (x >= E.n[0]) return;
-    const CellConsts C = load_consts(E, frames[0]);
     const bool stamped = __ldg(stamps + E.stamp_off + (c >> 5)) == st->stamp;
     float fb[3] = {0.f, 0.f, 0.f}, lr = 0.f, lu[3] = {0.f, 0.f, 0.f};
     if (stamped) {
