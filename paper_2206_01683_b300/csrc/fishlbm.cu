@@ -154,6 +154,7 @@ struct fg_domain {
     int staged_grid = 0;                 // persistent blocks of the staged kernel
     int staged_gc = 256;                 // staged: slots per population in shared memory
     bool staged_pair = false;            // staged: two neighbouring cells per thread
+    bool plain_pair = false;             // plain: two neighbouring cells per thread
     size_t staged_smem = 0;
     size_t mass_part_cap = 0;
     int max_P = 8;
@@ -410,6 +411,11 @@ void enqueue_k1_order(fg_domain* d, const typename S::raw* gin, typename S::raw*
     } else if (d->k1 == K1_STAGED512) {
         enqueue_staged<S, 512, EQ3>(d, gin, gout, s);
     } else {
+        if (d->plain_pair)
+            k_stream_collide<S, EQ3, true><<<d->total_blocks, K1_THREADS, 0, s>>>(gin, gout, d->d_env, d->d_frame,
+                                                                              d->n_envs, d->fib, d->stamps,
+                                                                              d->d_state, d->mass_part);
+        else
         k_stream_collide<S, EQ3><<<d->total_blocks, K1_THREADS, 0, s>>>(gin, gout, d->d_env, d->d_frame,
                                                                         d->n_envs, d->fib, d->stamps, d->d_state,
                                                                         d->mass_part);
@@ -596,6 +602,22 @@ fg_status configure_k1(fg_domain* d, int v, bool allocate) {
     d->staged_pair = d->staged && d->esize == 2;
     for (int e = 0; e < d->n_envs; ++e)
         if (d->env[e].n[0] % 2 != 0) d->staged_pair = false;
+    // the plain kernel takes two cells per thread when every row length is
+    // even: its blocks cover 2 x 256 slots
+    d->plain_pair = !d->staged;
+    for (int e = 0; e < d->n_envs; ++e)
+        if (d->env[e].n[0] % 2 != 0) d->plain_pair = false;
+    {
+        const unsigned per_block = (d->plain_pair ? 2u : 1u) * K1_THREADS;
+        int block0 = 0;
+        for (int e = 0; e < d->n_envs; ++e) {
+            EnvDev& E = d->env[e];
+            E.block0 = block0;
+            E.nblocks = (int)((E.nslot + per_block - 1) / per_block);
+            block0 += E.nblocks;
+        }
+        d->total_blocks = block0;
+    }
     int group0 = 0;
     for (int e = 0; e < d->n_envs; ++e) {
         EnvDev& E = d->env[e];

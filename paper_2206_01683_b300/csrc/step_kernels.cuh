@@ -471,7 +471,7 @@ __device__ __forceinline__ float block_sum_f32(float v, float* wsum) {
 }
 
 // Plain variant: one thread per slot, direct loads.
-template <class S, bool EQ3 = false>
+template <class S, bool EQ3 = false, bool PAIR = false>
 __global__ void __launch_bounds__(K1_THREADS)
 k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __restrict__ gout,
                  const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, int n_envs,
@@ -485,8 +485,37 @@ k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __res
     const EnvDev& E = envs[e];
     if (threadIdx.x == 0) C = load_consts(E, frames[e]);
     __syncthreads();
-    const uint32_t c = (uint32_t)(b - E.block0) * K1_THREADS + threadIdx.x;
     float drout = 0.0f;
+    if constexpr (PAIR) {
+        // cells x (even) and x + 1 of one row; every row length is even, so
+        // both are real cells and share a 32-slot tile
+        const uint32_t c = ((uint32_t)(b - E.block0) * K1_THREADS + threadIdx.x) * 2u;
+        if (c < E.nslot) {
+            const uint32_t row = fdiv(c, E.div_P);
+            const int x = (int)(c - row * (uint32_t)E.P);
+            if (x < E.n[0]) {
+                const uint32_t zz = fdiv(row, E.div_ny);
+                const int y = (int)(row - zz * (uint32_t)E.n[1]);
+                const int z = (int)zz;
+                float fa[3], fb[3];
+                take_ib_force(E, fib, stamps, stamp, c, fa[0], fa[1], fa[2]);
+                take_ib_force(E, fib, stamps, stamp, c + 1, fb[0], fb[1], fb[2]);
+                const int sxa = inward(E, 0, x), sxb = inward(E, 0, x + 1);
+                const int sy = inward(E, 1, y), sz = inward(E, 2, z);
+                const int ry = (sy + sz * E.n[1]) * E.P;
+                const Moments ma = pull_moments<S, true>(gin + E.pop_off, E.nslot, (uint32_t)((int)c + sxa + ry),
+                                                         pull_offsets(E, x + sxa, y + sy, z + sz));
+                const Moments mb = pull_moments<S, true>(gin + E.pop_off, E.nslot,
+                                                         (uint32_t)((int)c + 1 + sxb + ry),
+                                                         pull_offsets(E, x + 1 + sxb, y + sy, z + sz));
+                const Herm ha = cell_coeffs<S, EQ3>(C, ma, x, y, z, sxa, sy, sz, fa[0], fa[1], fa[2]);
+                const Herm hb = cell_coeffs<S, EQ3>(C, mb, x + 1, y, z, sxb, sy, sz, fb[0], fb[1], fb[2]);
+                drout = ha.drout + hb.drout;
+                emit_pair<S, EQ3>(ha, hb, gout + E.pop_off, E.nslot, c);
+            }
+        }
+    } else {
+    const uint32_t c = (uint32_t)(b - E.block0) * K1_THREADS + threadIdx.x;
     if (c < E.nslot) {
         const uint32_t row = fdiv(c, E.div_P);
         const int x = (int)(c - row * (uint32_t)E.P);
@@ -504,6 +533,7 @@ k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __res
             const Moments m = pull_moments<S, true>(gin + E.pop_off, E.nslot, p, o);
             drout = update_cell<S, EQ3>(C, m, x, y, z, sx, sy, sz, fx, fy, fz, gout + E.pop_off, c);
         }
+    }
     }
     const float t = block_sum_f32(drout, wsum);
     if (threadIdx.x == 0) {
