@@ -32,13 +32,16 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS and % HBM roofline per step (FP32 vs FP16-storage vs batched), 1×B300"
 OPEN_X = (1, 2, 3, 3, 3, 3)   # inlet, outflow, free-slip walls
 
-# DRAM traffic of k_stream_collide per cell update from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum divided by the cells of the
-# launch), valid only for the kernel source it was taken on.
+# DRAM traffic of the stream-collide kernel per cell update from an ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum divided by the cells of
+# the launch), keyed by the kernel source it was taken on and the variant in
+# use, and valid only for those.
 NCU_TRAFFIC = {
-    # k_stream_collide_staged<StoreF32, 256, 4, false, false>, swimmer channel: 440.25 MB read +
-    # 400.00 MB written per launch over 4,194,304 cells
-    "651af01f53672eb3f14fd9c95afe4ac4721a71dfe1fa903670bab90afc3f2f43": 200.33,
+    # k_stream_collide<StoreF32, false, true> (two cells per thread), swimmer channel:
+    # 442.12 MB read + 401.48 MB written per launch over 4,194,304 cells
+    ("fe3a819e76f0826faff29e8cc215d570880e3bc9e75d3a8b2b0684af87ab0f69", "plain"): 201.13,
+    # k_stream_collide_staged<StoreF32, 256, 4, false, false>: 440.41 MB read + 400.25 MB written
+    ("fe3a819e76f0826faff29e8cc215d570880e3bc9e75d3a8b2b0684af87ab0f69", "staged256"): 200.43,
 }
 
 
@@ -536,7 +539,7 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return None
     achieved = algo_bytes / (k1_ms * 1e-3) / 1e9
-    bpc = NCU_TRAFFIC.get(kernel_source_hash()) if args.storage == "f32" else None
+    bpc = NCU_TRAFFIC.get((kernel_source_hash(), dom.stream_collide_variant())) if args.storage == "f32" else None
     mlups = world * ncell * K / (ms * 1e-3) / 1e6
     h2d = 2 * X[0].nbytes + 100   # X, U and the frame (25 floats)
     d2h = out.size * 8 + 4        # the force/torque rows as FP32 pairs, and the status word
