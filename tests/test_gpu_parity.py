@@ -604,14 +604,14 @@ def test_graph_replay_matches_direct_launches():
 @pytest.mark.parametrize("storage", ["f16", "bf16", "f32"])
 @pytest.mark.parametrize("nx", [64, 63])
 def test_stream_collide_variants_agree(storage, nx):
-    """One cell per thread (plain kernel) and the staged kernels -- which take
-    two neighbouring cells per thread with 16-bit storage when every row
-    length is even (nx = 64), one otherwise (nx = 63) -- agree to rounding:
-    the kernels inline the same per-cell arithmetic, and the compiler's
-    choice of fused multiply-adds may differ between them (measured: FP32
-    deviations differ by at most a few 1e-9, FP16 stores in about 1e-4 of the
-    entries).  Open x faces, a moving frame, markers with the deterministic
-    spread, 12 steps."""
+    """The plain and staged stream-collide kernels agree to rounding, with
+    two neighbouring cells per thread where every row length is even (nx =
+    64: the plain kernel in every storage, the staged kernels with 16-bit
+    storage) and one otherwise (nx = 63).  The kernels inline the same
+    per-cell arithmetic, and the compiler's choice of fused multiply-adds
+    may differ between them (measured: FP32 deviations differ by at most a
+    few 1e-9, FP16 stores in about 1e-4 of the entries).  Open x faces, a
+    moving frame, markers with the deterministic spread, 12 steps."""
     shape = (nx, 20, 18)
     rho, u = inputs.random_fields(shape, seed=61, u_amp=0.02, rho_amp=0.01)
     c = np.array([nx / 2.0, 10.0, 9.0])
