@@ -387,6 +387,47 @@ def test_batched_environments_match_separate_oracles(variant):
         assert rel_l2(dom.get_body_force_torque(env=e), ors[e].force_torque()) <= TOL_F32, e
 
 
+@pytest.mark.parametrize("variant", ["plain", "staged", "staged512"])
+@pytest.mark.parametrize("even", [True, False])
+def test_many_small_environments(variant, even):
+    """96 small environments of four shapes and mixed faces in one domain
+    (environment tables, binary searches, per-environment blocks and row
+    groups; with every row length even the kernels take two cells per
+    thread), each against its own oracle after 12 steps, two markers in
+    every periodic environment."""
+    rng = np.random.default_rng(inputs.seed_for(9))
+    shapes_even = [(8, 8, 8), (10, 7, 6), (12, 5, 7), (16, 4, 4)]
+    shapes = shapes_even if even else [(8, 8, 8), (9, 7, 6), (12, 5, 7), (15, 4, 4)]
+    faces_set = [(PERIODIC,) * 6, OPEN_X, (PERIODIC, PERIODIC, FREESLIP, FREESLIP, PERIODIC, PERIODIC)]
+    envs, ors, periodic_envs = [], [], []
+    for e in range(96):
+        sh = shapes[int(rng.integers(0, 4))]
+        fc = faces_set[int(rng.integers(0, 3))]
+        if fc == faces_set[0]:
+            periodic_envs.append(e)
+        tau = float(rng.uniform(0.55, 0.9))
+        envs.append(fishlbm.env_desc(sh, tau, fc, f32((0.01, 0, 0)), 1.0, f32((0.01, 0, 0))))
+        o = oracle.Oracle(sh, tau, faces=fc, u_in=f32((0.01, 0, 0)))
+        o.init_fields(None, np.tile(f32((0.01, 0, 0)), (o.ncell, 1)))
+        ors.append(o)
+    dom = fishlbm.Domain(envs, variant=variant)
+    for e in periodic_envs:
+        X = f32(np.array([[3.3, 3.1, 2.6], [4.2, 2.7, 2.4]]))
+        U = f32(np.array([[0.01, 0.0, 0.0], [0.0, 0.005, 0.0]]))
+        dV = f32(np.array([1.0, 1.0]))
+        dom.set_markers(np.float32(X), np.float32(U), np.float32(dV), env=e)
+        ors[e].set_markers(X, U, dV)
+    for n in range(12):
+        dom.step(1)
+        for o in ors:
+            o.step()
+    for e in range(96):
+        ro, uo = ors[e].fields()
+        rg, ug = dom.fields(env=e)
+        assert rel_l2(rg, ro) <= TOL_F32 and rel_l2(ug, uo) <= TOL_F32, (e, rel_l2(ug, uo))
+    dom.get_body_force_torque(env=0)
+
+
 # ------------------------------------------------------------ edge cases
 
 @pytest.mark.parametrize("variant", VARIANTS)
