@@ -70,7 +70,7 @@ SIGNATURES = {
     "fg_region_momentum": (_I, [_V, _I, _P(_D), _D, _P(_D), _P(_D)]),
     "fg_step": (_I, [_V, _I, _P(fg_frame)]),
     "fg_get_body_force_torque": (_I, [_V, _I, _P(_D)]),
-    "fg_step_io": (_I, [_V, _V, _V, _I, _P(fg_frame), _P(_D)]),
+    "fg_step_io": (_I, [_V, _V, _V, _I, _P(fg_frame), _V]),
     "fg_destroy": (None, [_V]),
     "fg_last_error": (ctypes.c_char_p, []),
     "fg_lattice": (_I, [_P(_I), _P(_D)]),
@@ -378,10 +378,18 @@ class Domain:
         if frames is not None:
             if not isinstance(frames, (list, tuple)):
                 frames = [frames]
-            fr = (fg_frame * len(frames))(*[f if isinstance(f, fg_frame) else frame_from_array(f) for f in frames])
+            if len(frames) == 1 and isinstance(frames[0], fg_frame):
+                fr = ctypes.byref(frames[0])   # the per-step case, without building an array
+            else:
+                fr = (fg_frame * len(frames))(*[f if isinstance(f, fg_frame) else frame_from_array(f)
+                                                 for f in frames])
         rows = [self.nseg[e] + 1 for e in range(len(self.nseg))]
-        out = np.zeros((sum(rows), 6))
-        _check(lib().fg_step_io(self.h, pX, pU, 1 if dev else 0, fr, _dp(out)))
+        total = sum(rows)
+        if getattr(self, "_io_out", None) is None or self._io_out.shape[0] != total:
+            self._io_out = np.zeros((total, 6))          # landing buffer, its address cached
+            self._io_addr = self._io_out.ctypes.data
+        _check(lib().fg_step_io(self.h, pX, pU, 1 if dev else 0, fr, self._io_addr))
+        out = self._io_out.copy()
         if len(rows) == 1:
             return out
         return np.split(out, np.cumsum(rows)[:-1])
