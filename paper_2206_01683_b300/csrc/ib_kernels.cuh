@@ -402,12 +402,23 @@ __device__ __forceinline__ void spread_force(const EnvDev& E, const MarkerRef& r
 // deterministic spread (fixed-point sums, converted to fib in a last phase).
 template <class S>
 __global__ void __launch_bounds__(IB_THREADS, 4)
-k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs,
-          const FrameDev* __restrict__ frames, int n_envs, int total_markers, int n_stamps,
+k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs_g,
+          const FrameDev* __restrict__ frames_g, int n_envs, int total_markers, int n_stamps,
           const float* __restrict__ X, const float* __restrict__ U, const float* __restrict__ dV,
           float* __restrict__ Fm, float4* fib, uint32_t* stamps, const StepState* __restrict__ st,
           float4* nodes, unsigned* bar, int ib_iters, float* dF, unsigned long long* fibq,
           const float* __restrict__ Nrm, int* status) {
+    // a single environment's table and frame in shared memory, read by every
+    // marker and node of the launch
+    __shared__ EnvDev sE;
+    __shared__ FrameDev sF;
+    if (n_envs == 1 && threadIdx.x == 0) {
+        sE = envs_g[0];
+        sF = frames_g[0];
+    }
+    __syncthreads();
+    const EnvDev* envs = n_envs == 1 ? &sE : envs_g;
+    const FrameDev* frames = n_envs == 1 ? &sF : frames_g;
     const int lane = threadIdx.x & 31, h = lane & 15;
     const int gw = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int nw = (int)((gridDim.x * blockDim.x) >> 5);
