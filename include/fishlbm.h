@@ -378,11 +378,12 @@ fg_status fg_profile_read(fg_domain* d, double* ms, long long* launches);
 /* Stream-collide variants (the autotuner's candidates). */
 enum { FG_K1_PLAIN = 0, FG_K1_STAGED256 = 1, FG_K1_STAGED512 = 2, FG_K1_NVARIANTS = 3 };
 
-/* Time every stream-collide variant that can run this domain's rows (a few
- * launches each, on the domain's own buffers: the state is not changed) and
- * keep the fastest.  choice (nullable) gets the FG_K1_* kept; ms (nullable,
- * FG_K1_NVARIANTS entries) the mean launch time of each, -1 where not
- * runnable.  Synchronises; graphs are recaptured on the next step. */
+/* Time every stream-collide variant that can run this domain's rows (three
+ * interleaved rounds of five launches each, on the domain's own buffers: the
+ * state is not changed) and keep the fastest.  choice (nullable) gets the
+ * FG_K1_* kept; ms (nullable, FG_K1_NVARIANTS entries) the mean launch time
+ * of each in its fastest round, -1 where not runnable.  Synchronises; graphs
+ * are recaptured on the next step. */
 fg_status fg_autotune(fg_domain* d, int* choice, double* ms);
 
 /* The FG_K1_* variant in use. */
