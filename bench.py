@@ -38,10 +38,10 @@ OPEN_X = (1, 2, 3, 3, 3, 3)   # inlet, outflow, free-slip walls
 # use, and valid only for those.
 NCU_TRAFFIC = {
     # k_stream_collide<StoreF32, false, true> (two cells per thread), swimmer channel:
-    # 442.12 MB read + 401.48 MB written per launch over 4,194,304 cells
-    ("fe3a819e76f0826faff29e8cc215d570880e3bc9e75d3a8b2b0684af87ab0f69", "plain"): 201.13,
-    # k_stream_collide_staged<StoreF32, 256, 4, false, false>: 440.41 MB read + 400.25 MB written
-    ("fe3a819e76f0826faff29e8cc215d570880e3bc9e75d3a8b2b0684af87ab0f69", "staged256"): 200.43,
+    # 442.16 MB read + 401.74 MB written per launch over 4,194,304 cells
+    ("efe9fccc521cd1b30ef22fe507227fc05a01189c496a7f74cfa07bf1aefae4bc", "plain"): 201.20,
+    # k_stream_collide_staged<StoreF32, 256, 4, false, false>: 440.30 MB read + 399.72 MB written
+    ("efe9fccc521cd1b30ef22fe507227fc05a01189c496a7f74cfa07bf1aefae4bc", "staged256"): 200.27,
 }
 
 

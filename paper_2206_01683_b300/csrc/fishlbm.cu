@@ -1,9 +1,9 @@
 // fishlbm.cu -- host runtime and C ABI of the library (declared in
 // include/fishlbm.h).  Owns the device state of a domain: two population
 // buffers (pull scheme), the sparse IB force density with its 32-cell tile
-// stamps, marker arrays, FP64 reduction outputs, and the per-step launch
-// sequence k_ib_step (cooperative) -> k_stream_collide -> k_reduce on one
-// CUDA stream.
+// stamps, marker arrays, the reduction outputs (compensated FP32 pairs), and
+// the per-step launch sequence k_ib_step (cooperative) -> k_stream_collide ->
+// k_reduce (a programmatic dependent of k_stream_collide) on one CUDA stream.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -458,10 +458,25 @@ fg_status enqueue_step_io(fg_domain* d, const typename S::raw* gin, typename S::
     enqueue_k1<S>(d, gin, gout, s);
     if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][1], s));
     if (ev) CK(cudaEventRecord(ev[FG_K_REDUCE][0], s));
-    k_reduce<<<dim3(d->n_envs, RED_ROWS, d->red_z), RED_THREADS, 0, s>>>(
-        d->d_env, d->X, d->Fm, d->dV, d->seg, d->seg_ref, d->mass_part, d->red_partials, d->red_counters,
-        d->n_envs, d->red_z, d->ft, d->mass, d->hist, d->opt.record_history, d->d_state, d->status,
-        d->rb_ft_all_dev, d->rb_status_dev);
+    {
+        // a programmatic dependent of the stream-collide kernel: its marker
+        // sums overlap that kernel's last blocks, the rest waits for it
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)d->n_envs, RED_ROWS, (unsigned)d->red_z);
+        cfg.blockDim = dim3(RED_THREADS);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        CK(cudaLaunchKernelEx(&cfg, k_reduce, (const EnvDev*)d->d_env, (const float*)d->X, (const float*)d->Fm,
+                              (const float*)d->dV, (const int*)d->seg, (const float*)d->seg_ref,
+                              (const Pair32*)d->mass_part, d->red_partials, d->red_counters, d->n_envs, d->red_z,
+                              d->ft, d->mass, d->hist, d->opt.record_history, d->d_state, d->status,
+                              d->rb_ft_all_dev, d->rb_status_dev));
+    }
     if (ev) CK(cudaEventRecord(ev[FG_K_REDUCE][1], s));
     CK(cudaGetLastError());
     return FG_OK;

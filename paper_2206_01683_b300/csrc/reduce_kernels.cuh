@@ -79,34 +79,47 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
     const bool is_mass = y == RED_ROWS - 1;
     if (is_mass ? z >= nch_m : (y > ns || z >= nch_f)) return;
     Pair32 acc[6];
-    if (is_mass) {
-        const int per_block = RED_THREADS * MASS_PER_THREAD;
-        Pair32 v[MASS_PER_THREAD];
-#pragma unroll
-        for (int k = 0; k < MASS_PER_THREAD; ++k) {
-            const int i = z * per_block + k * RED_THREADS + tid;
-            if (i < E.nparts) v[k] = mass_part[E.part0 + i];
-        }
-#pragma unroll
-        for (int k = 0; k < MASS_PER_THREAD; ++k) acc[0].add(v[k]);
-    } else {
+    if (!is_mass) {
+        // The marker forces come from the IB kernel, which completed before
+        // the stream-collide kernel started, so these sums may run while the
+        // stream-collide kernel's last blocks finish (reads through L2).
         const int l = z * RED_THREADS + tid;
         if (l < E.n_markers) {
             const int q = E.marker_off + l;
-            if (y == ns || seg[q] == y) {
-                const float v = -dV[q];
-                const float Fx = Fm[3 * q] * v, Fy = Fm[3 * q + 1] * v, Fz = Fm[3 * q + 2] * v;
+            if (y == ns || __ldcg(seg + q) == y) {
+                const float v = -__ldcg(dV + q);
+                const float Fx = __ldcg(Fm + 3 * q) * v, Fy = __ldcg(Fm + 3 * q + 1) * v,
+                            Fz = __ldcg(Fm + 3 * q + 2) * v;
                 // segment rows about the segment's point, the total row about ref
                 const float* rp = seg_ref + ((size_t)e * MAX_SEG + (y < ns ? y : 0)) * 3;
-                const float px = y < ns ? rp[0] : (float)E.ref[0], py = y < ns ? rp[1] : (float)E.ref[1],
-                            pz = y < ns ? rp[2] : (float)E.ref[2];
-                const float rx = X[3 * q] - px, ry = X[3 * q + 1] - py, rz = X[3 * q + 2] - pz;
+                const float px = y < ns ? __ldcg(rp) : (float)E.ref[0], py = y < ns ? __ldcg(rp + 1) : (float)E.ref[1],
+                            pz = y < ns ? __ldcg(rp + 2) : (float)E.ref[2];
+                const float rx = __ldcg(X + 3 * q) - px, ry = __ldcg(X + 3 * q + 1) - py,
+                            rz = __ldcg(X + 3 * q + 2) - pz;
                 acc[0].add(Fx); acc[1].add(Fy); acc[2].add(Fz);
                 acc[3].add(ry * Fz - rz * Fy);
                 acc[4].add(rz * Fx - rx * Fz);
                 acc[5].add(rx * Fy - ry * Fx);
             }
         }
+    }
+    // Everything below reads the stream-collide kernel's mass sums or writes
+    // what the step's kernels read (the step state), so it waits for that
+    // kernel when launched as its programmatic dependent.
+    wait_prerequisites();
+    if (is_mass) {
+        const int per_block = RED_THREADS * MASS_PER_THREAD;
+        Pair32 v[MASS_PER_THREAD];
+#pragma unroll
+        for (int k = 0; k < MASS_PER_THREAD; ++k) {
+            const int i = z * per_block + k * RED_THREADS + tid;
+            if (i < E.nparts) {
+                v[k].hi = __ldcg(&mass_part[E.part0 + i].hi);
+                v[k].lo = __ldcg(&mass_part[E.part0 + i].lo);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < MASS_PER_THREAD; ++k) acc[0].add(v[k]);
     }
     const int ncomp = is_mass ? 1 : 6;
 #pragma unroll

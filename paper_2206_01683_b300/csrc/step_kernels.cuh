@@ -459,6 +459,15 @@ __device__ __forceinline__ void take_ib_force(const EnvDev& E, float4* __restric
 
 // ------------------------------------------------- K1: stream + collide
 
+// Programmatic dependent launch (PTX griddepcontrol).  A kernel launched with
+// programmatic stream serialization may start once every block of the kernel
+// before it has called allow_dependents (or exited), and must call
+// wait_prerequisites before it reads that kernel's results: the wait returns
+// when the earlier kernel has completed and its writes are visible.  Both
+// are no-ops in a kernel launched without the attribute.
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void wait_prerequisites() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ float block_sum_f32(float v, float* wsum) {
 #pragma unroll
     for (int k = 16; k >= 1; k >>= 1) v += __shfl_xor_sync(0xffffffffu, v, k);
@@ -485,6 +494,9 @@ k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __res
     const EnvDev& E = envs[e];
     if (threadIdx.x == 0) C = load_consts(E, frames[e]);
     __syncthreads();
+    // the step's reduction may start its marker sums once the last wave of
+    // blocks is in (it waits for this kernel before it reads the mass sums)
+    allow_dependents();
     float drout = 0.0f;
     if constexpr (PAIR) {
         // cells x (even) and x + 1 of one row; every row length is even, so
@@ -634,6 +646,7 @@ k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw
         fence_mbar_init();
     }
     __syncthreads();
+    allow_dependents();   // as in k_stream_collide
 
     int g = blockIdx.x;
     if (g < total_groups) {
