@@ -380,7 +380,10 @@ enum { FG_K1_PLAIN = 0, FG_K1_STAGED256 = 1, FG_K1_STAGED512 = 2, FG_K1_NVARIANT
 
 /* Time every stream-collide variant that can run this domain's rows (three
  * interleaved rounds of five launches each, on the domain's own buffers: the
- * state is not changed) and keep the fastest.  choice (nullable) gets the
+ * state is not changed) and keep the fastest, where a staged variant must be
+ * more than 2% faster than the plain one (timed alone the two miss what the
+ * rest of the step adds; whole steps favour the plain kernel by about that
+ * much where the two are level alone).  choice (nullable) gets the
  * FG_K1_* kept; ms (nullable, FG_K1_NVARIANTS entries) the mean launch time
  * of each in its fastest round, -1 where not runnable.  Synchronises; graphs
  * are recaptured on the next step. */

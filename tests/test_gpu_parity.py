@@ -691,7 +691,8 @@ def test_stream_collide_variants_agree(storage, nx):
 
 def test_autotune_keeps_a_runnable_variant_and_the_state():
     """The autotuner times the candidates on the domain's own buffers without
-    changing the state, keeps the fastest, and steps continue identically."""
+    changing the state, keeps the fastest (a staged variant by a margin of
+    more than 2%), and steps continue identically."""
     shape = (96, 40, 24)
     rho, u = inputs.random_fields(shape, seed=51)
     a = fishlbm.Domain([fishlbm.env_desc(shape, 0.6)], variant="plain")
@@ -702,7 +703,9 @@ def test_autotune_keeps_a_runnable_variant_and_the_state():
     before = b.populations()
     kept, ms = b.autotune()
     assert set(ms) == {"plain", "staged256", "staged512"} and all(v > 0 for v in ms.values())
-    assert kept == min(ms, key=ms.get) == b.stream_collide_variant()
+    # a staged variant is kept only when more than 2% faster than the plain one
+    score = {k: (v if k == "plain" else v / 0.98) for k, v in ms.items()}
+    assert kept == min(score, key=score.get) == b.stream_collide_variant()
     assert np.array_equal(b.populations(), before)
     for d in (a, b):
         d.step(4)
