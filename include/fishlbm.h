@@ -69,8 +69,19 @@ typedef struct {
  * STAGED stages the source rows of each row group in shared memory with bulk
  * copies (persistent, double-buffered), 256 slots per population when rows
  * fit, else 512; STAGED512 forces 512.  PLAIN reads global memory directly,
- * one thread per cell.  All compute the same step. */
-typedef enum { FG_KERNEL_AUTO = 0, FG_KERNEL_PLAIN = 1, FG_KERNEL_STAGED = 2, FG_KERNEL_STAGED512 = 3 } fg_kernel_variant;
+ * one thread per cell (two where every row length is even).  FUSED runs the
+ * whole step but its final reduction in one persistent launch: the IB
+ * phases (stamping the marker stencils, node moments, interpolation and
+ * spreading) and PLAIN's cell update taken from one work queue, so that cell
+ * blocks no marker reaches (and, in a batch, other environments' blocks)
+ * proceed while the IB phases run.  All compute the same step. */
+typedef enum {
+    FG_KERNEL_AUTO = 0,
+    FG_KERNEL_PLAIN = 1,
+    FG_KERNEL_STAGED = 2,
+    FG_KERNEL_STAGED512 = 3,
+    FG_KERNEL_FUSED = 4
+} fg_kernel_variant;
 
 #define FG_MAX_IB_ITERS 8
 
@@ -91,7 +102,11 @@ typedef struct {
     int record_history; /* steps of (force, torque, mass) history kept on the
                            device per environment (0 = none), ring buffer */
     int kernel_variant; /* fg_kernel_variant */
-    int autotune;       /* 1 (with kernel_variant AUTO): run fg_autotune at creation */
+    int autotune;       /* 1 (with kernel_variant AUTO): run fg_autotune at the
+                           first fg_step (or fg_step_io / fg_step_state) with
+                           n_steps > 0, so that it times the step with its
+                           markers; that first call synchronises and must not
+                           be made under stream capture */
     int ib_slip;        /* 1: slip (Neumann) direct forcing: only the normal
                            component of the marker slip is enforced,
                            dF = 2 R ((U - U~).n) n, with the unit normals given
@@ -376,17 +391,18 @@ fg_status fg_profile(fg_domain* d, int enable);
 fg_status fg_profile_read(fg_domain* d, double* ms, long long* launches);
 
 /* Stream-collide variants (the autotuner's candidates). */
-enum { FG_K1_PLAIN = 0, FG_K1_STAGED256 = 1, FG_K1_STAGED512 = 2, FG_K1_NVARIANTS = 3 };
+enum { FG_K1_PLAIN = 0, FG_K1_STAGED256 = 1, FG_K1_STAGED512 = 2, FG_K1_FUSED = 3, FG_K1_NVARIANTS = 4 };
 
-/* Time every stream-collide variant that can run this domain's rows (three
- * interleaved rounds of five launches each, on the domain's own buffers: the
- * state is not changed) and keep the fastest, where a staged variant must be
- * more than 2% faster than the plain one (timed alone the two miss what the
- * rest of the step adds; whole steps favour the plain kernel by about that
- * much where the two are level alone).  choice (nullable) gets the
- * FG_K1_* kept; ms (nullable, FG_K1_NVARIANTS entries) the mean launch time
- * of each in its fastest round, -1 where not runnable.  Synchronises; graphs
- * are recaptured on the next step. */
+/* Time every stream-collide variant that can run this domain's rows with the
+ * step's IB work (the IB kernel and the variant's kernel; the fused kernel
+ * does both), three interleaved rounds of five passes each, on the domain's
+ * own buffers with its current markers: the populations, the step count and
+ * the marker forces are not changed.  Keep the fastest, where a staged
+ * variant must be more than 2% faster (whole steps favour the plain kernel by
+ * about that much where the two are level in this timing).  choice
+ * (nullable) gets the FG_K1_* kept; ms (nullable, FG_K1_NVARIANTS entries)
+ * the mean pass time of each in its fastest round, -1 where not runnable.
+ * Synchronises; graphs are recaptured on the next step. */
 fg_status fg_autotune(fg_domain* d, int* choice, double* ms);
 
 /* The FG_K1_* variant in use. */

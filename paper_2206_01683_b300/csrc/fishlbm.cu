@@ -2,8 +2,11 @@
 // include/fishlbm.h).  Owns the device state of a domain: two population
 // buffers (pull scheme), the sparse IB force density with its 32-cell tile
 // stamps, marker arrays, the reduction outputs (compensated FP32 pairs), and
-// the per-step launch sequence k_ib_step (cooperative) -> k_stream_collide ->
-// k_reduce (a programmatic dependent of k_stream_collide) on one CUDA stream.
+// the per-step launch sequence on one CUDA stream: k_ib_step (cooperative)
+// -> k_stream_collide -> k_reduce (a programmatic dependent of
+// k_stream_collide), or with the fused variant k_step_fused (one persistent
+// cooperative launch for the IB phases and the stream-collide blocks) ->
+// k_reduce.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,6 +25,7 @@
 #include "adjoint_kernels.cuh"
 #include "ib_kernels.cuh"
 #include "reduce_kernels.cuh"
+#include "fused_kernels.cuh"
 #include "state_kernels.cuh"
 
 using namespace fl;
@@ -93,9 +97,12 @@ constexpr int PROFILE_CAP = 1 << 14;
 constexpr int MAX_STAGED_P = 512;   // longest row pitch the staged kernel takes
 
 // Stream-collide variants the domain can run (and the autotuner times):
-// the plain kernel, and the staged kernel with 256 or 512 slots per
-// population in shared memory.
-enum { K1_PLAIN = 0, K1_STAGED256 = 1, K1_STAGED512 = 2, K1_NVARIANTS = 3 };
+// the plain kernel, the staged kernel with 256 or 512 slots per population
+// in shared memory, and the fused step kernel (the plain kernel's cell
+// update and the IB phases in one persistent launch).
+enum { K1_PLAIN = 0, K1_STAGED256 = 1, K1_STAGED512 = 2, K1_FUSED = 3, K1_NVARIANTS = 4 };
+static_assert((int)K1_FUSED == (int)FG_K1_FUSED && (int)K1_NVARIANTS == (int)FG_K1_NVARIANTS, "variant ids of the header");
+static_assert(MAX_IB_PASSES == FG_MAX_IB_ITERS, "direct-forcing passes of the fused kernel");
 
 // Blocks per SM the staged kernel is compiled for.  The 512-slot row buffers
 // take 2 x 27 x 512 x sizeof(raw) bytes of shared memory, 110.6 KB in FP32
@@ -150,7 +157,17 @@ struct fg_domain {
     int total_blocks = 0;                // plain stream-collide grid
     int total_groups = 0;                // staged kernel row groups
     int k1 = K1_PLAIN;                   // stream-collide variant in use (K1_*)
-    bool staged = false;                 // k1 != K1_PLAIN
+    bool staged = false;                 // a staged variant
+    int fused_grid = 0;                  // persistent blocks of k_step_fused
+    // work queue of k_step_fused: the segment table (host copy and device),
+    // the queue words and the per-environment completion counters
+    std::vector<WorkSeg> work_host;
+    WorkSeg* work_segs = nullptr;
+    int work_seg_cap = 0;
+    int* work = nullptr;                 // WQ_WORDS
+    int* work_done = nullptr;            // [n_envs][N_SLOTS]
+    bool work_dirty = true;              // the table no longer matches the markers or kernel layout
+    bool autotune_pending = false;       // autotune option: run fg_autotune before the first step
     int staged_grid = 0;                 // persistent blocks of the staged kernel
     int staged_gc = 256;                 // staged: slots per population in shared memory
     bool staged_pair = false;            // staged: two neighbouring cells per thread
@@ -278,7 +295,7 @@ void free_all(fg_domain* d) {
     void* ptrs[] = {d->d_env, d->d_frame, d->pop[0], d->pop[1], d->fib, d->stamps, d->ib_nodes, d->ib_bar,
                     d->fibq, d->mass_part, d->red_partials, d->red_counters, d->d_state,
                     d->X, d->U, d->dV, d->Fm, d->dF, d->Nrm, d->seg, d->seg_ref, d->region_part, d->mk_stage, d->ft, d->mass,
-                    d->hist, d->status};
+                    d->hist, d->status, d->work_segs, d->work, d->work_done};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (d->rb) cudaFreeHost(d->rb);
@@ -386,6 +403,102 @@ void refresh_marker_table(fg_domain* d) {
         begin += d->mk[e].n;
     }
     d->total_markers = begin;
+    d->work_dirty = true;
+}
+
+// Work queue of the fused step kernel for the current markers and kernel
+// layout, in queue order.  One environment's IB phases: MARK, NODE, FORCE,
+// (INTERP, SPREAD) per extra direct-forcing pass, CONVERT (deterministic
+// spread), REDUCE; then its stream-collide blocks (SC).  With several
+// environments the IB phases of environment e + 1 come before the SC blocks
+// of environment e, so they run beside them: IB(0) IB(1) SC(0) IB(2) SC(1)
+// ... SC(n-1).  Every dependency points to earlier items of the same
+// environment.
+void build_work_table(fg_domain* d) {
+    std::vector<WorkSeg>& w = d->work_host;
+    w.clear();
+    int pos = 0;
+    auto add = [&](int kind, int e, int count, int slot, int dep_slot, int dep_count, int pass, int per) {
+        if (count <= 0) return;
+        WorkSeg g;
+        std::memset(&g, 0, sizeof(g));
+        g.begin = pos; g.count = count; g.kind = kind; g.env = e; g.slot = slot;
+        g.dep_slot = dep_count > 0 ? dep_slot : -1;
+        g.dep_count = dep_count; g.cond_slot = -1; g.cond_count = 0; g.pass = pass; g.per_item = per;
+        w.push_back(g);
+        pos += count;
+    };
+    const int M = d->opt.ib_iters;
+    std::vector<int> ib_slot(d->n_envs, SLOT_MARK), ib_count(d->n_envs, 0);
+    auto ib_phases = [&](int e) {
+        const EnvDev& E = d->env[e];
+        const int n = d->mk[e].n;
+        if (n == 0) return;
+        const int nm = (n + MARKERS_PER_ITEM - 1) / MARKERS_PER_ITEM;
+        const int ntiles = (int)((E.nslot + 31u) / 32u);
+        const int nn = (ntiles + TILES_PER_ITEM - 1) / TILES_PER_ITEM;
+        add(W_MARK, e, nm, SLOT_MARK, -1, 0, 0, MARKERS_PER_ITEM);
+        add(W_NODE, e, nn, SLOT_NODE, SLOT_MARK, nm, 0, TILES_PER_ITEM);
+        add(W_FORCE, e, nm, SLOT_FORCE, SLOT_NODE, nn, 0, MARKERS_PER_ITEM);
+        int last = SLOT_FORCE, force_final = SLOT_FORCE;
+        for (int p = 1; p < M; ++p) {
+            const int si = SLOT_PASS0 + 2 * (p - 1), ss = si + 1;
+            add(W_INTERP, e, nm, si, last, nm, p, MARKERS_PER_ITEM);
+            add(W_SPREAD, e, nm, ss, si, nm, p, MARKERS_PER_ITEM);
+            last = ss;
+            force_final = si;
+        }
+        int final_slot = last, final_count = nm;
+        if (d->opt.deterministic) {
+            add(W_CONVERT, e, nn, SLOT_CONVERT, last, nm, 0, TILES_PER_ITEM);
+            final_slot = SLOT_CONVERT;
+            final_count = nn;
+        }
+        add(W_REDUCE, e, (n + FUSED_THREADS - 1) / FUSED_THREADS, SLOT_REDUCE, force_final, nm, 0, FUSED_THREADS);
+        ib_slot[e] = final_slot;
+        ib_count[e] = final_count;
+    };
+    auto sc_blocks = [&](int e) {
+        const int n = d->mk[e].n;
+        const int nm = n > 0 ? (n + MARKERS_PER_ITEM - 1) / MARKERS_PER_ITEM : 0;
+        const size_t at = w.size();
+        add(W_SC, e, d->env[e].nblocks, SLOT_SC, SLOT_MARK, nm, 0, 0);
+        if (w.size() > at) {
+            w.back().cond_slot = ib_count[e] > 0 ? ib_slot[e] : -1;
+            w.back().cond_count = ib_count[e];
+        }
+    };
+    ib_phases(0);
+    for (int e = 0; e < d->n_envs; ++e) {
+        if (e + 1 < d->n_envs) ib_phases(e + 1);
+        sc_blocks(e);
+    }
+}
+
+// Upload the fused kernel's work table if it is out of date (on the stream,
+// before the step's launches; never inside a capture).
+fg_status sync_work_table(fg_domain* d) {
+    if (d->k1 != K1_FUSED || !d->work_dirty) return FG_OK;
+    build_work_table(d);
+    const int n = (int)d->work_host.size();
+    if (n > d->work_seg_cap) {
+        WorkSeg* p = nullptr;
+        fg_status st = dalloc(&p, (size_t)std::max(n, 2 * d->work_seg_cap));
+        if (st != FG_OK) return st;
+        CK(cudaStreamSynchronize(d->stream));
+        if (d->work_segs) cudaFree(d->work_segs);
+        d->work_segs = p;
+        d->work_seg_cap = std::max(n, 2 * d->work_seg_cap);
+    }
+    const int items = n > 0 ? d->work_host.back().begin + d->work_host.back().count : 0;
+    const int hdr[2] = {items, n};
+    if (n > 0)
+        CK(cudaMemcpyAsync(d->work_segs, d->work_host.data(), sizeof(WorkSeg) * n, cudaMemcpyHostToDevice,
+                           d->stream));
+    CK(cudaMemcpyAsync(d->work + WQ_ITEMS, hdr, sizeof(hdr), cudaMemcpyHostToDevice, d->stream));
+    CK(cudaStreamSynchronize(d->stream));   // the host table may change on the next call
+    d->work_dirty = false;
+    return FG_OK;
 }
 
 // The stream-collide launch of the variant in use (gin -> gout), with the
@@ -428,41 +541,101 @@ void enqueue_k1(fg_domain* d, const typename S::raw* gin, typename S::raw* gout,
     else enqueue_k1_order<S, false>(d, gin, gout, s);
 }
 
-// Launch the kernels of one step reading buffer `parity` on stream s; with
-// ev != nullptr an event pair is recorded around each kernel.
+// The cooperative IB kernel of a step reading gin (all resident blocks: the
+// scan phase covers every tile stamp).
+template <class S>
+fg_status enqueue_ib(fg_domain* d, const typename S::raw* gin, cudaStream_t s) {
+    const int blocks = d->ib_per_sm * d->n_sms;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(IB_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, k_ib_step<S>, gin, (const EnvDev*)d->d_env, (const FrameDev*)d->d_frame,
+                          d->n_envs, d->total_markers, (int)d->n_stamps, (const float*)d->X, (const float*)d->U,
+                          (const float*)d->dV, d->Fm, d->fib, d->stamps, (const StepState*)d->d_state,
+                          d->ib_nodes, d->ib_bar, d->opt.ib_iters, d->dF, d->fibq,
+                          (const float*)(d->opt.ib_slip ? d->Nrm : nullptr), d->status));
+    return FG_OK;
+}
+
+// The fused step kernel (IB phases and stream-collide blocks of every
+// environment from one work queue; all blocks resident) reading gin and
+// writing gout.
+template <class S, bool EQ3, bool PAIR>
+fg_status enqueue_fused_of(fg_domain* d, const typename S::raw* gin, typename S::raw* gout, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)d->fused_grid);
+    cfg.blockDim = dim3(FUSED_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    IbArgs a;
+    a.envs = d->d_env;
+    a.frames = d->d_frame;
+    a.X = d->X;
+    a.U = d->U;
+    a.dV = d->dV;
+    a.Fm = d->Fm;
+    a.fib = d->fib;
+    a.stamps = d->stamps;
+    a.nodes = d->ib_nodes;
+    a.dF = d->dF;
+    a.fibq = d->fibq;
+    a.Nrm = d->opt.ib_slip ? d->Nrm : nullptr;
+    a.status = d->status;
+    CK(cudaLaunchKernelEx(&cfg, k_step_fused<S, EQ3, PAIR>, gin, gout, a, (const StepState*)d->d_state,
+                          (const int*)d->seg, (const float*)d->seg_ref, d->red_partials, d->red_z, d->mass_part,
+                          (const WorkSeg*)d->work_segs, d->work, d->work_done, d->n_envs));
+    return FG_OK;
+}
+
+template <class S>
+fg_status enqueue_fused(fg_domain* d, const typename S::raw* gin, typename S::raw* gout, cudaStream_t s) {
+    const bool eq3 = d->opt.eq_order == 3;
+    if (d->plain_pair)
+        return eq3 ? enqueue_fused_of<S, true, true>(d, gin, gout, s) : enqueue_fused_of<S, false, true>(d, gin, gout, s);
+    return eq3 ? enqueue_fused_of<S, true, false>(d, gin, gout, s) : enqueue_fused_of<S, false, false>(d, gin, gout, s);
+}
+
+// Launch the kernels of one step reading gin and writing gout on stream s;
+// with ev != nullptr an event pair is recorded around each kernel (the fused
+// kernel counts as the stream-collide kernel; it has no separate IB launch).
 template <class S>
 fg_status enqueue_step_io(fg_domain* d, const typename S::raw* gin, typename S::raw* gout, cudaStream_t s,
                           cudaEvent_t* const* ev) {
-    if (d->total_markers > 0) {
+    const bool fused = d->k1 == K1_FUSED;
+    if (!fused && d->total_markers > 0) {
         if (ev) CK(cudaEventRecord(ev[FG_K_IB][0], s));
-        // all resident blocks: the scan phase covers every tile stamp
-        const int blocks = d->ib_per_sm * d->n_sms;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)blocks);
-        cfg.blockDim = dim3(IB_THREADS);
-        cfg.dynamicSmemBytes = 0;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeCooperative;
-        attr[0].val.cooperative = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        CK(cudaLaunchKernelEx(&cfg, k_ib_step<S>, gin, (const EnvDev*)d->d_env, (const FrameDev*)d->d_frame,
-                              d->n_envs, d->total_markers, (int)d->n_stamps, (const float*)d->X, (const float*)d->U,
-                              (const float*)d->dV, d->Fm, d->fib, d->stamps, (const StepState*)d->d_state,
-                              d->ib_nodes, d->ib_bar, d->opt.ib_iters, d->dF, d->fibq,
-                              (const float*)(d->opt.ib_slip ? d->Nrm : nullptr), d->status));
+        fg_status st = enqueue_ib<S>(d, gin, s);
+        if (st != FG_OK) return st;
         if (ev) CK(cudaEventRecord(ev[FG_K_IB][1], s));
     }
     if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][0], s));
-    enqueue_k1<S>(d, gin, gout, s);
+    if (fused) {
+        fg_status st = enqueue_fused<S>(d, gin, gout, s);
+        if (st != FG_OK) return st;
+    } else {
+        enqueue_k1<S>(d, gin, gout, s);
+    }
     if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][1], s));
     if (ev) CK(cudaEventRecord(ev[FG_K_REDUCE][0], s));
     {
         // a programmatic dependent of the stream-collide kernel: its marker
-        // sums overlap that kernel's last blocks, the rest waits for it
+        // sums overlap that kernel's last blocks, the rest waits for it (after
+        // the fused kernel, which wrote the marker chunk sums, only the mass
+        // is summed)
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)d->n_envs, RED_ROWS, (unsigned)d->red_z);
+        cfg.gridDim = dim3((unsigned)d->n_envs, fused ? 1u : (unsigned)RED_ROWS, (unsigned)d->red_z);
         cfg.blockDim = dim3(RED_THREADS);
         cfg.dynamicSmemBytes = 0;
         cfg.stream = s;
@@ -475,7 +648,7 @@ fg_status enqueue_step_io(fg_domain* d, const typename S::raw* gin, typename S::
                               (const float*)d->dV, (const int*)d->seg, (const float*)d->seg_ref,
                               (const Pair32*)d->mass_part, d->red_partials, d->red_counters, d->n_envs, d->red_z,
                               d->ft, d->mass, d->hist, d->opt.record_history, d->d_state, d->status,
-                              d->rb_ft_all_dev, d->rb_status_dev));
+                              d->rb_ft_all_dev, d->rb_status_dev, fused ? 1 : 0));
     }
     if (ev) CK(cudaEventRecord(ev[FG_K_REDUCE][1], s));
     CK(cudaGetLastError());
@@ -507,7 +680,7 @@ fg_status launch_step(fg_domain* d) {
                 d->ev_used[k] = 0;
             }
             evp[k] = &d->ev[k][d->ev_used[k]];
-            if (k != FG_K_IB || d->total_markers > 0) d->ev_used[k] += 2;
+            if (k != FG_K_IB || (d->total_markers > 0 && d->k1 != K1_FUSED)) d->ev_used[k] += 2;
         }
         use_ev = true;
     }
@@ -596,7 +769,7 @@ fg_status staged_occupancy(fg_domain* d, int* per_sm) {
 }
 
 bool k1_runnable(const fg_domain* d, int v) {
-    if (v == K1_PLAIN) return true;
+    if (v == K1_PLAIN || v == K1_FUSED) return true;
     if (v == K1_STAGED256) return d->max_P <= 256;
     return v == K1_STAGED512 && d->max_P <= 512;
 }
@@ -607,7 +780,8 @@ bool k1_runnable(const fg_domain* d, int v) {
 fg_status configure_k1(fg_domain* d, int v, bool allocate) {
     if (!k1_runnable(d, v)) return fail(FG_ERR_INVALID, "stream-collide variant cannot run these rows");
     d->k1 = v;
-    d->staged = v != K1_PLAIN;
+    d->staged = v == K1_STAGED256 || v == K1_STAGED512;
+    d->work_dirty = true;
     d->staged_gc = v == K1_STAGED512 ? 512 : 256;
     // 16-bit storage is bound by instruction issue, not by DRAM: two cells
     // per thread share the per-cell index work and store their outputs as
@@ -658,6 +832,22 @@ fg_status configure_k1(fg_domain* d, int v, bool allocate) {
         if (st != FG_OK) return st;
         if (per_sm < 1) return fail(FG_ERR_INVALID, "staged kernel does not fit on an SM");
         d->staged_grid = std::min(d->total_groups, sms * per_sm);
+    }
+    if (v == K1_FUSED) {
+        int per_sm = 0;
+        fg_status st = dispatch(d->opt.storage, [&](auto tag) -> fg_status {
+            typedef decltype(tag) S;
+            const bool eq3 = d->opt.eq_order == 3;
+            const void* fn = d->plain_pair ? (eq3 ? (const void*)k_step_fused<S, true, true>
+                                                  : (const void*)k_step_fused<S, false, true>)
+                                           : (eq3 ? (const void*)k_step_fused<S, true, false>
+                                                  : (const void*)k_step_fused<S, false, false>);
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, FUSED_THREADS, 0));
+            return FG_OK;
+        });
+        if (st != FG_OK) return st;
+        if (per_sm < 1) return fail(FG_ERR_CUDA, "fused step kernel cannot be resident");
+        d->fused_grid = per_sm * d->n_sms;
     }
     if (!allocate) return FG_OK;
     const size_t need = (size_t)std::max(d->total_blocks, d->total_groups);
@@ -722,7 +912,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     o.use_graphs = 1;
     o.autotune = 0;
     if (opt) o = *opt;
-    if (o.kernel_variant < FG_KERNEL_AUTO || o.kernel_variant > FG_KERNEL_STAGED512)
+    if (o.kernel_variant < FG_KERNEL_AUTO || o.kernel_variant > FG_KERNEL_FUSED)
         return fail(FG_ERR_INVALID, "unknown kernel variant");
     if (o.storage < 0 || o.storage > 2) return fail(FG_ERR_INVALID, "unknown storage");
     if (o.layout != 0) return fail(FG_ERR_INVALID, "only the two-buffer pull layout (0) exists");
@@ -840,6 +1030,8 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     DA(d->mass, n_envs);
     if (o.record_history > 0) DA(d->hist, (size_t)n_envs * o.record_history * HIST_ROW);
     DA(d->status, 1);
+    DA(d->work, WQ_WORDS);
+    DA(d->work_done, (size_t)n_envs * N_SLOTS);
 #undef DA
     {
         cudaError_t e = cudaHostAlloc((void**)&d->rb, sizeof(*d->rb), cudaHostAllocMapped);
@@ -872,6 +1064,8 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         (d->fibq && (ce = cudaMemsetAsync(d->fibq, 0, sizeof(unsigned long long) * 3ull * slot_off,
                                           d->stream)) != cudaSuccess) ||
         (ce = cudaMemsetAsync(d->red_counters, 0, sizeof(int) * n_envs * RED_ROWS, d->stream)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(d->work, 0, sizeof(int) * WQ_WORDS, d->stream)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(d->work_done, 0, sizeof(int) * n_envs * N_SLOTS, d->stream)) != cudaSuccess ||
         (ce = cudaMemcpyAsync(d->d_state, &initial_state, sizeof(StepState), cudaMemcpyHostToDevice,
                               d->stream)) != cudaSuccess) {
         st = cuda_fail(ce, "cudaMemsetAsync");
@@ -881,7 +1075,8 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     }
     refresh_marker_table(d);
     {
-        const int first = o.kernel_variant == FG_KERNEL_PLAIN || !can_stage ? K1_PLAIN
+        const int first = o.kernel_variant == FG_KERNEL_FUSED                    ? K1_FUSED
+                          : o.kernel_variant == FG_KERNEL_PLAIN || !can_stage ? K1_PLAIN
                           : o.kernel_variant == FG_KERNEL_STAGED512              ? K1_STAGED512
                           : (d->max_P <= 256 ? K1_STAGED256 : K1_STAGED512);
         if ((st = configure_k1(d, first, true)) != FG_OK) {
@@ -907,7 +1102,8 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         return st;
     }
     for (int e = 0; e < n_envs && st == FG_OK; ++e) st = fg_init_fields(d, e, nullptr, nullptr);
-    if (st == FG_OK && o.autotune && o.kernel_variant == FG_KERNEL_AUTO) st = fg_autotune(d, nullptr, nullptr);
+    // the autotuner runs before the first step, when the step's markers are known
+    d->autotune_pending = o.autotune && o.kernel_variant == FG_KERNEL_AUTO;
     if (st != FG_OK) {
         free_all(d);
         delete d;
@@ -957,8 +1153,10 @@ fg_status fg_init_fields(fg_domain* d, int env, const double* rho, const double*
     const long long zero_step = 0;
     CK(cudaMemcpyAsync(&d->d_state->step, &zero_step, sizeof(long long), cudaMemcpyHostToDevice, d->stream));
     CK(cudaMemsetAsync(d->status, 0, sizeof(int), d->stream));
-    // after a barrier timeout the barrier words are inconsistent
+    // after a timeout the barrier words and the work queue are inconsistent
     CK(cudaMemsetAsync(d->ib_bar, 0, 2 * sizeof(unsigned), d->stream));
+    CK(cudaMemsetAsync(d->work, 0, sizeof(int) * WQ_ITEMS, d->stream));
+    CK(cudaMemsetAsync(d->work_done, 0, sizeof(int) * d->n_envs * N_SLOTS, d->stream));
     CK(cudaStreamSynchronize(d->stream));
     return FG_OK;
 }
@@ -1292,6 +1490,11 @@ fg_status fg_step(fg_domain* d, int n_steps, const fg_frame* frames) {
         for (int e = 0; e < d->n_envs; ++e)
             if (d->mk[e].n > 0 && !d->mk[e].has_normals)
                 return fail(FG_ERR_STATE, "slip forcing needs the markers' normals (fg_set_marker_normals)");
+    if (n_steps > 0 && d->autotune_pending) {
+        fg_status st = fg_autotune(d, nullptr, nullptr);
+        if (st != FG_OK) return st;
+    }
+    if (fg_status st = sync_work_table(d); st != FG_OK) return st;
     const bool graphs = d->opt.use_graphs && !d->profiling;
     for (int s = 0; s < n_steps; ++s) {
         fg_status st = dispatch(d->opt.storage, [&](auto tag) {
@@ -1320,6 +1523,7 @@ fg_status fg_step_state(fg_domain* d, const void* in, void* out, const fg_frame*
     }
     if (d->opt.ib_slip && d->mk[0].n > 0 && !d->mk[0].has_normals)
         return fail(FG_ERR_STATE, "slip forcing needs the markers' normals (fg_set_marker_normals)");
+    if (fg_status st0 = sync_work_table(d); st0 != FG_OK) return st0;
     fg_status st = dispatch(d->opt.storage, [&](auto tag) {
         typedef typename decltype(tag)::raw raw;
         return enqueue_step_io<decltype(tag)>(d, (const raw*)in, (raw*)out, d->stream, nullptr);
@@ -1764,7 +1968,17 @@ fg_status fg_autotune(fg_domain* d, int* choice, double* ms) {
     NvtxRange nvtx_range("fg_autotune");
     if (!d) return fail(FG_ERR_INVALID, "null domain");
     if (d->poisoned) return fail(FG_ERR_STATE, "domain poisoned by a numeric fault; call fg_init_fields");
+    d->autotune_pending = false;
     CK(cudaStreamSynchronize(d->stream));
+    // The IB pass of a timed candidate rewrites the marker forces; the last
+    // step's are kept aside and put back.
+    float* fm_keep = nullptr;
+    const size_t fm_n = 3ull * (size_t)d->marker_slots;
+    if (d->total_markers > 0) {
+        fg_status st0 = dalloc(&fm_keep, fm_n);
+        if (st0 != FG_OK) return st0;
+        CK(cudaMemcpyAsync(fm_keep, d->Fm, sizeof(float) * fm_n, cudaMemcpyDeviceToDevice, d->stream));
+    }
     cudaEvent_t a, b;
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
@@ -1780,19 +1994,34 @@ fg_status fg_autotune(fg_domain* d, int* choice, double* ms) {
         for (int v = 0; v < K1_NVARIANTS && st == FG_OK; ++v) {
             if (!k1_runnable(d, v)) continue;
             if ((st = configure_k1(d, v, true)) != FG_OK) break;
-            // The stream-collide kernel alone, reading the current state and
-            // writing the other buffer (which the next step overwrites); no
-            // tile carries the next step's stamp yet, so the IB force field is
-            // left untouched.
+            if ((st = sync_work_table(d)) != FG_OK) break;
+            // The step without its reduction: the IB kernel and the
+            // stream-collide kernel (the fused kernel does both), reading the
+            // current state and writing the other buffer, which the next step
+            // overwrites.  The stamp does not advance (the reduction advances
+            // it), so the next step stamps the same tiles again; every tile
+            // that received IB force is stamped, so the stream-collide pass
+            // leaves the force field zero.
             st = dispatch(d->opt.storage, [&](auto tag) -> fg_status {
                 typedef decltype(tag) S;
                 typedef typename S::raw raw;
                 const raw* gin = (const raw*)d->pop[d->cur];
                 raw* gout = (raw*)d->pop[d->cur ^ 1];
-                for (int w = 0; w < 2; ++w) enqueue_k1<S>(d, gin, gout, d->stream);
+                auto pass = [&]() -> fg_status {
+                    if (v == K1_FUSED) return enqueue_fused<S>(d, gin, gout, d->stream);
+                    if (d->total_markers > 0) {
+                        fg_status s1 = enqueue_ib<S>(d, gin, d->stream);
+                        if (s1 != FG_OK) return s1;
+                    }
+                    enqueue_k1<S>(d, gin, gout, d->stream);
+                    return FG_OK;
+                };
+                fg_status s2 = FG_OK;
+                for (int w = 0; w < 2 && s2 == FG_OK; ++w) s2 = pass();
                 CK(cudaEventRecord(a, d->stream));
-                for (int r = 0; r < REPS; ++r) enqueue_k1<S>(d, gin, gout, d->stream);
+                for (int r = 0; r < REPS && s2 == FG_OK; ++r) s2 = pass();
                 CK(cudaEventRecord(b, d->stream));
+                if (s2 != FG_OK) return s2;
                 CK(cudaGetLastError());
                 CK(cudaEventSynchronize(b));
                 float t = 0.f;
@@ -1805,23 +2034,28 @@ fg_status fg_autotune(fg_domain* d, int* choice, double* ms) {
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    if (fm_keep) {
+        cudaMemcpyAsync(d->Fm, fm_keep, sizeof(float) * fm_n, cudaMemcpyDeviceToDevice, d->stream);
+        cudaStreamSynchronize(d->stream);
+        cudaFree(fm_keep);
+    }
     if (st != FG_OK) return st;
-    // Timed alone, the variants miss what the step adds around them: on the
-    // 256x128x128 swimmer channel the plain and staged-256 kernels come out
-    // within 1% of each other alone, in either order from run to run, while
-    // whole steps with the plain kernel are 2% faster (0.1825 against
-    // 0.1864 ms, three runs each).  So a staged variant is kept only when it
-    // is faster alone by more than that.
+    // Timed alone, the stream-collide variants miss what the step adds around
+    // them: on the 256x128x128 swimmer channel the plain and staged-256
+    // kernels came out within 1% of each other alone, in either order from
+    // run to run, while whole steps with the plain kernel were 2% faster
+    // (0.1825 against 0.1864 ms, three runs each).  So a staged variant is
+    // kept only when it is faster by more than that.
     constexpr double STAGED_MARGIN = 0.98;
+    auto score = [&](int v) { return (v == K1_STAGED256 || v == K1_STAGED512) ? best_of[v] / STAGED_MARGIN : best_of[v]; };
     int best = -1;
     for (int v = 0; v < K1_NVARIANTS; ++v) {
         if (ms) ms[v] = best_of[v];
         if (best_of[v] < 0.0) continue;
-        const double t = v == K1_PLAIN ? best_of[v] : best_of[v] / STAGED_MARGIN;
-        const double tb = best < 0 ? 0.0 : (best == K1_PLAIN ? best_of[best] : best_of[best] / STAGED_MARGIN);
-        if (best < 0 || t < tb) best = v;
+        if (best < 0 || score(v) < score(best)) best = v;
     }
     if ((st = configure_k1(d, best, true)) != FG_OK) return st;
+    if ((st = sync_work_table(d)) != FG_OK) return st;
     if (choice) *choice = best;
     return FG_OK;
 }

@@ -235,14 +235,12 @@ __device__ __forceinline__ void ib_mark(const EnvDev& E, const Stencil& S, int h
     }
 }
 
-// nodes: post-stream rho and u~ of the 32 cells of tile t (one warp).
+// nodes: post-stream rho and u~ of the 32 cells of tile t_local (counted
+// from the environment's first tile) of environment E (one warp).
 template <class S>
-__device__ __forceinline__ void ib_nodes(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs,
-                                         const FrameDev* __restrict__ frames, int n_envs, int t, int lane,
-                                         float4* nodes) {
-    const int e = n_envs > 1 ? env_of<&EnvDev::stamp_off>(envs, n_envs, t) : 0;
-    const EnvDev& E = envs[e];
-    const uint32_t c = (uint32_t)(t - E.stamp_off) * 32u + (uint32_t)lane;
+__device__ __forceinline__ void ib_nodes_of(const typename S::raw* __restrict__ gin, const EnvDev& E,
+                                            const FrameDev& F, int t_local, int lane, float4* nodes) {
+    const uint32_t c = (uint32_t)t_local * 32u + (uint32_t)lane;
     if (c >= E.nslot) return;
     const uint32_t row = fdiv(c, E.div_P);
     const int x = (int)(c - row * (uint32_t)E.P);
@@ -257,9 +255,18 @@ __device__ __forceinline__ void ib_nodes(const typename S::raw* __restrict__ gin
     const Moments m = pull_moments<S, false>(gin + E.pop_off, E.nslot, c, o);
     const float rho = 1.0f + m.dr, inv = 1.0f / rho;
     float a0[3];
-    frame_accel(frames[e], (float)x, (float)y, (float)z, a0);
+    frame_accel(F, (float)x, (float)y, (float)z, a0);
     nodes[E.slot_off + c] = make_float4(rho, m.jx * inv + 0.5f * a0[0], m.jy * inv + 0.5f * a0[1],
                                         m.jz * inv + 0.5f * a0[2]);
+}
+
+// nodes of the domain-wide tile t (the environment found from its tile offset)
+template <class S>
+__device__ __forceinline__ void ib_nodes(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs,
+                                         const FrameDev* __restrict__ frames, int n_envs, int t, int lane,
+                                         float4* nodes) {
+    const int e = n_envs > 1 ? env_of<&EnvDev::stamp_off>(envs, n_envs, t) : 0;
+    ib_nodes_of<S>(gin, envs[e], frames[e], t - envs[e].stamp_off, lane, nodes);
 }
 
 // One marker of a half-warp: its environment, slot, stencil, U and dV.
@@ -269,17 +276,23 @@ struct MarkerRef {
     float U[3], dV;
 };
 
+__device__ __forceinline__ MarkerRef load_marker_slot(const EnvDev& E, int e, int slot, const float* __restrict__ X,
+                                                      const float* __restrict__ U, const float* __restrict__ dV) {
+    MarkerRef r;
+    r.e = e;
+    r.slot = slot;
+    r.S = marker_stencil(E, X, slot);
+    r.U[0] = U[3 * slot]; r.U[1] = U[3 * slot + 1]; r.U[2] = U[3 * slot + 2];
+    r.dV = dV[slot];
+    return r;
+}
+
 __device__ __forceinline__ MarkerRef load_marker(const EnvDev* __restrict__ envs, int n_envs, int m,
                                                  const float* __restrict__ X, const float* __restrict__ U,
                                                  const float* __restrict__ dV) {
-    MarkerRef r;
-    r.e = n_envs > 1 ? env_of<&EnvDev::mk_begin>(envs, n_envs, m) : 0;
-    const EnvDev& E = envs[r.e];
-    r.slot = E.marker_off + (m - E.mk_begin);
-    r.S = marker_stencil(E, X, r.slot);
-    r.U[0] = U[3 * r.slot]; r.U[1] = U[3 * r.slot + 1]; r.U[2] = U[3 * r.slot + 2];
-    r.dV = dV[r.slot];
-    return r;
+    const int e = n_envs > 1 ? env_of<&EnvDev::mk_begin>(envs, n_envs, m) : 0;
+    const EnvDev& E = envs[e];
+    return load_marker_slot(E, e, E.marker_off + (m - E.mk_begin), X, U, dV);
 }
 
 // Stencil nodes of half-lane h for one marker: the slots of its column's

@@ -41,6 +41,63 @@ __device__ __forceinline__ double block_sum(Pair32 v, Pair32* sh) {
 constexpr int MASS_PER_THREAD = 8;
 constexpr int RED_ROWS = MAX_SEG + 2;   // force/torque rows 0..MAX_SEG, then the mass
 
+// Terms of marker l (counted from environment e's first marker) in
+// force/torque row y (y < nseg: segment y, its torque about seg_ref[e][y];
+// y == nseg: every marker, torque about the environment's ref): force on the
+// body -F_l dV_l and torque (X_l - p) x (-F_l dV_l), added to acc.  Reads
+// through L2 (the marker forces may come from another block of the same
+// launch).
+__device__ __forceinline__ void marker_row_terms(const EnvDev& E, int e, int y, int l, const float* __restrict__ X,
+                                                 const float* __restrict__ Fm, const float* __restrict__ dV,
+                                                 const int* __restrict__ seg, const float* __restrict__ seg_ref,
+                                                 Pair32 (&acc)[6]) {
+    const int ns = E.nseg;
+    if (l >= E.n_markers) return;
+    const int q = E.marker_off + l;
+    if (y != ns && __ldcg(seg + q) != y) return;
+    const float v = -__ldcg(dV + q);
+    const float Fx = __ldcg(Fm + 3 * q) * v, Fy = __ldcg(Fm + 3 * q + 1) * v, Fz = __ldcg(Fm + 3 * q + 2) * v;
+    // segment rows about the segment's point, the total row about ref
+    const float* rp = seg_ref + ((size_t)e * MAX_SEG + (y < ns ? y : 0)) * 3;
+    const float px = y < ns ? __ldcg(rp) : (float)E.ref[0], py = y < ns ? __ldcg(rp + 1) : (float)E.ref[1],
+                pz = y < ns ? __ldcg(rp + 2) : (float)E.ref[2];
+    const float rx = __ldcg(X + 3 * q) - px, ry = __ldcg(X + 3 * q + 1) - py, rz = __ldcg(X + 3 * q + 2) - pz;
+    acc[0].add(Fx); acc[1].add(Fy); acc[2].add(Fz);
+    acc[3].add(ry * Fz - rz * Fy);
+    acc[4].add(rz * Fx - rx * Fz);
+    acc[5].add(rx * Fy - ry * Fx);
+}
+
+// Sum components c < ncomp of acc over a block of RED_THREADS threads (a
+// shuffle tree per component inside each warp, then the warp totals in warp
+// order: a fixed order, so the result is deterministic) and store them to
+// out[c] (threads c < ncomp, followed by a fence).  Called by every thread.
+__device__ __forceinline__ void block_pair_sums(Pair32 (&acc)[6], int ncomp, Pair32 (*sh)[6], Pair32* out) {
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    constexpr int NW = RED_THREADS / 32;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        if (c < ncomp) {
+#pragma unroll
+            for (int k = 16; k >= 1; k >>= 1) {
+                Pair32 o;
+                o.hi = __shfl_xor_sync(0xffffffffu, acc[c].hi, k);
+                o.lo = __shfl_xor_sync(0xffffffffu, acc[c].lo, k);
+                acc[c].add(o);
+            }
+            if (lane == 0) sh[w][c] = acc[c];
+        }
+    }
+    __syncthreads();
+    if (tid < ncomp) {
+        Pair32 t;
+        for (int i = 0; i < NW; ++i) t.add(sh[i][tid]);
+        out[tid] = t;
+        __threadfence();
+    }
+    __syncthreads();
+}
+
 // Grid (n_envs, RED_ROWS, chunks).  Block (e, y, z) sums chunk z of row y of
 // environment e: y <= nseg is force/torque row y (segment y, its torque
 // about seg_ref[e][y]; y == nseg is the total over all markers, its torque
@@ -58,7 +115,10 @@ constexpr int RED_ROWS = MAX_SEG + 2;   // force/torque rows 0..MAX_SEG, then th
 // force/torque rows are also written to host_ft and, by the last environment
 // to finish (which advances the step state), the status word to host_status:
 // pinned host memory mapped into the device's address space, so a coupled
-// step reads them back with no copy (either may be NULL).
+// step reads them back with no copy (either may be NULL).  markers_pre = 1:
+// the force/torque chunk sums are already in `partials` (the fused step
+// kernel wrote them, with the same chunks and order); the grid is then
+// (n_envs, 1, chunks) and only the mass is summed before the combine.
 static __global__ void __launch_bounds__(RED_THREADS)
 k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const float* __restrict__ Fm,
          const float* __restrict__ dV, const int* __restrict__ seg, const float* __restrict__ seg_ref,
@@ -66,11 +126,11 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
          Pair32* __restrict__ partials, int* __restrict__ counters, int n_envs, int zmax,
          Pair32* __restrict__ ft, Pair32* __restrict__ mass, Pair32* __restrict__ hist, int hist_cap,
          StepState* __restrict__ st, int* __restrict__ status, Pair32* __restrict__ host_ft,
-         int* __restrict__ host_status) {
+         int* __restrict__ host_status, int markers_pre) {
     constexpr int NW = RED_THREADS / 32;
     __shared__ Pair32 sh[NW][6];
     __shared__ int is_last;
-    const int e = blockIdx.x, y = blockIdx.y, z = blockIdx.z, tid = threadIdx.x;
+    const int e = blockIdx.x, y = markers_pre ? RED_ROWS - 1 : (int)blockIdx.y, z = blockIdx.z, tid = threadIdx.x;
     const int w = tid >> 5, lane = tid & 31;
     const EnvDev& E = envs[e];
     const int ns = E.nseg;
@@ -79,30 +139,10 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
     const bool is_mass = y == RED_ROWS - 1;
     if (is_mass ? z >= nch_m : (y > ns || z >= nch_f)) return;
     Pair32 acc[6];
-    if (!is_mass) {
-        // The marker forces come from the IB kernel, which completed before
-        // the stream-collide kernel started, so these sums may run while the
-        // stream-collide kernel's last blocks finish (reads through L2).
-        const int l = z * RED_THREADS + tid;
-        if (l < E.n_markers) {
-            const int q = E.marker_off + l;
-            if (y == ns || __ldcg(seg + q) == y) {
-                const float v = -__ldcg(dV + q);
-                const float Fx = __ldcg(Fm + 3 * q) * v, Fy = __ldcg(Fm + 3 * q + 1) * v,
-                            Fz = __ldcg(Fm + 3 * q + 2) * v;
-                // segment rows about the segment's point, the total row about ref
-                const float* rp = seg_ref + ((size_t)e * MAX_SEG + (y < ns ? y : 0)) * 3;
-                const float px = y < ns ? __ldcg(rp) : (float)E.ref[0], py = y < ns ? __ldcg(rp + 1) : (float)E.ref[1],
-                            pz = y < ns ? __ldcg(rp + 2) : (float)E.ref[2];
-                const float rx = __ldcg(X + 3 * q) - px, ry = __ldcg(X + 3 * q + 1) - py,
-                            rz = __ldcg(X + 3 * q + 2) - pz;
-                acc[0].add(Fx); acc[1].add(Fy); acc[2].add(Fz);
-                acc[3].add(ry * Fz - rz * Fy);
-                acc[4].add(rz * Fx - rx * Fz);
-                acc[5].add(rx * Fy - ry * Fx);
-            }
-        }
-    }
+    // The marker forces come from the IB kernel, which completed before the
+    // stream-collide kernel started, so these sums may run while the
+    // stream-collide kernel's last blocks finish (reads through L2).
+    if (!is_mass) marker_row_terms(E, e, y, z * RED_THREADS + tid, X, Fm, dV, seg, seg_ref, acc);
     // Everything below reads the stream-collide kernel's mass sums or writes
     // what the step's kernels read (the step state), so it waits for that
     // kernel when launched as its programmatic dependent.
@@ -122,30 +162,10 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
         for (int k = 0; k < MASS_PER_THREAD; ++k) acc[0].add(v[k]);
     }
     const int ncomp = is_mass ? 1 : 6;
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        if (c < ncomp) {
-#pragma unroll
-            for (int k = 16; k >= 1; k >>= 1) {
-                Pair32 o;
-                o.hi = __shfl_xor_sync(0xffffffffu, acc[c].hi, k);
-                o.lo = __shfl_xor_sync(0xffffffffu, acc[c].lo, k);
-                acc[c].add(o);
-            }
-            if (lane == 0) sh[w][c] = acc[c];
-        }
-    }
-    __syncthreads();
     Pair32* slot = partials + ((size_t)(e * RED_ROWS + y) * zmax) * 6;
-    if (tid < ncomp) {
-        Pair32 t;
-        for (int i = 0; i < NW; ++i) t.add(sh[i][tid]);
-        if (FG_IN_RANGE(DBG_REDUCE, z, zmax)) slot[(size_t)z * 6 + tid] = t;
-        __threadfence();
-    }
-    __syncthreads();
+    if (FG_IN_RANGE(DBG_REDUCE, z, zmax)) block_pair_sums(acc, ncomp, sh, slot + (size_t)z * 6);
     if (tid == 0) {
-        is_last = atomicAdd(counters + e, 1) == (ns + 1) * nch_f + nch_m - 1;
+        is_last = atomicAdd(counters + e, 1) == (markers_pre ? 0 : (ns + 1) * nch_f) + nch_m - 1;
         if (is_last) __threadfence();
     }
     __syncthreads();

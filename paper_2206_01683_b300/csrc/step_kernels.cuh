@@ -445,13 +445,17 @@ __device__ __forceinline__ int inward(const EnvDev& E, int axis, int v) {
 
 // IB force density at a slot if its 32-slot tile was stamped this step; the
 // stored value is cleared so the field is zero again for the next step.
+// COHERENT reads the stamp and the force through L2 (ld.global.cg), for a
+// kernel in which other blocks wrote them earlier in the same launch.
+template <bool COHERENT = false>
 __device__ __forceinline__ void take_ib_force(const EnvDev& E, float4* __restrict__ fib,
                                               const uint32_t* __restrict__ stamps, uint32_t stamp,
                                               uint32_t slot, float& fx, float& fy, float& fz) {
     fx = fy = fz = 0.f;
-    if (__ldg(stamps + E.stamp_off + (slot >> 5)) == stamp) {
+    const uint32_t* sp = stamps + E.stamp_off + (slot >> 5);
+    if ((COHERENT ? __ldcg(sp) : __ldg(sp)) == stamp) {
         float4* fb = fib + E.slot_off + slot;
-        const float4 f = *fb;
+        const float4 f = COHERENT ? __ldcg(fb) : *fb;
         fx = f.x; fy = f.y; fz = f.z;
         *fb = make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -479,7 +483,69 @@ __device__ __forceinline__ float block_sum_f32(float v, float* wsum) {
     return t;  // valid in thread 0
 }
 
-// Plain variant: one thread per slot, direct loads.
+// The cells of plain-kernel block b of environment E (b counted from the
+// environment's first block): one cell per thread, or with PAIR two
+// neighbouring cells (x even and x + 1) per thread.  Returns the thread's
+// sum of rho_out - 1.  C holds the environment's constants.
+template <class S, bool EQ3, bool PAIR, bool COHERENT = false>
+__device__ __forceinline__ float plain_block_cells(const typename S::raw* __restrict__ gin,
+                                                   typename S::raw* __restrict__ gout, const EnvDev& E,
+                                                   const CellConsts& C, int b, float4* __restrict__ fib,
+                                                   const uint32_t* __restrict__ stamps, uint32_t stamp) {
+    float drout = 0.0f;
+    if constexpr (PAIR) {
+        // cells x (even) and x + 1 of one row; every row length is even, so
+        // both are real cells and share a 32-slot tile
+        const uint32_t c = ((uint32_t)b * K1_THREADS + threadIdx.x) * 2u;
+        if (c < E.nslot) {
+            const uint32_t row = fdiv(c, E.div_P);
+            const int x = (int)(c - row * (uint32_t)E.P);
+            if (x < E.n[0]) {
+                const uint32_t zz = fdiv(row, E.div_ny);
+                const int y = (int)(row - zz * (uint32_t)E.n[1]);
+                const int z = (int)zz;
+                float fa[3], fb[3];
+                take_ib_force<COHERENT>(E, fib, stamps, stamp, c, fa[0], fa[1], fa[2]);
+                take_ib_force<COHERENT>(E, fib, stamps, stamp, c + 1, fb[0], fb[1], fb[2]);
+                const int sxa = inward(E, 0, x), sxb = inward(E, 0, x + 1);
+                const int sy = inward(E, 1, y), sz = inward(E, 2, z);
+                const int ry = (sy + sz * E.n[1]) * E.P;
+                const Moments ma = pull_moments<S, true>(gin + E.pop_off, E.nslot, (uint32_t)((int)c + sxa + ry),
+                                                         pull_offsets(E, x + sxa, y + sy, z + sz));
+                const Moments mb = pull_moments<S, true>(gin + E.pop_off, E.nslot,
+                                                         (uint32_t)((int)c + 1 + sxb + ry),
+                                                         pull_offsets(E, x + 1 + sxb, y + sy, z + sz));
+                const Herm ha = cell_coeffs<S, EQ3>(C, ma, x, y, z, sxa, sy, sz, fa[0], fa[1], fa[2]);
+                const Herm hb = cell_coeffs<S, EQ3>(C, mb, x + 1, y, z, sxb, sy, sz, fb[0], fb[1], fb[2]);
+                drout = ha.drout + hb.drout;
+                emit_pair<S, EQ3>(ha, hb, gout + E.pop_off, E.nslot, c);
+            }
+        }
+    } else {
+        const uint32_t c = (uint32_t)b * K1_THREADS + threadIdx.x;
+        if (c < E.nslot) {
+            const uint32_t row = fdiv(c, E.div_P);
+            const int x = (int)(c - row * (uint32_t)E.P);
+            if (x < E.n[0]) {
+                const uint32_t zz = fdiv(row, E.div_ny);
+                const int y = (int)(row - zz * (uint32_t)E.n[1]);
+                const int z = (int)zz;
+                float fx, fy, fz;
+                take_ib_force<COHERENT>(E, fib, stamps, stamp, c, fx, fy, fz);
+                const int sx = inward(E, 0, x), sy = inward(E, 1, y), sz = inward(E, 2, z);
+                // a boundary cell takes its moments from the inward neighbour x_f
+                const int px = x + sx, py = y + sy, pz = z + sz;
+                const uint32_t p = (uint32_t)((int)c + sx + (sy + sz * E.n[1]) * E.P);
+                const PullOffsets o = pull_offsets(E, px, py, pz);
+                const Moments m = pull_moments<S, true>(gin + E.pop_off, E.nslot, p, o);
+                drout = update_cell<S, EQ3>(C, m, x, y, z, sx, sy, sz, fx, fy, fz, gout + E.pop_off, c);
+            }
+        }
+    }
+    return drout;
+}
+
+// Plain variant: one thread per slot (two with PAIR), direct loads.
 template <class S, bool EQ3 = false, bool PAIR = false>
 __global__ void __launch_bounds__(K1_THREADS)
 k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __restrict__ gout,
@@ -497,56 +563,7 @@ k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __res
     // the step's reduction may start its marker sums once the last wave of
     // blocks is in (it waits for this kernel before it reads the mass sums)
     allow_dependents();
-    float drout = 0.0f;
-    if constexpr (PAIR) {
-        // cells x (even) and x + 1 of one row; every row length is even, so
-        // both are real cells and share a 32-slot tile
-        const uint32_t c = ((uint32_t)(b - E.block0) * K1_THREADS + threadIdx.x) * 2u;
-        if (c < E.nslot) {
-            const uint32_t row = fdiv(c, E.div_P);
-            const int x = (int)(c - row * (uint32_t)E.P);
-            if (x < E.n[0]) {
-                const uint32_t zz = fdiv(row, E.div_ny);
-                const int y = (int)(row - zz * (uint32_t)E.n[1]);
-                const int z = (int)zz;
-                float fa[3], fb[3];
-                take_ib_force(E, fib, stamps, stamp, c, fa[0], fa[1], fa[2]);
-                take_ib_force(E, fib, stamps, stamp, c + 1, fb[0], fb[1], fb[2]);
-                const int sxa = inward(E, 0, x), sxb = inward(E, 0, x + 1);
-                const int sy = inward(E, 1, y), sz = inward(E, 2, z);
-                const int ry = (sy + sz * E.n[1]) * E.P;
-                const Moments ma = pull_moments<S, true>(gin + E.pop_off, E.nslot, (uint32_t)((int)c + sxa + ry),
-                                                         pull_offsets(E, x + sxa, y + sy, z + sz));
-                const Moments mb = pull_moments<S, true>(gin + E.pop_off, E.nslot,
-                                                         (uint32_t)((int)c + 1 + sxb + ry),
-                                                         pull_offsets(E, x + 1 + sxb, y + sy, z + sz));
-                const Herm ha = cell_coeffs<S, EQ3>(C, ma, x, y, z, sxa, sy, sz, fa[0], fa[1], fa[2]);
-                const Herm hb = cell_coeffs<S, EQ3>(C, mb, x + 1, y, z, sxb, sy, sz, fb[0], fb[1], fb[2]);
-                drout = ha.drout + hb.drout;
-                emit_pair<S, EQ3>(ha, hb, gout + E.pop_off, E.nslot, c);
-            }
-        }
-    } else {
-    const uint32_t c = (uint32_t)(b - E.block0) * K1_THREADS + threadIdx.x;
-    if (c < E.nslot) {
-        const uint32_t row = fdiv(c, E.div_P);
-        const int x = (int)(c - row * (uint32_t)E.P);
-        if (x < E.n[0]) {
-            const uint32_t zz = fdiv(row, E.div_ny);
-            const int y = (int)(row - zz * (uint32_t)E.n[1]);
-            const int z = (int)zz;
-            float fx, fy, fz;
-            take_ib_force(E, fib, stamps, stamp, c, fx, fy, fz);
-            const int sx = inward(E, 0, x), sy = inward(E, 1, y), sz = inward(E, 2, z);
-            // a boundary cell takes its moments from the inward neighbour x_f
-            const int px = x + sx, py = y + sy, pz = z + sz;
-            const uint32_t p = (uint32_t)((int)c + sx + (sy + sz * E.n[1]) * E.P);
-            const PullOffsets o = pull_offsets(E, px, py, pz);
-            const Moments m = pull_moments<S, true>(gin + E.pop_off, E.nslot, p, o);
-            drout = update_cell<S, EQ3>(C, m, x, y, z, sx, sy, sz, fx, fy, fz, gout + E.pop_off, c);
-        }
-    }
-    }
+    const float drout = plain_block_cells<S, EQ3, PAIR>(gin, gout, E, C, b - E.block0, fib, stamps, stamp);
     const float t = block_sum_f32(drout, wsum);
     if (threadIdx.x == 0) {
         Pair32 p;

@@ -22,11 +22,11 @@ FG_ERR_TIMEOUT, FG_ERR_NUMERIC, FG_ERR_STATE = -4, -5, -6
 FG_F32, FG_F16, FG_BF16 = 0, 1, 2
 FG_PERIODIC, FG_VELOCITY, FG_OUTFLOW, FG_FREESLIP = 0, 1, 2, 3
 FG_K_IB, FG_K_STREAM_COLLIDE, FG_K_REDUCE, FG_K_COUNT = 0, 1, 2, 3
-FG_KERNEL_AUTO, FG_KERNEL_PLAIN, FG_KERNEL_STAGED, FG_KERNEL_STAGED512 = 0, 1, 2, 3
-FG_K1_PLAIN, FG_K1_STAGED256, FG_K1_STAGED512, FG_K1_NVARIANTS = 0, 1, 2, 3
-K1_NAMES = {0: "plain", 1: "staged256", 2: "staged512"}
+FG_KERNEL_AUTO, FG_KERNEL_PLAIN, FG_KERNEL_STAGED, FG_KERNEL_STAGED512, FG_KERNEL_FUSED = 0, 1, 2, 3, 4
+FG_K1_PLAIN, FG_K1_STAGED256, FG_K1_STAGED512, FG_K1_FUSED, FG_K1_NVARIANTS = 0, 1, 2, 3, 4
+K1_NAMES = {0: "plain", 1: "staged256", 2: "staged512", 3: "fused"}
 VARIANT = {"auto": FG_KERNEL_AUTO, "plain": FG_KERNEL_PLAIN, "staged": FG_KERNEL_STAGED,
-           "staged512": FG_KERNEL_STAGED512}
+           "staged512": FG_KERNEL_STAGED512, "fused": FG_KERNEL_FUSED}
 STORAGE = {"f32": FG_F32, "f16": FG_F16, "bf16": FG_BF16}
 
 
