@@ -18,11 +18,17 @@ import pytest
 
 from paper_2206_01683_b300 import fishlbm, inputs
 
-from parity_util import Pair, rel_l2
+from parity_util import Pair, assert_local, rel_l2
 
 pytestmark = pytest.mark.gpu
 
 TOL = {"f16": 2e-3, "bf16": 5e-2}
+# Per-cell bound of the 16-bit storage (largest cell difference of u and of
+# f - w over the field's largest magnitude), frozen at each dtype's L2 bar as
+# for FP32 after one measurement (largest of the sphere box and swimmer
+# cases: FP16 6.7e-4, BF16 8.0e-3; the boundary-layer and stencil-support
+# rel-L2: FP16 6.4e-4, BF16 1.5e-2).
+TOL_MAX = {"f16": 2e-3, "bf16": 5e-2}
 OPEN_X = (1, 2, 3, 3, 3, 3)
 
 
@@ -39,6 +45,7 @@ def test_sphere_box_reduced_storage(storage, variant):
     err = p.errors()
     print("sphere box", storage, variant, {k: "%.3g" % v for k, v in err.items()})
     assert err["u"] <= TOL[storage], err
+    assert_local(err, tol=TOL[storage], tol_max=TOL_MAX[storage], where="sphere %s %s" % (storage, variant))
     assert err["force"] <= TOL[storage], err
     assert err["torque"] <= TOL[storage], err
 
@@ -57,6 +64,7 @@ def test_swimmer_channel_reduced_storage(storage):
     err = p.errors()
     print("swimmer", storage, {k: "%.3g" % v for k, v in err.items()})
     assert err["u"] <= TOL[storage], err
+    assert_local(err, tol=TOL[storage], tol_max=TOL_MAX[storage], where="swimmer %s" % storage)
     assert err["force"] <= TOL[storage], err
 
 
