@@ -29,6 +29,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+REPEATS = 5   # timed repetitions of K steps; the median is reported
+
 METRIC = "MLUPS and % HBM roofline per step (FP32 vs FP16-storage vs batched), 1×B300"
 OPEN_X = (1, 2, 3, 3, 3, 3)   # inlet, outflow, free-slip walls
 
@@ -136,11 +138,10 @@ def fish_workload(total_steps, shape=(256, 128, 128), length=64.0, n_markers=600
     traj = inputs.FrameTrajectory(inputs.seed_for(2), inputs.domain_centre(shape))
     X = np.zeros((total_steps, n_markers, 3), np.float32)
     U = np.zeros((total_steps, n_markers, 3), np.float32)
-    frames = []
-    for n in range(total_steps):
-        x, u = fish.pose(n)
-        X[n], U[n] = x, u
-        frames.append(traj.at(n))
+    for n0 in range(0, total_steps, 256):
+        ts = np.arange(n0, min(n0 + 256, total_steps))
+        X[ts], U[ts] = fish.poses(ts)
+    frames = [traj.at(n) for n in range(total_steps)]
     return fish, X, U, np.array(frames)
 
 
@@ -152,12 +153,43 @@ def _barrier(world):
         torch.cuda.synchronize()
 
 
-def _timed(stream, world, fn, steps):
+def _sleep_ahead(stream, ms):
+    """A spin kernel on the stream ahead of the start event: the host enqueues
+    the timed steps while it runs, so no host launch gap falls inside the
+    timed region (the e2e metric keeps the host's time)."""
+    import torch
+    if ms > 0:
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(int(ms * 2.1e6))   # clock cycles, at up to 2.1 GHz
+
+
+def _ahead_ms(host_ms_per_step, steps):
+    """How long the GPU is kept busy before a timed region of `steps` steps:
+    1.5 x the host's enqueue time for them (measured on the warm-up steps),
+    at least 0.5 ms, at most 200 ms."""
+    return min(200.0, max(0.5, 1.5 * host_ms_per_step * steps))
+
+
+def _warm(fn, steps):
+    """Run the warm-up steps; returns the host's enqueue time per step (ms)
+    over the second half of them (the first step may run the autotuner)."""
+    steps = list(steps)
+    half = len(steps) // 2
+    for n in steps[:half]:
+        fn(n)
+    t0 = time.perf_counter()
+    for n in steps[half:]:
+        fn(n)
+    return (time.perf_counter() - t0) * 1e3 / max(len(steps) - half, 1)
+
+
+def _timed(stream, world, fn, steps, ahead_ms=0.0):
     """Milliseconds for fn(n) over the given step indices, CUDA events on the
     library's stream, barrier + synchronize on both sides."""
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     _barrier(world)
+    _sleep_ahead(stream, ahead_ms)
     e0.record(stream)
     for n in steps:
         fn(n)
@@ -234,9 +266,8 @@ def storage_form(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W,
         dom.set_markers(Xd[n], Ud[n], None, None, n_seg=5, ref=ref)
         dom.step(1, [fr[n]])
 
-    for n in range(W):
-        step(n)
-    ms = _max_over_ranks(_timed(stream, world, step, range(W, W + K)), world)
+    hms = _warm(step, range(W))
+    ms = _max_over_ranks(_timed(stream, world, step, range(W, W + K), _ahead_ms(hms, K)), world)
     dom.get_body_force_torque()
     k = _kernel_ms(dom, step, range(W + K, W + 2 * K))
     ncell = shape[0] * shape[1] * shape[2]
@@ -306,9 +337,8 @@ def school_form(W, K, world, peak, vkw):
         dom.set_markers(Xd[n], Ud[n], None, None, n_seg=school.n_seg, ref=tuple(school.ref))
         dom.step(1, [fr[n]])
 
-    for n in range(W):
-        step(n)
-    ms = _max_over_ranks(_timed(stream, world, step, range(W, W + K)), world)
+    hms = _warm(step, range(W))
+    ms = _max_over_ranks(_timed(stream, world, step, range(W, W + K), _ahead_ms(hms, K)), world)
     ft = dom.get_body_force_torque()
     k = _kernel_ms(dom, step, range(W + K, W + 2 * K))
     ncell = shape[0] * shape[1] * shape[2]
@@ -347,6 +377,55 @@ def free_sphere_form(W, K, world, vkw):
     return out
 
 
+def large_sphere_form(W, K, world, peak, vkw):
+    """The precision workload: a 13,500-marker sphere (R = 32.78, dV = 1)
+    translating at 0.05 lu/step through a 384x192x192 periodic box at tau =
+    0.56, with populations stored as FP32, FP16 and BF16 (f - w), FP32
+    arithmetic; marker poses resident in HBM.  Each storage's MLUPS and
+    stream-collide roofline, and its speed-up over the FP32 storage."""
+    import torch
+    from paper_2206_01683_b300 import fishlbm, inputs
+    shape, tau, nm = (384, 192, 192), 0.56, 13500
+    centre = (383 / 2 - 48.0, 95.5, 95.5)
+    R = (nm / (4 * np.pi)) ** 0.5
+    X0, dV = inputs.fibonacci_sphere(nm, R, centre)
+    T = W + 2 * K
+    U1 = np.array([0.05, 0.0, 0.0])
+    X = np.stack([X0 + U1 * n for n in range(T)]).astype(np.float32)
+    Xd = torch.from_numpy(X).cuda()
+    Ud = torch.from_numpy(np.tile(U1, (nm, 1)).astype(np.float32)).cuda()
+    dVd = torch.from_numpy(dV.astype(np.float32)).cuda()
+    ncell = shape[0] * shape[1] * shape[2]
+    out = {"workload": "large_sphere_box_384x192x192", "markers": nm,
+           "accuracy": "FP64-oracle parity per storage: tests/test_gpu_full_configs.py (bars f32 1e-5, f16 2e-3, "
+                       "bf16 5e-2)"}
+    for st in ("f32", "f16", "bf16"):
+        stream = torch.cuda.Stream()
+        dom = fishlbm.Domain([fishlbm.env_desc(shape, tau)], storage=st, stream=stream.cuda_stream, **vkw)
+        dom.set_markers(Xd[0], Ud, dVd)
+
+        def step(n):
+            dom.set_markers(Xd[n], Ud, None)
+            dom.step(1)
+
+        hms = _warm(step, range(W))
+        ms = _max_over_ranks(_timed(stream, world, step, range(W, W + K), _ahead_ms(hms, K)), world)
+        dom.get_body_force_torque()
+        k = _kernel_ms(dom, step, range(W + K, W + 2 * K))
+        gbs = dom.stream_collide_bytes() / (k[1] * 1e-3) / 1e9
+        out[st] = {"value": round(world * ncell * K / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+                   "ms_per_step": round(ms / K, 5), "kernel_variant": dom.stream_collide_variant(),
+                   "roofline": {"bound": "hbm", "kernel": "k_stream_collide", "achieved": round(gbs, 1),
+                                "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+                                "algorithmic_bytes_per_cell": 216 if st == "f32" else 108,
+                                "kernel_ms": round(k[1], 5), "ib_ms": round(k[0], 5)}}
+        dom.close()
+        del dom
+    for st in ("f16", "bf16"):
+        out[st]["speedup_vs_f32_storage"] = round(out[st]["value"] / out["f32"]["value"], 3)
+    return out
+
+
 def batched_form(W, K, world, peak, vkw, n_envs=64):
     """64 independent single-fish environments, grid sizes drawn by seed from
     {96x64x64, 128x64x64, 160x80x80, 192x96x96}, fish of 0.4 x grid length
@@ -366,36 +445,44 @@ def batched_form(W, K, world, peak, vkw, n_envs=64):
         trajs.append(inputs.FrameTrajectory(d["frame_seed"], inputs.domain_centre(shape)))
     T = W + 2 * K
     ts = np.arange(T)
-    stream = torch.cuda.Stream()
-    dom = fishlbm.Domain(descs, stream=stream.cuda_stream, **vkw)
     Xs, Us = [], []
-    for e, f in enumerate(fishes):
+    for f in fishes:
         X, U = f.poses(ts)
         Xs.append(X.astype(np.float32))
         Us.append(U.astype(np.float32))
-        ref = tuple(float(v) for v in f.joints_rest[0])
-        dom.set_markers(torch.from_numpy(Xs[e][0]).cuda(), torch.from_numpy(Us[e][0]).cuda(),
-                        torch.from_numpy(f.dV.astype(np.float32)).cuda(), torch.from_numpy(f.seg).cuda(),
-                        n_seg=5, ref=ref, env=e)
     # every step's markers of all environments, resident in HBM in the compact order
     Xall = torch.from_numpy(np.concatenate(Xs, axis=1)).cuda()
     Uall = torch.from_numpy(np.concatenate(Us, axis=1)).cuda()
     frames = [[fishlbm.frame_from_array(t.at(n)) for t in trajs] for n in range(T)]
-
-    def step(n):
-        dom.set_markers_all(Xall[n], Uall[n])
-        dom.step(1, frames[n])
-
-    for n in range(W):
-        step(n)
-    ms = _max_over_ranks(_timed(stream, world, step, range(W, W + K)), world)
-    for e in range(n_envs):
-        dom.get_body_force_torque(env=e)
-    k = _kernel_ms(dom, step, range(W + K, W + 2 * K))
     cells = sum(d["shape"][0] * d["shape"][1] * d["shape"][2] for d in draws)
-    gbs = dom.stream_collide_bytes() / (k[1] * 1e-3) / 1e9
-    variant = dom.stream_collide_variant()
-    dom.close()
+
+    def run(kw):
+        stream = torch.cuda.Stream()
+        dom = fishlbm.Domain(descs, stream=stream.cuda_stream, **kw)
+        for e, f in enumerate(fishes):
+            ref = tuple(float(v) for v in f.joints_rest[0])
+            dom.set_markers(torch.from_numpy(Xs[e][0]).cuda(), torch.from_numpy(Us[e][0]).cuda(),
+                            torch.from_numpy(f.dV.astype(np.float32)).cuda(), torch.from_numpy(f.seg).cuda(),
+                            n_seg=5, ref=ref, env=e)
+
+        def step(n):
+            dom.set_markers_all(Xall[n], Uall[n])
+            dom.step(1, frames[n])
+
+        hms = _warm(step, range(W))
+        ms = _max_over_ranks(_timed(stream, world, step, range(W, W + K), _ahead_ms(hms, K)), world)
+        for e in range(n_envs):
+            dom.get_body_force_torque(env=e)
+        k = _kernel_ms(dom, step, range(W + K, W + 2 * K))
+        gbs = dom.stream_collide_bytes() / (k[1] * 1e-3) / 1e9
+        variant = dom.stream_collide_variant()
+        dom.close()
+        return ms, k, gbs, variant, stream
+
+    ms, k, gbs, variant, stream = run(vkw)
+    # the same batch with the fused persistent kernel: one launch per step for
+    # the IB phases and stream-collide blocks of all environments
+    ms_f, k_f, gbs_f, _, _ = run({"variant": "fused"})
 
     # the same 64 environments as 64 plain FP32 single-environment domains,
     # stepped one after another on the same stream (no batching)
@@ -413,9 +500,8 @@ def batched_form(W, K, world, peak, vkw, n_envs=64):
             de.set_markers(Xe[n], Ue[n], None, None, n_seg=5, ref=ref)
             de.step(1, [frames[n][e]])
 
-    for n in range(W):
-        step_each(n)
-    ms_seq = _max_over_ranks(_timed(stream, world, step_each, range(W, W + K)), world)
+    hms = _warm(step_each, range(W))
+    ms_seq = _max_over_ranks(_timed(stream, world, step_each, range(W, W + K), _ahead_ms(hms, K)), world)
     for de, _, _, _ in doms:
         de.get_body_force_torque()
         de.close()
@@ -426,6 +512,11 @@ def batched_form(W, K, world, peak, vkw, n_envs=64):
                                    "ms_per_step": round(ms_seq / K, 5),
                                    "what": "the same envs as 64 FP32 single-env domains stepped in turn"},
             "speedup_vs_one_domain_per_env": round(ms_seq / ms, 3),
+            "fused_persistent": {"value": round(world * cells * K / (ms_f * 1e-3) / 1e6, 1), "unit": "MLUPS",
+                                 "ms_per_step": round(ms_f / K, 5), "kernel_ms": round(k_f[1], 5),
+                                 "reduce_ms": round(k_f[2], 5),
+                                 "what": "k_step_fused: IB phases and stream-collide blocks of all 64 envs in "
+                                         "one persistent launch per step (+ the reduction)"},
             "roofline": {"bound": "hbm", "kernel": "k_stream_collide", "achieved": round(gbs, 1),
                          "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
                          "kernel_ms": round(k[1], 5), "ib_ms": round(k[0], 5), "reduce_ms": round(k[2], 5)}}
@@ -444,7 +535,7 @@ def run_ours(args):
     shape, tau, u_in = (256, 128, 128), 0.52, 0.02
     ncell = shape[0] * shape[1] * shape[2]
     W, K = args.warmup, args.steps
-    T = W + 2 * K + K   # warm-up, timed, roofline pass, e2e pass
+    T = 2 * W + 2 * REPEATS * K   # warm-up, timed repetitions, roofline pass and e2e (warm-up, repetitions)
     fish, X, U, frames = fish_workload(T, shape)
     fr = [fishlbm.frame_from_array(f) for f in frames]
     stream = torch.cuda.Stream()
@@ -473,23 +564,35 @@ def run_ours(args):
     barrier()
     dom.get_body_force_torque()
 
-    # ---- timed region: inputs resident in HBM
+    # ---- timed region: inputs resident in HBM.  The clock sampler starts
+    # first and the warm-up steps run after it, so the GPU does not sit idle
+    # (and drop its clocks) between the warm-up and the timed steps; the K
+    # steps are timed REPEATS times back to back and the median is reported.
     clocks = ClockSampler(local)
     clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    e0.record(stream)
-    for n in range(W, W + K):
-        dev_step(n)
-    e1.record(stream)
-    barrier()
+    hms = _warm(dev_step, range(W))
+    reps, host_ms = [], []
+    for r in range(REPEATS):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        _sleep_ahead(stream, _ahead_ms(hms, K))
+        e0.record(stream)
+        t0 = time.perf_counter()
+        for n in range(W + r * K, W + (r + 1) * K):
+            dev_step(n)
+        t1 = time.perf_counter()
+        e1.record(stream)
+        barrier()
+        reps.append(e0.elapsed_time(e1))
+        host_ms.append((t1 - t0) * 1e3)
     clock_info = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    ms = float(np.median(reps))
     dom.get_body_force_torque()   # raises on a numeric fault
+    base = W + REPEATS * K
 
     # ---- per-kernel durations over a second timed region (events around each launch)
     dom.profile(True)
-    for n in range(W + K, W + 2 * K):
+    for n in range(base, base + K):
         dev_step(n)
     kms, kcount = dom.profile_read()
     dom.profile(False)
@@ -498,18 +601,24 @@ def run_ours(args):
     red_ms = kms[fishlbm.FG_K_REDUCE] / max(kcount[fishlbm.FG_K_REDUCE], 1)
     algo_bytes = dom.stream_collide_bytes()
 
-    # ---- end to end: host (pinned) marker buffers in, body force out, every step
+    # ---- end to end: host (pinned) marker buffers in, body force out, every
+    # step; W untimed calls first (the first calls load kernels lazily)
     Xh = torch.from_numpy(X).pin_memory()
     Uh = torch.from_numpy(U).pin_memory()
     out = np.zeros((6, 6))
-    barrier()
-    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    h0.record(stream)
-    for n in range(W + 2 * K, W + 3 * K):
-        out = dom.step_io(Xh[n], Uh[n], [fr[n]])   # markers in, one step, force/torque out
-    h1.record(stream)
-    barrier()
-    e2e_ms = h0.elapsed_time(h1)
+    for n in range(base, base + W):
+        out = dom.step_io(Xh[n], Uh[n], [fr[n]])
+    e2e_reps = []
+    for r in range(REPEATS):
+        barrier()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for n in range(base + r * K, base + (r + 1) * K):
+            out = dom.step_io(Xh[n], Uh[n], [fr[n]])   # markers in, one step, force/torque out
+        h1.record(stream)
+        barrier()
+        e2e_reps.append(h0.elapsed_time(h1))
+    e2e_ms = float(np.median(e2e_reps))
 
     ms = _max_over_ranks(ms, world)
     e2e_ms = _max_over_ranks(e2e_ms, world)
@@ -518,11 +627,9 @@ def run_ours(args):
     if not args.no_forms:
         # every rank runs every form (their barriers and reductions pair up)
         Kf = min(K, args.form_steps)
+        # ordered so that the reduced-precision, large-sphere and batched forms
+        # come last in the printed line
         forms = {
-            "f16": storage_form("f16", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world, peak,
-                                _variant_kw(args)),
-            "bf16": storage_form("bf16", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world, peak,
-                                 _variant_kw(args)),
             "mdf3": storage_form("f32", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world, peak,
                                  _variant_kw(args), ib_iters=3),
             "deterministic": storage_form("f32", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world,
@@ -531,8 +638,13 @@ def run_ours(args):
                                 _variant_kw(args), eq_order=3),
             "school": school_form(W, Kf, world, peak, _variant_kw(args)),
             "free_sphere": free_sphere_form(W, Kf, world, _variant_kw(args)),
-            "batched": batched_form(W, Kf, world, peak, _variant_kw(args)),
             "adjoint": adjoint_form(),
+            "f16": storage_form("f16", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world, peak,
+                                _variant_kw(args)),
+            "bf16": storage_form("bf16", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world, peak,
+                                 _variant_kw(args)),
+            "large_sphere": large_sphere_form(W, Kf, world, peak, _variant_kw(args)),
+            "batched": batched_form(W, Kf, world, peak, _variant_kw(args)),
         }
     if rank != 0:
         if world > 1:
@@ -573,8 +685,14 @@ def run_ours(args):
                      "reduce_ms": round(red_ms, 5)},
         "e2e": {"value": round(world * ncell * K / (e2e_ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": 4 * K,   # marker copy, k_ib_step, stream-collide, k_reduce
+        "gpu_launches": 4 * K,   # per timed repetition: marker copy, k_ib_step, stream-collide, k_reduce
         "clocks": clock_info,
+        "timing": {"repeats": REPEATS, "ms_per_step_each": [round(r / K, 5) for r in reps],
+                   "e2e_ms_per_step_each": [round(r / K, 5) for r in e2e_reps],
+                   "host_submit_ms_per_step": round(float(np.median(host_ms)) / K, 5),
+                   "what": "median of the repetitions; host_submit = host time to enqueue a step (no "
+                           "sync); a spin kernel ahead of each timed region lets the host enqueue the K steps "
+                           "before the GPU reaches them (e2e keeps the host's time)"},
     }
     if forms is not None:
         line["forms"] = dict(

@@ -419,32 +419,40 @@ fg_status fg_stream_collide_bytes(fg_domain* d, unsigned long long* bytes);
  * control loop that cannot afford the device-wide synchronisation that
  * cudaMalloc and cudaFree imply.
  *
- * fg_body_force_noalloc computes what fg_step reports through
- * fg_get_body_force_torque for a step that starts from the state g: the
- * post-stream velocity interpolated at the markers (Peskin 4-point delta,
- * frame half-force shift), the direct-forcing marker force F_l =
- * 2 R_l (U_l - U~_l), and the force and torque on the body, FP64.  It does
- * not spread the force or advance the fluid.  It allocates nothing: its
- * scratch (one float triple per marker and a flag word) is a static device
- * array of FG_NOALLOC_MAX_MARKERS markers, about 0.8 MB, that every GPU
- * loading this library holds until the process exits.
+ * fg_body_force_noalloc computes, for a step that starts from the state g,
+ * the post-stream velocity interpolated at the markers (Peskin 4-point
+ * delta, frame half-force shift), the direct-forcing marker force F_l =
+ * 2 R_l (U_l - U~_l), and the force and torque on the body, FP64.  That is
+ * what fg_step reports through fg_get_body_force_torque for a domain with
+ * one no-slip direct-forcing pass (ib_iters = 1, ib_slip = 0) whose segment
+ * rows are all taken about ref (no fg_set_segment_refs); it is not that for
+ * other domains.  It does not spread the force or advance the fluid.  It
+ * allocates nothing: its scratch (one float triple per marker and a flag
+ * word) is a static device array of FG_NOALLOC_MAX_MARKERS markers, about
+ * 0.8 MB, that every GPU loading this library holds until the process exits.
  *   env     grid size and faces (tau, u_in, rho0, u0 are not used)
  *   g       device, FP32, the populations in the library's storage layout:
  *           f_i - w_i as g[27][nz][ny][P], P = nx rounded up to a multiple of
  *           8, velocity order of fg_lattice (what fg_save_state returns for
  *           an FP32 domain)
  *   X, U    device, float [n][3]; dV device float [n]; seg device int [n] in
- *           [0, n_seg) or NULL; 1 <= n_seg <= 16; ref[3] host (NULL: origin)
+ *           [0, n_seg) or NULL; 1 <= n_seg <= 16; ref[3] host (NULL: origin),
+ *           the point every row's torque is taken about
  *   frame   host, or NULL for a frame at rest with origin at the centre
  *   out     device, double [(n_seg + 1) * 6]: one row per segment, then the
  *           total; NaN rows if a marker lay outside its allowed range
  *           (2 <= X < n-3 along non-periodic axes)
  * Runs asynchronously on cuda_stream (a cudaStream_t, NULL = legacy default).
  * The first call on a device looks up the scratch's device address with that
- * device current; make that first call before any stream capture.  Every
- * call uses the same scratch: calls that overlap on the GPU (on different
- * streams, or from different threads) race and must be serialised by the
- * caller.  n > FG_NOALLOC_MAX_MARKERS is rejected with FG_ERR_INVALID. */
+ * device current; make that first call before any stream capture.  Later
+ * calls outside a capture look it up again (a context created anew, after a
+ * device reset, is then served at its own address); a call under capture
+ * uses the address found last, and fails with FG_ERR_STATE if there is none.
+ * Every call uses the same scratch, which keeps the last call's contents
+ * (each call clears the flag word before use): calls that overlap on the GPU
+ * (on different streams, or from different threads) race and must be
+ * serialised by the caller.  n > FG_NOALLOC_MAX_MARKERS is rejected with
+ * FG_ERR_INVALID. */
 #define FG_NOALLOC_MAX_MARKERS 65536
 fg_status fg_body_force_noalloc(const fg_env_desc* env, const float* g, const float* X, const float* U,
                                 const float* dV, const int* seg, int n, int n_seg, const double ref[3],

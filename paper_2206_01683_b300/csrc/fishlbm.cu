@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -205,11 +206,13 @@ struct fg_domain {
         Pair32 ft[FT_ROW];
         Pair32 mass;
         int status;
+        long long seq;                   // the step number k_reduce wrote last
     }* rb = nullptr;
     Pair32* rb_ft_all = nullptr;         // pinned: the force/torque rows of all environments
     // device addresses of the mapped pinned copies k_reduce writes every step
     Pair32* rb_ft_all_dev = nullptr;
     int* rb_status_dev = nullptr;
+    long long* rb_seq_dev = nullptr;
     long long steps = 0;
     StepState* d_state = nullptr;        // stamp / step / completion count on the device
     bool poisoned = false;
@@ -648,7 +651,7 @@ fg_status enqueue_step_io(fg_domain* d, const typename S::raw* gin, typename S::
                               (const float*)d->dV, (const int*)d->seg, (const float*)d->seg_ref,
                               (const Pair32*)d->mass_part, d->red_partials, d->red_counters, d->n_envs, d->red_z,
                               d->ft, d->mass, d->hist, d->opt.record_history, d->d_state, d->status,
-                              d->rb_ft_all_dev, d->rb_status_dev, fused ? 1 : 0));
+                              d->rb_ft_all_dev, d->rb_status_dev, d->rb_seq_dev, fused ? 1 : 0));
     }
     if (ev) CK(cudaEventRecord(ev[FG_K_REDUCE][1], s));
     CK(cudaGetLastError());
@@ -1042,6 +1045,8 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         }
         if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&d->rb_ft_all_dev, d->rb_ft_all, 0);
         if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&d->rb_status_dev, &d->rb->status, 0);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&d->rb_seq_dev, &d->rb->seq, 0);
+        if (e == cudaSuccess) d->rb->seq = -1;
         if (e != cudaSuccess) {
             free_all(d);
             delete d;
@@ -1584,9 +1589,28 @@ fg_status fg_step_io(fg_domain* d, const float* X, const float* U, int device_pt
     fg_status st = FG_OK;
     if (X && (st = fg_set_markers_all(d, d->total_markers, X, U, device_ptrs)) != FG_OK) return st;
     if ((st = fg_step(d, 1, frames)) != FG_OK) return st;
-    // the step's k_reduce wrote the rows and the status word to mapped pinned
-    // memory: no copy to issue, the synchronisation makes them visible
-    CK(cudaStreamSynchronize(d->stream));
+    // The step's k_reduce writes the rows, the status word and then the step
+    // number to mapped pinned memory: no copy to issue.  The host polls the
+    // step number (waking from a stream synchronisation takes longer than the
+    // step on a busy host) for at most 20 ms, then synchronises the stream.
+    {
+        const long long want = d->steps;
+        volatile const long long* seq = &d->rb->seq;
+        const auto t0 = std::chrono::steady_clock::now();
+        bool seen = false;
+        for (unsigned i = 0;; ++i) {
+            if (*seq == want) {
+                seen = true;
+                break;
+            }
+            if ((i & 1023u) == 1023u && std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(20)) break;
+        }
+        std::atomic_thread_fence(std::memory_order_acquire);
+        if (!seen) CK(cudaStreamSynchronize(d->stream));
+        // a launch or execution error of the step, if any, surfaces here
+        const cudaError_t q = cudaStreamQuery(d->stream);
+        if (q != cudaSuccess && q != cudaErrorNotReady) return cuda_fail(q, "fg_step_io");
+    }
     if ((st = status_to_error(d, d->rb->status)) != FG_OK) return st;
     size_t o = 0;
     for (int e = 0; e < d->n_envs; ++e) {

@@ -11,10 +11,12 @@
 // loads this library holds until the process exits.
 //
 // Host code must not pass the array's name to a kernel: on the host that name
-// is a stand-in, not a device address.  The device address is looked up once
-// per device with cudaGetSymbolAddress, with that device current, on the
-// first call made on it (so that first call should come before any stream
-// capture), and passed to the kernels.
+// is a stand-in, not a device address.  The device address is looked up with
+// cudaGetSymbolAddress, with the device current, on the first call made on a
+// device (so that first call should come before any stream capture), and
+// looked up again on every later call made outside a stream capture, so that
+// a context created anew (after cudaDeviceReset, say) is served at its own
+// address; a call under capture uses the address found last.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -44,19 +46,26 @@ fg_status nf_fail(fg_status s, const std::string& m) {
     return s;
 }
 
-// Per-device set-up: the device address of the scratch array.
-fg_status scratch_for_current_device(float** out) {
+// Per-device set-up: the device address of the scratch array, looked up
+// outside stream capture (the lookup may load the module), else the address
+// found by the last lookup on this device.
+fg_status scratch_for_current_device(cudaStream_t s, float** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return nf_fail(FG_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= MAX_DEVICES) return nf_fail(FG_ERR_INVALID, "device ordinal beyond 63");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return nf_fail(FG_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess)
             return nf_fail(FG_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         g_scratch_addr[dev] = static_cast<float*>(p);
+    } else if (!g_scratch_addr[dev]) {
+        return nf_fail(FG_ERR_STATE, "fg_body_force_noalloc: the first call on a device must precede stream capture");
     }
     *out = g_scratch_addr[dev];
     return FG_OK;
@@ -191,7 +200,7 @@ extern "C" fg_status fg_body_force_noalloc(const fg_env_desc* env, const float* 
     const unsigned long long P = (unsigned long long)(env->nx + 7) / 8 * 8;
     if (P * env->ny * env->nz >= (1ull << 31)) return nf_fail(FG_ERR_INVALID, "fg_body_force_noalloc: grid too large");
     float* scratch = nullptr;
-    fg_status st = scratch_for_current_device(&scratch);
+    fg_status st = scratch_for_current_device((cudaStream_t)cuda_stream, &scratch);
     if (st != FG_OK) return st;
 
     EnvDev E;
@@ -213,7 +222,8 @@ extern "C" fg_status fg_body_force_noalloc(const fg_env_desc* env, const float* 
     }
     F.inv_1pom2 = (float)(1.0 / (1.0 + oo));
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    // the flag word must start at zero on every call; the forces are overwritten
+    // the flag word must start at zero on every call (the scratch keeps the
+    // last call's contents); the forces are overwritten
     cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(int), s);
     if (e == cudaSuccess && n > 0) {
         const int blocks = (n + IB_THREADS / 32 - 1) / (IB_THREADS / 32);

@@ -126,7 +126,7 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
          Pair32* __restrict__ partials, int* __restrict__ counters, int n_envs, int zmax,
          Pair32* __restrict__ ft, Pair32* __restrict__ mass, Pair32* __restrict__ hist, int hist_cap,
          StepState* __restrict__ st, int* __restrict__ status, Pair32* __restrict__ host_ft,
-         int* __restrict__ host_status, int markers_pre) {
+         int* __restrict__ host_status, long long* __restrict__ host_seq, int markers_pre) {
     constexpr int NW = RED_THREADS / 32;
     __shared__ Pair32 sh[NW][6];
     __shared__ int is_last;
@@ -236,7 +236,10 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
     if (tid != 0) return;
     counters[e] = 0;   // ready for the next step
     if (n_envs > 1) {
-        __threadfence();
+        // the host-mapped rows of this environment are ordered before the
+        // sequence word the last environment writes
+        if (host_ft) __threadfence_system();
+        else __threadfence();
         if (atomicAdd(&st->envs_done, 1) != n_envs - 1) return;
         st->envs_done = 0;
     }
@@ -245,6 +248,11 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
     // the step's status word (every kernel of the step, and every
     // environment's combine, has set its bits by now) to the host-mapped copy
     if (host_status) *host_status = atomicOr(status, 0);
+    // then the step number: a host waiting for this step's rows may poll it
+    if (host_seq) {
+        __threadfence_system();
+        *reinterpret_cast<volatile long long*>(host_seq) = st->step;
+    }
 }
 
 // Momentum and angular momentum of the fluid inside a sphere (centre c,

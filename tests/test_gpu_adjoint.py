@@ -175,7 +175,14 @@ def test_thrust_gradient_matches_oracle_central_differences():
     scale = np.abs(fd).max()
     assert scale > 0
     err = np.abs(g - fd)
-    assert np.all(err <= 1e-3 * np.abs(fd) + 2e-3 * scale), (g, fd)
+    print("thrust gradient: adjoint", g, "oracle FD", fd, "rel", err / np.abs(fd))
+    # 1e-3 relative per component, above a floor for what neither side
+    # resolves: the oracle's central difference carries O(h^2) truncation
+    # (about 1e-7 of the largest component at h = 1e-3) and the CUDA forward
+    # sees float32 marker data (rounding 6e-8 relative), so a component below
+    # about 1e-5 of the largest is compared at that absolute level
+    floor = 1e-5 * scale
+    assert np.all(err <= 1e-3 * np.abs(fd) + floor), (g, fd, err)
 
 
 def test_thrust_gradient_full_size_matches_gpu_central_differences():
@@ -198,6 +205,12 @@ def test_thrust_gradient_full_size_matches_gpu_central_differences():
         e[k] = h
         fd[k] = (adjoint.SwimThrust.apply(th0 + e, prob).item() -
                  adjoint.SwimThrust.apply(th0 - e, prob).item()) / (2 * h)
-    scale = np.abs(fd).max()
-    assert np.all(np.abs(g - fd) <= 1e-2 * np.abs(fd) + 1e-2 * scale), (g, fd)
+    # 1e-2 relative per component (central differences of an FP32 forward),
+    # above the differences' own noise: the loss is resolved to about 1e-7 of
+    # |L| (FP32 dynamics, FP64 force rows), so a difference quotient carries
+    # about 1e-7 |L| / h; the floor is ten times that
+    floor = 10 * 1e-7 * abs(Lgpu.item()) / h
+    err = np.abs(g - fd)
+    print("full-size thrust gradient: adjoint", g, "GPU FD", fd, "floor", floor)
+    assert np.all(err <= 1e-2 * np.abs(fd) + floor), (g, fd, err, floor)
     assert prob.backward_ms is not None and prob.forward_ms > 0
