@@ -74,13 +74,18 @@ typedef struct {
  * phases (stamping the marker stencils, node moments, interpolation and
  * spreading) and PLAIN's cell update taken from one work queue, so that cell
  * blocks no marker reaches (and, in a batch, other environments' blocks)
- * proceed while the IB phases run.  All compute the same step. */
+ * proceed while the IB phases run.  OVERLAP runs PLAIN with the IB beside it:
+ * a small kernel stamps the markers' stencils and flags the PLAIN blocks they
+ * fall in, a second, high-priority stream runs the IB kernel and then the
+ * flagged blocks, while the domain's stream runs the other blocks.  All
+ * compute the same step. */
 typedef enum {
     FG_KERNEL_AUTO = 0,
     FG_KERNEL_PLAIN = 1,
     FG_KERNEL_STAGED = 2,
     FG_KERNEL_STAGED512 = 3,
-    FG_KERNEL_FUSED = 4
+    FG_KERNEL_FUSED = 4,
+    FG_KERNEL_OVERLAP = 5
 } fg_kernel_variant;
 
 #define FG_MAX_IB_ITERS 8
@@ -391,7 +396,14 @@ fg_status fg_profile(fg_domain* d, int enable);
 fg_status fg_profile_read(fg_domain* d, double* ms, long long* launches);
 
 /* Stream-collide variants (the autotuner's candidates). */
-enum { FG_K1_PLAIN = 0, FG_K1_STAGED256 = 1, FG_K1_STAGED512 = 2, FG_K1_FUSED = 3, FG_K1_NVARIANTS = 4 };
+enum {
+    FG_K1_PLAIN = 0,
+    FG_K1_STAGED256 = 1,
+    FG_K1_STAGED512 = 2,
+    FG_K1_FUSED = 3,
+    FG_K1_OVERLAP = 4,
+    FG_K1_NVARIANTS = 5
+};
 
 /* Time every stream-collide variant that can run this domain's rows with the
  * step's IB work (the IB kernel and the variant's kernel; the fused kernel

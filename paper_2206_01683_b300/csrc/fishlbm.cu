@@ -99,10 +99,14 @@ constexpr int MAX_STAGED_P = 512;   // longest row pitch the staged kernel takes
 
 // Stream-collide variants the domain can run (and the autotuner times):
 // the plain kernel, the staged kernel with 256 or 512 slots per population
-// in shared memory, and the fused step kernel (the plain kernel's cell
-// update and the IB phases in one persistent launch).
-enum { K1_PLAIN = 0, K1_STAGED256 = 1, K1_STAGED512 = 2, K1_FUSED = 3, K1_NVARIANTS = 4 };
-static_assert((int)K1_FUSED == (int)FG_K1_FUSED && (int)K1_NVARIANTS == (int)FG_K1_NVARIANTS, "variant ids of the header");
+// in shared memory, the fused step kernel (the plain kernel's cell update
+// and the IB phases in one persistent launch), and the plain kernel with the
+// IB beside it (the IB kernel on a second stream next to the plain kernel's
+// blocks that no stencil node falls in).
+enum { K1_PLAIN = 0, K1_STAGED256 = 1, K1_STAGED512 = 2, K1_FUSED = 3, K1_OVERLAP = 4, K1_NVARIANTS = 5 };
+static_assert((int)K1_FUSED == (int)FG_K1_FUSED && (int)K1_OVERLAP == (int)FG_K1_OVERLAP &&
+                  (int)K1_NVARIANTS == (int)FG_K1_NVARIANTS,
+              "variant ids of the header");
 static_assert(MAX_IB_PASSES == FG_MAX_IB_ITERS, "direct-forcing passes of the fused kernel");
 
 // Blocks per SM the staged kernel is compiled for.  The 512-slot row buffers
@@ -160,6 +164,13 @@ struct fg_domain {
     int k1 = K1_PLAIN;                   // stream-collide variant in use (K1_*)
     bool staged = false;                 // a staged variant
     int fused_grid = 0;                  // persistent blocks of k_step_fused
+    // the IB beside the stream-collide kernel: a second (high-priority)
+    // stream, the fork and join events, the blocks flagged by k_mark_tiles
+    cudaStream_t stream2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    uint32_t* blk_flag = nullptr;        // per plain block: the stamp of the last step a stencil node fell in it
+    size_t blk_flag_n = 0;
+    int prio_high = 0;                   // greatest stream priority
     // work queue of k_step_fused: the segment table (host copy and device),
     // the queue words and the per-environment completion counters
     std::vector<WorkSeg> work_host;
@@ -305,6 +316,10 @@ void free_all(fg_domain* d) {
     if (d->rb_ft_all) cudaFreeHost(d->rb_ft_all);
     for (int k = 0; k < FG_K_COUNT; ++k)
         for (cudaEvent_t e : d->ev[k]) cudaEventDestroy(e);
+    if (d->blk_flag) cudaFree(d->blk_flag);
+    if (d->ev_fork) cudaEventDestroy(d->ev_fork);
+    if (d->ev_join) cudaEventDestroy(d->ev_join);
+    if (d->stream2) cudaStreamDestroy(d->stream2);
 }
 
 template <class T>
@@ -567,6 +582,104 @@ fg_status enqueue_ib(fg_domain* d, const typename S::raw* gin, cudaStream_t s) {
     return FG_OK;
 }
 
+// The plain stream-collide kernel over the blocks `which` selects, on
+// stream s, at the given launch priority (0: the stream's own).
+template <class S, bool EQ3, bool PAIR>
+fg_status enqueue_plain_of(fg_domain* d, const typename S::raw* gin, typename S::raw* gout, cudaStream_t s,
+                           int which, int priority) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)d->total_blocks);
+    cfg.blockDim = dim3(K1_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = priority;
+    cfg.attrs = attr;
+    cfg.numAttrs = priority != 0 ? 1 : 0;
+    CK(cudaLaunchKernelEx(&cfg, k_stream_collide<S, EQ3, PAIR>, gin, gout, (const EnvDev*)d->d_env,
+                          (const FrameDev*)d->d_frame, d->n_envs, d->fib, (const uint32_t*)d->stamps,
+                          (const StepState*)d->d_state, d->mass_part, (const uint32_t*)d->blk_flag, which));
+    return FG_OK;
+}
+
+template <class S>
+fg_status enqueue_plain(fg_domain* d, const typename S::raw* gin, typename S::raw* gout, cudaStream_t s, int which,
+                        int priority) {
+    const bool eq3 = d->opt.eq_order == 3;
+    if (d->plain_pair)
+        return eq3 ? enqueue_plain_of<S, true, true>(d, gin, gout, s, which, priority)
+                   : enqueue_plain_of<S, false, true>(d, gin, gout, s, which, priority);
+    return eq3 ? enqueue_plain_of<S, true, false>(d, gin, gout, s, which, priority)
+               : enqueue_plain_of<S, false, false>(d, gin, gout, s, which, priority);
+}
+
+// The IB beside the stream-collide kernel (markers present): k_mark_tiles
+// stamps the stencil tiles and flags their blocks on stream s; a second,
+// high-priority stream then runs the IB phases as separate kernels
+// (k_ib_tiles, k_ib_markers) and the flagged blocks, while s runs the
+// unflagged blocks; s joins the second stream at the end.  With ev, the IB
+// phases are timed on the second stream and the stream-collide section
+// (from the unflagged launch to the join) on s.
+template <class S>
+fg_status enqueue_overlap(fg_domain* d, const typename S::raw* gin, typename S::raw* gout, cudaStream_t s,
+                          cudaEvent_t* const* ev) {
+    const int mblocks = (int)(((long long)d->total_markers * 16 + IB_THREADS - 1) / IB_THREADS);
+    k_mark_tiles<<<mblocks, IB_THREADS, 0, s>>>((const EnvDev*)d->d_env, d->n_envs, d->total_markers,
+                                                (const float*)d->X, (const StepState*)d->d_state, d->stamps,
+                                                d->blk_flag, d->plain_pair ? 9 : 8);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(d->ev_fork, s));
+    CK(cudaStreamWaitEvent(d->stream2, d->ev_fork, 0));
+    if (ev) CK(cudaEventRecord(ev[FG_K_IB][0], d->stream2));
+    {
+        // the IB phases as separate launches at the high priority
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributePriority;
+        attr[0].val.priority = d->prio_high;
+        cudaLaunchConfig_t cfg = {};
+        cfg.blockDim = dim3(IB_THREADS);
+        cfg.stream = d->stream2;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const int tile_blocks = std::max(1, std::min(4 * d->n_sms, (int)((d->n_stamps + 4095) / 4096)));
+        const int mk_blocks = (int)(((long long)d->total_markers * 16 + IB_THREADS - 1) / IB_THREADS);
+        const float* nrm = d->opt.ib_slip ? d->Nrm : nullptr;
+        cfg.gridDim = dim3((unsigned)tile_blocks);
+        CK(cudaLaunchKernelEx(&cfg, k_ib_tiles<S, false>, gin, (const EnvDev*)d->d_env, (const FrameDev*)d->d_frame,
+                              d->n_envs, (int)d->n_stamps, (const uint32_t*)d->stamps, (const StepState*)d->d_state,
+                              d->ib_nodes, d->fib, d->fibq));
+        cfg.gridDim = dim3((unsigned)mk_blocks);
+        CK(cudaLaunchKernelEx(&cfg, k_ib_markers<S, false>, (const EnvDev*)d->d_env, d->n_envs, d->total_markers,
+                              (const float*)d->X, (const float*)d->U, (const float*)d->dV, d->Fm, d->fib,
+                              (const float4*)d->ib_nodes, d->dF, d->fibq, nrm, 0, d->status));
+        for (int pass = 1; pass < d->opt.ib_iters; ++pass) {
+            CK(cudaLaunchKernelEx(&cfg, k_ib_markers<S, false>, (const EnvDev*)d->d_env, d->n_envs,
+                                  d->total_markers, (const float*)d->X, (const float*)d->U, (const float*)d->dV,
+                                  d->Fm, d->fib, (const float4*)d->ib_nodes, d->dF, d->fibq, nrm, pass, d->status));
+            CK(cudaLaunchKernelEx(&cfg, k_ib_markers<S, true>, (const EnvDev*)d->d_env, d->n_envs,
+                                  d->total_markers, (const float*)d->X, (const float*)d->U, (const float*)d->dV,
+                                  d->Fm, d->fib, (const float4*)d->ib_nodes, d->dF, d->fibq, nrm, pass, d->status));
+        }
+        if (d->fibq) {
+            cfg.gridDim = dim3((unsigned)tile_blocks);
+            CK(cudaLaunchKernelEx(&cfg, k_ib_tiles<S, true>, gin, (const EnvDev*)d->d_env,
+                                  (const FrameDev*)d->d_frame, d->n_envs, (int)d->n_stamps,
+                                  (const uint32_t*)d->stamps, (const StepState*)d->d_state, d->ib_nodes, d->fib,
+                                  d->fibq));
+        }
+    }
+    if (ev) CK(cudaEventRecord(ev[FG_K_IB][1], d->stream2));
+    fg_status st = enqueue_plain<S>(d, gin, gout, d->stream2, K1_FLAGGED_BLOCKS, d->prio_high);
+    if (st != FG_OK) return st;
+    CK(cudaEventRecord(d->ev_join, d->stream2));
+    if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][0], s));
+    if ((st = enqueue_plain<S>(d, gin, gout, s, K1_UNFLAGGED_BLOCKS, 0)) != FG_OK) return st;
+    CK(cudaStreamWaitEvent(s, d->ev_join, 0));
+    if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][1], s));
+    return FG_OK;
+}
+
 // The fused step kernel (IB phases and stream-collide blocks of every
 // environment from one work queue; all blocks resident) reading gin and
 // writing gout.
@@ -617,20 +730,26 @@ template <class S>
 fg_status enqueue_step_io(fg_domain* d, const typename S::raw* gin, typename S::raw* gout, cudaStream_t s,
                           cudaEvent_t* const* ev) {
     const bool fused = d->k1 == K1_FUSED;
-    if (!fused && d->total_markers > 0) {
-        if (ev) CK(cudaEventRecord(ev[FG_K_IB][0], s));
-        fg_status st = enqueue_ib<S>(d, gin, s);
-        if (st != FG_OK) return st;
-        if (ev) CK(cudaEventRecord(ev[FG_K_IB][1], s));
-    }
-    if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][0], s));
-    if (fused) {
-        fg_status st = enqueue_fused<S>(d, gin, gout, s);
+    const bool overlap = d->k1 == K1_OVERLAP && d->total_markers > 0;
+    if (overlap) {
+        fg_status st = enqueue_overlap<S>(d, gin, gout, s, ev);
         if (st != FG_OK) return st;
     } else {
-        enqueue_k1<S>(d, gin, gout, s);
+        if (!fused && d->total_markers > 0) {
+            if (ev) CK(cudaEventRecord(ev[FG_K_IB][0], s));
+            fg_status st = enqueue_ib<S>(d, gin, s);
+            if (st != FG_OK) return st;
+            if (ev) CK(cudaEventRecord(ev[FG_K_IB][1], s));
+        }
+        if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][0], s));
+        if (fused) {
+            fg_status st = enqueue_fused<S>(d, gin, gout, s);
+            if (st != FG_OK) return st;
+        } else {
+            enqueue_k1<S>(d, gin, gout, s);
+        }
+        if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][1], s));
     }
-    if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][1], s));
     if (ev) CK(cudaEventRecord(ev[FG_K_REDUCE][0], s));
     {
         // a programmatic dependent of the stream-collide kernel: its marker
@@ -772,7 +891,7 @@ fg_status staged_occupancy(fg_domain* d, int* per_sm) {
 }
 
 bool k1_runnable(const fg_domain* d, int v) {
-    if (v == K1_PLAIN || v == K1_FUSED) return true;
+    if (v == K1_PLAIN || v == K1_FUSED || v == K1_OVERLAP) return true;
     if (v == K1_STAGED256) return d->max_P <= 256;
     return v == K1_STAGED512 && d->max_P <= 512;
 }
@@ -915,7 +1034,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     o.use_graphs = 1;
     o.autotune = 0;
     if (opt) o = *opt;
-    if (o.kernel_variant < FG_KERNEL_AUTO || o.kernel_variant > FG_KERNEL_FUSED)
+    if (o.kernel_variant < FG_KERNEL_AUTO || o.kernel_variant > FG_KERNEL_OVERLAP)
         return fail(FG_ERR_INVALID, "unknown kernel variant");
     if (o.storage < 0 || o.storage > 2) return fail(FG_ERR_INVALID, "unknown storage");
     if (o.layout != 0) return fail(FG_ERR_INVALID, "only the two-buffer pull layout (0) exists");
@@ -1035,6 +1154,8 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     DA(d->status, 1);
     DA(d->work, WQ_WORDS);
     DA(d->work_done, (size_t)n_envs * N_SLOTS);
+    d->blk_flag_n = (size_t)block0;   // one-cell blocks: the most any layout has
+    DA(d->blk_flag, d->blk_flag_n);
 #undef DA
     {
         cudaError_t e = cudaHostAlloc((void**)&d->rb, sizeof(*d->rb), cudaHostAllocMapped);
@@ -1053,6 +1174,20 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
             return cuda_fail(e, "cudaHostAlloc");
         }
     }
+    {
+        // the second stream of the IB beside the stream-collide kernel
+        int lo = 0, hi = 0;
+        cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&d->stream2, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            free_all(d);
+            delete d;
+            return cuda_fail(e, "stream or event creation");
+        }
+        d->prio_high = hi;
+    }
     cudaError_t ce;
     StepState initial_state;
     initial_state.stamp = 1;
@@ -1070,6 +1205,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
                                           d->stream)) != cudaSuccess) ||
         (ce = cudaMemsetAsync(d->red_counters, 0, sizeof(int) * n_envs * RED_ROWS, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->work, 0, sizeof(int) * WQ_WORDS, d->stream)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(d->blk_flag, 0, sizeof(uint32_t) * d->blk_flag_n, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->work_done, 0, sizeof(int) * n_envs * N_SLOTS, d->stream)) != cudaSuccess ||
         (ce = cudaMemcpyAsync(d->d_state, &initial_state, sizeof(StepState), cudaMemcpyHostToDevice,
                               d->stream)) != cudaSuccess) {
@@ -1080,7 +1216,8 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     }
     refresh_marker_table(d);
     {
-        const int first = o.kernel_variant == FG_KERNEL_FUSED                    ? K1_FUSED
+        const int first = o.kernel_variant == FG_KERNEL_OVERLAP                  ? K1_OVERLAP
+                          : o.kernel_variant == FG_KERNEL_FUSED                    ? K1_FUSED
                           : o.kernel_variant == FG_KERNEL_PLAIN || !can_stage ? K1_PLAIN
                           : o.kernel_variant == FG_KERNEL_STAGED512              ? K1_STAGED512
                           : (d->max_P <= 256 ? K1_STAGED256 : K1_STAGED512);
@@ -1471,7 +1608,10 @@ fg_status fg_set_marker_normals(fg_domain* d, int env, int n, const float* N, in
 // would take them as stamped this step, so all stamps are cleared then.
 static fg_status note_stamp_advance(fg_domain* d) {
     d->stamp_host = d->stamp_host == 0xffffffffu ? 1u : d->stamp_host + 1u;
-    if (d->stamp_host == 1u) CK(cudaMemsetAsync(d->stamps, 0, sizeof(uint32_t) * d->n_stamps, d->stream));
+    if (d->stamp_host == 1u) {
+        CK(cudaMemsetAsync(d->stamps, 0, sizeof(uint32_t) * d->n_stamps, d->stream));
+        CK(cudaMemsetAsync(d->blk_flag, 0, sizeof(uint32_t) * d->blk_flag_n, d->stream));
+    }
     return FG_OK;
 }
 
@@ -2033,6 +2173,7 @@ fg_status fg_autotune(fg_domain* d, int* choice, double* ms) {
                 raw* gout = (raw*)d->pop[d->cur ^ 1];
                 auto pass = [&]() -> fg_status {
                     if (v == K1_FUSED) return enqueue_fused<S>(d, gin, gout, d->stream);
+                    if (v == K1_OVERLAP && d->total_markers > 0) return enqueue_overlap<S>(d, gin, gout, d->stream, nullptr);
                     if (d->total_markers > 0) {
                         fg_status s1 = enqueue_ib<S>(d, gin, d->stream);
                         if (s1 != FG_OK) return s1;

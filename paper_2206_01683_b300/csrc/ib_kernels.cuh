@@ -559,6 +559,131 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
     }
 }
 
+// The mark phase as a kernel of its own, for the step that runs the IB
+// beside the stream-collide kernel: half a warp per marker stamps the tiles
+// of its stencil and flags the plain stream-collide block of every stencil
+// node (blocks of 2^block_shift slots), so that the stream-collide launches
+// can split the cells into the blocks the IB force reaches and the rest.
+__global__ void __launch_bounds__(IB_THREADS)
+k_mark_tiles(const EnvDev* __restrict__ envs, int n_envs, int total_markers, const float* __restrict__ X,
+             const StepState* __restrict__ st, uint32_t* __restrict__ stamps, uint32_t* __restrict__ blk_flag,
+             int block_shift) {
+    const int m = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 4);
+    if (m >= total_markers) return;   // whole half-warps
+    const int h = threadIdx.x & 15;
+    const uint32_t stamp = st->stamp;
+    const int e = n_envs > 1 ? env_of<&EnvDev::mk_begin>(envs, n_envs, m) : 0;
+    const EnvDev& E = envs[e];
+    const Stencil S = marker_stencil(E, X, E.marker_off + (m - E.mk_begin));
+    if (!S.ok) return;   // the IB kernel reports it
+    const Column col = stencil_column(E, S, h);
+#pragma unroll
+    for (int kz = 0; kz < 4; ++kz) {
+        const uint32_t c = column_slot(E, col, S.base[2] + kz);
+        if (FG_IN_RANGE(DBG_NODE, c, E.nslot)) {
+            stamps[E.stamp_off + (c >> 5)] = stamp;
+            blk_flag[E.block0 + (c >> block_shift)] = stamp;
+        }
+    }
+}
+
+// The IB phases after the mark as separate, non-cooperative kernels, for
+// the step that runs the IB beside the stream-collide kernel: no grid
+// barrier holds a block between phases, so each block occupies its SM slot
+// only while it works (the phase order is the launch order on the stream).
+// The arithmetic is k_ib_step's.
+//
+// Node moments of the stamped tiles: warp w of the launch reads the stamps
+// of tiles w + nw (lane + 32 j), so that the stamped tiles, which come in
+// runs, spread over the warps; a hit tile is computed by the warp.
+// CONVERT != 0: instead, the deterministic spread's fixed-point sums of the
+// stamped tiles become the FP32 force field and are cleared.
+template <class S, bool CONVERT>
+__global__ void __launch_bounds__(IB_THREADS)
+k_ib_tiles(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs,
+           const FrameDev* __restrict__ frames, int n_envs, int n_stamps, const uint32_t* __restrict__ stamps,
+           const StepState* __restrict__ st, float4* __restrict__ nodes, float4* __restrict__ fib,
+           unsigned long long* __restrict__ fibq) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    const uint32_t stamp = st->stamp;
+    for (int t0 = gw; t0 < n_stamps; t0 += 32 * nw) {
+        const long long t = (long long)t0 + (long long)lane * nw;
+        const bool hit = t < n_stamps && __ldg(stamps + t) == stamp;
+        unsigned hits = __ballot_sync(0xffffffffu, hit);
+        while (hits) {
+            const int k = __ffs(hits) - 1;
+            hits &= hits - 1u;
+            const int tt = t0 + k * nw;
+            if (!CONVERT) {
+                ib_nodes<S>(gin, envs, frames, n_envs, tt, lane, nodes);
+            } else {
+                const int e = n_envs > 1 ? env_of<&EnvDev::stamp_off>(envs, n_envs, tt) : 0;
+                const EnvDev& E = envs[e];
+                const uint32_t c = (uint32_t)(tt - E.stamp_off) * 32u + (uint32_t)lane;
+                if (c < E.nslot) {
+                    unsigned long long* q = fibq + 3ull * (E.slot_off + c);
+                    fib[E.slot_off + c] = make_float4(fixed_to_float(q[0]), fixed_to_float(q[1]),
+                                                      fixed_to_float(q[2]), 0.f);
+                    q[0] = 0ull; q[1] = 0ull; q[2] = 0ull;
+                }
+            }
+        }
+    }
+}
+
+// Direct-forcing pass `pass` at half a warp per marker: pass 0 interpolates,
+// forms F and spreads it (a marker outside its allowed range gets F = 0 and
+// raises ST_BAD_MARKER); a later pass (SPREAD = false) interpolates the
+// corrected velocity, adds the increment to F and keeps it in dF; SPREAD =
+// true spreads the kept increments.
+template <class S, bool SPREAD>
+__global__ void __launch_bounds__(IB_THREADS)
+k_ib_markers(const EnvDev* __restrict__ envs, int n_envs, int total_markers, const float* __restrict__ X,
+             const float* __restrict__ U, const float* __restrict__ dV, float* __restrict__ Fm,
+             float4* __restrict__ fib, const float4* __restrict__ nodes, float* __restrict__ dF,
+             unsigned long long* __restrict__ fibq, const float* __restrict__ Nrm, int pass, int* status) {
+    const int m = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 4);
+    const int h = threadIdx.x & 15;
+    const bool here = m < total_markers;
+    MarkerRef r;
+    r.e = 0;
+    r.slot = 0;
+    r.S.ok = false;
+    if (here) r = load_marker(envs, n_envs, m, X, U, dV);
+    const bool active = here && r.S.ok;
+    const EnvDev& E = envs[r.e];
+    ColumnNodes cn;
+    if (active) cn = column_nodes(E, r, h);
+    if (SPREAD) {
+        if (active) {
+            const float* d = dF + 3 * r.slot;
+            const float3 F = make_float3(d[0], d[1], d[2]);
+            if (fibq) spread_force_fixed(E, r, cn, F, fibq, status);
+            else spread_force(E, r, cn, F, fib);
+        }
+        return;
+    }
+    if (pass == 0 && here && !r.S.ok && h == 0) {
+        Fm[3 * r.slot] = 0.f; Fm[3 * r.slot + 1] = 0.f; Fm[3 * r.slot + 2] = 0.f;
+        atomicOr(status, ST_BAD_MARKER);
+    }
+    // every lane takes part in the half-warp shuffles
+    const float3 F = interp_force(E, r, cn, active, pass, fib, fibq, nodes, Nrm);
+    if (!active) return;
+    if (pass == 0) {
+        if (fibq) spread_force_fixed(E, r, cn, F, fibq, status);
+        else spread_force(E, r, cn, F, fib);
+        if (h == 0) { Fm[3 * r.slot] = F.x; Fm[3 * r.slot + 1] = F.y; Fm[3 * r.slot + 2] = F.z; }
+    } else if (h == 0) {
+        float* Fl = Fm + 3 * r.slot;
+        Fl[0] += F.x; Fl[1] += F.y; Fl[2] += F.z;
+        float* d = dF + 3 * r.slot;
+        d[0] = F.x; d[1] = F.y; d[2] = F.z;
+    }
+}
+
 // Failure-detection self test of the bounded waits above, on conditions
 // that never come: (1) an mbarrier that expects one arrival nobody makes,
 // (2) the grid barrier with a target the counter never reaches.  Each wait

@@ -545,17 +545,25 @@ __device__ __forceinline__ float plain_block_cells(const typename S::raw* __rest
     return drout;
 }
 
+// Which blocks of the plain kernel a launch updates: all of them, or, when
+// the IB runs beside the stream-collide kernel, only the blocks that no
+// stencil node of this step falls in (their flag is not this step's stamp)
+// or only those that one does.
+enum { K1_ALL_BLOCKS = 0, K1_UNFLAGGED_BLOCKS = 1, K1_FLAGGED_BLOCKS = 2 };
+
 // Plain variant: one thread per slot (two with PAIR), direct loads.
 template <class S, bool EQ3 = false, bool PAIR = false>
 __global__ void __launch_bounds__(K1_THREADS)
 k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __restrict__ gout,
                  const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, int n_envs,
                  float4* __restrict__ fib, const uint32_t* __restrict__ stamps, const StepState* __restrict__ st,
-                 Pair32* __restrict__ mass_part) {
+                 Pair32* __restrict__ mass_part, const uint32_t* __restrict__ blk_flag = nullptr,
+                 int which = K1_ALL_BLOCKS) {
     __shared__ float wsum[K1_THREADS / 32];
     __shared__ CellConsts C;   // the block's environment constants, read by every cell
     const uint32_t stamp = st->stamp;
     const int b = blockIdx.x;
+    if (which != K1_ALL_BLOCKS && (__ldg(blk_flag + b) == stamp) != (which == K1_FLAGGED_BLOCKS)) return;
     const int e = n_envs > 1 ? env_of<&EnvDev::block0>(envs, n_envs, b) : 0;
     const EnvDev& E = envs[e];
     if (threadIdx.x == 0) C = load_consts(E, frames[e]);

@@ -22,11 +22,12 @@ FG_ERR_TIMEOUT, FG_ERR_NUMERIC, FG_ERR_STATE = -4, -5, -6
 FG_F32, FG_F16, FG_BF16 = 0, 1, 2
 FG_PERIODIC, FG_VELOCITY, FG_OUTFLOW, FG_FREESLIP = 0, 1, 2, 3
 FG_K_IB, FG_K_STREAM_COLLIDE, FG_K_REDUCE, FG_K_COUNT = 0, 1, 2, 3
-FG_KERNEL_AUTO, FG_KERNEL_PLAIN, FG_KERNEL_STAGED, FG_KERNEL_STAGED512, FG_KERNEL_FUSED = 0, 1, 2, 3, 4
-FG_K1_PLAIN, FG_K1_STAGED256, FG_K1_STAGED512, FG_K1_FUSED, FG_K1_NVARIANTS = 0, 1, 2, 3, 4
-K1_NAMES = {0: "plain", 1: "staged256", 2: "staged512", 3: "fused"}
+FG_KERNEL_AUTO, FG_KERNEL_PLAIN, FG_KERNEL_STAGED, FG_KERNEL_STAGED512 = 0, 1, 2, 3
+FG_KERNEL_FUSED, FG_KERNEL_OVERLAP = 4, 5
+FG_K1_PLAIN, FG_K1_STAGED256, FG_K1_STAGED512, FG_K1_FUSED, FG_K1_OVERLAP, FG_K1_NVARIANTS = 0, 1, 2, 3, 4, 5
+K1_NAMES = {0: "plain", 1: "staged256", 2: "staged512", 3: "fused", 4: "overlap"}
 VARIANT = {"auto": FG_KERNEL_AUTO, "plain": FG_KERNEL_PLAIN, "staged": FG_KERNEL_STAGED,
-           "staged512": FG_KERNEL_STAGED512, "fused": FG_KERNEL_FUSED}
+           "staged512": FG_KERNEL_STAGED512, "fused": FG_KERNEL_FUSED, "overlap": FG_KERNEL_OVERLAP}
 STORAGE = {"f32": FG_F32, "f16": FG_F16, "bf16": FG_BF16}
 
 

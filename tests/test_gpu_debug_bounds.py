@@ -52,7 +52,7 @@ def ball(c, R, n):
     return f
 
 fr = oracle.make_frame(acc=(1e-5, 0, 0), omega=(1e-4, -2e-4, 1e-4), domega=(1e-6, 0, 0), origin=(4, 3, 3))
-for v in ("plain", "staged", "staged512", "fused"):
+for v in ("plain", "staged", "staged512", "fused", "overlap"):
     for M in (1, 2):
         run("periodic_%s_M%d" % (v, M), (8, 8, 8), (0,) * 6, ball((4.0, 3.5, 4.2), 1.5, 4), 20, variant=v, ib_iters=M)
     run("open_%s_eq3_det" % v, (9, 7, 6), OPEN, ball((4.3, 3.1, 2.6), 0.4, 3), 20, fr, variant=v, eq_order=3,

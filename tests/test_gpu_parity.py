@@ -18,7 +18,7 @@ from paper_2206_01683_b300 import fishlbm, inputs
 from parity_util import TOL_F32, Pair, assert_local, f32, rel_l2
 
 pytestmark = pytest.mark.gpu
-VARIANTS = ["plain", "staged", "staged512", "fused"]
+VARIANTS = ["plain", "staged", "staged512", "fused", "overlap"]
 
 OPEN_X = (VELOCITY, OUTFLOW, FREESLIP, FREESLIP, FREESLIP, FREESLIP)
 
@@ -126,7 +126,7 @@ def test_multi_direct_forcing_sphere_box(M):
     assert rel_l2(Fg, Fo) <= TOL_F32
 
 
-@pytest.mark.parametrize("variant", ["plain", "staged", "fused"])
+@pytest.mark.parametrize("variant", ["plain", "staged", "fused", "overlap"])
 def test_multi_direct_forcing_swimmer_open_channel(variant):
     """Three passes on the skinned swimmer in the moving frame with open
     faces (96x48x48, 900 markers, 80 steps)."""
@@ -703,7 +703,7 @@ def test_autotune_keeps_a_runnable_variant_and_the_state():
         d.step(3)
     before = b.populations()
     kept, ms = b.autotune()
-    assert set(ms) == {"plain", "staged256", "staged512", "fused"} and all(v > 0 for v in ms.values())
+    assert set(ms) == {"plain", "staged256", "staged512", "fused", "overlap"} and all(v > 0 for v in ms.values())
     # a staged variant is kept only when more than 2% faster than the plain one
     score = {k: (v / 0.98 if k.startswith("staged") else v) for k, v in ms.items()}
     assert kept == min(score, key=score.get) == b.stream_collide_variant()
@@ -713,7 +713,7 @@ def test_autotune_keeps_a_runnable_variant_and_the_state():
     assert rel_l2(b.populations(), a.populations()) < 1e-6
     big = fishlbm.Domain([fishlbm.env_desc((300, 4, 4), 0.6)], autotune=True)
     big.step(1)   # the autotune option runs before the first step
-    assert big.stream_collide_variant() in ("plain", "staged512", "fused")
+    assert big.stream_collide_variant() in ("plain", "staged512", "fused", "overlap")
 
 
 def test_region_momentum_matches_oracle():
@@ -945,22 +945,24 @@ def test_step_state_steps_between_buffers():
         two.step_state(bufs[1], bufs[2])
 
 
+@pytest.mark.parametrize("other", ["fused", "overlap"])
 @pytest.mark.parametrize("M", [1, 3])
-def test_fused_step_equals_plain_bit_for_bit(M):
+def test_fused_step_equals_plain_bit_for_bit(M, other):
     """The fused step kernel (IB phases and cell blocks from one work queue,
-    one persistent launch) against the plain chain (IB kernel, plain
-    stream-collide kernel, reduction) with the deterministic spread: the same
-    populations, force/torque rows of every segment and mass, bit for bit,
-    over 25 steps of three environments (the swimmer channel with open faces
-    and a moving frame, a periodic box with a sphere, one without markers),
-    with one and three direct-forcing passes."""
+    one persistent launch), and the plain kernel with the IB beside it (a
+    second stream), against the plain chain (IB kernel, plain stream-collide
+    kernel, reduction) with the deterministic spread: the same populations,
+    force/torque rows of every segment and mass, bit for bit, over 25 steps of
+    three environments (the swimmer channel with open faces and a moving
+    frame, a periodic box with a sphere, one without markers), with one and
+    three direct-forcing passes."""
     fish = inputs.fish_for_grid((96, 48, 48), 24.0, 900)
     traj = inputs.FrameTrajectory(inputs.seed_for(2), inputs.domain_centre((96, 48, 48)))
     envs = [fishlbm.env_desc((96, 48, 48), 0.52, OPEN_X, (0.02, 0, 0), 1.0, (0.02, 0, 0)),
             fishlbm.env_desc((40, 32, 24), 0.6), fishlbm.env_desc((24, 16, 16), 0.7)]
     Xs, dVs = inputs.fibonacci_sphere(200, 4.0, (20.0, 16.0, 12.0))
     doms = [fishlbm.Domain(envs, variant=v, deterministic=True, ib_iters=M, record_history=25)
-            for v in ("plain", "fused")]
+            for v in ("plain", other)]
     for n in range(25):
         X, U = fish.pose(n)
         Us = np.tile([0.02, -0.01 * math.sin(0.2 * n), 0.0], (200, 1))
@@ -971,7 +973,7 @@ def test_fused_step_equals_plain_bit_for_bit(M):
                           ref=fish.joints_rest[0], env=0)
             d.set_markers(np.float32(Xs + Us * n), np.float32(Us), np.float32(dVs), env=1)
             d.step(1, frames)
-    assert doms[1].stream_collide_variant() == "fused"
+    assert doms[1].stream_collide_variant() == other
     for e in range(3):
         assert np.array_equal(doms[0].populations(env=e), doms[1].populations(env=e)), e
         assert np.array_equal(doms[0].history(25, env=e), doms[1].history(25, env=e)), e
