@@ -183,15 +183,18 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
 fg_status fg_debug_flags(unsigned int* flags, int reset);
 
 /* Failure-detection self test of the library's bounded device waits (the
- * mbarrier waits of the staged stream-collide kernel and the grid barrier of
- * the IB kernel), run on conditions that never come: an mbarrier nobody
- * arrives on and a grid barrier whose target is never reached.  Each wait
- * gives up after `limit` polls (the step kernels use 2^22) and reports
- * instead of hanging or trapping: result[0] = 1 if the mbarrier wait gave up,
- * result[1] = 1 if the grid barrier gave up, result[2] = 1 if the timeout bit
- * was set in the status word.  Runs on the current device, allocates and
- * frees its own 12 bytes, synchronises; the context stays usable.  The paper
- * has no counterpart. */
+ * mbarrier waits of the staged stream-collide kernel, the grid barrier of the
+ * IB kernel, and the dependency wait of the fused step kernel's work queue),
+ * run on conditions that never come: an mbarrier nobody arrives on, a grid
+ * barrier whose target is never reached, a completion counter that stays
+ * short.  Each wait gives up after `limit` polls (the step kernels use 2^22)
+ * and reports instead of hanging or trapping: result[0] = 1 if the mbarrier
+ * wait gave up, result[1] = 1 if the grid barrier gave up, result[2] = 1 if
+ * the timeout bit was set in the status word, result[3] = 1 if the queue wait
+ * gave up and set the queue's abort word (which stops the other blocks of a
+ * fused launch).  result holds 4 ints.  Runs on the current device, allocates
+ * and frees its own 60 bytes, synchronises; the context stays usable.  The
+ * paper has no counterpart. */
 fg_status fg_selftest_waits(unsigned int limit, int* result);
 
 /* New positions and velocities for the markers of all environments at once

@@ -1425,18 +1425,8 @@ fg_status fg_region_momentum(fg_domain* d, int env, const double* center, double
         if (!std::isfinite(center[a]) || std::fabs(center[a]) > 1e6) return fail(FG_ERR_INVALID, "centre not finite");
     const EnvDev& E = d->env[env];
     int lo[3], ext[3];
-    for (int a = 0; a < 3; ++a) {
-        lo[a] = (int)std::floor(center[a] - radius - 1.0);
-        ext[a] = (int)std::ceil(center[a] + radius + 1.0) - lo[a] + 1;
-        if (!E.per[a]) {   // open axis: clamp the box to the domain
-            const int hi = std::min(lo[a] + ext[a], E.n[a]);
-            lo[a] = std::max(lo[a], 0);
-            ext[a] = std::max(hi - lo[a], 0);
-        } else if (ext[a] > E.n[a]) {   // periodic axis: each cell once
-            lo[a] = 0;
-            ext[a] = E.n[a];
-        }
-    }
+    const double cc[3] = {center[0], center[1], center[2]};
+    sphere_box(E, cc, radius, lo, ext);
     const long long n_box = (long long)ext[0] * ext[1] * ext[2];
     const int blocks = (int)std::max<long long>(1, std::min<long long>((n_box + RED_THREADS - 1) / RED_THREADS,
                                                                        4ll * d->n_sms));
@@ -1504,31 +1494,39 @@ fg_status fg_selftest_waits(unsigned int limit, int* result) {
     if (!result) return fail(FG_ERR_INVALID, "null result");
     if (limit == 0) return fail(FG_ERR_INVALID, "limit must be positive");
     unsigned* bar = nullptr;
-    int *out = nullptr, *status = nullptr;
+    int *out = nullptr, *status = nullptr, *queue = nullptr;
     fg_status st = dalloc(&bar, 1);
-    if (st == FG_OK) st = dalloc(&out, 2);
+    if (st == FG_OK) st = dalloc(&out, 4);
     if (st == FG_OK) st = dalloc(&status, 1);
+    if (st == FG_OK) st = dalloc(&queue, 1 + WQ_WORDS);   // a dependency counter and the queue words
     cudaError_t e = cudaSuccess;
     if (st == FG_OK) {
         e = cudaMemset(bar, 0, sizeof(unsigned));
-        if (e == cudaSuccess) e = cudaMemset(out, 0, 2 * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(out, 0, 4 * sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(status, 0, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(queue, 0, (1 + WQ_WORDS) * sizeof(int));
         if (e == cudaSuccess) {
             k_selftest_waits<<<1, 64>>>(bar, limit, out, status);
             e = cudaGetLastError();
         }
+        if (e == cudaSuccess) {
+            k_selftest_queue_wait<<<1, 32>>>(queue, queue + 1, limit, out + 2, status);
+            e = cudaGetLastError();
+        }
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
-        int h[3] = {0, 0, 0};
-        if (e == cudaSuccess) e = cudaMemcpy(h, out, 2 * sizeof(int), cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess) e = cudaMemcpy(h + 2, status, sizeof(int), cudaMemcpyDeviceToHost);
+        int h[5] = {0, 0, 0, 0, 0};
+        if (e == cudaSuccess) e = cudaMemcpy(h, out, 4 * sizeof(int), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(h + 4, status, sizeof(int), cudaMemcpyDeviceToHost);
         result[0] = h[0];
         result[1] = h[1];
-        result[2] = (h[2] & ST_TIMEOUT) ? 1 : 0;
+        result[2] = (h[4] & ST_TIMEOUT) ? 1 : 0;
+        result[3] = h[2] && h[3];
         if (e != cudaSuccess) st = cuda_fail(e, "k_selftest_waits");
     }
     if (bar) cudaFree(bar);
     if (out) cudaFree(out);
     if (status) cudaFree(status);
+    if (queue) cudaFree(queue);
     return st;
 }
 

@@ -88,14 +88,16 @@ __device__ __forceinline__ int find_seg(const WorkSeg* __restrict__ segs, int n,
     return lo;
 }
 
-// Wait (thread 0) until *counter >= target; false if the wait gave up or the
-// launch was aborted.
-__device__ __forceinline__ bool wait_count(const int* counter, int target, int* work, int* status) {
+// Wait (thread 0) until *counter >= target; false if the wait gave up (it
+// then records ST_TIMEOUT and sets the abort word, so that the other blocks
+// stop too) or the launch was aborted.
+__device__ __forceinline__ bool wait_count(const int* counter, int target, int* work, int* status,
+                                           uint32_t limit = FUSED_WAIT_LIMIT) {
     if (target <= 0) return true;
     for (uint32_t i = 0;; ++i) {
         if ((int)ld_acquire_gpu(reinterpret_cast<const unsigned*>(counter)) >= target) return true;
         if ((i & 63u) == 63u && __ldcg(work + WQ_ABORT) != 0) return false;
-        if (i == FUSED_WAIT_LIMIT) {
+        if (i == limit) {
             atomicOr(status, ST_TIMEOUT);
             atomicExch(work + WQ_ABORT, 1);
             return false;
@@ -364,6 +366,16 @@ k_step_fused(const typename S::raw* __restrict__ gin, typename S::raw* __restric
         work[WQ_EXITS] = 0;
         work[WQ_ABORT] = 0;
     }
+}
+
+// Failure-detection self test of the work queue's bounded wait: a
+// dependency counter that never reaches its target.  out[0] = 1 if the wait
+// gave up, out[1] = 1 if it set the abort word.
+static __global__ void k_selftest_queue_wait(const int* counter, int* work, uint32_t limit, int* out,
+                                             int* status) {
+    if (threadIdx.x != 0) return;
+    out[0] = wait_count(counter, 1, work, status, limit) ? 0 : 1;
+    out[1] = __ldcg(work + WQ_ABORT) != 0 ? 1 : 0;
 }
 
 }  // namespace fl

@@ -256,28 +256,26 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
 }
 
 // Momentum and angular momentum of the fluid inside a sphere (centre c,
-// radius R) in the stored state g of environment e: P = sum alpha j,
+// radius R) in the stored state g of environment E: P = sum alpha j,
 // L = sum alpha (x - c) x j, j = sum_i c_i g_i (the rest populations w_i
 // carry no momentum), alpha = clamp(R + 1/2 - |x - c|, 0, 1), x - c the
 // minimal image on periodic axes.  The free-body coupling needs it every step
-// (the inner fluid's momentum change, Kempe & Froehlich 2012).  Threads walk
-// the cells of the sphere's bounding box [lo, lo + ext); every block writes
-// seven compensated pairs (P, L, sum alpha) to part[block]; the host adds
-// them in block order.
+// (the inner fluid's momentum change, Kempe & Froehlich 2012).  Block `blk`
+// of `nblk` walks its share of the cells of the sphere's bounding box
+// [lo, lo + ext) and writes seven compensated pairs (P, L, sum alpha) to
+// out[0..6]; the blocks' pairs are added in block order.  Called by every
+// thread of a block of RED_THREADS.
 template <class S>
-__global__ void __launch_bounds__(RED_THREADS)
-k_region_momentum(const typename S::raw* __restrict__ g, const EnvDev* __restrict__ envs, int e, float cx_,
-                  float cy_, float cz_, float R, int lo_x, int lo_y, int lo_z, int ext_x, int ext_y, int ext_z,
-                  Pair32* __restrict__ part) {
-    __shared__ Pair32 sh[RED_THREADS / 32][7];
-    const EnvDev& E = envs[e];
+__device__ __forceinline__ void region_block_sums(const typename S::raw* __restrict__ g, const EnvDev& E,
+                                                  const float (&c)[3], float R, const int (&lo)[3],
+                                                  const int (&ext)[3], int blk, int nblk, Pair32 (*sh)[7],
+                                                  Pair32* __restrict__ out) {
     const typename S::raw* G = g + E.pop_off;
-    const float c[3] = {cx_, cy_, cz_};
     Pair32 acc[7];
-    const long long n_box = (long long)ext_x * ext_y * ext_z;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n_box;
-         k += (long long)gridDim.x * blockDim.x) {
-        int p[3] = {lo_x + (int)(k % ext_x), lo_y + (int)((k / ext_x) % ext_y), lo_z + (int)(k / ((long long)ext_x * ext_y))};
+    const long long n_box = (long long)ext[0] * ext[1] * ext[2];
+    for (long long k = blk * (long long)blockDim.x + threadIdx.x; k < n_box; k += (long long)nblk * blockDim.x) {
+        int p[3] = {lo[0] + (int)(k % ext[0]), lo[1] + (int)((k / ext[0]) % ext[1]),
+                    lo[2] + (int)(k / ((long long)ext[0] * ext[1]))};
         float r[3];
         bool inside = true;
 #pragma unroll
@@ -326,8 +324,39 @@ k_region_momentum(const typename S::raw* __restrict__ g, const EnvDev* __restric
     if (threadIdx.x < 7) {
         Pair32 t;
         for (int i = 0; i < RED_THREADS / 32; ++i) t.add(sh[i][threadIdx.x]);
-        part[(size_t)blockIdx.x * 7 + threadIdx.x] = t;
+        out[threadIdx.x] = t;
     }
+}
+
+// The sphere's bounding box in the cells of E: [lo, lo + ext) per axis,
+// clamped to the domain along an open axis, each cell once along a periodic
+// one (the box fg_region_momentum and the device-resident sphere use).
+__host__ __device__ inline void sphere_box(const EnvDev& E, const double (&c)[3], double R, int (&lo)[3],
+                                           int (&ext)[3]) {
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (int)floor(c[a] - R - 1.0);
+        ext[a] = (int)ceil(c[a] + R + 1.0) - lo[a] + 1;
+        if (!E.per[a]) {
+            const int hi = min(lo[a] + ext[a], E.n[a]);
+            lo[a] = max(lo[a], 0);
+            ext[a] = max(hi - lo[a], 0);
+        } else if (ext[a] > E.n[a]) {
+            lo[a] = 0;
+            ext[a] = E.n[a];
+        }
+    }
+}
+
+// fg_region_momentum: block b's pairs to part[b][0..6], the host adds them.
+template <class S>
+__global__ void __launch_bounds__(RED_THREADS)
+k_region_momentum(const typename S::raw* __restrict__ g, const EnvDev* __restrict__ envs, int e, float cx_,
+                  float cy_, float cz_, float R, int lo_x, int lo_y, int lo_z, int ext_x, int ext_y, int ext_z,
+                  Pair32* __restrict__ part) {
+    __shared__ Pair32 sh[RED_THREADS / 32][7];
+    const float c[3] = {cx_, cy_, cz_};
+    const int lo[3] = {lo_x, lo_y, lo_z}, ext[3] = {ext_x, ext_y, ext_z};
+    region_block_sums<S>(g, envs[e], c, R, lo, ext, blockIdx.x, gridDim.x, sh, part + (size_t)blockIdx.x * 7);
 }
 
 }  // namespace fl

@@ -248,10 +248,11 @@ def debug_flags(reset=True):
 
 def selftest_waits(limit=4096):
     """Run the bounded device waits on conditions that never come; returns
-    (mbarrier wait gave up, grid barrier gave up, status timeout bit)."""
-    out = (_I * 3)()
+    (mbarrier wait gave up, grid barrier gave up, status timeout bit, work
+    queue wait gave up and set the abort word)."""
+    out = (_I * 4)()
     _check(lib().fg_selftest_waits(int(limit), out))
-    return bool(out[0]), bool(out[1]), bool(out[2])
+    return bool(out[0]), bool(out[1]), bool(out[2]), bool(out[3])
 
 
 class Domain:

@@ -1,7 +1,9 @@
 """Failure detection on the GPU without a fault: the library's bounded waits
 run on conditions that never come (an mbarrier nobody arrives on, a grid
-barrier whose target is never reached), give up after their poll limit and
-report through the status word; the context stays usable afterwards."""
+barrier whose target is never reached, a work-queue counter that stays
+short), give up after their poll limit and report through the status word
+(the queue wait also raises the abort word that stops a fused launch); the
+context stays usable afterwards."""
 import time
 
 import numpy as np
@@ -14,8 +16,8 @@ pytestmark = pytest.mark.gpu
 
 def test_bounded_waits_give_up_and_report():
     t0 = time.time()
-    mbar, grid, status = fishlbm.selftest_waits(limit=4096)
-    assert mbar and grid and status
+    mbar, grid, status, queue = fishlbm.selftest_waits(limit=4096)
+    assert mbar and grid and status and queue
     assert time.time() - t0 < 60
     # the device is still usable: a domain steps and matches a fresh one
     X, dV = inputs.fibonacci_sphere(100, 3.0, (8.0, 8.0, 8.0))
