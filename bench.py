@@ -249,15 +249,16 @@ def _variant_kw(args):
 
 
 def storage_form(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, K, world, peak, vkw,
-                 ib_iters=1, deterministic=False, eq_order=2):
+                 ib_iters=1, deterministic=False, eq_order=2, layout="pull"):
     """The swimmer-channel step with populations stored as FP16 / BF16 (or
-    FP32 with ib_iters direct-forcing passes)."""
+    FP32 with ib_iters direct-forcing passes), in either population layout
+    (two buffers, or one updated in place)."""
     import torch
     from paper_2206_01683_b300 import fishlbm
     stream = torch.cuda.Stream()
     dom = fishlbm.Domain([fishlbm.env_desc(shape, tau, OPEN_X, (u_in, 0, 0), 1.0, (u_in, 0, 0))],
                          storage=storage, stream=stream.cuda_stream, ib_iters=ib_iters,
-                         deterministic=deterministic, eq_order=eq_order, **vkw)
+                         deterministic=deterministic, eq_order=eq_order, layout=layout, **vkw)
     dom.set_markers(Xd[0], Ud[0], dVd, segd, n_seg=5, ref=ref)
 
     def step(n):
@@ -275,7 +276,9 @@ def storage_form(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W,
     return {"value": round(world * ncell * K / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
             "ms_per_step": round(ms / K, 5), "storage": storage, "kernel_variant": variant,
             "ib_iters": ib_iters, "deterministic": bool(deterministic), "eq_order": eq_order,
-            "roofline": {"bound": "hbm", "kernel": "k_stream_collide", "achieved": round(gbs, 1),
+            "layout": layout, "population_bytes": (1 if layout == "aa" else 2) * 27 * ncell * (4 if storage == "f32" else 2),
+            "roofline": {"bound": "hbm", "kernel": "k_stream_collide_aa" if layout == "aa" else "k_stream_collide",
+                         "achieved": round(gbs, 1),
                          "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
                          "algorithmic_bytes_per_cell": 216 if storage == "f32" else 108,
                          "kernel_ms": round(k[1], 5), "ib_ms": round(k[0], 5)}}
@@ -540,7 +543,7 @@ def run_ours(args):
     fr = [fishlbm.frame_from_array(f) for f in frames]
     stream = torch.cuda.Stream()
     dom = fishlbm.Domain([fishlbm.env_desc(shape, tau, OPEN_X, (u_in, 0, 0), 1.0, (u_in, 0, 0))],
-                         stream=stream.cuda_stream, storage=args.storage, **_variant_kw(args))
+                         stream=stream.cuda_stream, storage=args.storage, layout=args.layout, **_variant_kw(args))
     Xd = torch.from_numpy(X).cuda()
     Ud = torch.from_numpy(U).cuda()
     dVd = torch.from_numpy(fish.dV.astype(np.float32)).cuda()
@@ -646,6 +649,11 @@ def run_ours(args):
                                 _variant_kw(args)),
             "bf16": storage_form("bf16", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world, peak,
                                  _variant_kw(args)),
+            # one population array updated in place (the plain kernel's own in-place form)
+            "aa": storage_form("f32", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world, peak, {},
+                               layout="aa"),
+            "aa_f16": storage_form("f16", shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W, Kf, world, peak,
+                                   {}, layout="aa"),
             "large_sphere": large_sphere_form(W, Kf, world, peak, _variant_kw(args)),
             "batched": batched_form(W, Kf, world, peak, _variant_kw(args)),
         }
@@ -654,7 +662,8 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return None
     achieved = algo_bytes / (k1_ms * 1e-3) / 1e9
-    bpc = NCU_TRAFFIC.get((kernel_source_hash(), dom.stream_collide_variant())) if args.storage == "f32" else None
+    bpc = (NCU_TRAFFIC.get((kernel_source_hash(), dom.stream_collide_variant()))
+           if args.storage == "f32" and args.layout == "pull" else None)
     mlups = world * ncell * K / (ms * 1e-3) / 1e6
     h2d = 2 * X[0].nbytes + 100   # X, U and the frame (25 floats)
     d2h = out.size * 8 + 4        # the force/torque rows as FP32 pairs, and the status word
@@ -675,10 +684,13 @@ def run_ours(args):
                    "faces": "inlet -x (u=0.02), outflow +x, free-slip y/z",
                    "markers": int(X.shape[1]), "segments": 5, "storage": args.storage,
                    "frame": "seeded accelerating + rotating (Eq. 3)",
-                   "l2": "inputs exceed L2 (populations 453 MB per buffer, 2 buffers)",
+                   "l2": "inputs exceed L2 (populations 453 MB per buffer, %s)"
+                         % ("1 buffer in place" if args.layout == "aa" else "2 buffers"),
+                   "layout": args.layout,
                    "parallelism": "replicas" if world > 1 else "single",
                    "kernel_variant": dom.stream_collide_variant()},
-        "roofline": {"bound": "hbm", "kernel": "k_stream_collide", "achieved": round(achieved, 1),
+        "roofline": {"bound": "hbm", "kernel": "k_stream_collide_aa" if args.layout == "aa" else "k_stream_collide",
+                     "achieved": round(achieved, 1),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
                      "nominal_peak": NOMINAL_HBM_GBS, "frac_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
@@ -800,6 +812,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16/batched forms")
     ap.add_argument("--form-steps", type=int, default=50)
+    ap.add_argument("--layout", default="pull", choices=["pull", "aa"],
+                    help="population layout of the main line: two buffers (pull) or one in place (aa)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="population storage of the main workload (f32 is the headline; the others for profiling)")
     ap.add_argument("--variant", default="autotune", choices=["autotune", "plain", "staged", "staged512"],

@@ -88,11 +88,22 @@ typedef enum {
     FG_KERNEL_OVERLAP = 5
 } fg_kernel_variant;
 
+/* Population layout.  PULL keeps two population arrays: each step pulls
+ * from one and writes the other.  AA keeps one array and updates it in place
+ * (the AA access pattern: even steps read and write each cell's own slots,
+ * odd steps read from and write to the neighbours' slots, with the
+ * directions reversed between the two), halving population memory; it runs
+ * the plain kernel (kernel_variant AUTO or PLAIN) and computes bit-identical
+ * populations, forces and torques.  fg_step_state and the adjoint take PULL
+ * only; the state buffers of fg_save_state, fg_load_state and fg_copy_state
+ * have the same format in both layouts. */
+typedef enum { FG_LAYOUT_PULL = 0, FG_LAYOUT_AA = 1 } fg_layout;
+
 #define FG_MAX_IB_ITERS 8
 
 typedef struct {
     int storage;        /* fg_storage */
-    int layout;         /* 0: two-buffer pull scheme (the only layout) */
+    int layout;         /* fg_layout */
     int deterministic;  /* 1: the IB spread sums each node's contributions as
                            64-bit fixed-point integers (multiples of 2^-48,
                            exact and order-independent), so every step is

@@ -143,8 +143,9 @@ struct fg_domain {
     std::vector<MarkerRegion> mk;
     EnvDev* d_env = nullptr;
     FrameDev* d_frame = nullptr;
-    void* pop[2] = {nullptr, nullptr};
-    int cur = 0;
+    void* pop[2] = {nullptr, nullptr};   // the in-place layout: both the one buffer
+    int cur = 0;                         // buffer parity; the in-place layout's phase
+    bool aa = false;                     // in-place (AA) layout
     unsigned long long pop_elems = 0, total_cells = 0, total_slots = 0;
     float4* fib = nullptr;               // IB force density per slot (x, y, z, unused)
     uint32_t* stamps = nullptr;
@@ -306,7 +307,7 @@ void free_all(fg_domain* d) {
     void* adj[] = {d->adj_lam[0], d->adj_lam[1], d->adj_lfib, d->adj_lrho, d->adj_lut, d->adj_gF};
     for (void* p : adj)
         if (p) cudaFree(p);
-    void* ptrs[] = {d->d_env, d->d_frame, d->pop[0], d->pop[1], d->fib, d->stamps, d->ib_nodes, d->ib_bar,
+    void* ptrs[] = {d->d_env, d->d_frame, d->pop[0], d->pop[1] != d->pop[0] ? d->pop[1] : nullptr, d->fib, d->stamps, d->ib_nodes, d->ib_bar,
                     d->fibq, d->mass_part, d->red_partials, d->red_counters, d->d_state,
                     d->X, d->U, d->dV, d->Fm, d->dF, d->Nrm, d->seg, d->seg_ref, d->region_part, d->mk_stage, d->ft, d->mass,
                     d->hist, d->status, d->work_segs, d->work, d->work_done};
@@ -562,7 +563,7 @@ void enqueue_k1(fg_domain* d, const typename S::raw* gin, typename S::raw* gout,
 // The cooperative IB kernel of a step reading gin (all resident blocks: the
 // scan phase covers every tile stamp).
 template <class S>
-fg_status enqueue_ib(fg_domain* d, const typename S::raw* gin, cudaStream_t s) {
+fg_status enqueue_ib(fg_domain* d, const typename S::raw* gin, cudaStream_t s, int layout = LAYOUT_PULL) {
     const int blocks = d->ib_per_sm * d->n_sms;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)blocks);
@@ -578,8 +579,31 @@ fg_status enqueue_ib(fg_domain* d, const typename S::raw* gin, cudaStream_t s) {
                           d->n_envs, d->total_markers, (int)d->n_stamps, (const float*)d->X, (const float*)d->U,
                           (const float*)d->dV, d->Fm, d->fib, d->stamps, (const StepState*)d->d_state,
                           d->ib_nodes, d->ib_bar, d->opt.ib_iters, d->dF, d->fibq,
-                          (const float*)(d->opt.ib_slip ? d->Nrm : nullptr), d->status));
+                          (const float*)(d->opt.ib_slip ? d->Nrm : nullptr), d->status, layout));
     return FG_OK;
+}
+
+// The in-place stream-collide kernel of phase `phase` (0: even step).
+template <class S, bool EQ3, bool PAIR>
+void enqueue_aa_of(fg_domain* d, typename S::raw* g, int phase, cudaStream_t s) {
+    if (phase == 0)
+        k_stream_collide_aa<S, EQ3, PAIR, 0><<<d->total_blocks, K1_THREADS, 0, s>>>(
+            g, d->d_env, d->d_frame, d->n_envs, d->fib, d->stamps, d->d_state, d->mass_part);
+    else
+        k_stream_collide_aa<S, EQ3, PAIR, 1><<<d->total_blocks, K1_THREADS, 0, s>>>(
+            g, d->d_env, d->d_frame, d->n_envs, d->fib, d->stamps, d->d_state, d->mass_part);
+}
+
+template <class S>
+void enqueue_aa(fg_domain* d, typename S::raw* g, int phase, cudaStream_t s) {
+    const bool eq3 = d->opt.eq_order == 3;
+    if (d->plain_pair) {
+        if (eq3) enqueue_aa_of<S, true, true>(d, g, phase, s);
+        else enqueue_aa_of<S, false, true>(d, g, phase, s);
+    } else {
+        if (eq3) enqueue_aa_of<S, true, false>(d, g, phase, s);
+        else enqueue_aa_of<S, false, false>(d, g, phase, s);
+    }
 }
 
 // The plain stream-collide kernel over the blocks `which` selects, on
@@ -726,12 +750,24 @@ fg_status enqueue_fused(fg_domain* d, const typename S::raw* gin, typename S::ra
 // Launch the kernels of one step reading gin and writing gout on stream s;
 // with ev != nullptr an event pair is recorded around each kernel (the fused
 // kernel counts as the stream-collide kernel; it has no separate IB launch).
+// aa_phase >= 0: the in-place layout at that phase (gin == gout, the one
+// buffer).
 template <class S>
 fg_status enqueue_step_io(fg_domain* d, const typename S::raw* gin, typename S::raw* gout, cudaStream_t s,
-                          cudaEvent_t* const* ev) {
+                          cudaEvent_t* const* ev, int aa_phase = -1) {
     const bool fused = d->k1 == K1_FUSED;
     const bool overlap = d->k1 == K1_OVERLAP && d->total_markers > 0;
-    if (overlap) {
+    if (aa_phase >= 0) {
+        if (d->total_markers > 0) {
+            if (ev) CK(cudaEventRecord(ev[FG_K_IB][0], s));
+            fg_status st = enqueue_ib<S>(d, gin, s, aa_phase == 0 ? LAYOUT_AA0 : LAYOUT_AA1);
+            if (st != FG_OK) return st;
+            if (ev) CK(cudaEventRecord(ev[FG_K_IB][1], s));
+        }
+        if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][0], s));
+        enqueue_aa<S>(d, gout, aa_phase, s);
+        if (ev) CK(cudaEventRecord(ev[FG_K_STREAM_COLLIDE][1], s));
+    } else if (overlap) {
         fg_status st = enqueue_overlap<S>(d, gin, gout, s, ev);
         if (st != FG_OK) return st;
     } else {
@@ -780,7 +816,8 @@ fg_status enqueue_step_io(fg_domain* d, const typename S::raw* gin, typename S::
 template <class S>
 fg_status enqueue_step(fg_domain* d, int parity, cudaStream_t s, cudaEvent_t* const* ev) {
     typedef typename S::raw raw;
-    return enqueue_step_io<S>(d, (const raw*)d->pop[parity], (raw*)d->pop[parity ^ 1], s, ev);
+    return enqueue_step_io<S>(d, (const raw*)d->pop[parity], (raw*)d->pop[parity ^ 1], s, ev,
+                              d->aa ? parity : -1);
 }
 
 // One step with direct launches (and per-kernel events when profiling).
@@ -891,6 +928,7 @@ fg_status staged_occupancy(fg_domain* d, int* per_sm) {
 }
 
 bool k1_runnable(const fg_domain* d, int v) {
+    if (d->aa) return v == K1_PLAIN;   // the in-place layout has its own plain kernel only
     if (v == K1_PLAIN || v == K1_FUSED || v == K1_OVERLAP) return true;
     if (v == K1_STAGED256) return d->max_P <= 256;
     return v == K1_STAGED512 && d->max_P <= 512;
@@ -916,6 +954,11 @@ fg_status configure_k1(fg_domain* d, int v, bool allocate) {
     // the plain kernel takes two cells per thread when every row length is
     // even: its blocks cover 2 x 256 slots
     d->plain_pair = !d->staged;
+    // in place, FP32 runs one cell per thread: two cells hold two sets of
+    // outputs and their addresses until the scattered stores of an odd step
+    // (108 registers against 64), and the even step's aligned accesses need
+    // no pairing to coalesce
+    if (d->aa && d->esize == 4) d->plain_pair = false;
     for (int e = 0; e < d->n_envs; ++e)
         if (d->env[e].n[0] % 2 != 0) d->plain_pair = false;
     {
@@ -993,6 +1036,10 @@ fg_status configure_k1(fg_domain* d, int v, bool allocate) {
     return upload_env(d);
 }
 
+// The layout argument of the state kernels: -1 for two buffers, else the
+// in-place phase.
+int aa_of(const fg_domain* d) { return d->aa ? d->cur : -1; }
+
 // FP64 value of a compensated pair produced on the device.
 double pair_value(const Pair32& p) { return (double)p.hi + (double)p.lo; }
 
@@ -1037,7 +1084,9 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     if (o.kernel_variant < FG_KERNEL_AUTO || o.kernel_variant > FG_KERNEL_OVERLAP)
         return fail(FG_ERR_INVALID, "unknown kernel variant");
     if (o.storage < 0 || o.storage > 2) return fail(FG_ERR_INVALID, "unknown storage");
-    if (o.layout != 0) return fail(FG_ERR_INVALID, "only the two-buffer pull layout (0) exists");
+    if (o.layout != FG_LAYOUT_PULL && o.layout != FG_LAYOUT_AA) return fail(FG_ERR_INVALID, "unknown layout");
+    if (o.layout == FG_LAYOUT_AA && o.kernel_variant != FG_KERNEL_AUTO && o.kernel_variant != FG_KERNEL_PLAIN)
+        return fail(FG_ERR_INVALID, "the in-place layout runs the plain kernel only");
     if (o.ib_iters < 1 || o.ib_iters > FG_MAX_IB_ITERS) return fail(FG_ERR_INVALID, "ib_iters must be in [1, 8]");
     if (o.deterministic != 0 && o.deterministic != 1) return fail(FG_ERR_INVALID, "deterministic must be 0 or 1");
     if (o.ib_slip != 0 && o.ib_slip != 1) return fail(FG_ERR_INVALID, "ib_slip must be 0 or 1");
@@ -1067,6 +1116,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     d->opt = o;
     d->stream = (cudaStream_t)cuda_stream;
     d->esize = o.storage == FG_F32 ? 4 : 2;
+    d->aa = o.layout == FG_LAYOUT_AA;
     {
         int dev = 0;
         cudaError_t ce = cudaGetDevice(&dev);
@@ -1137,8 +1187,12 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         char *p0 = nullptr, *p1 = nullptr;
         DA(p0, d->pop_elems * d->esize);
         d->pop[0] = p0;
-        DA(p1, d->pop_elems * d->esize);
-        d->pop[1] = p1;
+        if (d->aa) {
+            d->pop[1] = p0;   // one buffer, updated in place
+        } else {
+            DA(p1, d->pop_elems * d->esize);
+            d->pop[1] = p1;
+        }
     }
     DA(d->fib, slot_off);
     DA(d->stamps, stamp_off);
@@ -1194,7 +1248,8 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     initial_state.envs_done = 0;
     initial_state.step = 0;
     if ((ce = cudaMemsetAsync(d->pop[0], 0, d->pop_elems * d->esize, d->stream)) != cudaSuccess ||
-        (ce = cudaMemsetAsync(d->pop[1], 0, d->pop_elems * d->esize, d->stream)) != cudaSuccess ||
+        (d->pop[1] != d->pop[0] &&
+         (ce = cudaMemsetAsync(d->pop[1], 0, d->pop_elems * d->esize, d->stream)) != cudaSuccess) ||
         (ce = cudaMemsetAsync(d->fib, 0, sizeof(float4) * slot_off, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->stamps, 0, sizeof(uint32_t) * stamp_off, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->ft, 0, sizeof(Pair32) * n_envs * FT_ROW, d->stream)) != cudaSuccess ||
@@ -1216,7 +1271,8 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     }
     refresh_marker_table(d);
     {
-        const int first = o.kernel_variant == FG_KERNEL_OVERLAP                  ? K1_OVERLAP
+        const int first = d->aa                                                  ? K1_PLAIN
+                          : o.kernel_variant == FG_KERNEL_OVERLAP                  ? K1_OVERLAP
                           : o.kernel_variant == FG_KERNEL_FUSED                    ? K1_FUSED
                           : o.kernel_variant == FG_KERNEL_PLAIN || !can_stage ? K1_PLAIN
                           : o.kernel_variant == FG_KERNEL_STAGED512              ? K1_STAGED512
@@ -1245,7 +1301,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
     }
     for (int e = 0; e < n_envs && st == FG_OK; ++e) st = fg_init_fields(d, e, nullptr, nullptr);
     // the autotuner runs before the first step, when the step's markers are known
-    d->autotune_pending = o.autotune && o.kernel_variant == FG_KERNEL_AUTO;
+    d->autotune_pending = o.autotune && o.kernel_variant == FG_KERNEL_AUTO && !d->aa;
     if (st != FG_OK) {
         free_all(d);
         delete d;
@@ -1280,7 +1336,8 @@ fg_status fg_init_fields(fg_domain* d, int env, const double* rho, const double*
     st = dispatch(d->opt.storage, [&](auto tag) -> fg_status {
         typedef decltype(tag) S;
         k_init_eq<S><<<blocks, 256, 0, d->stream>>>((typename S::raw*)d->pop[d->cur], d->d_env, env, drho, du,
-                                                    s.rho0, s.u0[0], s.u0[1], s.u0[2], d->opt.eq_order == 3 ? 1 : 0);
+                                                    s.rho0, s.u0[0], s.u0[1], s.u0[2], d->opt.eq_order == 3 ? 1 : 0,
+                                                    aa_of(d));
         return FG_OK;
     });
     cudaError_t e1 = cudaGetLastError();
@@ -1440,7 +1497,8 @@ fg_status fg_region_momentum(fg_domain* d, int env, const double* center, double
         typedef decltype(tag) S;
         k_region_momentum<S><<<blocks, RED_THREADS, 0, d->stream>>>(
             (const typename S::raw*)d->pop[d->cur], d->d_env, env, (float)center[0], (float)center[1],
-            (float)center[2], (float)radius, lo[0], lo[1], lo[2], ext[0], ext[1], ext[2], d->region_part);
+            (float)center[2], (float)radius, lo[0], lo[1], lo[2], ext[0], ext[1], ext[2], d->region_part,
+            aa_of(d));
         CK(cudaGetLastError());
         return FG_OK;
     });
@@ -1654,6 +1712,7 @@ fg_status fg_step_state(fg_domain* d, const void* in, void* out, const fg_frame*
     if (!d) return fail(FG_ERR_INVALID, "null domain");
     if (d->n_envs != 1) return fail(FG_ERR_INVALID, "fg_step_state takes a single environment");
     if (!in || !out || in == out) return fail(FG_ERR_INVALID, "in and out must be distinct device buffers");
+    if (d->aa) return fail(FG_ERR_INVALID, "fg_step_state steps the two-buffer layout only");
     if (d->poisoned) return fail(FG_ERR_STATE, "domain poisoned by a numeric fault; call fg_init_fields");
     if (frames) {
         for (int a = 0; a < 3; ++a)
@@ -1856,7 +1915,7 @@ fg_status fg_get_fields(fg_domain* d, int env, double* rho, double* u) {
     dispatch(d->opt.storage, [&](auto tag) -> fg_status {
         typedef decltype(tag) S;
         k_get_fields<S><<<blocks, 256, 0, d->stream>>>((const typename S::raw*)d->pop[d->cur], d->d_env, env,
-                                                       dr, du);
+                                                       dr, du, aa_of(d));
         return FG_OK;
     });
     cudaError_t e = cudaGetLastError();
@@ -1881,7 +1940,8 @@ fg_status fg_get_populations(fg_domain* d, int env, double* f) {
     const int blocks = (int)((ncell + 255) / 256);
     dispatch(d->opt.storage, [&](auto tag) -> fg_status {
         typedef decltype(tag) S;
-        k_get_pop<S><<<blocks, 256, 0, d->stream>>>((const typename S::raw*)d->pop[d->cur], d->d_env, env, df);
+        k_get_pop<S><<<blocks, 256, 0, d->stream>>>((const typename S::raw*)d->pop[d->cur], d->d_env, env, df,
+                                                    aa_of(d));
         return FG_OK;
     });
     cudaError_t e = cudaGetLastError();
@@ -1905,7 +1965,8 @@ fg_status fg_set_populations(fg_domain* d, int env, const double* f) {
     if (e == cudaSuccess) {
         dispatch(d->opt.storage, [&](auto tag) -> fg_status {
             typedef decltype(tag) S;
-            k_set_pop<S><<<blocks, 256, 0, d->stream>>>((typename S::raw*)d->pop[d->cur], d->d_env, env, df);
+            k_set_pop<S><<<blocks, 256, 0, d->stream>>>((typename S::raw*)d->pop[d->cur], d->d_env, env, df,
+                                                        aa_of(d));
             return FG_OK;
         });
         e = cudaGetLastError();
@@ -1915,6 +1976,48 @@ fg_status fg_set_populations(fg_domain* d, int env, const double* f) {
     if (e != cudaSuccess) return cuda_fail(e, "fg_set_populations");
     return FG_OK;
 }
+
+}  // extern "C"
+
+namespace {
+
+// The in-place layout's state in the two-buffer format ([27][nslot] raw
+// values, post-collision population i at (i, slot)): converted on the way
+// out and in by k_aa_state, so that a saved state loads at either phase.
+// buf is a device buffer of fg_state_bytes bytes.
+fg_status aa_state_copy(fg_domain* d, int env, void* buf, bool to_buf) {
+    const EnvDev& E = d->env[env];
+    const int blocks = (int)((E.nslot + 255) / 256);
+    return dispatch(d->opt.storage, [&](auto tag) -> fg_status {
+        typedef typename decltype(tag)::raw raw;
+        k_aa_state<decltype(tag)><<<blocks, 256, 0, d->stream>>>((raw*)d->pop[0], d->d_env, env, d->cur, (raw*)buf,
+                                                                 to_buf ? 1 : 0);
+        CK(cudaGetLastError());
+        return FG_OK;
+    });
+}
+
+// The same through a device staging buffer, to or from host memory.
+fg_status aa_state_host(fg_domain* d, int env, void* host_buf, bool save) {
+    const size_t bytes = 27ull * d->env[env].nslot * d->esize;
+    char* tmp = nullptr;
+    fg_status st = dalloc(&tmp, bytes);
+    if (st != FG_OK) return st;
+    cudaError_t e = cudaSuccess;
+    if (!save) e = cudaMemcpyAsync(tmp, host_buf, bytes, cudaMemcpyHostToDevice, d->stream);
+    if (e == cudaSuccess) st = aa_state_copy(d, env, tmp, save);
+    if (e == cudaSuccess && st == FG_OK && save)
+        e = cudaMemcpyAsync(host_buf, tmp, bytes, cudaMemcpyDeviceToHost, d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    cudaFree(tmp);
+    if (st != FG_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, save ? "fg_save_state" : "fg_load_state");
+    return FG_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 fg_status fg_state_bytes(fg_domain* d, int env, unsigned long long* bytes) {
     fg_status st = check_env(d, env);
@@ -1928,6 +2031,7 @@ fg_status fg_save_state(fg_domain* d, int env, void* host_buf) {
     fg_status st = check_env(d, env);
     if (st != FG_OK) return st;
     if (!host_buf) return fail(FG_ERR_INVALID, "null buffer");
+    if (d->aa) return aa_state_host(d, env, host_buf, true);
     const EnvDev& E = d->env[env];
     const char* src = (const char*)d->pop[d->cur] + E.pop_off * d->esize;
     CK(cudaMemcpyAsync(host_buf, src, 27ull * E.nslot * d->esize, cudaMemcpyDeviceToHost, d->stream));
@@ -1939,6 +2043,7 @@ fg_status fg_load_state(fg_domain* d, int env, const void* host_buf) {
     fg_status st = check_env(d, env);
     if (st != FG_OK) return st;
     if (!host_buf) return fail(FG_ERR_INVALID, "null buffer");
+    if (d->aa) return aa_state_host(d, env, const_cast<void*>(host_buf), false);
     const EnvDev& E = d->env[env];
     char* dst = (char*)d->pop[d->cur] + E.pop_off * d->esize;
     CK(cudaMemcpyAsync(dst, host_buf, 27ull * E.nslot * d->esize, cudaMemcpyHostToDevice, d->stream));
@@ -1993,6 +2098,7 @@ static fg_status adjoint_check(fg_domain* d) {
     if (!d) return fail(FG_ERR_INVALID, "null domain");
     if (d->n_envs != 1) return fail(FG_ERR_INVALID, "the adjoint takes a single environment");
     if (d->opt.storage != FG_F32) return fail(FG_ERR_INVALID, "the adjoint takes FP32 storage");
+    if (d->aa) return fail(FG_ERR_INVALID, "the adjoint takes the two-buffer layout");
     if (d->opt.ib_iters != 1) return fail(FG_ERR_INVALID, "the adjoint takes one direct-forcing pass");
     if (d->opt.ib_slip) return fail(FG_ERR_INVALID, "the adjoint takes no-slip forcing");
     if (d->opt.eq_order != 2) return fail(FG_ERR_INVALID, "the adjoint takes the second-order equilibrium");
@@ -2116,6 +2222,7 @@ fg_status fg_copy_state(fg_domain* d, int env, void* buf, int to_buf) {
     fg_status st = check_env(d, env);
     if (st != FG_OK) return st;
     if (!buf) return fail(FG_ERR_INVALID, "null buffer");
+    if (d->aa) return aa_state_copy(d, env, buf, to_buf != 0);
     const EnvDev& E = d->env[env];
     char* state = (char*)d->pop[d->cur] + E.pop_off * d->esize;
     const size_t bytes = 27ull * E.nslot * d->esize;
@@ -2131,6 +2238,14 @@ fg_status fg_autotune(fg_domain* d, int* choice, double* ms) {
     if (!d) return fail(FG_ERR_INVALID, "null domain");
     if (d->poisoned) return fail(FG_ERR_STATE, "domain poisoned by a numeric fault; call fg_init_fields");
     d->autotune_pending = false;
+    if (d->aa) {
+        // in place, a timed pass would advance the state; the layout has one
+        // stream-collide kernel
+        if (ms)
+            for (int v = 0; v < K1_NVARIANTS; ++v) ms[v] = -1.0;
+        if (choice) *choice = K1_PLAIN;
+        return FG_OK;
+    }
     CK(cudaStreamSynchronize(d->stream));
     // The IB pass of a timed candidate rewrites the marker forces; the last
     // step's are kept aside and put back.

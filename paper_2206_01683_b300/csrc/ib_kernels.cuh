@@ -236,10 +236,12 @@ __device__ __forceinline__ void ib_mark(const EnvDev& E, const Stencil& S, int h
 }
 
 // nodes: post-stream rho and u~ of the 32 cells of tile t_local (counted
-// from the environment's first tile) of environment E (one warp).
+// from the environment's first tile) of environment E (one warp), the
+// populations found where `layout` (LAYOUT_*) keeps them.
 template <class S>
 __device__ __forceinline__ void ib_nodes_of(const typename S::raw* __restrict__ gin, const EnvDev& E,
-                                            const FrameDev& F, int t_local, int lane, float4* nodes) {
+                                            const FrameDev& F, int t_local, int lane, float4* nodes,
+                                            int layout = LAYOUT_PULL) {
     const uint32_t c = (uint32_t)t_local * 32u + (uint32_t)lane;
     if (c >= E.nslot) return;
     const uint32_t row = fdiv(c, E.div_P);
@@ -252,7 +254,10 @@ __device__ __forceinline__ void ib_nodes_of(const typename S::raw* __restrict__ 
     // axis; other cells of the tile may not, and pull_offsets then wraps
     // (in-bounds reads of values that no marker uses)
     const PullOffsets o = pull_offsets(E, x, y, z);
-    const Moments m = pull_moments<S, false>(gin + E.pop_off, E.nslot, c, o);
+    const typename S::raw* G = gin + E.pop_off;
+    const Moments m = layout == LAYOUT_AA0   ? layout_moments<S, false, LAYOUT_AA0>(G, E.nslot, c, o)
+                      : layout == LAYOUT_AA1 ? layout_moments<S, false, LAYOUT_AA1>(G, E.nslot, c, o)
+                                             : pull_moments<S, false>(G, E.nslot, c, o);
     const float rho = 1.0f + m.dr, inv = 1.0f / rho;
     float a0[3];
     frame_accel(F, (float)x, (float)y, (float)z, a0);
@@ -264,9 +269,9 @@ __device__ __forceinline__ void ib_nodes_of(const typename S::raw* __restrict__ 
 template <class S>
 __device__ __forceinline__ void ib_nodes(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs,
                                          const FrameDev* __restrict__ frames, int n_envs, int t, int lane,
-                                         float4* nodes) {
+                                         float4* nodes, int layout = LAYOUT_PULL) {
     const int e = n_envs > 1 ? env_of<&EnvDev::stamp_off>(envs, n_envs, t) : 0;
-    ib_nodes_of<S>(gin, envs[e], frames[e], t - envs[e].stamp_off, lane, nodes);
+    ib_nodes_of<S>(gin, envs[e], frames[e], t - envs[e].stamp_off, lane, nodes, layout);
 }
 
 // One marker of a half-warp: its environment, slot, stencil, U and dV.
@@ -413,6 +418,7 @@ __device__ __forceinline__ void spread_force(const EnvDev& E, const MarkerRef& r
 // first marker of each half-warp stays in registers from the mark phase to
 // the force phase), warps over tile stamps.  fibq != nullptr selects the
 // deterministic spread (fixed-point sums, converted to fib in a last phase).
+// layout (LAYOUT_*) says where the node moments find the populations.
 template <class S>
 __global__ void __launch_bounds__(IB_THREADS, 4)
 k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs_g,
@@ -420,7 +426,7 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
           const float* __restrict__ X, const float* __restrict__ U, const float* __restrict__ dV,
           float* __restrict__ Fm, float4* fib, uint32_t* stamps, const StepState* __restrict__ st,
           float4* nodes, unsigned* bar, int ib_iters, float* dF, unsigned long long* fibq,
-          const float* __restrict__ Nrm, int* status) {
+          const float* __restrict__ Nrm, int* status, int layout) {
     // a single environment's table and frame in shared memory, read by every
     // marker and node of the launch
     __shared__ EnvDev sE;
@@ -472,7 +478,7 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
         while (hits) {
             const int k = __ffs(hits) - 1;
             hits &= hits - 1u;
-            ib_nodes<S>(gin, envs, frames, n_envs, t0 + k * nw, lane, nodes);
+            ib_nodes<S>(gin, envs, frames, n_envs, t0 + k * nw, lane, nodes, layout);
         }
     }
     if (!barrier()) return;

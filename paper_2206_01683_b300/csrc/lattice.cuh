@@ -31,6 +31,9 @@ __host__ __device__ constexpr float store_scale(int i) { return (float)(4 << (2 
 
 // Population storage.  load/store take the velocity index so that reduced
 // formats can apply their per-velocity scale; FP32 stores f_i - w_i as is.
+// load2_rw reads two neighbouring slots (the first aligned to twice the
+// element size) with one ordinary, coherent load, for a kernel that also
+// writes the array it reads.
 // emit(v, i) stores the population whose Hermite polynomial value is v
 // (g_i = w_i v) given coefficients pre-multiplied by POLY: FP32 stores w_i v;
 // the reduced formats store s_i g_i = (32/27) v, so with POLY = 32/27 they
@@ -45,6 +48,9 @@ struct StoreF32 {
         *reinterpret_cast<float2*>(p) = make_float2(wf(i) * a, wf(i) * b);
     }
     static __device__ __forceinline__ float load(const raw* p, int) { return __ldg(p); }
+    static __device__ __forceinline__ float2 load2_rw(const raw* p, int) {
+        return *reinterpret_cast<const float2*>(p);
+    }
     static __device__ __forceinline__ void store(raw* p, float v, int) { *p = v; }
     static __device__ __forceinline__ float decode(raw v, int) { return v; }
     static __device__ __forceinline__ raw encode(float v, int) { return v; }
@@ -64,6 +70,10 @@ struct StoreF16 {
         return __float2half_rn(v * store_scale(i));
     }
     static __device__ __forceinline__ float load(const raw* p, int i) { return decode(__ldg(p), i); }
+    static __device__ __forceinline__ float2 load2_rw(const raw* p, int i) {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
+        return make_float2(v.x * (1.0f / store_scale(i)), v.y * (1.0f / store_scale(i)));
+    }
     static __device__ __forceinline__ void store(raw* p, float v, int i) { *p = encode(v, i); }
 };
 
@@ -81,6 +91,10 @@ struct StoreBF16 {
         return __float2bfloat16_rn(v * store_scale(i));
     }
     static __device__ __forceinline__ float load(const raw* p, int i) { return decode(__ldg(p), i); }
+    static __device__ __forceinline__ float2 load2_rw(const raw* p, int i) {
+        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+        return make_float2(v.x * (1.0f / store_scale(i)), v.y * (1.0f / store_scale(i)));
+    }
     static __device__ __forceinline__ void store(raw* p, float v, int i) { *p = encode(v, i); }
 };
 

@@ -259,7 +259,8 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
 // radius R) in the stored state g of environment E: P = sum alpha j,
 // L = sum alpha (x - c) x j, j = sum_i c_i g_i (the rest populations w_i
 // carry no momentum), alpha = clamp(R + 1/2 - |x - c|, 0, 1), x - c the
-// minimal image on periodic axes.  The free-body coupling needs it every step
+// minimal image on periodic axes (population i where post_loc keeps it under
+// layout aa).  The free-body coupling needs it every step
 // (the inner fluid's momentum change, Kempe & Froehlich 2012).  Block `blk`
 // of `nblk` walks its share of the cells of the sphere's bounding box
 // [lo, lo + ext) and writes seven compensated pairs (P, L, sum alpha) to
@@ -269,7 +270,7 @@ template <class S>
 __device__ __forceinline__ void region_block_sums(const typename S::raw* __restrict__ g, const EnvDev& E,
                                                   const float (&c)[3], float R, const int (&lo)[3],
                                                   const int (&ext)[3], int blk, int nblk, Pair32 (*sh)[7],
-                                                  Pair32* __restrict__ out) {
+                                                  Pair32* __restrict__ out, int aa) {
     const typename S::raw* G = g + E.pop_off;
     Pair32 acc[7];
     const long long n_box = (long long)ext[0] * ext[1] * ext[2];
@@ -297,7 +298,10 @@ __device__ __forceinline__ void region_block_sums(const typename S::raw* __restr
         float j[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const float v = S::decode(G[(size_t)i * E.nslot + slot], i);
+            int dir;
+            const uint32_t loc = post_loc(E, aa, i, p[0], p[1], p[2], slot, &dir);
+            if (!FG_IN_RANGE(DBG_REGION, loc, E.nslot)) continue;
+            const float v = S::decode(G[(size_t)dir * E.nslot + loc], i);
             j[0] += cx(i) * v;
             j[1] += cy(i) * v;
             j[2] += cz(i) * v;
@@ -352,11 +356,11 @@ template <class S>
 __global__ void __launch_bounds__(RED_THREADS)
 k_region_momentum(const typename S::raw* __restrict__ g, const EnvDev* __restrict__ envs, int e, float cx_,
                   float cy_, float cz_, float R, int lo_x, int lo_y, int lo_z, int ext_x, int ext_y, int ext_z,
-                  Pair32* __restrict__ part) {
+                  Pair32* __restrict__ part, int aa) {
     __shared__ Pair32 sh[RED_THREADS / 32][7];
     const float c[3] = {cx_, cy_, cz_};
     const int lo[3] = {lo_x, lo_y, lo_z}, ext[3] = {ext_x, ext_y, ext_z};
-    region_block_sums<S>(g, envs[e], c, R, lo, ext, blockIdx.x, gridDim.x, sh, part + (size_t)blockIdx.x * 7);
+    region_block_sums<S>(g, envs[e], c, R, lo, ext, blockIdx.x, gridDim.x, sh, part + (size_t)blockIdx.x * 7, aa);
 }
 
 }  // namespace fl

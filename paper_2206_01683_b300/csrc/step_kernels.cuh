@@ -206,6 +206,58 @@ __device__ __forceinline__ Moments pull_moments(const typename S::raw* __restric
     return m;
 }
 
+// ------------------------------------------------ population layouts
+// Where the populations arriving at a cell p in the coming step are stored.
+//   LAYOUT_PULL  two buffers: population i arrives from (i, p - c_i) of the
+//                input buffer (the post-collision state of the last step).
+//   LAYOUT_AA0   one buffer in place (AA pattern), even phase: (i, p) holds it.
+//   LAYOUT_AA1   one buffer in place, odd phase: (26 - i, p - c_i) holds it.
+// (direction, slot) pairs; aa_kernels.cuh describes the in-place layout.
+enum { LAYOUT_PULL = 0, LAYOUT_AA0 = 1, LAYOUT_AA1 = 2 };
+
+// Moments of the populations arriving at slot p under a layout.  NC reads
+// through the non-coherent path (the array is not written by the launch);
+// the in-place step kernels read with ordinary loads.
+template <class S, bool SECOND, int LAYOUT, bool NC = true>
+__device__ __forceinline__ Moments layout_moments(const typename S::raw* G, uint32_t nslot, uint32_t p,
+                                                  const PullOffsets& o) {
+    Moments m = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int idx = LAYOUT == LAYOUT_AA0 ? (int)p : (int)p + pull_off(o, i);
+        const int dir = LAYOUT == LAYOUT_AA1 ? Q - 1 - i : i;
+        const typename S::raw* q = G + (size_t)dir * nslot + (uint32_t)idx;
+        g[i] = FG_IN_RANGE(DBG_PULL, idx, nslot) ? (NC ? S::load(q, i) : S::decode(*q, i)) : 0.0f;
+    }
+    accumulate<SECOND>(m, g);
+    return m;
+}
+
+// Location of the post-collision population i of cell (x, y, z) (slot s):
+// the slot returned, the direction in *dir.  aa < 0: the two-buffer layout,
+// (i, s); aa = 1: (26 - i, s); aa = 0: (i, s + c_i) with periodic wrap, or
+// (26 - i, s) where s + c_i lies beyond an open face.
+__device__ __forceinline__ uint32_t post_loc(const EnvDev& E, int aa, int i, int x, int y, int z, uint32_t s,
+                                             int* dir) {
+    if (aa < 0) {
+        *dir = i;
+        return s;
+    }
+    *dir = Q - 1 - i;
+    if (aa == 1) return s;
+    int p[3] = {x + cx(i), y + cy(i), z + cz(i)};
+    for (int a = 0; a < 3; ++a) {
+        const int n = E.n[a];
+        if (p[a] < 0 || p[a] >= n) {
+            if (!E.per[a]) return s;
+            p[a] = p[a] < 0 ? p[a] + n : p[a] - n;
+        }
+    }
+    *dir = i;
+    return (uint32_t)p[0] + (uint32_t)E.P * ((uint32_t)p[1] + (uint32_t)E.n[1] * (uint32_t)p[2]);
+}
+
 // A sum kept as an unevaluated pair hi + lo of FP32 numbers (compensated
 // summation, close to FP64 accuracy for these sums).  B300 runs FP64 --
 // conversions included -- at a small fraction of its FP32 rate and with long

@@ -29,6 +29,8 @@ K1_NAMES = {0: "plain", 1: "staged256", 2: "staged512", 3: "fused", 4: "overlap"
 VARIANT = {"auto": FG_KERNEL_AUTO, "plain": FG_KERNEL_PLAIN, "staged": FG_KERNEL_STAGED,
            "staged512": FG_KERNEL_STAGED512, "fused": FG_KERNEL_FUSED, "overlap": FG_KERNEL_OVERLAP}
 STORAGE = {"f32": FG_F32, "f16": FG_F16, "bf16": FG_BF16}
+FG_LAYOUT_PULL, FG_LAYOUT_AA = 0, 1
+LAYOUT = {"pull": FG_LAYOUT_PULL, "aa": FG_LAYOUT_AA}
 
 
 class FgError(RuntimeError):
@@ -259,11 +261,12 @@ class Domain:
     """Owns one fg_domain (one or many environments)."""
 
     def __init__(self, envs, storage="f32", record_history=0, stream=None, variant="auto",
-                 graphs=True, autotune=False, ib_iters=1, deterministic=False, slip=False, eq_order=2):
+                 graphs=True, autotune=False, ib_iters=1, deterministic=False, slip=False, eq_order=2,
+                 layout="pull"):
         self.envs = list(envs)
         opt = fg_options()
         opt.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
-        opt.layout = 0
+        opt.layout = LAYOUT[layout] if isinstance(layout, str) else int(layout)
         opt.deterministic = 1 if deterministic else 0
         opt.ib_iters = int(ib_iters)
         opt.record_history = int(record_history)

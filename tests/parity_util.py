@@ -126,7 +126,7 @@ class Pair:
     """One GPU domain (single environment) and one oracle, stepped together."""
 
     def __init__(self, shape, tau, faces=(0,) * 6, u_in=(0.0, 0.0, 0.0), rho0=1.0, storage="f32",
-                 variant="auto", ib_iters=1, deterministic=False, slip=False, eq_order=2):
+                 variant="auto", ib_iters=1, deterministic=False, slip=False, eq_order=2, layout="pull"):
         self.shape = tuple(shape)
         self.faces = tuple(int(f) for f in faces)
         self.X = None
@@ -134,7 +134,7 @@ class Pair:
                                slip=slip, eq_order=eq_order)
         self.g = fishlbm.Domain([fishlbm.env_desc(shape, tau, faces, f32(u_in), rho0)], storage=storage,
                                 variant=variant, ib_iters=ib_iters, deterministic=deterministic, slip=slip,
-                                eq_order=eq_order)
+                                eq_order=eq_order, layout=layout)
         self.perm = gpu_to_oracle_perm()
         _, self.w = oracle.lattice()
         self.nseg = 1

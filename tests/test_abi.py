@@ -107,3 +107,33 @@ def test_domain_limits_are_rejected_before_gpu_work():
             assert e.status == fishlbm.FG_ERR_INVALID, name
         else:
             raise AssertionError(name + " accepted")
+
+
+def test_layout_options_are_checked_before_gpu_work():
+    """An unknown layout, and the in-place layout with a kernel other than
+    the plain one, fail with FG_ERR_INVALID before any GPU work."""
+    env = fishlbm.env_desc((8, 8, 8), 0.6)
+    bad = [(2, fishlbm.FG_KERNEL_AUTO), (-1, fishlbm.FG_KERNEL_AUTO)]
+    bad += [(fishlbm.FG_LAYOUT_AA, v) for v in (fishlbm.FG_KERNEL_STAGED, fishlbm.FG_KERNEL_STAGED512,
+                                                 fishlbm.FG_KERNEL_FUSED, fishlbm.FG_KERNEL_OVERLAP)]
+    for layout, variant in bad:
+        opt = fishlbm.fg_options()
+        opt.storage = 0
+        opt.layout = layout
+        opt.ib_iters = 1
+        opt.eq_order = 2
+        opt.use_graphs = 1
+        opt.kernel_variant = variant
+        try:
+            fishlbm.fg_create_domain([env], opt)
+        except fishlbm.FgError as e:
+            assert e.status == fishlbm.FG_ERR_INVALID, (layout, variant)
+        else:
+            raise AssertionError("layout %d with variant %d accepted" % (layout, variant))
+
+
+def test_layout_enum_matches_header():
+    text = open(os.path.join(ROOT, "include", "fishlbm.h")).read()
+    assert "FG_LAYOUT_PULL = 0" in text and "FG_LAYOUT_AA = 1" in text
+    assert (fishlbm.FG_LAYOUT_PULL, fishlbm.FG_LAYOUT_AA) == (0, 1)
+    assert fishlbm.LAYOUT == {"pull": 0, "aa": 1}

@@ -5,7 +5,7 @@ libfishlbm_debug.so is the library compiled with -DFG_DEBUG_BOUNDS: every
 kernel checks the indices it computes and records a flag instead of making
 an out-of-range access.  A child process loads it (FISHLBM_LIB) and runs
 tiny periodic and open domains through every stream-collide variant and
-option (multi-direct forcing, deterministic spread, slip forcing, third-order
+population layout and option (multi-direct forcing, deterministic spread, slip forcing, third-order
 equilibrium, FP16/BF16 storage with two cells per thread and one, several
 environments, fg_step_io, region momentum, 1- and 2-cell domains) against
 the oracle; no flag may be set and the FP32 cases
@@ -58,6 +58,31 @@ for v in ("plain", "staged", "staged512", "fused", "overlap"):
     run("open_%s_eq3_det" % v, (9, 7, 6), OPEN, ball((4.3, 3.1, 2.6), 0.4, 3), 20, fr, variant=v, eq_order=3,
         deterministic=True)
     run("periodic_%s_slip" % v, (8, 8, 8), (0,) * 6, ball((4.0, 3.5, 4.2), 1.5, 6), 10, variant=v, slip=True)
+# the in-place layout: both phases, open faces on every axis, short axes
+for M in (1, 2):
+    run("aa_periodic_M%d" % M, (8, 8, 8), (0,) * 6, ball((4.0, 3.5, 4.2), 1.5, 4), 21, layout="aa", ib_iters=M)
+run("aa_open_eq3_det", (9, 7, 6), OPEN, ball((4.3, 3.1, 2.6), 0.4, 3), 21, fr, layout="aa", eq_order=3,
+    deterministic=True)
+run("aa_open_even", (10, 7, 6), OPEN, ball((4.3, 3.1, 2.6), 0.4, 3), 20, fr, layout="aa")
+run("aa_all_open", (6, 5, 4), (1, 2, 3, 2, 2, 3), None, 9, fr, layout="aa")
+run("aa_open3", (3, 3, 3), (2, 2, 3, 1, 3, 3), None, 8, layout="aa")
+for st in ("f16", "bf16"):
+    for nx in (10, 9):
+        a = fishlbm.Domain([fishlbm.env_desc((8, 8, 8), 0.7),
+                            fishlbm.env_desc((nx, 7, 6), 0.7, OPEN, (0.01, 0, 0), 1.0, (0.01, 0, 0))],
+                           storage=st, layout="aa")
+        a.set_markers(np.float32([[4.3, 3.1, 2.6]]), np.zeros((1, 3), np.float32), np.float32([1.0]), env=1)
+        a.step(5)
+        a.region_momentum((1.0, 3.0, 2.0), 3.0, env=1)
+        s_ = a.save_state(env=1)
+        a.step(1)
+        a.load_state(s_, env=1)
+        a.step(2)
+for shape in ((1, 1, 1), (2, 1, 1), (4, 3, 3)):
+    t = fishlbm.Domain([fishlbm.env_desc(shape, 0.8, (0, 0, 0, 0, 0, 0) if shape[1] == 1 else
+                                         (1, 2, 3, 3, 2, 1))], layout="aa")
+    t.step(3)
+    t.populations()
 # several environments, FP16, region momentum, tiny domains
 d = fishlbm.Domain([fishlbm.env_desc((8, 8, 8), 0.7), fishlbm.env_desc((9, 7, 6), 0.7, OPEN, (0.01, 0, 0))])
 X, dV = inputs.fibonacci_sphere(4, 1.5, (4.0, 3.5, 4.2))
