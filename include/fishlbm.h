@@ -237,6 +237,39 @@ fg_status fg_region_momentum(fg_domain* d, int env, const double center[3], doub
  * call synchronises the stream. */
 fg_status fg_set_segment_refs(fg_domain* d, int env, int n_seg, const double* refs);
 
+/* A free rigid sphere advanced on the device: the body update of Eq. 1
+ * (Sec. III-A) for a body whose only generalised forces are the fluid's
+ * tau_ext, gravity and buoyancy, two-way coupled every step with no host
+ * round trip.  Each step of the environment (fg_step, fg_step_io) then
+ * places the n markers on the shell, X = c + R d_l, U = V + W x (X - c),
+ * with torques about c; after the reduction it sums the momentum P and
+ * angular momentum L of the fluid inside the shell (as fg_region_momentum)
+ * and advances the body in FP64, with the inner fluid's change of momentum
+ * (Kempe & Froehlich, J. Comput. Phys. 231, 2012):
+ *   m_p dV = F + dP_in + (m_p - m_f) g,  I_p dW = T + dL_in,
+ *   c += (V_old + V_new) / 2,
+ * m_f = 4 pi R^3 / 3, m_p = density_ratio m_f, I_p = 0.4 m_p R^2, F and T
+ * the environment's total force/torque row.  The body starts at rest at
+ * center.  dirs[n][3] are unit directions (FP64, host), dV[n] the marker
+ * weights (host); box_reaction = 1 adds -(m_p - m_f) g / (cells) to the
+ * environment's frame acceleration (Eq. 3's acc term), so that in a closed
+ * box the fluid carries the body's excess weight.  While attached, the
+ * environment's markers, segment points and torque point follow the body:
+ * fg_set_markers and fg_set_segment_refs on it, and fg_set_markers_all and
+ * fg_step_io with marker arrays on the domain, fail with FG_ERR_STATE;
+ * fg_init_fields leaves the body state alone.  One sphere per environment.
+ * Errors: FG_ERR_INVALID (arguments, markers outside the domain's limits),
+ * FG_ERR_STATE (a sphere attached already), FG_ERR_OOM, FG_ERR_CUDA.
+ * Synchronises. */
+fg_status fg_attach_sphere(fg_domain* d, int env, double radius, const double center[3], double density_ratio,
+                           const double gravity[3], int n, const double* dirs, const float* dV, int box_reaction);
+/* out[9] = centre, velocity, spin of the sphere attached to env (after the
+ * steps enqueued so far; synchronises).  FG_ERR_STATE if none. */
+fg_status fg_sphere_state(fg_domain* d, int env, double* out);
+/* Detach the sphere of env (its markers stay where the last step put them;
+ * the box reaction is removed from the frame).  FG_ERR_STATE if none. */
+fg_status fg_detach_sphere(fg_domain* d, int env);
+
 /* Unit surface normals of env's current markers for slip forcing
  * (fg_options.ib_slip = 1): N[n][3] float, host or device (device_ptrs), n
  * equal to the count given to the last fg_set_markers (normalised by the

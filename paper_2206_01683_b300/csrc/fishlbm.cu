@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -28,6 +29,7 @@
 #include "reduce_kernels.cuh"
 #include "fused_kernels.cuh"
 #include "state_kernels.cuh"
+#include "body_kernels.cuh"
 
 using namespace fl;
 
@@ -234,11 +236,26 @@ struct fg_domain {
     struct GraphKey {
         const void* X = nullptr;
         const void* red = nullptr;
-        int total_markers = -1, red_z = -1;
+        const void* sph = nullptr;
+        int total_markers = -1, red_z = -1, n_sph = 0, sph_max_n = 0;
         bool operator==(const GraphKey& o) const {
-            return X == o.X && red == o.red && total_markers == o.total_markers && red_z == o.red_z;
+            return X == o.X && red == o.red && total_markers == o.total_markers && red_z == o.red_z &&
+                   sph == o.sph && n_sph == o.n_sph && sph_max_n == o.sph_max_n;
         }
     } graph_key;
+    // free spheres advanced on the device (fg_attach_sphere): the host copy
+    // of the table (its body state is current only after sphere_download),
+    // the device table, the marker directions and the inner-fluid partials
+    std::vector<SphereDev> sph_host;
+    std::vector<std::vector<double>> sph_dirs_host;
+    SphereDev* sph = nullptr;
+    double* sph_dirs = nullptr;
+    Pair32* sph_part = nullptr;
+    int sph_cap = 0, sph_dirs_cap = 0, sph_max_n = 0;
+    // the caller's last frame of each environment, and the frame acceleration
+    // an attached sphere's box reaction adds to it
+    std::vector<fg_frame> user_frame;
+    std::vector<std::array<double, 3>> box_acc;
     bool profiling = false;
     std::vector<cudaEvent_t> ev[FG_K_COUNT];
     int ev_used[FG_K_COUNT] = {0, 0, 0};
@@ -300,6 +317,25 @@ void set_frame(FrameDev& f, const fg_frame& src) {
     }
 }
 
+// The caller's frame of environment e plus the box reaction of a sphere
+// attached there.
+void set_env_frame(fg_domain* d, int e, const fg_frame& f) {
+    d->user_frame[e] = f;
+    fg_frame g = f;
+    for (int a = 0; a < 3; ++a) g.acc[a] += d->box_acc[e][a];
+    set_frame(d->frame[e], g);
+}
+
+fg_status sphere_download(fg_domain* d);
+fg_status sphere_upload(fg_domain* d);
+
+// Whether a sphere is attached to environment env.
+bool has_sphere(const fg_domain* d, int env) {
+    for (const SphereDev& s : d->sph_host)
+        if (s.env == env) return true;
+    return false;
+}
+
 void free_all(fg_domain* d) {
     if (!d) return;
     for (int p = 0; p < 2; ++p)
@@ -310,7 +346,7 @@ void free_all(fg_domain* d) {
     void* ptrs[] = {d->d_env, d->d_frame, d->pop[0], d->pop[1] != d->pop[0] ? d->pop[1] : nullptr, d->fib, d->stamps, d->ib_nodes, d->ib_bar,
                     d->fibq, d->mass_part, d->red_partials, d->red_counters, d->d_state,
                     d->X, d->U, d->dV, d->Fm, d->dF, d->Nrm, d->seg, d->seg_ref, d->region_part, d->mk_stage, d->ft, d->mass,
-                    d->hist, d->status, d->work_segs, d->work, d->work_done};
+                    d->hist, d->status, d->work_segs, d->work, d->work_done, d->sph, d->sph_dirs, d->sph_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (d->rb) cudaFreeHost(d->rb);
@@ -757,6 +793,10 @@ fg_status enqueue_step_io(fg_domain* d, const typename S::raw* gin, typename S::
                           cudaEvent_t* const* ev, int aa_phase = -1) {
     const bool fused = d->k1 == K1_FUSED;
     const bool overlap = d->k1 == K1_OVERLAP && d->total_markers > 0;
+    const int n_sph = (int)d->sph_host.size();
+    if (n_sph > 0)   // attached spheres: their markers from the body state
+        k_sphere_place<<<dim3((unsigned)((d->sph_max_n + 255) / 256), (unsigned)n_sph), 256, 0, s>>>(
+            d->sph, d->sph_dirs, d->X, d->U, d->d_env, d->seg_ref);
     if (aa_phase >= 0) {
         if (d->total_markers > 0) {
             if (ev) CK(cudaEventRecord(ev[FG_K_IB][0], s));
@@ -809,6 +849,13 @@ fg_status enqueue_step_io(fg_domain* d, const typename S::raw* gin, typename S::
                               d->rb_ft_all_dev, d->rb_status_dev, d->rb_seq_dev, fused ? 1 : 0));
     }
     if (ev) CK(cudaEventRecord(ev[FG_K_REDUCE][1], s));
+    if (n_sph > 0) {
+        // the inner fluid's momentum in the new state, then the body update
+        const int grid = 4 * d->n_sms;
+        k_sphere_fluid<S><<<dim3((unsigned)grid, (unsigned)n_sph), RED_THREADS, 0, s>>>(
+            gout, d->d_env, d->sph, aa_phase < 0 ? -1 : (aa_phase ^ 1), d->sph_part);
+        k_sphere_update<<<n_sph, 32, 0, s>>>(d->sph, d->sph_part, grid, d->ft, 0);
+    }
     CK(cudaGetLastError());
     return FG_OK;
 }
@@ -859,6 +906,9 @@ fg_status graph_step(fg_domain* d) {
     key.red = d->red_partials;
     key.total_markers = d->total_markers;
     key.red_z = d->red_z;
+    key.sph = d->sph;
+    key.n_sph = (int)d->sph_host.size();
+    key.sph_max_n = d->sph_max_n;
     if (!(key == d->graph_key)) {
         for (int p = 0; p < 2; ++p)
             if (d->graph[p]) {
@@ -1127,6 +1177,8 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         }
     }
     d->desc.assign(envs, envs + n_envs);
+    d->user_frame.resize(n_envs);
+    d->box_acc.assign(n_envs, {0.0, 0.0, 0.0});
     d->env.resize(n_envs);
     d->frame.resize(n_envs);
     d->mk.resize(n_envs);
@@ -1163,6 +1215,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         block0 += E.nblocks;
         fg_frame fr{};
         fr.origin[0] = (s.nx - 1) * 0.5; fr.origin[1] = (s.ny - 1) * 0.5; fr.origin[2] = (s.nz - 1) * 0.5;
+        d->user_frame[e] = fr;
         set_frame(d->frame[e], fr);
     }
     if ((o.kernel_variant == FG_KERNEL_STAGED || o.kernel_variant == FG_KERNEL_STAGED512) && !can_stage) {
@@ -1409,11 +1462,13 @@ static const char* first_marker_problem(const EnvDev& E, int n, const float* X, 
     return "invalid marker";
 }
 
-fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const float* U, const float* dV,
-                         const int* seg, int n_seg, const double ref[3], int device_ptrs) {
-    NvtxRange nvtx_range("fg_set_markers");
-    fg_status st = check_env(d, env);
-    if (st != FG_OK) return st;
+}  // extern "C"
+
+namespace {
+
+fg_status set_markers_impl(fg_domain* d, int env, int n, const float* X, const float* U, const float* dV,
+                           const int* seg, int n_seg, const double ref[3], int device_ptrs) {
+    fg_status st = FG_OK;
     if (n < 0) return fail(FG_ERR_INVALID, "negative marker count");
     if (n > 0 && (!X || !U)) return fail(FG_ERR_INVALID, "X and U are required");
     if (n_seg < 1 || n_seg > MAX_SEG) return fail(FG_ERR_INVALID, "n_seg must be in [1, 16]");
@@ -1471,6 +1526,19 @@ fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const flo
     return FG_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+fg_status fg_set_markers(fg_domain* d, int env, int n, const float* X, const float* U, const float* dV,
+                         const int* seg, int n_seg, const double ref[3], int device_ptrs) {
+    NvtxRange nvtx_range("fg_set_markers");
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    if (has_sphere(d, env)) return fail(FG_ERR_STATE, "the markers follow an attached sphere (fg_detach_sphere)");
+    return set_markers_impl(d, env, n, X, U, dV, seg, n_seg, ref, device_ptrs);
+}
+
 fg_status fg_region_momentum(fg_domain* d, int env, const double* center, double radius, double* out,
                              double* alpha_sum) {
     NvtxRange nvtx_range("fg_region_momentum");
@@ -1517,6 +1585,7 @@ fg_status fg_region_momentum(fg_domain* d, int env, const double* center, double
 fg_status fg_set_segment_refs(fg_domain* d, int env, int n_seg, const double* refs) {
     fg_status st = check_env(d, env);
     if (st != FG_OK) return st;
+    if (has_sphere(d, env)) return fail(FG_ERR_STATE, "torques of an attached sphere are about its centre");
     MarkerRegion& m = d->mk[env];
     if (!refs) {
         m.has_seg_ref = false;
@@ -1592,6 +1661,7 @@ fg_status fg_set_markers_all(fg_domain* d, int n, const float* X, const float* U
     NvtxRange nvtx_range("fg_set_markers_all");
     if (!d) return fail(FG_ERR_INVALID, "null domain");
     if (n != d->total_markers) return fail(FG_ERR_INVALID, "n must equal the markers of all environments");
+    if (!d->sph_host.empty()) return fail(FG_ERR_STATE, "markers follow an attached sphere (fg_detach_sphere)");
     if (n == 0) return FG_OK;
     if (!X || !U) return fail(FG_ERR_INVALID, "null marker array");
     const float* xs = X;
@@ -1683,7 +1753,7 @@ fg_status fg_step(fg_domain* d, int n_steps, const fg_frame* frames) {
                     !std::isfinite(frames[e].domega[a]) || !std::isfinite(frames[e].origin[a]))
                     return fail(FG_ERR_INVALID, "frame not finite");
         }
-        for (int e = 0; e < d->n_envs; ++e) set_frame(d->frame[e], frames[e]);
+        for (int e = 0; e < d->n_envs; ++e) set_env_frame(d, e, frames[e]);
         fg_status st = upload_frames(d);
         if (st != FG_OK) return st;
     }
@@ -1696,6 +1766,13 @@ fg_status fg_step(fg_domain* d, int n_steps, const fg_frame* frames) {
         if (st != FG_OK) return st;
     }
     if (fg_status st = sync_work_table(d); st != FG_OK) return st;
+    for (const SphereDev& sp : d->sph_host)
+        if (sp.mk_off != d->mk[sp.env].off) {   // the marker layout moved: the table follows it
+            fg_status st = sphere_download(d);
+            if (st == FG_OK) st = sphere_upload(d);
+            if (st != FG_OK) return st;
+            break;
+        }
     const bool graphs = d->opt.use_graphs && !d->profiling;
     for (int s = 0; s < n_steps; ++s) {
         fg_status st = dispatch(d->opt.storage, [&](auto tag) {
@@ -1719,7 +1796,7 @@ fg_status fg_step_state(fg_domain* d, const void* in, void* out, const fg_frame*
             if (!std::isfinite(frames[0].acc[a]) || !std::isfinite(frames[0].omega[a]) ||
                 !std::isfinite(frames[0].domega[a]) || !std::isfinite(frames[0].origin[a]))
                 return fail(FG_ERR_INVALID, "frame not finite");
-        set_frame(d->frame[0], frames[0]);
+        set_env_frame(d, 0, frames[0]);
         fg_status st = upload_frames(d);
         if (st != FG_OK) return st;
     }
@@ -2136,7 +2213,7 @@ static fg_status adjoint_step_from(fg_domain* d, const float* f, const fg_frame*
     const int n = d->mk[0].n;
     if (n > 0 && (!gX || !gU)) return fail(FG_ERR_INVALID, "gX and gU are required");
     if (frames) {
-        set_frame(d->frame[0], frames[0]);
+        set_env_frame(d, 0, frames[0]);
         if ((st = upload_frames(d)) != FG_OK) return st;
     }
     const int rows = d->mk[0].nseg + 1;
@@ -2348,6 +2425,172 @@ fg_status fg_stream_collide_bytes(fg_domain* d, unsigned long long* bytes) {
     if (!d || !bytes) return fail(FG_ERR_INVALID, "null argument");
     *bytes = 2ull * 27ull * d->total_cells * d->esize;
     return FG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The device table's body states -> the host copy.
+fg_status sphere_download(fg_domain* d) {
+    if (d->sph_host.empty() || !d->sph) return FG_OK;
+    CK(cudaMemcpyAsync(d->sph_host.data(), d->sph, sizeof(SphereDev) * d->sph_host.size(), cudaMemcpyDeviceToHost,
+                       d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    return FG_OK;
+}
+
+// The host table -> the device, with the marker offsets of the current
+// marker layout; grows the device arrays (a captured step that baked the old
+// ones is captured again: the graph key holds the table's address).
+fg_status sphere_upload(fg_domain* d) {
+    const int n = (int)d->sph_host.size();
+    size_t ndirs = 0;
+    int max_n = 0;
+    for (int k = 0; k < n; ++k) {
+        SphereDev& s = d->sph_host[k];
+        s.mk_off = d->mk[s.env].off;
+        s.dir_off = (int)(ndirs / 3);
+        ndirs += d->sph_dirs_host[k].size();
+        max_n = std::max(max_n, s.n);
+    }
+    d->sph_max_n = max_n;
+    if (n == 0) return FG_OK;
+    if (n > d->sph_cap) {
+        SphereDev* p = nullptr;
+        Pair32* q = nullptr;
+        fg_status st = dalloc(&p, (size_t)n);
+        if (st == FG_OK) st = dalloc(&q, (size_t)n * 4 * d->n_sms * 7);
+        if (st != FG_OK) {
+            if (p) cudaFree(p);
+            return st;
+        }
+        CK(cudaStreamSynchronize(d->stream));
+        if (d->sph) cudaFree(d->sph);
+        if (d->sph_part) cudaFree(d->sph_part);
+        d->sph = p;
+        d->sph_part = q;
+        d->sph_cap = n;
+    }
+    if (ndirs > (size_t)d->sph_dirs_cap) {
+        double* p = nullptr;
+        fg_status st = dalloc(&p, ndirs);
+        if (st != FG_OK) return st;
+        CK(cudaStreamSynchronize(d->stream));
+        if (d->sph_dirs) cudaFree(d->sph_dirs);
+        d->sph_dirs = p;
+        d->sph_dirs_cap = (int)ndirs;
+    }
+    std::vector<double> all;
+    all.reserve(ndirs);
+    for (const auto& v : d->sph_dirs_host) all.insert(all.end(), v.begin(), v.end());
+    CK(cudaMemcpyAsync(d->sph_dirs, all.data(), sizeof(double) * ndirs, cudaMemcpyHostToDevice, d->stream));
+    CK(cudaMemcpyAsync(d->sph, d->sph_host.data(), sizeof(SphereDev) * n, cudaMemcpyHostToDevice, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    return FG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fg_status fg_attach_sphere(fg_domain* d, int env, double radius, const double* center, double density_ratio,
+                           const double* gravity, int n, const double* dirs, const float* dV, int box_reaction) {
+    NvtxRange nvtx_range("fg_attach_sphere");
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    if (d->poisoned) return fail(FG_ERR_STATE, "domain poisoned by a numeric fault; call fg_init_fields");
+    if (!center || !gravity || !dirs || !dV) return fail(FG_ERR_INVALID, "null argument");
+    if (!(radius > 0.0) || !std::isfinite(radius)) return fail(FG_ERR_INVALID, "radius must be positive");
+    if (!(density_ratio > 0.0) || !std::isfinite(density_ratio))
+        return fail(FG_ERR_INVALID, "density ratio must be positive");
+    if (n < 1) return fail(FG_ERR_INVALID, "a sphere needs markers");
+    if (box_reaction != 0 && box_reaction != 1) return fail(FG_ERR_INVALID, "box_reaction must be 0 or 1");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(center[a]) || !std::isfinite(gravity[a])) return fail(FG_ERR_INVALID, "not finite");
+    for (size_t k = 0; k < 3ull * n; ++k)
+        if (!std::isfinite(dirs[k])) return fail(FG_ERR_INVALID, "direction not finite");
+    if (has_sphere(d, env)) return fail(FG_ERR_STATE, "a sphere is attached to this environment already");
+    // the shell at rest: X = c + R d, U = 0 (the checks of fg_set_markers apply)
+    std::vector<float> X(3ull * n), U(3ull * n, 0.0f);
+    for (int l = 0; l < n; ++l)
+        for (int a = 0; a < 3; ++a) X[3ull * l + a] = (float)(center[a] + radius * dirs[3ull * l + a]);
+    if ((st = set_markers_impl(d, env, n, X.data(), U.data(), dV, nullptr, 1, center, 0)) != FG_OK) return st;
+    if ((st = sphere_download(d)) != FG_OK) return st;
+    SphereDev s;
+    std::memset(&s, 0, sizeof(s));
+    const double volume = 4.0 * M_PI * std::pow(radius, 3) / 3.0;
+    s.R = radius;
+    s.mp = density_ratio * volume;
+    s.mf = volume;
+    s.Ip = 0.4 * s.mp * std::pow(radius, 2);
+    for (int a = 0; a < 3; ++a) {
+        s.c[a] = center[a];
+        s.g[a] = gravity[a];
+    }
+    s.env = env;
+    s.n = n;
+    // in a periodic box nothing else holds the excess weight: the fluid gets
+    // the reaction as a uniform frame acceleration (Eq. 3's acc term)
+    const double fluid_mass = (double)env_cells(d, env);
+    for (int a = 0; a < 3; ++a) d->box_acc[env][a] = box_reaction ? (s.mp - s.mf) * gravity[a] / fluid_mass : 0.0;
+    set_env_frame(d, env, d->user_frame[env]);
+    if ((st = upload_frames(d)) != FG_OK) return st;
+    d->sph_host.push_back(s);
+    d->sph_dirs_host.emplace_back(dirs, dirs + 3ull * n);
+    if ((st = sphere_upload(d)) != FG_OK) {
+        d->sph_host.pop_back();
+        d->sph_dirs_host.pop_back();
+        return st;
+    }
+    // the inner fluid's momentum in the current state: the first step's dP_in
+    // and dL_in are measured from it
+    const int k = (int)d->sph_host.size() - 1;
+    const int grid = 4 * d->n_sms;
+    st = dispatch(d->opt.storage, [&](auto tag) -> fg_status {
+        typedef decltype(tag) S;
+        k_sphere_fluid<S><<<dim3((unsigned)grid, 1u), RED_THREADS, 0, d->stream>>>(
+            (const typename S::raw*)d->pop[d->cur], d->d_env, d->sph + k, aa_of(d), d->sph_part + (size_t)k * grid * 7);
+        k_sphere_update<<<1, 32, 0, d->stream>>>(d->sph + k, d->sph_part + (size_t)k * grid * 7, grid, d->ft, 1);
+        CK(cudaGetLastError());
+        return FG_OK;
+    });
+    if (st != FG_OK) return st;
+    CK(cudaStreamSynchronize(d->stream));
+    return FG_OK;
+}
+
+fg_status fg_sphere_state(fg_domain* d, int env, double* out) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    if (!out) return fail(FG_ERR_INVALID, "null output");
+    if ((st = sphere_download(d)) != FG_OK) return st;
+    for (const SphereDev& s : d->sph_host)
+        if (s.env == env) {
+            for (int a = 0; a < 3; ++a) {
+                out[a] = s.c[a];
+                out[3 + a] = s.V[a];
+                out[6 + a] = s.W[a];
+            }
+            return FG_OK;
+        }
+    return fail(FG_ERR_STATE, "no sphere attached to this environment");
+}
+
+fg_status fg_detach_sphere(fg_domain* d, int env) {
+    fg_status st = check_env(d, env);
+    if (st != FG_OK) return st;
+    if ((st = sphere_download(d)) != FG_OK) return st;
+    for (size_t k = 0; k < d->sph_host.size(); ++k)
+        if (d->sph_host[k].env == env) {
+            d->sph_host.erase(d->sph_host.begin() + (long)k);
+            d->sph_dirs_host.erase(d->sph_dirs_host.begin() + (long)k);
+            d->box_acc[env] = {0.0, 0.0, 0.0};
+            set_env_frame(d, env, d->user_frame[env]);
+            if ((st = upload_frames(d)) != FG_OK) return st;
+            return sphere_upload(d);
+        }
+    return fail(FG_ERR_STATE, "no sphere attached to this environment");
 }
 
 }  // extern "C"

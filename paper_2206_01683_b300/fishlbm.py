@@ -71,6 +71,9 @@ SIGNATURES = {
     "fg_selftest_waits": (_I, [ctypes.c_uint, _P(_I)]),
     "fg_debug_flags": (_I, [_P(ctypes.c_uint), _I]),
     "fg_region_momentum": (_I, [_V, _I, _P(_D), _D, _P(_D), _P(_D)]),
+    "fg_attach_sphere": (_I, [_V, _I, _D, _P(_D), _D, _P(_D), _I, _P(_D), _P(ctypes.c_float), _I]),
+    "fg_sphere_state": (_I, [_V, _I, _P(_D)]),
+    "fg_detach_sphere": (_I, [_V, _I]),
     "fg_step": (_I, [_V, _I, _P(fg_frame)]),
     "fg_get_body_force_torque": (_I, [_V, _I, _P(_D)]),
     "fg_step_io": (_I, [_V, _V, _V, _I, _P(fg_frame), _V]),
@@ -331,6 +334,30 @@ class Domain:
             raise ValueError("X and U must both be host or both be device arrays")
         _check(lib().fg_set_markers_all(self.h, n, pX, pU, 1 if devX else 0))
         self._keep_all = (kX, kU)
+
+    def attach_sphere(self, radius, center, density_ratio, gravity, dirs, dV, env=0, box_reaction=True):
+        """Advance a free rigid sphere of the given radius on the device,
+        two-way coupled every step (fg_attach_sphere): markers on the shell
+        along the unit directions dirs (n, 3) with weights dV (n,)."""
+        c = np.ascontiguousarray(center, dtype=np.float64).reshape(3)
+        g = np.ascontiguousarray(gravity, dtype=np.float64).reshape(3)
+        d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+        w = np.ascontiguousarray(dV, dtype=np.float32).reshape(-1)
+        if w.shape[0] != d.shape[0]:
+            raise ValueError("dirs and dV must have the same length")
+        _check(lib().fg_attach_sphere(self.h, env, float(radius), _dp(c), float(density_ratio), _dp(g),
+                                      d.shape[0], _dp(d), w.ctypes.data_as(_P(ctypes.c_float)),
+                                      1 if box_reaction else 0))
+        self.nmark[env] = d.shape[0]
+
+    def sphere_state(self, env=0):
+        """(centre, velocity, spin) of the sphere attached to env."""
+        out = np.zeros(9)
+        _check(lib().fg_sphere_state(self.h, env, _dp(out)))
+        return out[0:3].copy(), out[3:6].copy(), out[6:9].copy()
+
+    def detach_sphere(self, env=0):
+        _check(lib().fg_detach_sphere(self.h, env))
 
     def set_segment_refs(self, refs, env=0):
         """Torque point per segment row (n_seg, 3); None: the common point."""

@@ -77,3 +77,46 @@ class FreeSphere:
         self.spin = self.spin + dw
         self._p_in, self._l_in = p_in, l_in
         return ft
+
+
+class DeviceFreeSphere:
+    """The same free sphere advanced on the device (fg_attach_sphere): the
+    markers, the inner-fluid sums and the body update run in the step's own
+    kernels, so stepping needs no synchronisation; ``centre``, ``vel`` and
+    ``spin`` read the body state back (and synchronise).  Same constructor
+    arguments as FreeSphere; the environment's frame is the box reaction
+    unless the caller passes frames of its own to the domain."""
+
+    def __init__(self, domain, radius, center, density_ratio, gravity, n_markers=None, env=0,
+                 box_reaction=True):
+        self.dom = domain
+        self.env = env
+        self.R = float(radius)
+        n = int(n_markers) if n_markers else int(round(4.0 * math.pi * self.R ** 2))
+        unit, w = inputs.fibonacci_sphere(n, 1.0, (0.0, 0.0, 0.0))
+        self.dirs = unit
+        self.dV = (w * self.R ** 2).astype(np.float32)
+        domain.attach_sphere(self.R, center, density_ratio, gravity, self.dirs, self.dV, env=env,
+                             box_reaction=box_reaction)
+
+    def step(self, n=1):
+        """Advance fluid and body by n steps (no synchronisation)."""
+        self.dom.step(n)
+
+    def state(self):
+        return self.dom.sphere_state(self.env)
+
+    @property
+    def centre(self):
+        return self.state()[0]
+
+    @property
+    def vel(self):
+        return self.state()[1]
+
+    @property
+    def spin(self):
+        return self.state()[2]
+
+    def detach(self):
+        self.dom.detach_sphere(self.env)

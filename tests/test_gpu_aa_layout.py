@@ -1,8 +1,9 @@
 """The in-place (AA) population layout: one population array updated in
 place, against the two-buffer pull layout (bit for bit) and the FP64 oracle.
 
-The two layouts run the same arithmetic in the same order, so populations,
-marker forces and the force/torque rows agree exactly (with the
+The AA layout runs the plain kernel's arithmetic in the same order, so
+against the plain kernel in the pull layout populations, marker forces and
+the force/torque rows agree exactly (with the
 deterministic spread, whose sums do not depend on arrival order); only the
 mass sums are grouped differently (the open-face cells are summed by the
 thread of their inward neighbour) and agree to FP32 rounding.
@@ -30,7 +31,9 @@ TOL_MASS_PER_CELL = 1e-9
 
 
 def _pair_of_domains(envs, **kw):
-    return [fishlbm.Domain(envs, layout=lay, **kw) for lay in ("pull", "aa")]
+    """The plain kernel in the pull layout (the kernel whose in-place form
+    the AA layout runs) and the AA layout."""
+    return [fishlbm.Domain(envs, layout=lay, variant="plain", **kw) for lay in ("pull", "aa")]
 
 
 def _assert_same(doms, n_envs, steps, where=""):
@@ -165,7 +168,7 @@ def test_aa_state_buffers_cross_layouts_and_phases():
     U = np.tile([0.01, 0.0, 0.0], (50, 1)).astype(np.float32)
 
     def dom(layout):
-        d = fishlbm.Domain([env], layout=layout, deterministic=True)
+        d = fishlbm.Domain([env], layout=layout, variant="plain", deterministic=True)
         d.init_fields(rho, u)
         d.set_markers(np.float32(X), U, np.float32(dV))
         return d
