@@ -23,14 +23,18 @@
 //
 // Cells on the outer layer of an open face take their update from the
 // moments of their inward neighbour x_f = x + n alone (the extrapolation
-// rule of cell_coeffs).  x_f's moments are read from locations x_f's thread
-// overwrites, so the thread of x_f ("the server") also updates the boundary
-// cells it serves -- up to 7 at a corner -- from the moments it already has,
-// and writes their outputs: (26 - i, x) in an even step; (i, x + c_i) in an
-// odd step, or (26 - i, x) where x + c_i lies beyond an open face (that
-// location belongs to nobody in an odd step).  The boundary cells' own
-// threads do nothing.  Markers keep their stencils off the outer layer, so
-// boundary cells carry no IB force.
+// rule of cell_coeffs), and x_f's thread overwrites the locations those
+// moments are read from.  So a small kernel, k_aa_boundary, updates the
+// boundary cells first (one per thread, reading x_f's arriving populations
+// before anything overwrites them) and writes their outputs: (26 - i, x) in
+// an even step; (i, x + c_i) in an odd step, or (26 - i, x) where x + c_i
+// lies beyond an open face (that location belongs to nobody in an odd
+// step).  Then the stream-collide kernel updates every other cell.  None of
+// the locations the boundary kernel writes is read or written by the
+// stream-collide kernel of the step.  (With two cells per thread, a pair
+// holding a cell on an open x face updates it from its partner's moments
+// instead.)  Markers keep their stencils off the outer layer, so boundary
+// cells carry no IB force.
 #pragma once
 
 #include "step_kernels.cuh"
@@ -47,20 +51,6 @@ __device__ __forceinline__ unsigned open_bits(const EnvDev& E, int x, int y, int
         if (!E.per[a]) {
             if (p[a] == 0) b |= 1u << (2 * a);
             if (p[a] == E.n[a] - 1) b |= 2u << (2 * a);
-        }
-    return b;
-}
-
-// Boundary neighbours a cell serves: bit 0 (1) when x - 1 (x + 1) is the
-// outer layer of an open x axis, bits 2, 3 for y, bits 4, 5 for z.
-__device__ __forceinline__ unsigned serve_bits(const EnvDev& E, int x, int y, int z) {
-    const int p[3] = {x, y, z};
-    unsigned b = 0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-        if (!E.per[a]) {
-            if (p[a] == 1) b |= 1u << (2 * a);
-            if (p[a] == E.n[a] - 2) b |= 2u << (2 * a);
         }
     return b;
 }
@@ -158,33 +148,98 @@ __device__ __forceinline__ void aa_emit_pair(const Herm& ha, const Herm& hb, typ
     }
 }
 
-// ------------------------------------------------------ one cell per thread
+// ------------------------------------------------------ boundary cells
 
-// The boundary cells cell (x, y, z) at slot c (moments m) serves (bits sv of
-// serve_bits): the neighbour at offset d = (dx, dy, dz) with every nonzero
-// component a served face has inward normal -d.  Returns their rho_out - 1.
-template <class S, bool EQ3, int K>
-__device__ __noinline__ float aa_serve_cells(const CellConsts& C, const Moments& m, typename S::raw* G,
-                                                const EnvDev& E, int x, int y, int z, uint32_t c, unsigned sv) {
-    float drout = 0.0f;
-#pragma unroll 1
-    for (int k = 0; k < 27; ++k) {
-        const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
-        if (k == 13) continue;
-        if ((dx == -1 && !(sv & 1u)) || (dx == 1 && !(sv & 2u))) continue;
-        if ((dy == -1 && !(sv & 4u)) || (dy == 1 && !(sv & 8u))) continue;
-        if ((dz == -1 && !(sv & 16u)) || (dz == 1 && !(sv & 32u))) continue;
-        const int bx = x + dx, by = y + dy, bz = z + dz;
-        const uint32_t bs = (uint32_t)((int)c + dx + (dy + dz * E.n[1]) * E.P);
-        const Herm h = cell_coeffs<S, EQ3>(C, m, bx, by, bz, -dx, -dy, -dz, 0.0f, 0.0f, 0.0f);
-        aa_emit_cell<S, EQ3, K, true>(h, G, E.nslot, bs, pull_offsets(E, bx, by, bz), open_bits(E, bx, by, bz));
-        drout += h.drout;
+// Boundary cell k of environment E, of those the boundary kernel updates:
+// first every cell of the rows on open y/z faces (x fastest, rows with z on
+// a face, then rows with only y on one), then, with xcells, the cells on
+// open x faces of the other rows.  False past the last one.
+__device__ __forceinline__ bool aa_boundary_cell(const EnvDev& E, long long k, bool xcells, int& x, int& y,
+                                                 int& z) {
+    const int nx = E.n[0], ny = E.n[1], nz = E.n[2];
+    const int Lx = E.per[0] ? 0 : 2, Ly = E.per[1] ? 0 : 2, Lz = E.per[2] ? 0 : 2;
+    const long long rows_z = (long long)Lz * ny;
+    const long long rows_y = (long long)Ly * (nz - Lz);
+    const long long nrow_cells = (rows_z + rows_y) * nx;
+    if (k < nrow_cells) {
+        const long long r = k / nx;
+        x = (int)(k - r * nx);
+        if (r < rows_z) {
+            const int zi = (int)(r / ny);
+            z = zi == 0 ? 0 : nz - 1;
+            y = (int)(r - (long long)zi * ny);
+        } else {
+            const long long r2 = r - rows_z;
+            y = (r2 & 1) == 0 ? 0 : ny - 1;
+            z = (int)(r2 >> 1) + (Lz ? 1 : 0);
+        }
+        return true;
     }
-    return drout;
+    k -= nrow_cells;
+    if (!xcells || Lx == 0) return false;
+    const long long ay = ny - Ly;
+    if (k >= ay * (nz - Lz) * 2) return false;
+    const long long r = k >> 1;
+    x = (k & 1) == 0 ? 0 : nx - 1;
+    y = (int)(r % ay) + (Ly ? 1 : 0);
+    z = (int)(r / ay) + (Lz ? 1 : 0);
+    return true;
 }
 
-// Cell b * K1_THREADS + threadIdx.x of environment E (G: its populations)
-// and the boundary cells it serves; returns the sum of rho_out - 1.
+// The number of cells aa_boundary_cell enumerates for E.
+__host__ __device__ inline long long aa_boundary_count(const EnvDev& E, bool xcells) {
+    const int Lx = E.per[0] ? 0 : 2, Ly = E.per[1] ? 0 : 2, Lz = E.per[2] ? 0 : 2;
+    const long long rows = (long long)Lz * E.n[1] + (long long)Ly * (E.n[2] - Lz);
+    return rows * E.n[0] + (xcells ? (long long)Lx * (E.n[1] - Ly) * (E.n[2] - Lz) : 0);
+}
+
+// The boundary cells of a step of phase K (one per thread), before the
+// stream-collide kernel of the step: each takes the moments of its inward
+// neighbour x_f from where x_f's populations arrive (read before the
+// stream-collide kernel overwrites them) and writes its outputs to its own
+// locations, which nothing else reads or writes in the step.  Block b of
+// environment E writes its mass partial after E's stream-collide partials.
+// xcells: the cells on open x faces of the other rows too (one cell per
+// thread in the stream-collide kernel; with two, the pair holding such a
+// cell updates it).
+template <class S, bool EQ3, int K>
+__global__ void __launch_bounds__(K1_THREADS)
+k_aa_boundary(typename S::raw* g, const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames,
+              int n_envs, Pair32* __restrict__ mass_part, int xcells) {
+    __shared__ float wsum[K1_THREADS / 32];
+    __shared__ CellConsts C;
+    const int b = blockIdx.x;
+    const int e = n_envs > 1 ? env_of<&EnvDev::bblock0>(envs, n_envs, b) : 0;
+    const EnvDev& E = envs[e];
+    if (threadIdx.x == 0) C = load_consts(E, frames[e]);
+    __syncthreads();
+    float drout = 0.0f;
+    const long long k = (long long)(b - E.bblock0) * K1_THREADS + threadIdx.x;
+    int x, y, z;
+    if (k < E.nbnd && aa_boundary_cell(E, k, xcells != 0, x, y, z)) {
+        const int sx = inward(E, 0, x), sy = inward(E, 1, y), sz = inward(E, 2, z);
+        const int px = x + sx, py = y + sy, pz = z + sz;
+        const uint32_t s = (uint32_t)x + (uint32_t)E.P * ((uint32_t)y + (uint32_t)E.n[1] * (uint32_t)z);
+        const uint32_t p = (uint32_t)px + (uint32_t)E.P * ((uint32_t)py + (uint32_t)E.n[1] * (uint32_t)pz);
+        typename S::raw* G = g + E.pop_off;
+        const Moments m =
+            layout_moments<S, true, K == 0 ? LAYOUT_AA0 : LAYOUT_AA1>(G, E.nslot, p, pull_offsets(E, px, py, pz));
+        const Herm h = cell_coeffs<S, EQ3>(C, m, x, y, z, sx, sy, sz, 0.0f, 0.0f, 0.0f);
+        aa_emit_cell<S, EQ3, K, true>(h, G, E.nslot, s, pull_offsets(E, x, y, z), open_bits(E, x, y, z));
+        drout = h.drout;
+    }
+    const float t = block_sum_f32(drout, wsum);
+    if (threadIdx.x == 0) {
+        Pair32 q;
+        q.hi = t;
+        mass_part[E.part0 + E.nblocks + (b - E.bblock0)] = q;
+    }
+}
+
+// ---------------------------------------------------- the other cells
+
+// Cell b * K1_THREADS + threadIdx.x of environment E (G: its populations),
+// unless it is a boundary cell (k_aa_boundary's); returns rho_out - 1.
 template <class S, bool EQ3, int K>
 __device__ __forceinline__ float aa_block_cell(typename S::raw* G, const EnvDev& E, const CellConsts& C, int b,
                                                float4* __restrict__ fib, const uint32_t* __restrict__ stamps,
@@ -197,51 +252,35 @@ __device__ __forceinline__ float aa_block_cell(typename S::raw* G, const EnvDev&
     const uint32_t zz = fdiv(row, E.div_ny);
     const int y = (int)(row - zz * (uint32_t)E.n[1]);
     const int z = (int)zz;
-    if (open_bits(E, x, y, z)) return 0.0f;   // updated by the cell it takes its moments from
+    if (open_bits(E, x, y, z)) return 0.0f;
     float fx, fy, fz;
     take_ib_force(E, fib, stamps, stamp, c, fx, fy, fz);
     const PullOffsets o = pull_offsets(E, x, y, z);
     const Moments m = layout_moments<S, true, K == 0 ? LAYOUT_AA0 : LAYOUT_AA1, false>(G, E.nslot, c, o);
     const Herm h = cell_coeffs<S, EQ3>(C, m, x, y, z, 0, 0, 0, fx, fy, fz);
     aa_emit_cell<S, EQ3, K, false>(h, opaque(G), opaque(E.nslot), opaque(c), opaque(o), 0u);
-    float drout = h.drout;
-    const unsigned sv = serve_bits(E, x, y, z);
-    if (sv) drout += aa_serve_cells<S, EQ3, K>(C, m, G, E, x, y, z, c, sv);
-    return drout;
+    return h.drout;
 }
 
-// ------------------------------------------------------ two cells per thread
-
-// The boundary rows that the row of pair (x, x + 1) at (y, z) serves (bits
-// sv & 0x3C of serve_bits): the pair at (y + dy, z + dz) takes the moments
-// sa, sb the pair's own cells took (its cells' inward neighbours lie in this
-// row).  a_open / b_open: x or x + 1 on an open x face.
-template <class S, bool EQ3, int K>
-__device__ __noinline__ float aa_serve_rows(const CellConsts& C, const Moments& sa, const Moments& sb,
-                                               typename S::raw* G, const EnvDev& E, int x, int y, int z, uint32_t c,
-                                               bool a_open, bool b_open, unsigned sv) {
-    float drout = 0.0f;
-#pragma unroll 1
-    for (int k = 0; k < 9; ++k) {
-        const int dy = k % 3 - 1, dz = k / 3 - 1;
-        if (k == 4) continue;
-        if ((dy == -1 && !(sv & 4u)) || (dy == 1 && !(sv & 8u))) continue;
-        if ((dz == -1 && !(sv & 16u)) || (dz == 1 && !(sv & 32u))) continue;
-        const int by = y + dy, bz = z + dz;
-        const uint32_t bs = (uint32_t)((int)c + (dy + dz * E.n[1]) * E.P);
-        const Herm ha = cell_coeffs<S, EQ3>(C, sa, x, by, bz, a_open ? 1 : 0, -dy, -dz, 0.0f, 0.0f, 0.0f);
-        const Herm hb = cell_coeffs<S, EQ3>(C, sb, x + 1, by, bz, b_open ? -1 : 0, -dy, -dz, 0.0f, 0.0f, 0.0f);
-        aa_emit_pair<S, EQ3, K, true>(ha, hb, G, E.nslot, bs, pull_offsets(E, x, by, bz),
-                                      pull_offsets(E, x + 1, by, bz), open_bits(E, x, by, bz),
-                                      open_bits(E, x + 1, by, bz));
-        drout += ha.drout + hb.drout;
-    }
-    return drout;
+__device__ __forceinline__ Moments select_moments(bool first, const Moments& a, const Moments& b) {
+    Moments m;
+    m.dr = first ? a.dr : b.dr;
+    m.jx = first ? a.jx : b.jx;
+    m.jy = first ? a.jy : b.jy;
+    m.jz = first ? a.jz : b.jz;
+    m.sxx = first ? a.sxx : b.sxx;
+    m.syy = first ? a.syy : b.syy;
+    m.szz = first ? a.szz : b.szz;
+    m.sxy = first ? a.sxy : b.sxy;
+    m.sxz = first ? a.sxz : b.sxz;
+    m.syz = first ? a.syz : b.syz;
+    return m;
 }
 
 // Cells x (even) and x + 1 of one row (every row length even, so both are
-// real cells) and the boundary cells they serve.  An open x face puts a
-// boundary cell in the first or last pair of a row, served by its partner.
+// real cells), unless the row lies on an open y/z face (k_aa_boundary's).
+// An open x face puts a boundary cell in the first or last pair of a row;
+// the pair updates it from its partner's moments.
 template <class S, bool EQ3, int K>
 __device__ __forceinline__ float aa_block_pair(typename S::raw* G, const EnvDev& E, const CellConsts& C, int b,
                                                float4* __restrict__ fib, const uint32_t* __restrict__ stamps,
@@ -254,7 +293,7 @@ __device__ __forceinline__ float aa_block_pair(typename S::raw* G, const EnvDev&
     const uint32_t zz = fdiv(row, E.div_ny);
     const int y = (int)(row - zz * (uint32_t)E.n[1]);
     const int z = (int)zz;
-    if (open_bits(E, x, y, z) & 0x3Cu) return 0.0f;   // a boundary row: updated by the row inward
+    if (open_bits(E, x, y, z) & 0x3Cu) return 0.0f;
     const bool a_open = !E.per[0] && x == 0;
     const bool b_open = !E.per[0] && x + 1 == E.n[0] - 1;
     float fa[3] = {0.0f, 0.0f, 0.0f}, fb[3] = {0.0f, 0.0f, 0.0f};
@@ -278,8 +317,9 @@ __device__ __forceinline__ float aa_block_pair(typename S::raw* G, const EnvDev&
         if (!a_open) ma = layout_moments<S, true, LAYOUT_AA1, false>(G, E.nslot, c, oa);
         if (!b_open) mb = layout_moments<S, true, LAYOUT_AA1, false>(G, E.nslot, c + 1, ob);
     }
-    const Moments& sa = a_open ? mb : ma;   // the moments each cell's update takes
-    const Moments& sb = b_open ? ma : mb;
+    // the moments each cell's update takes (an open-face cell its partner's)
+    const Moments sa = select_moments(!a_open, ma, mb);
+    const Moments sb = select_moments(b_open, ma, mb);
     const Herm ha = cell_coeffs<S, EQ3>(C, sa, x, y, z, a_open ? 1 : 0, 0, 0, fa[0], fa[1], fa[2]);
     const Herm hb = cell_coeffs<S, EQ3>(C, sb, x + 1, y, z, b_open ? -1 : 0, 0, 0, fb[0], fb[1], fb[2]);
     if (a_open || b_open)
@@ -288,19 +328,21 @@ __device__ __forceinline__ float aa_block_pair(typename S::raw* G, const EnvDev&
     else
         aa_emit_pair<S, EQ3, K, false>(ha, hb, opaque(G), opaque(E.nslot), opaque(c), opaque(oa), opaque(ob), 0u,
                                        0u);
-    float drout = ha.drout + hb.drout;
-    const unsigned sv = serve_bits(E, x, y, z) & 0x3Cu;
-    if (sv) drout += aa_serve_rows<S, EQ3, K>(C, sa, sb, G, E, x, y, z, c, a_open, b_open, sv);
-    return drout;
+    return ha.drout + hb.drout;
 }
 
 // ------------------------------------------------------------- the kernel
 
-
 // One step in place over every environment: phase K = 0 (even step) or 1
-// (odd step), the blocks and mass partials of the plain kernel.
+// (odd step), after k_aa_boundary of the same phase; the blocks of the
+// plain kernel, mass partials from E.part0.  Compiled for four resident
+// blocks (64 registers): on the 256x128x128 swimmer channel that measured
+// 0.172 / 0.213 ms for even / odd FP32 steps with two cells per thread
+// against 0.186 / 0.205 uncapped (69 and 78 registers, three blocks), and
+// 0.213 / 0.209 against 0.225 / 0.252 with one cell per thread (255 cells
+// per row).
 template <class S, bool EQ3, bool PAIR, int K>
-__global__ void __launch_bounds__(K1_THREADS)
+__global__ void __launch_bounds__(K1_THREADS, 4)
 k_stream_collide_aa(typename S::raw* g, const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames,
                     int n_envs, float4* __restrict__ fib, const uint32_t* __restrict__ stamps,
                     const StepState* __restrict__ st, Pair32* __restrict__ mass_part) {
@@ -320,11 +362,9 @@ k_stream_collide_aa(typename S::raw* g, const EnvDev* __restrict__ envs, const F
     if (threadIdx.x == 0) {
         Pair32 p;
         p.hi = t;
-        mass_part[b] = p;
+        mass_part[E.part0 + (b - E.block0)] = p;
     }
 }
-
-// ------------------------------------------------ state outside the step
 
 // Raw copy of one environment's state between the layout `aa` of G and the
 // two-buffer layout of buf ([27][nslot], the state-buffer format); padding

@@ -163,6 +163,7 @@ struct fg_domain {
     int* red_counters = nullptr;         // per environment: finished blocks of k_reduce
     int red_z = 1;                       // chunks per row of k_reduce
     int total_blocks = 0;                // plain stream-collide grid
+    int total_bblocks = 0;               // in-place layout: boundary-cell kernel grid
     int total_groups = 0;                // staged kernel row groups
     int k1 = K1_PLAIN;                   // stream-collide variant in use (K1_*)
     bool staged = false;                 // a staged variant
@@ -620,14 +621,24 @@ fg_status enqueue_ib(fg_domain* d, const typename S::raw* gin, cudaStream_t s, i
 }
 
 // The in-place stream-collide kernel of phase `phase` (0: even step).
+// (the boundary-cell kernel first: it reads populations the stream-collide
+// kernel overwrites).
 template <class S, bool EQ3, bool PAIR>
 void enqueue_aa_of(fg_domain* d, typename S::raw* g, int phase, cudaStream_t s) {
-    if (phase == 0)
+    const int xcells = PAIR ? 0 : 1;
+    if (phase == 0) {
+        if (d->total_bblocks > 0)
+            k_aa_boundary<S, EQ3, 0><<<d->total_bblocks, K1_THREADS, 0, s>>>(g, d->d_env, d->d_frame, d->n_envs,
+                                                                            d->mass_part, xcells);
         k_stream_collide_aa<S, EQ3, PAIR, 0><<<d->total_blocks, K1_THREADS, 0, s>>>(
             g, d->d_env, d->d_frame, d->n_envs, d->fib, d->stamps, d->d_state, d->mass_part);
-    else
+    } else {
+        if (d->total_bblocks > 0)
+            k_aa_boundary<S, EQ3, 1><<<d->total_bblocks, K1_THREADS, 0, s>>>(g, d->d_env, d->d_frame, d->n_envs,
+                                                                            d->mass_part, xcells);
         k_stream_collide_aa<S, EQ3, PAIR, 1><<<d->total_blocks, K1_THREADS, 0, s>>>(
             g, d->d_env, d->d_frame, d->n_envs, d->fib, d->stamps, d->d_state, d->mass_part);
+    }
 }
 
 template <class S>
@@ -1004,11 +1015,6 @@ fg_status configure_k1(fg_domain* d, int v, bool allocate) {
     // the plain kernel takes two cells per thread when every row length is
     // even: its blocks cover 2 x 256 slots
     d->plain_pair = !d->staged;
-    // in place, FP32 runs one cell per thread: two cells hold two sets of
-    // outputs and their addresses until the scattered stores of an odd step
-    // (108 registers against 64), and the even step's aligned accesses need
-    // no pairing to coalesce
-    if (d->aa && d->esize == 4) d->plain_pair = false;
     for (int e = 0; e < d->n_envs; ++e)
         if (d->env[e].n[0] % 2 != 0) d->plain_pair = false;
     {
@@ -1022,7 +1028,7 @@ fg_status configure_k1(fg_domain* d, int v, bool allocate) {
         }
         d->total_blocks = block0;
     }
-    int group0 = 0;
+    int group0 = 0, bblock0 = 0, part0 = 0;
     for (int e = 0; e < d->n_envs; ++e) {
         EnvDev& E = d->env[e];
         E.rpg = std::max(1, std::min(d->staged_gc / E.P, (int)E.rows));
@@ -1032,8 +1038,20 @@ fg_status configure_k1(fg_domain* d, int v, bool allocate) {
         // one mass partial per row group (staged) or per block (plain)
         E.part0 = d->staged ? E.group0 : E.block0;
         E.nparts = d->staged ? E.ngroups : E.nblocks;
+        // in place: the boundary-cell kernel's blocks, and each environment's
+        // partials of both kernels side by side
+        E.nbnd = d->aa ? (int)aa_boundary_count(E, !d->plain_pair) : 0;
+        E.bblock0 = bblock0;
+        E.nbblocks = (E.nbnd + K1_THREADS - 1) / K1_THREADS;
+        bblock0 += E.nbblocks;
+        if (d->aa) {
+            E.part0 = part0;
+            E.nparts = E.nblocks + E.nbblocks;
+            part0 += E.nparts;
+        }
     }
     d->total_groups = group0;
+    d->total_bblocks = bblock0;
     if (d->staged) {
         d->staged_smem = 2ull * 27 * d->staged_gc * d->esize;
         int dev = 0, sms = 0, per_sm = 0;
@@ -1065,7 +1083,7 @@ fg_status configure_k1(fg_domain* d, int v, bool allocate) {
         d->fused_grid = per_sm * d->n_sms;
     }
     if (!allocate) return FG_OK;
-    const size_t need = (size_t)std::max(d->total_blocks, d->total_groups);
+    const size_t need = (size_t)std::max(d->total_blocks + d->total_bblocks, d->total_groups);
     if (need > d->mass_part_cap) {
         Pair32* p = nullptr;
         fg_status st = dalloc(&p, need);

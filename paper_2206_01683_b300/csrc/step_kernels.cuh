@@ -56,6 +56,8 @@ struct EnvDev {
     int group0, ngroups;      // row groups of the staged kernel
     int rpg;                  // rows per group
     int part0, nparts;        // mass partials written by the kernel in use
+    int bblock0, nbblocks;    // in-place layout: blocks of the boundary-cell kernel
+    int nbnd;                 // in-place layout: cells the boundary-cell kernel updates
     int stamp_off;            // first 32-slot tile stamp
     int mk_begin;             // first marker in the compact marker numbering
     int n_markers;
