@@ -281,3 +281,34 @@ def test_aa_halves_population_memory_and_refuses_two_buffer_calls():
     assert aa.stream_collide_variant() == "plain"
     choice, _ = aa.autotune()
     assert choice == "plain"
+
+
+def test_aa_options_step_io_slip_multi_pass():
+    """The in-place layout under fg_step_io (pinned host markers), three
+    direct-forcing passes and slip forcing, against the plain kernel in the
+    pull layout (the variant bars) over 12 steps of the open swimmer
+    channel."""
+    torch = pytest.importorskip("torch")
+    shape = (96, 48, 48)
+    fish = inputs.fish_for_grid(shape, 24.0, 900)
+    traj = inputs.FrameTrajectory(inputs.seed_for(2), inputs.domain_centre(shape))
+    env = fishlbm.env_desc(shape, 0.52, OPEN_X, (0.02, 0, 0), 1.0, (0.02, 0, 0))
+    for kw in (dict(ib_iters=3, deterministic=True), dict(slip=True, deterministic=True)):
+        doms = _pair_of_domains([env], **kw)
+        X0, U0 = fish.pose(0)
+        normals = np.float32(np.asarray(X0) - np.asarray(X0).mean(axis=0))
+        normals /= np.linalg.norm(normals, axis=1, keepdims=True)
+        for d in doms:
+            d.set_markers(np.float32(X0), np.float32(U0), np.float32(fish.dV), seg=fish.seg, n_seg=5,
+                          ref=fish.joints_rest[0])
+            if kw.get("slip"):
+                d.set_marker_normals(normals)
+        rows = [[], []]
+        for n in range(12):
+            X, U = fish.pose(n)
+            Xh = torch.from_numpy(np.float32(X)).pin_memory()
+            Uh = torch.from_numpy(np.float32(U)).pin_memory()
+            for k, d in enumerate(doms):
+                rows[k].append(d.step_io(Xh, Uh, [fishlbm.frame_from_array(traj.at(n))]))
+        _assert_agree(doms[0].populations(), doms[1].populations(), "f32", kw)
+        assert rel_l2(np.array(rows[1]), np.array(rows[0])) <= 1e-5, kw

@@ -158,3 +158,21 @@ def test_device_sphere_rules():
     with pytest.raises(fishlbm.FgError):
         d.sphere_state()
     assert np.all(np.isfinite(c_before))
+
+
+@pytest.mark.parametrize("variant", ["fused", "overlap"])
+def test_device_sphere_with_other_step_kernels(variant):
+    """The device sphere around the fused step kernel and around the IB
+    beside the cell blocks: the same trajectory bit for bit as around the
+    plain chain (deterministic spread), in a two-environment batch."""
+    envs = [fishlbm.env_desc((L, L, L), 1.0), fishlbm.env_desc((32, 24, 24), 0.6)]
+    states = []
+    for v in ("plain", variant):
+        d = fishlbm.Domain(envs, deterministic=True, variant=v)
+        s = rigid.DeviceFreeSphere(d, R, C0, 1.08, G)
+        X, dV = inputs.fibonacci_sphere(120, 3.0, (16.0, 12.0, 12.0))
+        d.set_markers(np.float32(X), np.tile(np.float32([0.01, 0, 0]), (120, 1)), np.float32(dV), env=1)
+        s.step(30)
+        states.append(np.concatenate(s.state()))
+        assert d.stream_collide_variant() == v
+    assert np.array_equal(states[0], states[1])
