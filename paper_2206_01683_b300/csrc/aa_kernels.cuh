@@ -349,7 +349,9 @@ k_stream_collide_aa(typename S::raw* g, const EnvDev* __restrict__ envs, const F
     __shared__ float wsum[K1_THREADS / 32];
     __shared__ CellConsts C;
     const uint32_t stamp = st->stamp;
-    const int b = blockIdx.x;
+    // odd steps take the blocks from the end of the domain first, where the
+    // even step ended (its outputs are still in L2)
+    const int b = K == 1 ? (int)(gridDim.x - 1u - blockIdx.x) : (int)blockIdx.x;
     const int e = n_envs > 1 ? env_of<&EnvDev::block0>(envs, n_envs, b) : 0;
     const EnvDev& E = envs[e];
     if (threadIdx.x == 0) C = load_consts(E, frames[e]);

@@ -163,6 +163,7 @@ struct fg_domain {
     int* red_counters = nullptr;         // per environment: finished blocks of k_reduce
     int red_z = 1;                       // chunks per row of k_reduce
     int total_blocks = 0;                // plain stream-collide grid
+    int sweep_reverse = 0;               // the step being enqueued sweeps its blocks from the end
     int total_bblocks = 0;               // in-place layout: boundary-cell kernel grid
     int total_groups = 0;                // staged kernel row groups
     int k1 = K1_PLAIN;                   // stream-collide variant in use (K1_*)
@@ -565,12 +566,12 @@ void enqueue_staged(fg_domain* d, const typename S::raw* gin, typename S::raw* g
         k_stream_collide_staged<S, GC, staged_minb<S, GC, true>(), EQ3, true>
             <<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(gin, gout, d->d_env, d->d_frame, d->n_envs,
                                                                 d->total_groups, d->fib, d->stamps, d->d_state,
-                                                                d->mass_part, d->status);
+                                                                d->mass_part, d->status, d->sweep_reverse);
     else
         k_stream_collide_staged<S, GC, staged_minb<S, GC, false>(), EQ3, false>
             <<<d->staged_grid, K1_THREADS, d->staged_smem, s>>>(gin, gout, d->d_env, d->d_frame, d->n_envs,
                                                                 d->total_groups, d->fib, d->stamps, d->d_state,
-                                                                d->mass_part, d->status);
+                                                                d->mass_part, d->status, d->sweep_reverse);
 }
 
 template <class S, bool EQ3>
@@ -581,13 +582,13 @@ void enqueue_k1_order(fg_domain* d, const typename S::raw* gin, typename S::raw*
         enqueue_staged<S, 512, EQ3>(d, gin, gout, s);
     } else {
         if (d->plain_pair)
-            k_stream_collide<S, EQ3, true><<<d->total_blocks, K1_THREADS, 0, s>>>(gin, gout, d->d_env, d->d_frame,
-                                                                              d->n_envs, d->fib, d->stamps,
-                                                                              d->d_state, d->mass_part);
+            k_stream_collide<S, EQ3, true><<<d->total_blocks, K1_THREADS, 0, s>>>(
+                gin, gout, d->d_env, d->d_frame, d->n_envs, d->fib, d->stamps, d->d_state, d->mass_part, nullptr,
+                K1_ALL_BLOCKS, d->sweep_reverse);
         else
-        k_stream_collide<S, EQ3><<<d->total_blocks, K1_THREADS, 0, s>>>(gin, gout, d->d_env, d->d_frame,
-                                                                        d->n_envs, d->fib, d->stamps, d->d_state,
-                                                                        d->mass_part);
+        k_stream_collide<S, EQ3><<<d->total_blocks, K1_THREADS, 0, s>>>(
+            gin, gout, d->d_env, d->d_frame, d->n_envs, d->fib, d->stamps, d->d_state, d->mass_part, nullptr,
+            K1_ALL_BLOCKS, d->sweep_reverse);
     }
 }
 
@@ -670,7 +671,8 @@ fg_status enqueue_plain_of(fg_domain* d, const typename S::raw* gin, typename S:
     cfg.numAttrs = priority != 0 ? 1 : 0;
     CK(cudaLaunchKernelEx(&cfg, k_stream_collide<S, EQ3, PAIR>, gin, gout, (const EnvDev*)d->d_env,
                           (const FrameDev*)d->d_frame, d->n_envs, d->fib, (const uint32_t*)d->stamps,
-                          (const StepState*)d->d_state, d->mass_part, (const uint32_t*)d->blk_flag, which));
+                          (const StepState*)d->d_state, d->mass_part, (const uint32_t*)d->blk_flag, which,
+                          d->sweep_reverse));
     return FG_OK;
 }
 
@@ -874,8 +876,11 @@ fg_status enqueue_step_io(fg_domain* d, const typename S::raw* gin, typename S::
 template <class S>
 fg_status enqueue_step(fg_domain* d, int parity, cudaStream_t s, cudaEvent_t* const* ev) {
     typedef typename S::raw raw;
-    return enqueue_step_io<S>(d, (const raw*)d->pop[parity], (raw*)d->pop[parity ^ 1], s, ev,
-                              d->aa ? parity : -1);
+    d->sweep_reverse = parity;
+    const fg_status st = enqueue_step_io<S>(d, (const raw*)d->pop[parity], (raw*)d->pop[parity ^ 1], s, ev,
+                                            d->aa ? parity : -1);
+    d->sweep_reverse = 0;
+    return st;
 }
 
 // One step with direct launches (and per-kernel events when profiling).

@@ -612,11 +612,14 @@ k_stream_collide(const typename S::raw* __restrict__ gin, typename S::raw* __res
                  const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, int n_envs,
                  float4* __restrict__ fib, const uint32_t* __restrict__ stamps, const StepState* __restrict__ st,
                  Pair32* __restrict__ mass_part, const uint32_t* __restrict__ blk_flag = nullptr,
-                 int which = K1_ALL_BLOCKS) {
+                 int which = K1_ALL_BLOCKS, int reverse = 0) {
     __shared__ float wsum[K1_THREADS / 32];
     __shared__ CellConsts C;   // the block's environment constants, read by every cell
     const uint32_t stamp = st->stamp;
-    const int b = blockIdx.x;
+    // reverse: blocks taken from the end of the domain first (alternate
+    // steps sweep in opposite directions, so a step starts where the last
+    // one ended, on outputs still in L2)
+    const int b = reverse ? (int)(gridDim.x - 1u - blockIdx.x) : (int)blockIdx.x;
     if (which != K1_ALL_BLOCKS && (__ldg(blk_flag + b) == stamp) != (which == K1_FLAGGED_BLOCKS)) return;
     const int e = n_envs > 1 ? env_of<&EnvDev::block0>(envs, n_envs, b) : 0;
     const EnvDev& E = envs[e];
@@ -710,7 +713,7 @@ k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw
                         const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames, int n_envs,
                         int total_groups, float4* __restrict__ fib, const uint32_t* __restrict__ stamps,
                         const StepState* __restrict__ st, Pair32* __restrict__ mass_part,
-                        int* __restrict__ status) {
+                        int* __restrict__ status, int reverse) {
     typedef typename S::raw raw;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     raw* bufs = reinterpret_cast<raw*>(smem_raw);
@@ -727,22 +730,29 @@ k_stream_collide_staged(const typename S::raw* __restrict__ gin, typename S::raw
     __syncthreads();
     allow_dependents();   // as in k_stream_collide
 
-    int g = blockIdx.x;
-    if (g < total_groups) {
-        const int e = n_envs > 1 ? env_of<&EnvDev::group0>(envs, n_envs, g) : 0;
-        issue_group<S, GC>(envs[e], g - envs[e].group0, gin, bufs, &bar[0]);
+    // the block walks groups blockIdx.x, blockIdx.x + gridDim.x, ... of the
+    // sweep; with reverse the sweep takes group total - 1 - j as its j-th
+    // (alternate steps run in opposite directions, as in k_stream_collide)
+    auto group_of = [&](int j) { return reverse ? total_groups - 1 - j : j; };
+    int gs = blockIdx.x;
+    if (gs < total_groups) {
+        const int g0 = group_of(gs);
+        const int e = n_envs > 1 ? env_of<&EnvDev::group0>(envs, n_envs, g0) : 0;
+        issue_group<S, GC>(envs[e], g0 - envs[e].group0, gin, bufs, &bar[0]);
     }
     int cur_e = -1;
     EnvRegs R;
     __shared__ CellConsts C;   // constants of the environment in hand, read by every cell
     __shared__ int abort_wait; // a wait gave up in this group
     if (threadIdx.x == 0) abort_wait = 0;
-    for (int k = 0; g < total_groups; g += gridDim.x, ++k) {
+    for (int k = 0; gs < total_groups; gs += gridDim.x, ++k) {
         const int b = k & 1;
-        const int gn = g + gridDim.x;
+        const int g = group_of(gs);
+        const int gn = gs + gridDim.x;
         if (gn < total_groups) {
-            const int en = n_envs > 1 ? env_of<&EnvDev::group0>(envs, n_envs, gn) : 0;
-            issue_group<S, GC>(envs[en], gn - envs[en].group0, gin, bufs + (size_t)(b ^ 1) * BUF, &bar[b ^ 1]);
+            const int gl = group_of(gn);
+            const int en = n_envs > 1 ? env_of<&EnvDev::group0>(envs, n_envs, gl) : 0;
+            issue_group<S, GC>(envs[en], gl - envs[en].group0, gin, bufs + (size_t)(b ^ 1) * BUF, &bar[b ^ 1]);
         }
         const int e = n_envs > 1 ? env_of<&EnvDev::group0>(envs, n_envs, g) : 0;
         if (e != cur_e) {   // block-uniform
