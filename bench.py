@@ -264,8 +264,7 @@ def storage_form(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W,
     dom.set_markers(Xd[0], Ud[0], dVd, segd, n_seg=5, ref=ref)
 
     def step(n):
-        dom.set_markers(Xd[n], Ud[n], None, None, n_seg=5, ref=ref)
-        dom.step(1, [fr[n]])
+        dom.step_markers(Xd[n], Ud[n], [fr[n]])
 
     hms = _warm(step, range(W))
     ms = _max_over_ranks(_timed(stream, world, step, range(W, W + K), _ahead_ms(hms, K)), world)
@@ -297,8 +296,7 @@ def storage_accuracy(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr
                              storage=st, **vkw)
         dom.set_markers(Xd[0], Ud[0], dVd, segd, n_seg=5, ref=ref)
         for n in range(steps):
-            dom.set_markers(Xd[n], Ud[n], None, None, n_seg=5, ref=ref)
-            dom.step(1, [fr[n]])
+            dom.step_markers(Xd[n], Ud[n], [fr[n]])
         torch.cuda.synchronize()
         us.append(dom.fields()[1])
         dom.close()
@@ -337,8 +335,7 @@ def school_form(W, K, world, peak, vkw):
     dom.set_segment_refs(school.seg_refs)
 
     def step(n):
-        dom.set_markers(Xd[n], Ud[n], None, None, n_seg=school.n_seg, ref=tuple(school.ref))
-        dom.step(1, [fr[n]])
+        dom.step_markers(Xd[n], Ud[n], [fr[n]])
 
     hms = _warm(step, range(W))
     ms = _max_over_ranks(_timed(stream, world, step, range(W, W + K), _ahead_ms(hms, K)), world)
@@ -419,8 +416,7 @@ def large_sphere_form(W, K, world, peak, vkw):
         dom.set_markers(Xd[0], Ud, dVd)
 
         def step(n):
-            dom.set_markers(Xd[n], Ud, None)
-            dom.step(1)
+            dom.step_markers(Xd[n], Ud)
 
         hms = _warm(step, range(W))
         ms = _max_over_ranks(_timed(stream, world, step, range(W, W + K), _ahead_ms(hms, K)), world)
@@ -480,8 +476,7 @@ def batched_form(W, K, world, peak, vkw, n_envs=64):
                             n_seg=5, ref=ref, env=e)
 
         def step(n):
-            dom.set_markers_all(Xall[n], Uall[n])
-            dom.step(1, frames[n])
+            dom.step_markers(Xall[n], Uall[n], frames[n])
 
         hms = _warm(step, range(W))
         ms = _max_over_ranks(_timed(stream, world, step, range(W, W + K), _ahead_ms(hms, K)), world)
@@ -511,8 +506,7 @@ def batched_form(W, K, world, peak, vkw, n_envs=64):
 
     def step_each(n):
         for e, (de, Xe, Ue, ref) in enumerate(doms):
-            de.set_markers(Xe[n], Ue[n], None, None, n_seg=5, ref=ref)
-            de.step(1, [frames[n][e]])
+            de.step_markers(Xe[n], Ue[n], [frames[n][e]])
 
     hms = _warm(step_each, range(W))
     ms_seq = _max_over_ranks(_timed(stream, world, step_each, range(W, W + K), _ahead_ms(hms, K)), world)
@@ -566,8 +560,7 @@ def run_ours(args):
     dom.set_markers(Xd[0], Ud[0], dVd, segd, n_seg=5, ref=ref)
 
     def dev_step(n):
-        dom.set_markers(Xd[n], Ud[n], None, None, n_seg=5, ref=ref)
-        dom.step(1, [fr[n]])
+        dom.step_markers(Xd[n], Ud[n], [fr[n]])
 
     def barrier():
         torch.cuda.synchronize()

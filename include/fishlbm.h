@@ -294,6 +294,25 @@ fg_status fg_step(fg_domain* d, int n_steps, const fg_frame* frames);
  * stream.  Returns FG_ERR_NUMERIC if the step produced NaN/Inf. */
 fg_status fg_get_body_force_torque(fg_domain* d, int env, double* out);
 
+/* New markers and one step in one call, asynchronous: the positions and
+ * velocities of all environments' markers (X and U float [n][3] as in
+ * fg_set_markers_all: n the total of the counts of each environment's last
+ * fg_set_markers, environment after environment; NULL keeps the current
+ * ones), then fg_step(d, 1, frames).  Results equal those of
+ * fg_set_markers_all followed by fg_step, bit for bit.  Where the step's IB
+ * kernel is the cooperative k_ib_step (every kernel_variant but FUSED and
+ * OVERLAP), no sphere is attached, and X, U are device arrays (device_ptrs =
+ * 1) or pinned host arrays with at most two markers per warp of that kernel,
+ * the arrays are not copied before the step: the IB kernel reads them in
+ * its first phase and fills the domain's marker arrays from them (Sec. III-B:
+ * the markers enter the step only through the interpolation stencils), which
+ * saves the copy launch between steps.  Otherwise the call copies them first
+ * as fg_set_markers_all does.  Either way the caller keeps X and U unchanged
+ * until the step has run on the stream (as for any asynchronous copy).  The
+ * same checks and errors as those calls; nothing is launched when a check
+ * fails.  With the autotune option pending, it runs first (and synchronises). */
+fg_status fg_step_markers(fg_domain* d, const float* X, const float* U, int device_ptrs, const fg_frame* frames);
+
 /* One two-way coupled step in one call, for a loop in which the body's next
  * pose depends on the force just computed (Eq. 1): the new positions and
  * velocities of all environments' markers (as fg_set_markers_all: X and U
@@ -304,9 +323,9 @@ fg_status fg_get_body_force_torque(fg_domain* d, int env, double* out);
  * (as fg_get_body_force_torque, environment after environment: (n_seg_e + 1)
  * x 6 FP64 values each, so out holds sum_e (n_seg_e + 1) * 6).  X, U: host
  * or device (device_ptrs); frames, out: host.  The same checks and errors as
- * those calls; nothing is launched when a check fails.  One synchronisation
- * at the end (the step's reduction writes the rows to mapped pinned memory,
- * so no copy is issued). */
+ * those calls; nothing is launched when a check fails.  The markers enter
+ * the step as in fg_step_markers.  One synchronisation at the end (the step's
+ * reduction writes the rows to mapped pinned memory, so no copy is issued). */
 fg_status fg_step_io(fg_domain* d, const float* X, const float* U, int device_ptrs, const fg_frame* frames,
                      double* out);
 

@@ -144,7 +144,9 @@ struct fg_domain {
     std::vector<FrameDev> frame;
     std::vector<MarkerRegion> mk;
     EnvDev* d_env = nullptr;
-    FrameDev* d_frame = nullptr;
+    FrameDev* d_frame = nullptr;         // n_envs frames, then the marker source (d_msrc)
+    MarkerSrc* d_msrc = nullptr;         // in the same allocation as d_frame, so one copy carries both
+    MarkerSrc msrc_next = {nullptr, nullptr, 0};   // posted for the next step (valid: not uploaded yet)
     void* pop[2] = {nullptr, nullptr};   // the in-place layout: both the one buffer
     int cur = 0;                         // buffer parity; the in-place layout's phase
     bool aa = false;                     // in-place (AA) layout
@@ -288,9 +290,38 @@ fg_status upload_env(fg_domain* d) {
     return FG_OK;
 }
 
+// Byte offset of the marker source after the frames (aligned for its pointers).
+size_t msrc_offset(int n_envs) { return (sizeof(FrameDev) * (size_t)n_envs + 15) & ~(size_t)15; }
+
+// The frames; with a marker source posted for the next step, the source in
+// the same copy (pageable: the copy takes the bytes when it is issued).
 fg_status upload_frames(fg_domain* d) {
-    CK(cudaMemcpyAsync(d->d_frame, d->frame.data(), sizeof(FrameDev) * d->n_envs,
-                       cudaMemcpyHostToDevice, d->stream));
+    if (!d->msrc_next.valid) {
+        CK(cudaMemcpyAsync(d->d_frame, d->frame.data(), sizeof(FrameDev) * d->n_envs,
+                           cudaMemcpyHostToDevice, d->stream));
+        return FG_OK;
+    }
+    const size_t off = msrc_offset(d->n_envs);
+    unsigned char buf[sizeof(FrameDev) * 4 + 16 + sizeof(MarkerSrc)];
+    std::vector<unsigned char> big;
+    unsigned char* b = buf;
+    if (off + sizeof(MarkerSrc) > sizeof(buf)) {
+        big.resize(off + sizeof(MarkerSrc));
+        b = big.data();
+    }
+    std::memcpy(b, d->frame.data(), sizeof(FrameDev) * d->n_envs);
+    std::memcpy(b + off, &d->msrc_next, sizeof(MarkerSrc));
+    CK(cudaMemcpyAsync(d->d_frame, b, off + sizeof(MarkerSrc), cudaMemcpyHostToDevice, d->stream));
+    d->msrc_next.valid = 0;
+    return FG_OK;
+}
+
+// A posted marker source alone (a step without a new frame).
+fg_status upload_msrc(fg_domain* d) {
+    if (!d->msrc_next.valid) return FG_OK;
+    const MarkerSrc m = d->msrc_next;
+    CK(cudaMemcpyAsync(d->d_msrc, &m, sizeof(MarkerSrc), cudaMemcpyHostToDevice, d->stream));
+    d->msrc_next.valid = 0;
     return FG_OK;
 }
 
@@ -614,10 +645,11 @@ fg_status enqueue_ib(fg_domain* d, const typename S::raw* gin, cudaStream_t s, i
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     CK(cudaLaunchKernelEx(&cfg, k_ib_step<S>, gin, (const EnvDev*)d->d_env, (const FrameDev*)d->d_frame,
-                          d->n_envs, d->total_markers, (int)d->n_stamps, (const float*)d->X, (const float*)d->U,
+                          d->n_envs, d->total_markers, (int)d->n_stamps, d->X, d->U,
                           (const float*)d->dV, d->Fm, d->fib, d->stamps, (const StepState*)d->d_state,
                           d->ib_nodes, d->ib_bar, d->opt.ib_iters, d->dF, d->fibq,
-                          (const float*)(d->opt.ib_slip ? d->Nrm : nullptr), d->status, layout));
+                          (const float*)(d->opt.ib_slip ? d->Nrm : nullptr), d->status, layout,
+                          (const MarkerSrc*)d->d_msrc));
     return FG_OK;
 }
 
@@ -859,7 +891,7 @@ fg_status enqueue_step_io(fg_domain* d, const typename S::raw* gin, typename S::
                               (const float*)d->dV, (const int*)d->seg, (const float*)d->seg_ref,
                               (const Pair32*)d->mass_part, d->red_partials, d->red_counters, d->n_envs, d->red_z,
                               d->ft, d->mass, d->hist, d->opt.record_history, d->d_state, d->status,
-                              d->rb_ft_all_dev, d->rb_status_dev, d->rb_seq_dev, fused ? 1 : 0));
+                              d->rb_ft_all_dev, d->rb_status_dev, d->rb_seq_dev, fused ? 1 : 0, d->d_msrc));
     }
     if (ev) CK(cudaEventRecord(ev[FG_K_REDUCE][1], s));
     if (n_sph > 0) {
@@ -1258,7 +1290,8 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         return st;                                   \
     }
     DA(d->d_env, n_envs);
-    DA(d->d_frame, n_envs);
+    DA(d->d_frame, n_envs + 1);   // room for the marker source after the frames (msrc_offset)
+    d->d_msrc = reinterpret_cast<MarkerSrc*>(reinterpret_cast<unsigned char*>(d->d_frame) + msrc_offset(n_envs));
     {
         char *p0 = nullptr, *p1 = nullptr;
         DA(p0, d->pop_elems * d->esize);
@@ -1332,6 +1365,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         (ce = cudaMemsetAsync(d->mass, 0, sizeof(Pair32) * n_envs, d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->status, 0, sizeof(int), d->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(d->ib_bar, 0, 2 * sizeof(unsigned), d->stream)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(d->d_msrc, 0, sizeof(MarkerSrc), d->stream)) != cudaSuccess ||
         (d->fibq && (ce = cudaMemsetAsync(d->fibq, 0, sizeof(unsigned long long) * 3ull * slot_off,
                                           d->stream)) != cudaSuccess) ||
         (ce = cudaMemsetAsync(d->red_counters, 0, sizeof(int) * n_envs * RED_ROWS, d->stream)) != cudaSuccess ||
@@ -1777,8 +1811,10 @@ fg_status fg_step(fg_domain* d, int n_steps, const fg_frame* frames) {
                     return fail(FG_ERR_INVALID, "frame not finite");
         }
         for (int e = 0; e < d->n_envs; ++e) set_env_frame(d, e, frames[e]);
-        fg_status st = upload_frames(d);
+        fg_status st = upload_frames(d);   // with a posted marker source, in the same copy
         if (st != FG_OK) return st;
+    } else if (fg_status st = upload_msrc(d); st != FG_OK) {
+        return st;
     }
     if (d->opt.ib_slip)
         for (int e = 0; e < d->n_envs; ++e)
@@ -1865,6 +1901,68 @@ static fg_status status_to_error(fg_domain* d, int s) {
     return FG_OK;
 }
 
+// The markers of every environment for the next step, in the compact order
+// of fg_set_markers_all.  Where that step's IB kernel is k_ib_step (every
+// variant but the fused and overlap ones), the arrays are device arrays or
+// pinned host arrays read once (each marker the first of its half-warp),
+// and no sphere is attached, the arrays are posted to the step (MarkerSrc):
+// its IB kernel reads them and fills the domain's marker arrays on the way,
+// with no copy launch before the step.  Otherwise fg_set_markers_all copies
+// them now.  The caller keeps the arrays unchanged until the step has run.
+static fg_status step_markers_in(fg_domain* d, const float* X, const float* U, int device_ptrs) {
+    if (d->autotune_pending) {   // the variant is settled before the markers are posted
+        fg_status st = fg_autotune(d, nullptr, nullptr);
+        if (st != FG_OK) return st;
+    }
+    const int n = d->total_markers;
+    const int ib_warps = d->ib_per_sm * d->n_sms * (IB_THREADS / 32);
+    bool post = n > 0 && X && U && d->sph_host.empty() && d->k1 != K1_FUSED && d->k1 != K1_OVERLAP;
+    const float* xs = X;
+    const float* us = U;
+    if (post && !device_ptrs) {
+        xs = mapped_device_ptr(X);
+        us = xs ? mapped_device_ptr(U) : nullptr;
+        post = xs && us && n <= 2 * ib_warps;
+        if (post) {   // the checks fg_set_markers_all makes of host arrays
+            size_t k = 0;
+            for (int e = 0; e < d->n_envs; ++e) {
+                const int m = d->mk[e].n;
+                if (!markers_valid(d->env[e], m, X + 3 * k, U + 3 * k))
+                    return fail(FG_ERR_INVALID, first_marker_problem(d->env[e], m, X + 3 * k, U + 3 * k));
+                k += m;
+            }
+        }
+    }
+    if (!post) return fg_set_markers_all(d, n, X, U, device_ptrs);
+    d->msrc_next.X = xs;
+    d->msrc_next.U = us;
+    d->msrc_next.valid = 1;
+    return FG_OK;
+}
+
+fg_status fg_step_markers(fg_domain* d, const float* X, const float* U, int device_ptrs, const fg_frame* frames) {
+    NvtxRange nvtx_range("fg_step_markers");
+    if (!d) return fail(FG_ERR_INVALID, "null domain");
+    if ((X == nullptr) != (U == nullptr)) return fail(FG_ERR_INVALID, "X and U must both be given or both NULL");
+    // fg_step's own checks first, so that a failing step posts and copies nothing
+    if (d->poisoned) return fail(FG_ERR_STATE, "domain poisoned by a numeric fault; call fg_init_fields");
+    if (frames)
+        for (int e = 0; e < d->n_envs; ++e)
+            for (int a = 0; a < 3; ++a)
+                if (!std::isfinite(frames[e].acc[a]) || !std::isfinite(frames[e].omega[a]) ||
+                    !std::isfinite(frames[e].domega[a]) || !std::isfinite(frames[e].origin[a]))
+                    return fail(FG_ERR_INVALID, "frame not finite");
+    if (d->opt.ib_slip)
+        for (int e = 0; e < d->n_envs; ++e)
+            if (d->mk[e].n > 0 && !d->mk[e].has_normals)
+                return fail(FG_ERR_STATE, "slip forcing needs the markers' normals (fg_set_marker_normals)");
+    fg_status st = FG_OK;
+    if (X && (st = step_markers_in(d, X, U, device_ptrs)) != FG_OK) return st;
+    st = fg_step(d, 1, frames);
+    d->msrc_next.valid = 0;   // (uploaded by the step; dropped if the step failed before)
+    return st;
+}
+
 fg_status fg_step_io(fg_domain* d, const float* X, const float* U, int device_ptrs, const fg_frame* frames,
                      double* out) {
     NvtxRange nvtx_range("fg_step_io");
@@ -1884,8 +1982,10 @@ fg_status fg_step_io(fg_domain* d, const float* X, const float* U, int device_pt
             if (d->mk[e].n > 0 && !d->mk[e].has_normals)
                 return fail(FG_ERR_STATE, "slip forcing needs the markers' normals (fg_set_marker_normals)");
     fg_status st = FG_OK;
-    if (X && (st = fg_set_markers_all(d, d->total_markers, X, U, device_ptrs)) != FG_OK) return st;
-    if ((st = fg_step(d, 1, frames)) != FG_OK) return st;
+    if (X && (st = step_markers_in(d, X, U, device_ptrs)) != FG_OK) return st;
+    st = fg_step(d, 1, frames);
+    d->msrc_next.valid = 0;
+    if (st != FG_OK) return st;
     // The step's k_reduce writes the rows, the status word and then the step
     // number to mapped pinned memory: no copy to issue.  The host polls the
     // step number (waking from a stream synchronisation takes longer than the

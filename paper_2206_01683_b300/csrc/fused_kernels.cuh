@@ -145,7 +145,7 @@ __device__ __forceinline__ void fused_marker_item(const IbArgs& a, int kind, int
         r.e = e;
         r.slot = slot;
         r.S.ok = false;
-        if (here) r = load_marker_slot(E, e, slot, a.X, a.U, a.dV);
+        if (here) r = load_marker_slot<false>(E, e, slot, a.X, a.U, a.dV);
         const bool active = here && r.S.ok;
         ColumnNodes cn;
         if (active) cn = column_nodes(E, r, h);

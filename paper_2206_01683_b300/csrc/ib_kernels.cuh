@@ -24,6 +24,7 @@
 #pragma once
 
 #include "step_kernels.cuh"
+#include "marker_src.cuh"
 
 namespace fl {
 
@@ -138,12 +139,12 @@ struct Stencil {
     bool ok;
 };
 
-__device__ __forceinline__ Stencil marker_stencil(const EnvDev& E, const float* __restrict__ X, int slot) {
+__device__ __forceinline__ Stencil stencil_at(const EnvDev& E, const float (&xm)[3]) {
     Stencil st;
     st.ok = true;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float x = X[3 * slot + a];
+        const float x = xm[a];
         const float N = (float)E.n[a];
         float w = x;
         if (!(fabsf(x) <= 1.0e6f)) st.ok = false;  // also rejects NaN
@@ -158,6 +159,11 @@ __device__ __forceinline__ Stencil marker_stencil(const EnvDev& E, const float* 
         st.base[a] = st.ok ? (int)floorf(w) - 1 : 0;
     }
     return st;
+}
+
+__device__ __forceinline__ Stencil marker_stencil(const EnvDev& E, const float* __restrict__ X, int slot) {
+    const float x[3] = {X[3 * slot], X[3 * slot + 1], X[3 * slot + 2]};
+    return stencil_at(E, x);
 }
 
 constexpr uint32_t GRID_WAIT_LIMIT = 1u << 22;  // barrier polls before giving up
@@ -281,23 +287,68 @@ struct MarkerRef {
     float U[3], dV;
 };
 
-__device__ __forceinline__ MarkerRef load_marker_slot(const EnvDev& E, int e, int slot, const float* __restrict__ X,
-                                                      const float* __restrict__ U, const float* __restrict__ dV) {
+__device__ __forceinline__ MarkerRef marker_ref(const EnvDev& E, int e, int slot, const float (&x)[3],
+                                                const float (&u)[3], const float* __restrict__ dV) {
     MarkerRef r;
     r.e = e;
     r.slot = slot;
-    r.S = marker_stencil(E, X, slot);
-    r.U[0] = U[3 * slot]; r.U[1] = U[3 * slot + 1]; r.U[2] = U[3 * slot + 2];
+    r.S = stencil_at(E, x);
+    r.U[0] = u[0]; r.U[1] = u[1]; r.U[2] = u[2];
     r.dV = dV[slot];
     return r;
 }
 
+// COHERENT reads X and U through L2 (ld.global.cg): in the step whose IB
+// kernel copies the markers into those arrays (a posted MarkerSrc), blocks
+// read there what other blocks wrote before a grid barrier.
+template <bool COHERENT = false>
+__device__ __forceinline__ MarkerRef load_marker_slot(const EnvDev& E, int e, int slot, const float* __restrict__ X,
+                                                      const float* __restrict__ U, const float* __restrict__ dV) {
+    float x[3], u[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        x[a] = COHERENT ? __ldcg(X + 3 * slot + a) : X[3 * slot + a];
+        u[a] = COHERENT ? __ldcg(U + 3 * slot + a) : U[3 * slot + a];
+    }
+    return marker_ref(E, e, slot, x, u, dV);
+}
+
+__device__ __forceinline__ int marker_env(const EnvDev* __restrict__ envs, int n_envs, int m) {
+    return n_envs > 1 ? env_of<&EnvDev::mk_begin>(envs, n_envs, m) : 0;
+}
+
+template <bool COHERENT = false>
 __device__ __forceinline__ MarkerRef load_marker(const EnvDev* __restrict__ envs, int n_envs, int m,
                                                  const float* __restrict__ X, const float* __restrict__ U,
                                                  const float* __restrict__ dV) {
-    const int e = n_envs > 1 ? env_of<&EnvDev::mk_begin>(envs, n_envs, m) : 0;
+    const int e = marker_env(envs, n_envs, m);
     const EnvDev& E = envs[e];
-    return load_marker_slot(E, e, E.marker_off + (m - E.mk_begin), X, U, dV);
+    return load_marker_slot<COHERENT>(E, e, E.marker_off + (m - E.mk_begin), X, U, dV);
+}
+
+// Marker m of a posted MarkerSrc (compact numbering), for a half-warp: lanes
+// h = 0..5 each read one value (X then U) and the half-warp shares them, so
+// a source in pinned host memory is read once, in a few requests.  Called by
+// all 32 lanes of the warp (`here` false for a half without a marker: its
+// values are 0).  The lane's own value is returned, for the copy into the
+// domain's arrays (marker_store).
+__device__ __forceinline__ float marker_fetch(const MarkerSrc& ms, int m, bool here, int lane, float (&x)[3],
+                                              float (&u)[3]) {
+    const int h = lane & 15;
+    float v = 0.0f;
+    if (here && h < 6) v = h < 3 ? ms.X[3 * m + h] : ms.U[3 * m + h - 3];
+    const int b = lane & 16;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        x[a] = __shfl_sync(0xffffffffu, v, b + a);
+        u[a] = __shfl_sync(0xffffffffu, v, b + 3 + a);
+    }
+    return v;
+}
+
+__device__ __forceinline__ void marker_store(float* X, float* U, int slot, int h, float v) {
+    if (h < 3) X[3 * slot + h] = v;
+    else if (h < 6) U[3 * slot + h - 3] = v;
 }
 
 // Stencil nodes of half-lane h for one marker: the slots of its column's
@@ -423,19 +474,27 @@ template <class S>
 __global__ void __launch_bounds__(IB_THREADS, 4)
 k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs_g,
           const FrameDev* __restrict__ frames_g, int n_envs, int total_markers, int n_stamps,
-          const float* __restrict__ X, const float* __restrict__ U, const float* __restrict__ dV,
+          float* X, float* U, const float* __restrict__ dV,
           float* __restrict__ Fm, float4* fib, uint32_t* stamps, const StepState* __restrict__ st,
           float4* nodes, unsigned* bar, int ib_iters, float* dF, unsigned long long* fibq,
-          const float* __restrict__ Nrm, int* status, int layout) {
+          const float* __restrict__ Nrm, int* status, int layout, const MarkerSrc* __restrict__ msrc) {
     // a single environment's table and frame in shared memory, read by every
-    // marker and node of the launch
+    // marker and node of the launch; the posted marker source, if any
     __shared__ EnvDev sE;
     __shared__ FrameDev sF;
-    if (n_envs == 1 && threadIdx.x == 0) {
-        sE = envs_g[0];
-        sF = frames_g[0];
+    __shared__ MarkerSrc sM;
+    if (threadIdx.x == 0) {
+        if (n_envs == 1) {
+            sE = envs_g[0];
+            sF = frames_g[0];
+        }
+        sM = *msrc;
     }
     __syncthreads();
+    // posted: the step's markers come from the caller's arrays; the mark
+    // phase copies them into X and U, which later phases read through L2
+    const MarkerSrc ms = sM;
+    const bool posted = ms.valid != 0;
     const EnvDev* envs = n_envs == 1 ? &sE : envs_g;
     const FrameDev* frames = n_envs == 1 ? &sF : frames_g;
     const int lane = threadIdx.x & 31, h = lane & 15;
@@ -455,19 +514,35 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
         if (fibq) spread_force_fixed(E, r, cn, F, fibq, status);
         else spread_force(E, r, cn, F, fib);
     };
+    // marker m of a later phase (after the mark phase's barrier)
+    auto reload = [&](int m) -> MarkerRef {
+        return posted ? load_marker<true>(envs, n_envs, m, X, U, dV) : load_marker<false>(envs, n_envs, m, X, U, dV);
+    };
     const int m0 = 2 * gw + (lane >> 4);
-    // mark
+    // mark (half-warps walk markers 2 gw + 2 nw k + (lane >> 4); both halves
+    // of a warp iterate alike, for the posted source's shuffles)
     MarkerRef first;
     first.S.ok = false;
-    if (m0 < total_markers) {
-        first = load_marker(envs, n_envs, m0, X, U, dV);
-        if (first.S.ok) ib_mark(envs[first.e], first.S, h, stamp, stamps);
-    }
-    for (int m = m0 + 2 * nw; m < total_markers; m += 2 * nw) {
-        const int e = n_envs > 1 ? env_of<&EnvDev::mk_begin>(envs, n_envs, m) : 0;
-        const EnvDev& E = envs[e];
-        const Stencil Sm = marker_stencil(E, X, E.marker_off + (m - E.mk_begin));
-        if (Sm.ok) ib_mark(E, Sm, h, stamp, stamps);   // invalid markers are reported by the force phase
+    for (int mb = 2 * gw; mb < total_markers; mb += 2 * nw) {
+        const int m = mb + (lane >> 4);
+        const bool here = m < total_markers;
+        MarkerRef r;
+        r.S.ok = false;
+        if (posted) {
+            float x[3], u[3];
+            const float v = marker_fetch(ms, m, here, lane, x, u);
+            if (here) {
+                const int e = marker_env(envs, n_envs, m);
+                const EnvDev& E = envs[e];
+                const int slot = E.marker_off + (m - E.mk_begin);
+                marker_store(X, U, slot, h, v);
+                r = marker_ref(E, e, slot, x, u, dV);
+            }
+        } else if (here) {
+            r = load_marker<false>(envs, n_envs, m, X, U, dV);
+        }
+        if (here && r.S.ok) ib_mark(envs[r.e], r.S, h, stamp, stamps);   // invalid markers: the force phase reports them
+        if (mb == 2 * gw) first = r;
     }
     if (!barrier()) return;
     // nodes: lane k of warp gw reads the stamp of tile gw + nw (k + 32 j)
@@ -491,7 +566,7 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
         r.e = 0;
         r.slot = 0;
         r.S.ok = false;
-        if (here) r = mb == 2 * gw ? first : load_marker(envs, n_envs, m, X, U, dV);
+        if (here) r = mb == 2 * gw ? first : reload(m);
         if (here && !r.S.ok && h == 0) {
             Fm[3 * r.slot] = 0.f; Fm[3 * r.slot + 1] = 0.f; Fm[3 * r.slot + 2] = 0.f;
             atomicOr(status, ST_BAD_MARKER);
@@ -518,7 +593,7 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
             r.e = 0;
             r.slot = 0;
             r.S.ok = false;
-            if (here) r = mb == 2 * gw ? first : load_marker(envs, n_envs, m, X, U, dV);
+            if (here) r = mb == 2 * gw ? first : reload(m);
             const bool active = here && r.S.ok;
             const EnvDev& E = envs[r.e];
             ColumnNodes cn;
@@ -533,7 +608,7 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
         }
         if (!barrier()) return;
         for (int m = m0; m < total_markers; m += 2 * nw) {
-            const MarkerRef r = m == m0 ? first : load_marker(envs, n_envs, m, X, U, dV);
+            const MarkerRef r = m == m0 ? first : reload(m);
             if (!r.S.ok) continue;
             const EnvDev& E = envs[r.e];
             const float* d = dF + 3 * r.slot;

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "step_kernels.cuh"
+#include "marker_src.cuh"
 
 namespace fl {
 
@@ -118,7 +119,8 @@ __device__ __forceinline__ void block_pair_sums(Pair32 (&acc)[6], int ncomp, Pai
 // step reads them back with no copy (either may be NULL).  markers_pre = 1:
 // the force/torque chunk sums are already in `partials` (the fused step
 // kernel wrote them, with the same chunks and order); the grid is then
-// (n_envs, 1, chunks) and only the mass is summed before the combine.
+// (n_envs, 1, chunks) and only the mass is summed before the combine.  The
+// last block also clears the step's posted marker source (msrc, may be NULL).
 static __global__ void __launch_bounds__(RED_THREADS)
 k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const float* __restrict__ Fm,
          const float* __restrict__ dV, const int* __restrict__ seg, const float* __restrict__ seg_ref,
@@ -126,7 +128,8 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
          Pair32* __restrict__ partials, int* __restrict__ counters, int n_envs, int zmax,
          Pair32* __restrict__ ft, Pair32* __restrict__ mass, Pair32* __restrict__ hist, int hist_cap,
          StepState* __restrict__ st, int* __restrict__ status, Pair32* __restrict__ host_ft,
-         int* __restrict__ host_status, long long* __restrict__ host_seq, int markers_pre) {
+         int* __restrict__ host_status, long long* __restrict__ host_seq, int markers_pre,
+         MarkerSrc* __restrict__ msrc) {
     constexpr int NW = RED_THREADS / 32;
     __shared__ Pair32 sh[NW][6];
     __shared__ int is_last;
@@ -245,6 +248,9 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
     }
     st->step += 1;
     st->stamp = st->stamp == 0xffffffffu ? 1u : st->stamp + 1u;
+    // a marker source posted for this step has been read (by the IB kernel,
+    // which completed before the stream-collide kernel began)
+    if (msrc) msrc->valid = 0;
     // the step's status word (every kernel of the step, and every
     // environment's combine, has set its bits by now) to the host-mapped copy
     if (host_status) *host_status = atomicOr(status, 0);

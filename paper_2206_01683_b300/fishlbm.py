@@ -77,6 +77,7 @@ SIGNATURES = {
     "fg_step": (_I, [_V, _I, _P(fg_frame)]),
     "fg_get_body_force_torque": (_I, [_V, _I, _P(_D)]),
     "fg_step_io": (_I, [_V, _V, _V, _I, _P(fg_frame), _V]),
+    "fg_step_markers": (_I, [_V, _V, _V, _I, _P(fg_frame)]),
     "fg_destroy": (None, [_V]),
     "fg_last_error": (ctypes.c_char_p, []),
     "fg_lattice": (_I, [_P(_I), _P(_D)]),
@@ -386,12 +387,16 @@ class Domain:
     def get_body_force_torque(self, env=0):
         return fg_get_body_force_torque(self.h, env, self.nseg[env])
 
-    def step_io(self, X=None, U=None, frames=None):
-        """One coupled step in one call (fg_step_io): new positions and
-        velocities of all environments' markers (numpy, torch CPU/pinned or
-        CUDA tensors, environment after environment; None keeps them), one
-        step, and the force/torque rows read back.  Returns the (n_seg + 1, 6)
-        rows of a single environment, else a list of them."""
+    def step_markers(self, X=None, U=None, frames=None):
+        """New markers and one step in one asynchronous call
+        (fg_step_markers): positions and velocities of all environments'
+        markers as for step_io (None keeps them), then one step."""
+        pX, pU, dev, fr = self._io_args(X, U, frames)
+        _check(lib().fg_step_markers(self.h, pX, pU, 1 if dev else 0, fr))
+
+    def _io_args(self, X, U, frames):
+        """Marker pointers (kept alive until the next call), device flag and
+        frames argument of fg_step_io / fg_step_markers."""
         if (X is None) != (U is None):
             raise ValueError("X and U must both be given or both be None")
         pX = pU = None
@@ -415,6 +420,15 @@ class Domain:
             else:
                 fr = (fg_frame * len(frames))(*[f if isinstance(f, fg_frame) else frame_from_array(f)
                                                  for f in frames])
+        return pX, pU, dev, fr
+
+    def step_io(self, X=None, U=None, frames=None):
+        """One coupled step in one call (fg_step_io): new positions and
+        velocities of all environments' markers (numpy, torch CPU/pinned or
+        CUDA tensors, environment after environment; None keeps them), one
+        step, and the force/torque rows read back.  Returns the (n_seg + 1, 6)
+        rows of a single environment, else a list of them."""
+        pX, pU, dev, fr = self._io_args(X, U, frames)
         rows = [self.nseg[e] + 1 for e in range(len(self.nseg))]
         total = sum(rows)
         if getattr(self, "_io_out", None) is None or self._io_out.shape[0] != total:
