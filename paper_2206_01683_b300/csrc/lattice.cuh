@@ -31,6 +31,9 @@ __host__ __device__ constexpr float store_scale(int i) { return (float)(4 << (2 
 
 // Population storage.  load/store take the velocity index so that reduced
 // formats can apply their per-velocity scale; FP32 stores f_i - w_i as is.
+// widen(v) is the stored value as a float without that scale (s_i g_i for
+// the reduced formats, SCALED), for moment sums that apply the scales
+// themselves (accumulate_stored).
 // load2_rw reads two neighbouring slots (the first aligned to twice the
 // element size) with one ordinary, coherent load, for a kernel that also
 // writes the array it reads.
@@ -43,6 +46,8 @@ __host__ __device__ constexpr float store_scale(int i) { return (float)(4 << (2 
 struct StoreF32 {
     typedef float raw;
     static constexpr float POLY = 1.0f;
+    static constexpr bool SCALED = false;
+    static __device__ __forceinline__ float widen(raw v) { return v; }
     static __device__ __forceinline__ void emit(raw* p, float v, int i) { *p = wf(i) * v; }
     static __device__ __forceinline__ void emit2(raw* p, float a, float b, int i) {
         *reinterpret_cast<float2*>(p) = make_float2(wf(i) * a, wf(i) * b);
@@ -59,6 +64,8 @@ struct StoreF32 {
 struct StoreF16 {
     typedef __half raw;
     static constexpr float POLY = 32.0f / 27.0f;
+    static constexpr bool SCALED = true;
+    static __device__ __forceinline__ float widen(raw v) { return __half2float(v); }   // s_i g_i
     static __device__ __forceinline__ void emit(raw* p, float v, int) { *p = __float2half_rn(v); }
     static __device__ __forceinline__ void emit2(raw* p, float a, float b, int) {
         *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
@@ -80,6 +87,8 @@ struct StoreF16 {
 struct StoreBF16 {
     typedef __nv_bfloat16 raw;
     static constexpr float POLY = 32.0f / 27.0f;
+    static constexpr bool SCALED = true;
+    static __device__ __forceinline__ float widen(raw v) { return __bfloat162float(v); }   // s_i g_i
     static __device__ __forceinline__ void emit(raw* p, float v, int) { *p = __float2bfloat16_rn(v); }
     static __device__ __forceinline__ void emit2(raw* p, float a, float b, int) {
         *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);

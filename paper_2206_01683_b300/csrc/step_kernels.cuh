@@ -193,6 +193,64 @@ __device__ __forceinline__ void accumulate(Moments& m, const float (&g)[Q]) {
     }
 }
 
+// The moments from the 27 values as stored and widened to float (S::widen):
+// FP32 stores g_i itself; the reduced formats store h_i = s_i g_i with
+// s_i = 4^(1 + |c_i|^2).  Along x-line l (cy, cz fixed, q = |cy| + |cz|) the
+// cx = +-1 values share the scale sig = 4^(2 + q) and the cx = 0 value has
+// sig / 4, so e' = h+ + h-, d' = h+ - h- and s' = 4 h0 + e' (one fused
+// multiply-add) are sig times the line sums of accumulate, exactly (powers
+// of two commute with rounding).  Each of accumulate's later additions of a
+// line quantity becomes a fused multiply-add with the exact product
+// (line quantity) x 1/sig, so every sum rounds as in accumulate and the
+// moments are bit-identical to accumulate of the decoded values, without
+// decoding each value (27 multiplies).
+template <class S, bool SECOND>
+__device__ __forceinline__ void accumulate_stored(Moments& m, const float (&h)[Q]) {
+    if constexpr (!S::SCALED) {
+        accumulate<SECOND>(m, h);
+    } else {
+        // 1/sig of line l = (cy+1) + 3 (cz+1)
+        auto inv_sig = [](int l) -> float {
+            const int q = (l % 3 != 1 ? 1 : 0) + (l / 3 != 1 ? 1 : 0);
+            return q == 0 ? 1.0f / 16.0f : (q == 1 ? 1.0f / 64.0f : 1.0f / 256.0f);
+        };
+        float sl[9], dl[9], el[9];
+#pragma unroll
+        for (int l = 0; l < 9; ++l) {
+            el[l] = h[3 * l + 2] + h[3 * l];
+            dl[l] = h[3 * l + 2] - h[3 * l];
+            sl[l] = __fmaf_rn(h[3 * l + 1], 4.0f, el[l]);
+        }
+        float dr = 0.f, jx = 0.f, sxx = 0.f;
+#pragma unroll
+        for (int l = 0; l < 9; ++l) {
+            dr = __fmaf_rn(sl[l], inv_sig(l), dr);
+            jx = __fmaf_rn(dl[l], inv_sig(l), jx);
+            if (SECOND) sxx = __fmaf_rn(el[l], inv_sig(l), sxx);
+        }
+        float jy = 0.f, syy = 0.f, jz = 0.f, szz = 0.f, sxy = 0.f, sxz = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float wy = inv_sig(3 * k), wz = inv_sig(k);   // lines 3k, 2 + 3k and k, k + 6 pair up
+            const float yp = sl[2 + 3 * k], ym = sl[0 + 3 * k];
+            const float zp = sl[k + 6], zm = sl[k];
+            jy = __fmaf_rn(yp - ym, wy, jy);
+            jz = __fmaf_rn(zp - zm, wz, jz);
+            if (SECOND) {
+                syy = __fmaf_rn(yp + ym, wy, syy);
+                szz = __fmaf_rn(zp + zm, wz, szz);
+                sxy = __fmaf_rn(dl[2 + 3 * k] - dl[0 + 3 * k], wy, sxy);
+                sxz = __fmaf_rn(dl[k + 6] - dl[k], wz, sxz);
+            }
+        }
+        m.dr += dr; m.jx += jx; m.jy += jy; m.jz += jz;
+        if (SECOND) {
+            const float syz = ((sl[8] - sl[2]) - (sl[6] - sl[0])) * (1.0f / 256.0f);
+            m.sxx += sxx; m.syy += syy; m.szz += szz; m.sxy += sxy; m.sxz += sxz; m.syz += syz;
+        }
+    }
+}
+
 // Moments at source slot p by direct (L2-cached) global loads.
 template <class S, bool SECOND>
 __device__ __forceinline__ Moments pull_moments(const typename S::raw* __restrict__ G, uint32_t nslot,
@@ -202,9 +260,9 @@ __device__ __forceinline__ Moments pull_moments(const typename S::raw* __restric
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int idx = (int)p + pull_off(o, i);
-        g[i] = FG_IN_RANGE(DBG_PULL, idx, nslot) ? S::load(G + (size_t)i * nslot + (uint32_t)idx, i) : 0.0f;
+        g[i] = FG_IN_RANGE(DBG_PULL, idx, nslot) ? S::widen(__ldg(G + (size_t)i * nslot + (uint32_t)idx)) : 0.0f;
     }
-    accumulate<SECOND>(m, g);
+    accumulate_stored<S, SECOND>(m, g);
     return m;
 }
 
@@ -230,9 +288,9 @@ __device__ __forceinline__ Moments layout_moments(const typename S::raw* G, uint
         const int idx = LAYOUT == LAYOUT_AA0 ? (int)p : (int)p + pull_off(o, i);
         const int dir = LAYOUT == LAYOUT_AA1 ? Q - 1 - i : i;
         const typename S::raw* q = G + (size_t)dir * nslot + (uint32_t)idx;
-        g[i] = FG_IN_RANGE(DBG_PULL, idx, nslot) ? (NC ? S::load(q, i) : S::decode(*q, i)) : 0.0f;
+        g[i] = FG_IN_RANGE(DBG_PULL, idx, nslot) ? S::widen(NC ? __ldg(q) : *q) : 0.0f;
     }
-    accumulate<SECOND>(m, g);
+    accumulate_stored<S, SECOND>(m, g);
     return m;
 }
 
@@ -688,10 +746,10 @@ __device__ __forceinline__ Moments staged_moments(const typename S::raw* rb, int
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int xi = cx(i) == 1 ? xm : (cx(i) == -1 ? xp : xs);
-        gv[i] = FG_IN_RANGE(DBG_SMEM, r * P + xi, GC) ? S::decode(rb[i * GC + xi], i) : 0.0f;
+        gv[i] = FG_IN_RANGE(DBG_SMEM, r * P + xi, GC) ? S::widen(rb[i * GC + xi]) : 0.0f;
     }
     Moments m = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    accumulate<true>(m, gv);
+    accumulate_stored<S, true>(m, gv);
     return m;
 }
 
