@@ -37,14 +37,14 @@ OPEN_X = (1, 2, 3, 3, 3, 3)   # inlet, outflow, free-slip walls
 
 # DRAM traffic of the stream-collide kernel per cell update from an ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum divided by the cells of
-# the launch), keyed by the kernel source it was taken on and the variant in
-# use, and valid only for those.
+# the launch; the mean of two launches, one of each sweep direction), keyed by
+# the kernel source it was taken on, the variant in use and the storage, and
+# valid only for those.  Swimmer channel, 4,194,304 cells.
 NCU_TRAFFIC = {
-    # k_stream_collide<StoreF32, false, true> (two cells per thread, odd steps
-    # sweeping from the end of the domain), swimmer channel: 440.54 MB read +
-    # 401.66 MB written per launch (mean of two launches, one of each sweep
-    # direction) over 4,194,304 cells
-    ("44de392f5b1f9396a18883dae4333aa56ed48a918dcbc68a0cd46ddc4dced1a4", "plain"): 200.79,
+    # k_stream_collide<StoreF32, false, true>: 440.61 MB read + 401.73 MB written
+    ("0e86f1289c854284652f538c650c223e2f3266ce67c48f539ceaa4aae74301b6", "plain", "f32"): 200.83,
+    # k_stream_collide_staged<StoreF16, 512, 3, false, true>: 220.58 MB read + 174.89 MB written
+    ("0e86f1289c854284652f538c650c223e2f3266ce67c48f539ceaa4aae74301b6", "staged512", "f16"): 94.29,
 }
 
 
@@ -274,6 +274,9 @@ def storage_form(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W,
     ncell = shape[0] * shape[1] * shape[2]
     gbs = dom.stream_collide_bytes() / (k[1] * 1e-3) / 1e9
     variant = dom.stream_collide_variant()
+    # (the captured kernels: pull layout, second-order equilibrium, this grid)
+    bpc = (NCU_TRAFFIC.get((kernel_source_hash(), variant, storage))
+           if layout == "pull" and eq_order == 2 and tuple(shape) == (256, 128, 128) else None)
     dom.close()
     return {"value": round(world * ncell * K / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
             "ms_per_step": round(ms / K, 5), "storage": storage, "kernel_variant": variant,
@@ -283,6 +286,7 @@ def storage_form(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W,
                          "achieved": round(gbs, 1),
                          "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
                          "algorithmic_bytes_per_cell": 216 if storage == "f32" else 108,
+                         "traffic": round(bpc * ncell) if bpc else None,
                          "kernel_ms": round(k[1], 5), "ib_ms": round(k[0], 5)}}
 
 
@@ -345,6 +349,9 @@ def school_form(W, K, world, peak, vkw):
     ncell = shape[0] * shape[1] * shape[2]
     gbs = dom.stream_collide_bytes() / (k[1] * 1e-3) / 1e9
     variant = dom.stream_collide_variant()
+    # (the captured kernels: pull layout, second-order equilibrium, this grid)
+    bpc = (NCU_TRAFFIC.get((kernel_source_hash(), variant, storage))
+           if layout == "pull" and eq_order == 2 and tuple(shape) == (256, 128, 128) else None)
     dom.close()
     return {"value": round(world * ncell * K / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
             "ms_per_step": round(ms / K, 5), "workload": "two_fish_school_150x50x100",
@@ -671,8 +678,8 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return None
     achieved = algo_bytes / (k1_ms * 1e-3) / 1e9
-    bpc = (NCU_TRAFFIC.get((kernel_source_hash(), dom.stream_collide_variant()))
-           if args.storage == "f32" and args.layout == "pull" else None)
+    bpc = (NCU_TRAFFIC.get((kernel_source_hash(), dom.stream_collide_variant(), args.storage))
+           if args.layout == "pull" else None)
     mlups = world * ncell * K / (ms * 1e-3) / 1e6
     h2d = 2 * X[0].nbytes + 100   # X, U and the frame (25 floats)
     d2h = out.size * 8 + 4        # the force/torque rows as FP32 pairs, and the status word
