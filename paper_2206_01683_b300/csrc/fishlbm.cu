@@ -1470,10 +1470,6 @@ fg_status fg_init_fields(fg_domain* d, int env, const double* rho, const double*
     return FG_OK;
 }
 
-// Host checks of marker positions and velocities: |x| <= 1e6 and finite,
-// 2 <= x < n - 3 along non-periodic axes, finite velocities.  The bulk check
-// has no early exit so that it vectorises (it runs every step for host
-// arrays); the slow pass names the first problem only when one exists.
 // The device address of a host pointer into pinned (page-locked, mapped)
 // memory, nullptr for pageable memory.  Kernels read such arrays directly,
 // which costs one launch instead of one copy call per array.
@@ -1486,6 +1482,10 @@ static const float* mapped_device_ptr(const float* p) {
     return a.type == cudaMemoryTypeHost ? static_cast<const float*>(a.devicePointer) : nullptr;
 }
 
+// Host checks of marker positions and velocities: |x| <= 1e6 and finite,
+// 2 <= x < n - 3 along non-periodic axes, finite velocities.  The bulk check
+// has no early exit so that it vectorises (it runs every step for host
+// arrays); the slow pass names the first problem only when one exists.
 static bool markers_valid(const EnvDev& E, int n, const float* X, const float* U) {
     // closed bounds per axis: [-1e6, 1e6] on a periodic axis, [2, n - 3) on
     // an open one (the largest float below n - 3 as the closed upper bound)
