@@ -637,7 +637,7 @@ fg_status enqueue_ib(fg_domain* d, const typename S::raw* gin, cudaStream_t s, i
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)blocks);
     cfg.blockDim = dim3(IB_THREADS);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = ib_smem_bytes(d->n_envs);   // the environments' tables
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -1395,7 +1395,7 @@ fg_status fg_create_domain(const fg_env_desc* envs, int n_envs, const fg_options
         // resident blocks per SM of the cooperative IB kernel
         st = dispatch(o.storage, [&](auto tag) -> fg_status {
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d->ib_per_sm, k_ib_step<decltype(tag)>, IB_THREADS,
-                                                             0));
+                                                             ib_smem_bytes(n_envs)));
             return d->ib_per_sm > 0 ? FG_OK : fail(FG_ERR_CUDA, "k_ib_step cannot be resident");
         });
         if (st != FG_OK) {

@@ -464,6 +464,15 @@ __device__ __forceinline__ void spread_force(const EnvDev& E, const MarkerRef& r
     }
 }
 
+// Environments whose tables k_ib_step keeps in dynamic shared memory, and
+// the bytes a launch provides for them.
+constexpr int IB_SMEM_ENVS = 128;   // 128 x 316 B = 40 KB, within the default 48 KB
+static_assert(sizeof(EnvDev) % 8 == 0 && sizeof(FrameDev) % 4 == 0,
+              "the tables are copied as 32-bit words and the frames follow the 8-byte aligned EnvDev array");
+__host__ __device__ constexpr size_t ib_smem_bytes(int n_envs) {
+    return n_envs > 1 && n_envs <= IB_SMEM_ENVS ? (sizeof(EnvDev) + sizeof(FrameDev)) * (size_t)n_envs : 0;
+}
+
 // The IB part of one step.  Launched cooperatively with at most as many
 // blocks as fit on the device at once; half-warps stride over markers (the
 // first marker of each half-warp stays in registers from the mark phase to
@@ -478,11 +487,26 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
           float* __restrict__ Fm, float4* fib, uint32_t* stamps, const StepState* __restrict__ st,
           float4* nodes, unsigned* bar, int ib_iters, float* dF, unsigned long long* fibq,
           const float* __restrict__ Nrm, int* status, int layout, const MarkerSrc* __restrict__ msrc) {
-    // a single environment's table and frame in shared memory, read by every
-    // marker and node of the launch; the posted marker source, if any
+    // the environments' tables and frames in shared memory, read by every
+    // marker and node of the launch (the environment of a marker or tile is
+    // found by a binary search over them): one environment in static shared
+    // memory, up to IB_SMEM_ENVS in the dynamic shared memory the launch
+    // provides (ib_smem_bytes), more read from global memory; the posted
+    // marker source, if any
     __shared__ EnvDev sE;
     __shared__ FrameDev sF;
     __shared__ MarkerSrc sM;
+    extern __shared__ __align__(16) unsigned char ib_tables[];
+    const bool staged_tables = n_envs > 1 && n_envs <= IB_SMEM_ENVS;
+    EnvDev* tE = reinterpret_cast<EnvDev*>(ib_tables);
+    FrameDev* tF = reinterpret_cast<FrameDev*>(ib_tables + sizeof(EnvDev) * (size_t)n_envs);
+    if (staged_tables) {
+        const int we = n_envs * (int)(sizeof(EnvDev) / 4), wf = n_envs * (int)(sizeof(FrameDev) / 4);
+        for (int k = threadIdx.x; k < we; k += blockDim.x)
+            reinterpret_cast<uint32_t*>(tE)[k] = reinterpret_cast<const uint32_t*>(envs_g)[k];
+        for (int k = threadIdx.x; k < wf; k += blockDim.x)
+            reinterpret_cast<uint32_t*>(tF)[k] = reinterpret_cast<const uint32_t*>(frames_g)[k];
+    }
     if (threadIdx.x == 0) {
         if (n_envs == 1) {
             sE = envs_g[0];
@@ -495,8 +519,8 @@ k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ en
     // phase copies them into X and U, which later phases read through L2
     const MarkerSrc ms = sM;
     const bool posted = ms.valid != 0;
-    const EnvDev* envs = n_envs == 1 ? &sE : envs_g;
-    const FrameDev* frames = n_envs == 1 ? &sF : frames_g;
+    const EnvDev* envs = n_envs == 1 ? &sE : (staged_tables ? tE : envs_g);
+    const FrameDev* frames = n_envs == 1 ? &sF : (staged_tables ? tF : frames_g);
     const int lane = threadIdx.x & 31, h = lane & 15;
     const int gw = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int nw = (int)((gridDim.x * blockDim.x) >> 5);
