@@ -349,9 +349,6 @@ def school_form(W, K, world, peak, vkw):
     ncell = shape[0] * shape[1] * shape[2]
     gbs = dom.stream_collide_bytes() / (k[1] * 1e-3) / 1e9
     variant = dom.stream_collide_variant()
-    # (the captured kernels: pull layout, second-order equilibrium, this grid)
-    bpc = (NCU_TRAFFIC.get((kernel_source_hash(), variant, storage))
-           if layout == "pull" and eq_order == 2 and tuple(shape) == (256, 128, 128) else None)
     dom.close()
     return {"value": round(world * ncell * K / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
             "ms_per_step": round(ms / K, 5), "workload": "two_fish_school_150x50x100",
