@@ -429,6 +429,39 @@ def test_many_small_environments(variant, even):
     dom.get_body_force_torque(env=0)
 
 
+def test_environment_tables_beyond_shared_memory():
+    """140 environments, more than the IB kernel keeps in shared memory (it
+    then reads the environment tables and frames from global memory), give
+    exactly what the same environments give as two domains of 70 (tables in
+    shared memory): deterministic spread, markers in every environment, ten
+    steps in a moving frame, populations and force/torque rows bit for bit."""
+    rng = np.random.default_rng(inputs.seed_for(10))
+    shapes = [(8, 8, 8), (10, 8, 6), (12, 6, 8)]
+    envs, marks, frames = [], [], []
+    for e in range(140):
+        sh = shapes[int(rng.integers(0, 3))]
+        envs.append(fishlbm.env_desc(sh, float(rng.uniform(0.55, 0.9)), (PERIODIC,) * 6, (0.0, 0.0, 0.0), 1.0,
+                                     f32((0.01, 0, 0))))
+        c = np.array(sh, float) / 2.0 + rng.uniform(-0.5, 0.5, 3)
+        X = f32(c + np.array([[0.4, 0.1, -0.3], [-0.6, 0.2, 0.5], [0.1, -0.7, 0.2]]))
+        U = f32(rng.uniform(-0.01, 0.01, (3, 3)))
+        marks.append((X, U, f32(np.ones(3))))
+        frames.append(fishlbm.make_frame(acc=tuple(rng.uniform(-1e-5, 1e-5, 3)), omega=(0.0, 0.0, 1e-4)))
+    one = fishlbm.Domain(envs, deterministic=True)
+    halves = [fishlbm.Domain(envs[:70], deterministic=True), fishlbm.Domain(envs[70:], deterministic=True)]
+    for e, (X, U, dV) in enumerate(marks):
+        one.set_markers(X, U, dV, env=e)
+        halves[e // 70].set_markers(X, U, dV, env=e % 70)
+    for n in range(10):
+        one.step(1, frames)
+        halves[0].step(1, frames[:70])
+        halves[1].step(1, frames[70:])
+    for e in range(140):
+        h, k = halves[e // 70], e % 70
+        assert np.array_equal(one.get_body_force_torque(e), h.get_body_force_torque(k)), e
+        assert np.array_equal(one.populations(e), h.populations(k)), e
+
+
 # ------------------------------------------------------------ edge cases
 
 @pytest.mark.parametrize("variant", VARIANTS)
