@@ -442,7 +442,7 @@ def large_sphere_form(W, K, world, peak, vkw):
 
 
 def batched_form(W, K, world, peak, vkw, n_envs=64):
-    """64 independent single-fish environments, grid sizes drawn by seed from
+    """n_envs (64) independent single-fish environments, grid sizes drawn by seed from
     {96x64x64, 128x64x64, 160x80x80, 192x96x96}, fish of 0.4 x grid length
     with 1500-4000 markers and its own wave amplitude and frame trajectory,
     all advanced by the same launches: one marker update for all
@@ -498,7 +498,7 @@ def batched_form(W, K, world, peak, vkw, n_envs=64):
     # the IB phases and stream-collide blocks of all environments
     ms_f, k_f, gbs_f, _, _ = run({"variant": "fused"})
 
-    # the same 64 environments as 64 plain FP32 single-environment domains,
+    # the same environments as as many plain FP32 single-environment domains,
     # stepped one after another on the same stream (no batching)
     doms = []
     for e, f in enumerate(fishes):
@@ -528,8 +528,8 @@ def batched_form(W, K, world, peak, vkw, n_envs=64):
             "fused_persistent": {"value": round(world * cells * K / (ms_f * 1e-3) / 1e6, 1), "unit": "MLUPS",
                                  "ms_per_step": round(ms_f / K, 5), "kernel_ms": round(k_f[1], 5),
                                  "reduce_ms": round(k_f[2], 5),
-                                 "what": "k_step_fused: IB phases and stream-collide blocks of all 64 envs in "
-                                         "one persistent launch per step (+ the reduction)"},
+                                 "what": "k_step_fused: IB phases and stream-collide blocks of all %d envs in "
+                                         "one persistent launch per step (+ the reduction)" % n_envs},
             "roofline": {"bound": "hbm", "kernel": "k_stream_collide", "achieved": round(gbs, 1),
                          "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
                          "kernel_ms": round(k[1], 5), "ib_ms": round(k[0], 5), "reduce_ms": round(k[2], 5),
@@ -815,6 +815,23 @@ def run_reference(args):
     }
 
 
+def run_form(args):
+    """One form alone on one GPU (no headline step, no CPU baseline)."""
+    import torch
+    torch.cuda.set_device(0)
+    W, K, vkw = args.warmup, args.steps, _variant_kw(args)
+    peak = measured_peaks()[0]
+    if args.form == "batched":
+        return batched_form(W, K, 1, peak, vkw, n_envs=args.batch_envs)
+    if args.form == "school":
+        return school_form(W, K, 1, peak, vkw)
+    if args.form == "large_sphere":
+        return large_sphere_form(W, K, 1, peak, vkw)
+    if args.form == "free_sphere":
+        return free_sphere_form(W, K, 1, vkw)
+    return adjoint_form()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -831,9 +848,16 @@ def main():
                     help="population storage of the main workload (f32 is the headline; the others for profiling)")
     ap.add_argument("--variant", default="autotune", choices=["autotune", "plain", "staged", "staged512"],
                     help="stream-collide kernel: autotuned at creation (default) or fixed")
+    ap.add_argument("--form", choices=["batched", "school", "large_sphere", "free_sphere", "adjoint"],
+                    help="run only this form (W warm-up and K timed steps) and print its result, for profiling")
+    ap.add_argument("--batch-envs", type=int, default=64,
+                    help="environments of the batched form (the first of the 64 seeded draws)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.form:
+        print(json.dumps({"form": args.form, **run_form(args)}), flush=True)
+        return
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)
