@@ -199,6 +199,12 @@ def _timed(stream, world, fn, steps, ahead_ms=0.0):
     return e0.elapsed_time(e1)
 
 
+def job_mlups(world, cells, steps, ms):
+    """Whole-job throughput of `world` replicas, each updating `cells` cells
+    `steps` times, the job taking `ms` (the slowest rank's time)."""
+    return world * cells * steps / (ms * 1e-3) / 1e6
+
+
 def _max_over_ranks(x, world):
     """Max of x over ranks (the slowest rank sets the job's time)."""
     if world == 1:
@@ -677,7 +683,7 @@ def run_ours(args):
     achieved = algo_bytes / (k1_ms * 1e-3) / 1e9
     bpc = (NCU_TRAFFIC.get((kernel_source_hash(), dom.stream_collide_variant(), args.storage))
            if args.layout == "pull" else None)
-    mlups = world * ncell * K / (ms * 1e-3) / 1e6
+    mlups = job_mlups(world, ncell, K, ms)
     h2d = 2 * X[0].nbytes + 100   # X, U and the frame (25 floats)
     d2h = out.size * 8 + 4        # the force/torque rows as FP32 pairs, and the status word
     line = {
@@ -711,7 +717,7 @@ def run_ours(args):
                      "algorithmic_bytes": int(algo_bytes),
                      "kernel_ms": round(k1_ms, 5), "ib_ms": round(ib_ms, 5),
                      "reduce_ms": round(red_ms, 5)},
-        "e2e": {"value": round(world * ncell * K / (e2e_ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+        "e2e": {"value": round(job_mlups(world, ncell, K, e2e_ms), 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": 4 * K,   # per timed repetition: marker copy, k_ib_step, stream-collide, k_reduce
         "clocks": clock_info,
