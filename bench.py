@@ -690,7 +690,9 @@ def run_ours(args):
     bpc = (NCU_TRAFFIC.get((kernel_source_hash(), dom.stream_collide_variant(), args.storage))
            if args.layout == "pull" else None)
     mlups = job_mlups(world, ncell, K, ms)
-    h2d = 2 * X[0].nbytes + 100   # X, U and the frame (25 floats)
+    # X and U (read by the step's IB kernel from pinned memory), then one copy
+    # of the frame (25 floats, padded to 112 bytes) and the 24-byte marker source
+    h2d = 2 * X[0].nbytes + 112 + 24
     d2h = out.size * 8 + 4        # the force/torque rows as FP32 pairs, and the status word
     line = {
         "metric": METRIC,
