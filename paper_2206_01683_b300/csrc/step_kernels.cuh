@@ -202,8 +202,10 @@ __device__ __forceinline__ void accumulate(Moments& m, const float (&g)[Q]) {
 // of two commute with rounding).  Each of accumulate's later additions of a
 // line quantity becomes a fused multiply-add with the exact product
 // (line quantity) x 1/sig, so every sum rounds as in accumulate and the
-// moments are bit-identical to accumulate of the decoded values, without
-// decoding each value (27 multiplies).
+// moments are bit-identical to accumulate of the decoded values.  The
+// instruction count is that of accumulate after the compiler contracts its
+// exact decode multiplies into the sums (ncu: 588 instructions per cell
+// either way); the kernel measured 1% faster (98.6 against 99.9 us, FP16).
 template <class S, bool SECOND>
 __device__ __forceinline__ void accumulate_stored(Moments& m, const float (&h)[Q]) {
     if constexpr (!S::SCALED) {
