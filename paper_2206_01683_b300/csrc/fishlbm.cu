@@ -1940,6 +1940,20 @@ static fg_status step_markers_in(fg_domain* d, const float* X, const float* U, i
     return FG_OK;
 }
 
+// One step after step_markers_in.  A posted source is uploaded by the step
+// and cleared on the device by its reduction; if the step fails after the
+// upload but before its launches, the device copy is cleared here, so that
+// no later step reads the caller's arrays.
+static fg_status step_posted(fg_domain* d, const fg_frame* frames) {
+    const bool posted = d->msrc_next.valid != 0;
+    const long long steps_before = d->steps;
+    const fg_status st = fg_step(d, 1, frames);
+    d->msrc_next.valid = 0;
+    if (posted && d->steps == steps_before)   // nothing launched: no reduction clears it
+        cudaMemsetAsync(&d->d_msrc->valid, 0, sizeof(int), d->stream);
+    return st;
+}
+
 fg_status fg_step_markers(fg_domain* d, const float* X, const float* U, int device_ptrs, const fg_frame* frames) {
     NvtxRange nvtx_range("fg_step_markers");
     if (!d) return fail(FG_ERR_INVALID, "null domain");
@@ -1958,9 +1972,7 @@ fg_status fg_step_markers(fg_domain* d, const float* X, const float* U, int devi
                 return fail(FG_ERR_STATE, "slip forcing needs the markers' normals (fg_set_marker_normals)");
     fg_status st = FG_OK;
     if (X && (st = step_markers_in(d, X, U, device_ptrs)) != FG_OK) return st;
-    st = fg_step(d, 1, frames);
-    d->msrc_next.valid = 0;   // (uploaded by the step; dropped if the step failed before)
-    return st;
+    return step_posted(d, frames);
 }
 
 fg_status fg_step_io(fg_domain* d, const float* X, const float* U, int device_ptrs, const fg_frame* frames,
@@ -1983,9 +1995,7 @@ fg_status fg_step_io(fg_domain* d, const float* X, const float* U, int device_pt
                 return fail(FG_ERR_STATE, "slip forcing needs the markers' normals (fg_set_marker_normals)");
     fg_status st = FG_OK;
     if (X && (st = step_markers_in(d, X, U, device_ptrs)) != FG_OK) return st;
-    st = fg_step(d, 1, frames);
-    d->msrc_next.valid = 0;
-    if (st != FG_OK) return st;
+    if ((st = step_posted(d, frames)) != FG_OK) return st;
     // The step's k_reduce writes the rows, the status word and then the step
     // number to mapped pinned memory: no copy to issue.  The host polls the
     // step number (waking from a stream synchronisation takes longer than the
