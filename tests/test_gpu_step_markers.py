@@ -31,16 +31,18 @@ def _case(shapes, n_markers, variant, layout="pull", ib_iters=1, storage="f32"):
     return fishes, trajs, make
 
 
-@pytest.mark.parametrize("variant,layout", [("plain", "pull"), ("staged", "pull"), ("staged512", "pull"),
-                                            ("plain", "aa"), ("fused", "pull"), ("overlap", "pull")])
-def test_step_markers_equals_set_then_step(variant, layout):
+@pytest.mark.parametrize("variant,layout,storage", [("plain", "pull", "f32"), ("staged", "pull", "f32"),
+                                                    ("staged512", "pull", "f32"), ("plain", "aa", "f32"),
+                                                    ("fused", "pull", "f32"), ("overlap", "pull", "f32"),
+                                                    ("staged512", "pull", "f16"), ("plain", "aa", "bf16")])
+def test_step_markers_equals_set_then_step(variant, layout, storage):
     """Seven steps of three environments (the markers kept unchanged on one
     step): force/torque rows after every step, then the populations, fields
     and marker forces, bit for bit against fg_set_markers_all + fg_step, with
-    device arrays and with pinned host arrays."""
+    device arrays and with pinned host arrays, in FP32 and 16-bit storage."""
     torch = pytest.importorskip("torch")
     shapes = [(40, 24, 24), (48, 20, 28), (32, 32, 24)]
-    fishes, trajs, make = _case(shapes, [300, 420, 260], variant, layout)
+    fishes, trajs, make = _case(shapes, [300, 420, 260], variant, layout, storage=storage)
     ref, dev, pin = make(), make(), make()
     for n in range(1, 8):
         poses = [f.pose(n) for f in fishes]
