@@ -179,6 +179,10 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
     // flight together.
     constexpr int ILP = 8;
     const int items = 6 * (ns + 1) + 1;
+    // chunks of the force/torque rows to add: the fused step kernel writes
+    // none for an environment without markers (its rows are zero; what the
+    // scratch holds there is from another step or environment)
+    const int nch_rows = markers_pre && E.n_markers == 0 ? 0 : nch_f;
     for (int k0 = w; k0 < items; k0 += ILP * NW) {
         Pair32 t[ILP];
         const Pair32* src[ILP];
@@ -189,7 +193,7 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
             const bool m_item = k == items - 1;
             const int yy = m_item ? RED_ROWS - 1 : k / 6;
             cc[j] = m_item ? 0 : k % 6;
-            nch[j] = k >= items ? 0 : (m_item ? nch_m : nch_f);
+            nch[j] = k >= items ? 0 : (m_item ? nch_m : nch_rows);
             src[j] = partials + ((size_t)(e * RED_ROWS + yy) * zmax) * 6;
         }
         const int nmax = max(nch_f, nch_m);

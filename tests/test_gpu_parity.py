@@ -1011,3 +1011,36 @@ def test_fused_step_equals_plain_bit_for_bit(M, other):
         assert np.array_equal(doms[0].populations(env=e), doms[1].populations(env=e)), e
         assert np.array_equal(doms[0].history(25, env=e), doms[1].history(25, env=e)), e
     assert np.array_equal(doms[0].marker_force(env=0), doms[1].marker_force(env=0))
+
+
+@pytest.mark.parametrize("variant", ["plain", "fused", "overlap"])
+def test_removed_markers_give_zero_rows(variant):
+    """An environment whose markers are removed reports zero force/torque
+    rows from its next step on, in every variant: the fused kernel writes no
+    chunk sums for an environment without markers, and the reduction must
+    add none (the scratch still holds the previous steps' sums).  The other
+    environment's rows and every population equal the plain chain's, bit for
+    bit."""
+    envs = [fishlbm.env_desc((40, 32, 24), 0.6), fishlbm.env_desc((32, 24, 24), 0.7)]
+    Xs, dVs = inputs.fibonacci_sphere(600, 5.0, (20.0, 16.0, 12.0))
+    Xt, dVt = inputs.fibonacci_sphere(400, 4.0, (16.0, 12.0, 12.0))
+    doms = [fishlbm.Domain(envs, variant=v, deterministic=True, record_history=8) for v in ("plain", variant)]
+    for n in range(8):
+        Us = np.tile([0.02, -0.01 * math.sin(0.3 * n), 0.0], (600, 1))
+        for d in doms:
+            d.set_markers(np.float32(Xs + Us * n), np.float32(Us), np.float32(dVs), env=0)
+            if n < 4:
+                Ut = np.tile([0.0, 0.015, 0.0], (400, 1))
+                d.set_markers(np.float32(Xt), np.float32(Ut), np.float32(dVt), env=1)
+            elif n == 4:   # removed: no markers from this step on
+                d.set_markers(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32),
+                              np.zeros(0, np.float32), env=1)
+            d.step(1)
+            if n >= 4:
+                assert not np.any(d.get_body_force_torque(1)), (n, variant)
+            elif n > 0:
+                assert np.any(d.get_body_force_torque(1)), (n, variant)
+    assert doms[1].stream_collide_variant() == variant
+    for e in range(2):
+        assert np.array_equal(doms[0].populations(env=e), doms[1].populations(env=e)), e
+        assert np.array_equal(doms[0].history(8, env=e), doms[1].history(8, env=e)), e
