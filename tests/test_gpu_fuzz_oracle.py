@@ -7,7 +7,8 @@ allows) in one or two segments, one to three direct-forcing passes, no-slip
 or slip forcing, second- or third-order equilibrium, the kernel variant and
 the population layout.  Eight steps, then density, velocity, populations,
 force and torque within the FP32 bar, and the local bars (open-face boundary
-layer, the markers' stencil support, the largest per-cell error)."""
+layer, the markers' stencil support, the largest per-cell error); and the
+same draws with FP16 or BF16 storage at those dtypes' bars."""
 import numpy as np
 import pytest
 
@@ -50,11 +51,15 @@ def _draw(seed):
                 field_seed=int(rng.integers(0, 2 ** 31)))
 
 
-@pytest.mark.parametrize("seed", list(range(31, 43)))
-def test_random_configuration_against_oracle(seed):
-    c = _draw(seed)
+# the frozen per-dtype bars of the precision form (velocity, force, torque,
+# the local rel-L2 bars and the per-cell bound)
+TOL16 = {"f16": 2e-3, "bf16": 5e-2}
+
+
+def _run(c, storage="f32"):
+    """Eight steps of configuration c on both sides; the errors."""
     p = Pair(c["shape"], c["tau"], faces=c["faces"], u_in=c["u_in"], rho0=c["rho0"], variant=c["variant"],
-             ib_iters=c["ib_iters"], slip=c["slip"], eq_order=c["eq_order"], layout=c["layout"])
+             ib_iters=c["ib_iters"], slip=c["slip"], eq_order=c["eq_order"], layout=c["layout"], storage=storage)
     rho, u = inputs.random_fields(c["shape"], seed=c["field_seed"], u_amp=0.01, rho_amp=0.005)
     p.init(rho, u)
     origin = tuple(0.5 * (v - 1) for v in c["shape"])
@@ -74,8 +79,30 @@ def test_random_configuration_against_oracle(seed):
             normals = (X0 - np.asarray(c["centre"])) if c["slip"] else None
             p.markers(X, U, dV, seg=seg, nseg=c["nseg"], ref=ref, normals=normals)
         p.step(frame)
-    err = p.errors()
-    where = {k: c[k] for k in ("shape", "faces", "layout", "variant", "n", "ib_iters", "slip", "eq_order")}
+    return p.errors()
+
+
+def _where(c):
+    return {k: c[k] for k in ("shape", "faces", "layout", "variant", "n", "ib_iters", "slip", "eq_order")}
+
+
+@pytest.mark.parametrize("seed", list(range(31, 43)))
+def test_random_configuration_against_oracle(seed):
+    c = _draw(seed)
+    err = _run(c)
     for key in ("rho", "u", "pop", "force", "torque", "seg_force"):
-        assert err[key] <= TOL, (key, err[key], where)
-    assert_local(err, where=str(where))
+        assert err[key] <= TOL, (key, err[key], _where(c))
+    assert_local(err, where=str(_where(c)))
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("seed", list(range(51, 57)))
+def test_random_configuration_reduced_storage_against_oracle(seed, storage):
+    """The same draws with FP16 or BF16 storage of f - w (FP32 arithmetic):
+    velocity, force and torque within the dtype's frozen bar, and its local
+    bars."""
+    c = _draw(seed)
+    err = _run(c, storage)
+    for key in ("u", "force", "torque"):
+        assert err[key] <= TOL16[storage], (key, err[key], storage, _where(c))
+    assert_local(err, tol=TOL16[storage], tol_max=TOL16[storage], where=str((storage, _where(c))))
