@@ -6,8 +6,11 @@ environments of random shapes (odd row lengths included, which take the
 one-cell kernels), periodic or open faces, an accelerating and rotating
 frame, zero to 1200 markers in one to three segments, one to three
 direct-forcing passes, and marker sets that grow, shrink, appear and go away
-between steps.  Compared after every step: every environment's force/torque
-history row and mass; at the end: the populations and the marker forces.
+between steps; and the plain chain with its markers posted with the step
+(fg_step_markers, device arrays the IB kernel reads in place) on the steps
+that keep every marker count.  Compared after every step: every
+environment's force/torque history row and mass; at the end: the
+populations and the marker forces.
 
 An environment without markers once read force sums its step had not
 written (the fused kernel writes none for it); a fixed batch missed that
@@ -63,27 +66,43 @@ def test_random_batches_agree_across_step_kernels(seed):
     envs, M = _draw(seed)
     descs = [fishlbm.env_desc(e["shape"], e["tau"], e["faces"], (0.02, 0, 0) if e["faces"][0] == V else (0, 0, 0))
              for e in envs]
+    torch = pytest.importorskip("torch")
     doms = {v: fishlbm.Domain(descs, variant=v, deterministic=True, ib_iters=M, record_history=STEPS)
             for v in ("plain", "fused", "overlap")}
+    # the plain chain again, its markers posted with the step (fg_step_markers,
+    # device arrays read in place by the IB kernel) whenever no environment's
+    # marker count changes
+    doms["posted"] = fishlbm.Domain(descs, variant="plain", deterministic=True, ib_iters=M, record_history=STEPS)
     for n in range(STEPS):
         half = 0 if n < STEPS // 2 else 1
         frames = [fishlbm.make_frame(acc=e["acc"], omega=e["omega"],
                                      origin=tuple(0.5 * (v - 1) for v in e["shape"])) for e in envs]
-        for d in doms.values():
+        recount = n == 0 or (n == STEPS // 2 and any(e["counts"][1] != e["counts"][0] for e in envs))
+        sets = [_markers(e, e["counts"][half], n) for e in envs]
+        for name, d in doms.items():
+            if name == "posted" and not recount:
+                if sum(e["counts"][half] for e in envs) > 0:
+                    Xd = torch.from_numpy(np.concatenate([m[0] for m in sets])).cuda()
+                    Ud = torch.from_numpy(np.concatenate([m[1] for m in sets])).cuda()
+                    d.step_markers(Xd, Ud, frames)
+                    torch.cuda.synchronize()   # the arrays live until the step has run
+                else:
+                    d.step(1, frames)
+                continue
             for k, e in enumerate(envs):
                 cnt = e["counts"][half]
                 if n == 0 or (n == STEPS // 2 and cnt != e["counts"][0]) or cnt > 0:
-                    X, U, dV, seg = _markers(e, cnt, n)
+                    X, U, dV, seg = sets[k]
                     d.set_markers(X, U, dV, seg=seg, n_seg=e["n_seg"], env=k)
             d.step(1, frames)
         want = [doms["plain"].history(STEPS, env=k) for k in range(len(envs))]
-        for v in ("fused", "overlap"):
+        for v in ("fused", "overlap", "posted"):
             for k in range(len(envs)):
                 got = doms[v].history(STEPS, env=k)
                 assert np.array_equal(got, want[k]), (seed, v, n, k, envs[k]["counts"])
     for k, e in enumerate(envs):
         ref = doms["plain"].populations(env=k)
-        for v in ("fused", "overlap"):
+        for v in ("fused", "overlap", "posted"):
             assert np.array_equal(doms[v].populations(env=k), ref), (seed, v, k)
             if e["counts"][1] > 0:
                 assert np.array_equal(doms[v].marker_force(env=k), doms["plain"].marker_force(env=k)), (seed, v, k)
