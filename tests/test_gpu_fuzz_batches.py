@@ -8,9 +8,9 @@ frame, zero to 1200 markers in one to three segments, one to three
 direct-forcing passes, and marker sets that grow, shrink, appear and go away
 between steps; and the plain chain with its markers posted with the step
 (fg_step_markers, device arrays the IB kernel reads in place) on the steps
-that keep every marker count.  Compared after every step: every
-environment's force/torque history row and mass; at the end: the
-populations and the marker forces.
+that keep every marker count, and launched without graphs.  Compared after
+every step: every environment's force/torque history row and mass; at the
+end: the populations and the marker forces.
 
 An environment without markers once read force sums its step had not
 written (the fused kernel writes none for it); a fixed batch missed that
@@ -73,6 +73,9 @@ def test_random_batches_agree_across_step_kernels(seed):
     # device arrays read in place by the IB kernel) whenever no environment's
     # marker count changes
     doms["posted"] = fishlbm.Domain(descs, variant="plain", deterministic=True, ib_iters=M, record_history=STEPS)
+    # and launched directly instead of replayed from a captured graph
+    doms["direct"] = fishlbm.Domain(descs, variant="plain", deterministic=True, ib_iters=M, record_history=STEPS,
+                                    graphs=False)
     for n in range(STEPS):
         half = 0 if n < STEPS // 2 else 1
         frames = [fishlbm.make_frame(acc=e["acc"], omega=e["omega"],
@@ -96,13 +99,13 @@ def test_random_batches_agree_across_step_kernels(seed):
                     d.set_markers(X, U, dV, seg=seg, n_seg=e["n_seg"], env=k)
             d.step(1, frames)
         want = [doms["plain"].history(STEPS, env=k) for k in range(len(envs))]
-        for v in ("fused", "overlap", "posted"):
+        for v in ("fused", "overlap", "posted", "direct"):
             for k in range(len(envs)):
                 got = doms[v].history(STEPS, env=k)
                 assert np.array_equal(got, want[k]), (seed, v, n, k, envs[k]["counts"])
     for k, e in enumerate(envs):
         ref = doms["plain"].populations(env=k)
-        for v in ("fused", "overlap", "posted"):
+        for v in ("fused", "overlap", "posted", "direct"):
             assert np.array_equal(doms[v].populations(env=k), ref), (seed, v, k)
             if e["counts"][1] > 0:
                 assert np.array_equal(doms[v].marker_force(env=k), doms["plain"].marker_force(env=k)), (seed, v, k)
