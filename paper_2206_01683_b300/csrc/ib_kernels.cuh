@@ -479,8 +479,11 @@ __host__ __device__ constexpr size_t ib_smem_bytes(int n_envs) {
 // the force phase), warps over tile stamps.  fibq != nullptr selects the
 // deterministic spread (fixed-point sums, converted to fib in a last phase).
 // layout (LAYOUT_*) says where the node moments find the populations.
+// Compiled for three resident blocks per SM (80 registers): at four (64
+// registers, 32 bytes of spills) the swimmer's IB took 24.3-24.4 against
+// 23.8-24.0 us and the 64-environment batch's 0.246 against 0.238 ms.
 template <class S>
-__global__ void __launch_bounds__(IB_THREADS, 4)
+__global__ void __launch_bounds__(IB_THREADS, 3)
 k_ib_step(const typename S::raw* __restrict__ gin, const EnvDev* __restrict__ envs_g,
           const FrameDev* __restrict__ frames_g, int n_envs, int total_markers, int n_stamps,
           float* X, float* U, const float* __restrict__ dV,
