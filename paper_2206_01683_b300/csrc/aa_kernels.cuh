@@ -335,14 +335,20 @@ __device__ __forceinline__ float aa_block_pair(typename S::raw* G, const EnvDev&
 
 // One step in place over every environment: phase K = 0 (even step) or 1
 // (odd step), after k_aa_boundary of the same phase; the blocks of the
-// plain kernel, mass partials from E.part0.  Compiled for four resident
-// blocks (64 registers): on the 256x128x128 swimmer channel that measured
-// 0.172 / 0.213 ms for even / odd FP32 steps with two cells per thread
-// against 0.186 / 0.205 uncapped (69 and 78 registers, three blocks), and
-// 0.213 / 0.209 against 0.225 / 0.252 with one cell per thread (255 cells
-// per row).
+// plain kernel, mass partials from E.part0.  Resident blocks per SM it is
+// compiled for (aa_minb): three for FP32 storage (80 registers), four for
+// the 16-bit formats (64).  On the 256x128x128 swimmer channel, two cells
+// per thread, mean of the even and odd phases: FP32 0.1677 ms at three
+// against 0.1805 at four (where it spilled 40 bytes); FP16 0.1416 at three
+// against 0.1346 at four.  (An earlier form of the kernel measured 0.172 /
+// 0.213 ms for even / odd FP32 steps at four blocks against 0.186 / 0.205
+// uncapped, and 0.213 / 0.209 against 0.225 / 0.252 with one cell per
+// thread, 255 cells per row.)
+template <class S>
+constexpr int aa_minb() { return sizeof(typename S::raw) == 4 ? 3 : 4; }
+
 template <class S, bool EQ3, bool PAIR, int K>
-__global__ void __launch_bounds__(K1_THREADS, 4)
+__global__ void __launch_bounds__(K1_THREADS, aa_minb<S>())
 k_stream_collide_aa(typename S::raw* g, const EnvDev* __restrict__ envs, const FrameDev* __restrict__ frames,
                     int n_envs, float4* __restrict__ fib, const uint32_t* __restrict__ stamps,
                     const StepState* __restrict__ st, Pair32* __restrict__ mass_part) {
