@@ -227,17 +227,22 @@ def adjoint_form():
     cfg = inputs.ADJOINT_CHANNEL
     prob = adjoint.ThrustProblem(cfg["shape"], cfg["tau"], cfg["length"], cfg["n_markers"], cfg["steps"],
                                  checkpoint=cfg["checkpoint"])
-    best = None
-    for _ in range(3):   # the first repetition warms up
+    reps = []
+    for r in range(5):   # the first repetition warms up
         th = adjoint.default_theta().requires_grad_(True)
         L = adjoint.SwimThrust.apply(th, prob)
         (g,) = torch.autograd.grad(L, th)
-        best = (prob.forward_ms, prob.backward_ms, float(L.detach()), g.detach().numpy().tolist())
-    fwd, bwd, L, g = best
+        if r > 0:
+            reps.append((prob.backward_ms / prob.forward_ms, prob.forward_ms, prob.backward_ms, float(L.detach()),
+                         g.detach().numpy().tolist()))
+    # the repetition with the median cost multiple (a single one can meet a
+    # disturbance on the host)
+    _, fwd, bwd, L, g = sorted(reps, key=lambda t: t[0])[len(reps) // 2]
     return {"workload": "adjoint_channel_128x64x64_periodic", "steps": cfg["steps"],
             "checkpoint": cfg["checkpoint"], "markers": cfg["n_markers"],
             "forward_ms": round(fwd, 3), "backward_ms": round(bwd, 3),
-            "cost_multiple": round(bwd / fwd, 3), "loss_thrust": L, "grad_norm": float(np.linalg.norm(g))}
+            "cost_multiple": round(bwd / fwd, 3), "loss_thrust": L, "grad_norm": float(np.linalg.norm(g)),
+            "repetitions": len(reps), "cost_multiple_each": [round(t[0], 3) for t in reps]}
 
 
 def _kernel_ms(dom, fn, steps):
