@@ -38,24 +38,32 @@ OPEN_X = (1, 2, 3, 3, 3, 3)   # inlet, outflow, free-slip walls
 
 # DRAM traffic of the stream-collide kernel per cell update from an ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum divided by the cells of
-# the launch; the mean of two launches, one of each sweep direction), keyed by
-# the kernel source it was taken on, the variant in use and the storage, and
-# valid only for those.  Swimmer channel, 4,194,304 cells.
+# the launch; the mean of two launches, one of each sweep direction, or in
+# place of an even and an odd step), keyed by the kernel source it was taken
+# on, the variant in use, the storage and the population layout, and valid
+# only for those.  Swimmer channel, 4,194,304 cells.
 NCU_TRAFFIC = {
     # k_stream_collide<StoreF32, false, true>: 440.53 MB read + 401.60 MB written
-    ("a8391d8732973f3c32b44a42a94abfa4b32accb5560a824b805624a767a6f2eb", "plain", "f32"): 200.78,
+    ("a8391d8732973f3c32b44a42a94abfa4b32accb5560a824b805624a767a6f2eb", "plain", "f32", "pull"): 200.78,
     # k_stream_collide_staged<StoreF16, 512, 3, false, true>: 220.59 MB read + 174.88 MB written
-    ("a8391d8732973f3c32b44a42a94abfa4b32accb5560a824b805624a767a6f2eb", "staged512", "f16"): 94.29,
+    ("a8391d8732973f3c32b44a42a94abfa4b32accb5560a824b805624a767a6f2eb", "staged512", "f16", "pull"): 94.29,
+    # in place: k_aa_boundary + k_stream_collide_aa<StoreF32, false, true, K>, the mean of an
+    # even and an odd step: (13.85 + 439.96 + 379.68 MB + 13.85 + 440.17 + 390.67 MB) / 2
+    ("ac85ed78c44d57df172a48785d85a2c587c414341033a1f1697f90ded12e7d7b", "plain", "f32", "aa"): 200.06,
+    # the same with StoreF16: (6.94 + 220.47 + 160.58 MB + 6.94 + 220.55 + 164.98 MB) / 2
+    ("ac85ed78c44d57df172a48785d85a2c587c414341033a1f1697f90ded12e7d7b", "plain", "f16", "aa"): 93.04,
 }
 
 
 NOMINAL_HBM_GBS = 8000.0   # B300 HBM3e, nominal (context only; the fraction that counts is of measured)
 
 
-def kernel_source_hash():
-    """sha256 over the sources the stream-collide kernel is compiled from."""
+def kernel_source_hash(layout="pull"):
+    """sha256 over the sources the stream-collide kernels of a population
+    layout are compiled from."""
     h = hashlib.sha256()
-    for name in ("step_kernels.cuh", "lattice.cuh", "async_copy.cuh"):
+    names = ("step_kernels.cuh", "lattice.cuh", "async_copy.cuh") + (("aa_kernels.cuh",) if layout == "aa" else ())
+    for name in names:
         h.update(open(os.path.join(ROOT, "paper_2206_01683_b300", "csrc", name), "rb").read())
     return h.hexdigest()
 
@@ -286,9 +294,10 @@ def storage_form(storage, shape, tau, u_in, fish, Xd, Ud, dVd, segd, ref, fr, W,
     ncell = shape[0] * shape[1] * shape[2]
     gbs = dom.stream_collide_bytes() / (k[1] * 1e-3) / 1e9
     variant = dom.stream_collide_variant()
-    # (the captured kernels: pull layout, second-order equilibrium, this grid)
-    bpc = (NCU_TRAFFIC.get((kernel_source_hash(), variant, storage))
-           if layout == "pull" and eq_order == 2 and tuple(shape) == (256, 128, 128) else None)
+    # (the captured kernels: second-order equilibrium, one direct-forcing
+    # pass, this grid)
+    bpc = (NCU_TRAFFIC.get((kernel_source_hash(layout), variant, storage, layout))
+           if eq_order == 2 and ib_iters == 1 and tuple(shape) == (256, 128, 128) else None)
     dom.close()
     return {"value": round(world * ncell * K / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
             "ms_per_step": round(ms / K, 5), "storage": storage, "kernel_variant": variant,
@@ -692,8 +701,7 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return None
     achieved = algo_bytes / (k1_ms * 1e-3) / 1e9
-    bpc = (NCU_TRAFFIC.get((kernel_source_hash(), dom.stream_collide_variant(), args.storage))
-           if args.layout == "pull" else None)
+    bpc = NCU_TRAFFIC.get((kernel_source_hash(args.layout), dom.stream_collide_variant(), args.storage, args.layout))
     mlups = job_mlups(world, ncell, K, ms)
     # X and U (read by the step's IB kernel from pinned memory), then one copy
     # of the frame (25 floats, padded to 112 bytes) and the 24-byte marker source
