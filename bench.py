@@ -47,6 +47,8 @@ NCU_TRAFFIC = {
     ("a8391d8732973f3c32b44a42a94abfa4b32accb5560a824b805624a767a6f2eb", "plain", "f32", "pull"): 200.78,
     # k_stream_collide_staged<StoreF16, 512, 3, false, true>: 220.59 MB read + 174.88 MB written
     ("a8391d8732973f3c32b44a42a94abfa4b32accb5560a824b805624a767a6f2eb", "staged512", "f16", "pull"): 94.29,
+    # k_stream_collide_staged<StoreBF16, 512, 3, false, true>: 220.58 MB read + 175.03 MB written
+    ("a8391d8732973f3c32b44a42a94abfa4b32accb5560a824b805624a767a6f2eb", "staged512", "bf16", "pull"): 94.32,
     # in place: k_aa_boundary + k_stream_collide_aa<StoreF32, false, true, K>, the mean of an
     # even and an odd step: (13.85 + 439.96 + 379.68 MB + 13.85 + 440.17 + 390.67 MB) / 2
     ("ac85ed78c44d57df172a48785d85a2c587c414341033a1f1697f90ded12e7d7b", "plain", "f32", "aa"): 200.06,
