@@ -13,6 +13,7 @@ must stay within the parity bar.
 """
 import json
 import os
+import re
 import subprocess
 import sys
 
@@ -126,3 +127,22 @@ def test_debug_build_index_checks_stay_clean():
     assert res["flags"] == 0, res
     bad = {k: v for k, v in res["errors"].items() if not v <= 1e-5}
     assert not bad, bad
+
+
+def test_debug_build_random_configurations_stay_clean():
+    """The seeded random configurations and batches (test_gpu_fuzz_oracle.py,
+    test_gpu_fuzz_batches.py: every variant, layout and storage type, marker
+    sets that change between steps, posted markers, direct launches) on the
+    debug build: every case passes its bars and no index check fires."""
+    sys.path.insert(0, ROOT)
+    from paper_2206_01683_b300 import build
+    lib = build.build(debug=True)
+    env = dict(os.environ, FISHLBM_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-m", "gpu", "-p", "no:cacheprovider",
+                        "tests/test_gpu_fuzz_oracle.py", "tests/test_gpu_fuzz_batches.py"],
+                       env=env, capture_output=True, text=True, timeout=1500, cwd=ROOT)
+    assert r.returncode == 0, r.stdout[-4000:] + r.stderr[-2000:]
+    summary = r.stdout.strip().splitlines()[-1]
+    print("debug build:", summary)
+    m = re.search(r"(\d+) passed", summary)
+    assert m and int(m.group(1)) == 30 and "skipped" not in summary, summary

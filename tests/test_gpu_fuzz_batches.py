@@ -29,6 +29,18 @@ FACE_SETS = [(P,) * 6, (V, O, S, S, S, S), (V, O, P, P, S, S), (P, P, S, S, P, P
 STEPS = 10
 
 
+@pytest.fixture(autouse=True)
+def _index_checks_clean():
+    """Run on the debug build (FISHLBM_LIB, as test_gpu_debug_bounds.py
+    does), no index check of any kernel may have fired in a case."""
+    yield
+    try:
+        flags = fishlbm.debug_flags()
+    except fishlbm.FgError:   # the release build carries no index checks
+        flags = 0
+    assert flags == 0, flags
+
+
 def _draw(seed):
     """A batch: per environment its shape, faces, tau, frame and the marker
     counts and segment counts of the two halves of the run."""

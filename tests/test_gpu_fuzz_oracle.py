@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 from oracle import FREESLIP, OUTFLOW, PERIODIC, VELOCITY
-from paper_2206_01683_b300 import inputs
+from paper_2206_01683_b300 import fishlbm, inputs
 
 from parity_util import Pair, assert_local
 
@@ -24,6 +24,18 @@ AXIS_FACES = [(PERIODIC, PERIODIC), (VELOCITY, OUTFLOW), (FREESLIP, FREESLIP)]
 VARIANTS = ["plain", "staged", "staged512", "fused", "overlap"]
 STEPS = 8
 TOL = 1e-5
+
+
+@pytest.fixture(autouse=True)
+def _index_checks_clean():
+    """Run on the debug build (FISHLBM_LIB, as test_gpu_debug_bounds.py
+    does), no index check of any kernel may have fired in a case."""
+    yield
+    try:
+        flags = fishlbm.debug_flags()
+    except fishlbm.FgError:   # the release build carries no index checks
+        flags = 0
+    assert flags == 0, flags
 
 
 def _draw(seed):
