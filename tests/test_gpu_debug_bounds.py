@@ -145,4 +145,4 @@ def test_debug_build_random_configurations_stay_clean():
     summary = r.stdout.strip().splitlines()[-1]
     print("debug build:", summary)
     m = re.search(r"(\d+) passed", summary)
-    assert m and int(m.group(1)) == 30 and "skipped" not in summary, summary
+    assert m and int(m.group(1)) == 60 and "skipped" not in summary, summary

@@ -73,7 +73,7 @@ def _markers(env, n, step):
     return np.float32(X + U * step), np.float32(U), np.float32(dV), seg
 
 
-@pytest.mark.parametrize("seed", [11, 12, 13, 14, 15, 16])
+@pytest.mark.parametrize("seed", list(range(11, 23)))
 def test_random_batches_agree_across_step_kernels(seed):
     envs, M = _draw(seed)
     descs = [fishlbm.env_desc(e["shape"], e["tau"], e["faces"], (0.02, 0, 0) if e["faces"][0] == V else (0, 0, 0))

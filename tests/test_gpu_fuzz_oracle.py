@@ -98,7 +98,7 @@ def _where(c):
     return {k: c[k] for k in ("shape", "faces", "layout", "variant", "n", "ib_iters", "slip", "eq_order")}
 
 
-@pytest.mark.parametrize("seed", list(range(31, 43)))
+@pytest.mark.parametrize("seed", list(range(31, 55)))
 def test_random_configuration_against_oracle(seed):
     c = _draw(seed)
     err = _run(c)
@@ -108,7 +108,7 @@ def test_random_configuration_against_oracle(seed):
 
 
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
-@pytest.mark.parametrize("seed", list(range(51, 57)))
+@pytest.mark.parametrize("seed", list(range(61, 73)))
 def test_random_configuration_reduced_storage_against_oracle(seed, storage):
     """The same draws with FP16 or BF16 storage of f - w (FP32 arithmetic):
     velocity, force and torque within the dtype's frozen bar, and its local
