@@ -5,7 +5,8 @@ beside the cell blocks -- over batches drawn at random: one to five
 environments of random shapes (odd row lengths included, which take the
 one-cell kernels), periodic or open faces, an accelerating and rotating
 frame, zero to 1200 markers in one to three segments, one to three
-direct-forcing passes, and marker sets that grow, shrink, appear and go away
+direct-forcing passes, FP32, FP16 or BF16 storage, second- or third-order
+equilibrium, and marker sets that grow, shrink, appear and go away
 between steps; and the plain chain with its markers posted with the step
 (fg_step_markers, device arrays the IB kernel reads in place) on the steps
 that keep every marker count, and launched without graphs.  Compared after
@@ -55,7 +56,9 @@ def _draw(seed):
                          acc=tuple(float(v) for v in rng.normal(0, 2e-5, 3)),
                          omega=tuple(float(v) for v in rng.normal(0, 2e-4, 3)),
                          seed=int(rng.integers(0, 2 ** 31))))
-    return envs, int(rng.integers(1, 4))
+    opts = dict(ib_iters=int(rng.integers(1, 4)), storage=str(rng.choice(["f32", "f16", "bf16"])),
+                eq_order=int(rng.choice([2, 3])))
+    return envs, opts
 
 
 def _markers(env, n, step):
@@ -75,19 +78,19 @@ def _markers(env, n, step):
 
 @pytest.mark.parametrize("seed", list(range(11, 23)))
 def test_random_batches_agree_across_step_kernels(seed):
-    envs, M = _draw(seed)
+    envs, opts = _draw(seed)
     descs = [fishlbm.env_desc(e["shape"], e["tau"], e["faces"], (0.02, 0, 0) if e["faces"][0] == V else (0, 0, 0))
              for e in envs]
     torch = pytest.importorskip("torch")
-    doms = {v: fishlbm.Domain(descs, variant=v, deterministic=True, ib_iters=M, record_history=STEPS)
+    doms = {v: fishlbm.Domain(descs, variant=v, deterministic=True, record_history=STEPS, **opts)
             for v in ("plain", "fused", "overlap")}
     # the plain chain again, its markers posted with the step (fg_step_markers,
     # device arrays read in place by the IB kernel) whenever no environment's
     # marker count changes
-    doms["posted"] = fishlbm.Domain(descs, variant="plain", deterministic=True, ib_iters=M, record_history=STEPS)
+    doms["posted"] = fishlbm.Domain(descs, variant="plain", deterministic=True, record_history=STEPS, **opts)
     # and launched directly instead of replayed from a captured graph
-    doms["direct"] = fishlbm.Domain(descs, variant="plain", deterministic=True, ib_iters=M, record_history=STEPS,
-                                    graphs=False)
+    doms["direct"] = fishlbm.Domain(descs, variant="plain", deterministic=True, record_history=STEPS,
+                                    graphs=False, **opts)
     for n in range(STEPS):
         half = 0 if n < STEPS // 2 else 1
         frames = [fishlbm.make_frame(acc=e["acc"], omega=e["omega"],
