@@ -241,10 +241,11 @@ struct fg_domain {
         const void* X = nullptr;
         const void* red = nullptr;
         const void* sph = nullptr;
-        int total_markers = -1, red_z = -1, n_sph = 0, sph_max_n = 0;
+        int total_markers = -1, red_z = -1, n_sph = 0, sph_max_n = 0, red_gy = -1, red_gz = -1;
         bool operator==(const GraphKey& o) const {
             return X == o.X && red == o.red && total_markers == o.total_markers && red_z == o.red_z &&
-                   sph == o.sph && n_sph == o.n_sph && sph_max_n == o.sph_max_n;
+                   sph == o.sph && n_sph == o.n_sph && sph_max_n == o.sph_max_n && red_gy == o.red_gy &&
+                   red_gz == o.red_gz;
         }
     } graph_key;
     // free spheres advanced on the device (fg_attach_sphere): the host copy
@@ -422,6 +423,24 @@ fg_status ensure_reduce_scratch(fg_domain* d) {
     d->red_partials = p;
     d->red_z = z;
     return FG_OK;
+}
+
+// Grid rows and chunks of k_reduce for the current markers and kernel
+// layout: the force/torque rows of the environment with the most segments
+// plus the mass row, and the most chunks any environment's rows need (at
+// most red_z, the partials' stride).  Launching only these leaves out the
+// blocks of unused rows and chunks (RED_ROWS x red_z for 64 fish of five
+// segments was 18 x 16, 60% of it rows no environment has).
+void reduce_grid(const fg_domain* d, bool markers_pre, int* rows, int* chunks) {
+    int r = 1, z = 1;
+    for (int e = 0; e < d->n_envs; ++e) {
+        const EnvDev& E = d->env[e];
+        r = std::max(r, E.nseg + 2);
+        z = std::max(z, (E.n_markers + RED_THREADS - 1) / RED_THREADS);
+        z = std::max(z, (E.nparts + RED_THREADS * MASS_PER_THREAD - 1) / (RED_THREADS * MASS_PER_THREAD));
+    }
+    *rows = markers_pre ? 1 : std::min(r, RED_ROWS);
+    *chunks = std::min(z, d->red_z);
 }
 
 // Re-layout marker storage so environment env can hold n markers.
@@ -878,7 +897,9 @@ fg_status enqueue_step_io(fg_domain* d, const typename S::raw* gin, typename S::
         // the fused kernel, which wrote the marker chunk sums, only the mass
         // is summed)
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)d->n_envs, fused ? 1u : (unsigned)RED_ROWS, (unsigned)d->red_z);
+        int gy = 1, gz = 1;
+        reduce_grid(d, fused, &gy, &gz);
+        cfg.gridDim = dim3((unsigned)d->n_envs, (unsigned)gy, (unsigned)gz);
         cfg.blockDim = dim3(RED_THREADS);
         cfg.dynamicSmemBytes = 0;
         cfg.stream = s;
@@ -954,6 +975,7 @@ fg_status graph_step(fg_domain* d) {
     key.red = d->red_partials;
     key.total_markers = d->total_markers;
     key.red_z = d->red_z;
+    reduce_grid(d, d->k1 == K1_FUSED, &key.red_gy, &key.red_gz);
     key.sph = d->sph;
     key.n_sph = (int)d->sph_host.size();
     key.sph_max_n = d->sph_max_n;

@@ -99,11 +99,13 @@ __device__ __forceinline__ void block_pair_sums(Pair32 (&acc)[6], int ncomp, Pai
     __syncthreads();
 }
 
-// Grid (n_envs, RED_ROWS, chunks).  Block (e, y, z) sums chunk z of row y of
-// environment e: y <= nseg is force/torque row y (segment y, its torque
-// about seg_ref[e][y]; y == nseg is the total over all markers, its torque
-// about the environment's ref), one marker per thread; y == RED_ROWS - 1 is
-// the mass, MASS_PER_THREAD partials per thread.  Force on the body
+// Grid (n_envs, rows, chunks), rows and chunks those the environments use
+// (reduce_grid).  Block (e, y, z) sums chunk z of row y of environment e:
+// y <= nseg is force/torque row y (segment y, its torque about
+// seg_ref[e][y]; y == nseg is the total over all markers, its torque about
+// the environment's ref), one marker per thread; the grid's last row is the
+// mass (row RED_ROWS - 1 of the partials), MASS_PER_THREAD partials per
+// thread.  Force on the body
 // F = -sum F_l dV_l, torque T = -sum (X_l - ref) x F_l dV_l, mass = ncell +
 // sum (rho - 1).  Chunk sums are compensated FP32 pairs (all components of a
 // block reduced together: one shuffle tree per component, then the warp
@@ -133,7 +135,11 @@ k_reduce(const EnvDev* __restrict__ envs, const float* __restrict__ X, const flo
     constexpr int NW = RED_THREADS / 32;
     __shared__ Pair32 sh[NW][6];
     __shared__ int is_last;
-    const int e = blockIdx.x, y = markers_pre ? RED_ROWS - 1 : (int)blockIdx.y, z = blockIdx.z, tid = threadIdx.x;
+    // the grid's last row is the mass (row RED_ROWS - 1 of the partials);
+    // the rows before it are force/torque rows 0, 1, ... (markers_pre: the
+    // grid has the mass row only)
+    const int yg = (int)blockIdx.y;
+    const int e = blockIdx.x, y = yg == (int)gridDim.y - 1 ? RED_ROWS - 1 : yg, z = blockIdx.z, tid = threadIdx.x;
     const int w = tid >> 5, lane = tid & 31;
     const EnvDev& E = envs[e];
     const int ns = E.nseg;
